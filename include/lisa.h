@@ -1,0 +1,183 @@
+/*
+ * lisa.h -- C ABI of the GB300 (sm_103a) time-domain LISA response library
+ * (liblisa.so), after Valencia & Husa, "Accelerating the time-domain LISA
+ * response model with central finite differences and hybridization
+ * techniques", arXiv:2505.09600.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers to series are DEVICE pointers owned by the caller, unless a
+ *    parameter says "host".  The library never frees them.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = legacy default stream) and returns an int status:
+ *      LISA_OK (0), LISA_EINVAL (-1, bad argument or shape), LISA_ERANGE (-2),
+ *      LISA_ECUDA (-3, a CUDA call failed; see lisa_last_error_message),
+ *      LISA_ETIMEOUT (-4, a bounded device-side wait gave up),
+ *      LISA_ENOMEM (-5), LISA_ECORRECTOR (-6, corrector fallback used).
+ *    Arguments are validated on the host before anything is launched; on an
+ *    error nothing is written.  The library never aborts and never prints.
+ *  - Time grids: sample i of grid g is at g.t0 + i*g.dt (absolute SSB
+ *    seconds, FP64).  Output times are never accumulated.
+ *  - Series of several components are stored component-major ("SoA"):
+ *    y[c*n + i].  Link order is l = +1,-1,+2,-2,+3,-3, i.e. y_312, y_2-13,
+ *    y_123, y_3-21, y_231, y_1-32 (sgn(l) = eps_{s|l|r}, Sec. II A).
+ *  - Precision: LISA_F64 = every step in FP64, series are double*.
+ *    LISA_MIXED = interpolation, projection, TDI sums and LFA stencils in
+ *    FP32 with absolute times, orbit phase and delays kept in FP64 (per tile)
+ *    plus an FP32 in-tile offset; series are float*.
+ *  - Samples outside an input grid are zero (the paper is silent on
+ *    boundaries); every output sample is defined.
+ *  - Scratch memory needed inside a call (orbit coefficient table, link or z
+ *    series) is taken from the device's stream-ordered pool
+ *    (cudaMallocAsync/cudaFreeAsync on `stream`).
+ */
+#ifndef LISA_H
+#define LISA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LISA_OK 0
+#define LISA_EINVAL (-1)
+#define LISA_ERANGE (-2)
+#define LISA_ECUDA (-3)
+#define LISA_ETIMEOUT (-4)
+#define LISA_ENOMEM (-5)
+#define LISA_ECORRECTOR (-6)
+
+/* Uniform time grid: n samples at t0 + i*dt (seconds). */
+typedef struct { double t0, dt; int64_t n; } lisa_grid;
+
+/* Orbit models (Sec. II B uses the LDC AnalyticOrbit, whose formula the paper
+ * does not print; the published Keplerian constellation stands in):
+ *   LISA_ORB_KEPLER1  first order in the eccentricity e = L/(2 sqrt3 AU),
+ *   LISA_ORB_KEPLER2  exact Keplerian ellipses, inclination
+ *                     asin(sqrt3 e kepler_tilt); kepler_tilt = 1.01 gives
+ *                     1% peak-to-peak arm flexing,
+ *   LISA_ORB_STATIC   KEPLER1 positions frozen at t_static (tests). */
+enum { LISA_ORB_KEPLER1 = 0, LISA_ORB_KEPLER2 = 1, LISA_ORB_STATIC = 2 };
+/* Light-time models T_l(t) = L_l(t)/c:
+ *   LISA_DELAY_LIGHTTIME  T = |R_r(t) - R_s(t - T)|/c (L_l != L_-l, Sec. II B),
+ *   LISA_DELAY_ANALYTIC   the paper's O(e^2) Eq. (L_of_t), e-terms scaled by
+ *                         flex_scale, phases xi0 and delta_l[|l|-1],
+ *   LISA_DELAY_EQUAL      T = L/c,
+ *   LISA_DELAY_LINEAR     T = lin_T0[l] + lin_Tdot[l] (t - t_ref) (tests). */
+enum { LISA_DELAY_LIGHTTIME = 0, LISA_DELAY_ANALYTIC = 1, LISA_DELAY_EQUAL = 2, LISA_DELAY_LINEAR = 3 };
+
+typedef struct {
+    int32_t kind, delay;
+    double L_m;                 /* nominal arm length, metres (2.5e9)          */
+    double kappa0, lambda0;     /* orbital and constellation phases, rad       */
+    double kepler_tilt;         /* KEPLER2 inclination multiplier (1 = design) */
+    double t_static;            /* STATIC freeze time, s                       */
+    double xi0, delta_l[3], flex_scale;         /* ANALYTIC only               */
+    double t_ref, lin_T0[6], lin_Tdot[6];       /* LINEAR only (s, s/s)        */
+} lisa_orbit;
+
+/* Ecliptic latitude beta, longitude lambda, polarisation angle psi (rad). */
+typedef struct { double beta, lambda, psi; } lisa_sky;
+
+enum { LISA_F64 = 0, LISA_MIXED = 1 };
+enum { LISA_TDI15 = 15, LISA_TDI20 = 20 };
+enum { LISA_XYZ = 0, LISA_AET = 1 };
+enum { LISA_FROZEN = 0, LISA_NESTED = 1 };
+enum { LISA_LFA_UNEQUAL = 0, LISA_LFA_EQUAL = 1 };
+
+/* Version of this ABI (major*10000 + minor*100 + patch). */
+int lisa_version(void);
+/* Static message for a status code. */
+const char* lisa_strerror(int status);
+/* Detail of the last error raised by a call on this host thread (static buffer). */
+const char* lisa_last_error_message(void);
+
+/* a1. Spacecraft positions, light times and link unit vectors at every sample
+ * of grid g (Sec. II B: R_s(t), L_l(t)/c, n_l(t) with
+ * n_l = (R_r(t) - R_s(t - T_l)) / |...|).
+ * Output (device, caller-allocated, FP64): R[3][3][n] (spacecraft, xyz, i),
+ * T[6][n] light times in seconds, nhat[6][3][n].  Any output may be NULL. */
+int lisa_orbits(const lisa_orbit* orbit, lisa_grid g, double* R, double* T, double* nhat, void* stream);
+
+/* a2-a5. Full single-link response (Sec. II A-B, Eqs. H, yslr, delta_s,
+ * delta_r): y_l(t) = [H_l(t - delta_s) - H_l(t - delta_r)] / (2 (1 - k.n_l))
+ * with h+/hx interpolated by 32-point Lagrange (stencil j-15..j+16 around
+ * j = floor of the retarded sample position), geometry at reception time t.
+ * hp, hc: device series on h_grid (double* for F64, float* for MIXED).
+ * y: device output [6][y_grid.n] of the same type. */
+int lisa_links_full(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                    const void* hp, const void* hc, int precision,
+                    lisa_grid y_grid, void* y, void* stream);
+
+/* a6-a7. Michelson TDI from the six links (Sec. II B, Eqs. X1.5, X2.0; Y, Z
+ * by cyclic permutation; A, E, T).  FROZEN evaluates every L_l at the output
+ * time (the paper's choice); NESTED applies the delays one after the other,
+ * each at its own retarded time.  y: device [6][y_grid.n]; xyz: device
+ * [3][out.n] (X,Y,Z or A,E,T). */
+int lisa_tdi(const lisa_orbit* orbit, lisa_grid y_grid, const void* y, int precision,
+             int tdi_gen, int delay_mode, int channels, lisa_grid out, void* xyz, void* stream);
+
+/* a1-a7 in one call: links on the output grid, then TDI (FROZEN). */
+int lisa_response_full(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                       const void* hp, const void* hc, int precision, int tdi_gen, int channels,
+                       lisa_grid out, void* xyz, void* stream);
+
+/* a8-a9. LFA link series shifted to the TDI retarded times (Sec. III, App. B,
+ * Eqs. yslr_strain_derivatives, X15_nonequal, X20_nonequal): per channel
+ * c = X,Y,Z and its links a, b (X: y_123, y_231),
+ *   z_a(t) = y_a(t - s_a(t)),  y_l(t') = -(T_l/2)[xi+ hdot+SSB(tau) + xix hdotxSSB(tau)],
+ *   tau = t' - T_l/2 - k.(R_s + R_r)/(2c),
+ * hdot from the 5-point central difference of h on h_grid, interpolated by
+ * 32-point Lagrange; s_a = T_a + T_b/2 (1.5) or 2T_a + 3T_b/2 (2.0).
+ * EQUAL replaces every T_l by L/c.  z: device [6][out.n] ordered
+ * X_a, X_b, Y_a, Y_b, Z_a, Z_b. */
+int lisa_links_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                   const void* hp, const void* hc, int precision, int tdi_gen, int lfa_kind,
+                   lisa_grid out, void* z, void* stream);
+
+/* a10. LFA Michelson variables from z (same passages):
+ *   1.5: X = 4 [T_a dz_a/dt - T_b dz_b/dt],
+ *   2.0: X = 8 (T_a + T_b) [T_a d2z_a/dt2 - T_b d2z_b/dt2],
+ * 5-point central differences on z_grid, arms at the output time. */
+int lisa_tdi_lfa(const lisa_orbit* orbit, lisa_grid z_grid, const void* z, int precision,
+                 int tdi_gen, int lfa_kind, int channels, void* xyz, void* stream);
+
+/* a8-a10 in one call (z kept on chip). */
+int lisa_response_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                      const void* hp, const void* hc, int precision, int tdi_gen, int lfa_kind,
+                      int channels, lisa_grid out, void* xyz, void* stream);
+
+/* a11. Hybrid response (Sec. IV, Eqs. sigmoid, hybridized_xs):
+ *   X(t) = S(t;+1) X_LFA(t) [t <= t_hyb + T_win/2] + S(t;-1) X_Full(t) [t >= t_hyb - T_win/2],
+ *   S(t; eps) = 1 / (1 + exp(eps (t - t_hyb)/sigma)),
+ * computing the LFA only where its indicator is set and the full response
+ * (links and TDI) only where its own is.  T_win <= 0 selects the paper's
+ * default 800 out.dt, sigma <= 0 selects T_win/40.  xyz: device [3][out.n]. */
+int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                         const void* hp, const void* hc, int precision, int tdi_gen, int lfa_kind,
+                         int channels, double t_hyb, double T_win, double sigma,
+                         lisa_grid out, void* xyz, void* stream);
+
+/* Hybridisation time at leading PN order (Sec. IV, Eq. thyb):
+ * t_hyb = tc - f^(-8/3) * 5/(8 pi)^(8/3) * (G Mc/c^3)^(-5/3); mc_s = G Mc/c^3 in s. */
+double lisa_t_hyb_from_f(double f_hyb, double mc_s, double tc);
+
+
+/* Instrumentation (no counterpart in the paper).
+ * lisa_profile_enable(1) clears the record and makes every kernel launch of
+ * this library on this process record a CUDA event pair on its own stream;
+ * lisa_profile_enable(0) stops recording.  lisa_profile_query synchronises
+ * the recorded events and returns, for kernels whose name contains `name`
+ * (NULL = all), the summed device time in ms and the number of launches.
+ * lisa_launch_count returns the number of kernels this library has launched
+ * since the process started (always counted). */
+int lisa_profile_enable(int enable);
+int lisa_profile_query(const char* name, double* total_ms, int64_t* launches);
+int64_t lisa_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LISA_H */

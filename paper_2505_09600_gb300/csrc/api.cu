@@ -1,0 +1,336 @@
+// C ABI of liblisa: argument validation, scratch management and the
+// orchestration of the kernels for each call declared in include/lisa.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "lisa_common.cuh"
+#include "lisa_internal.cuh"
+
+namespace lisa {
+
+// ---------------------------------------------------------------------------
+// scratch from the device's stream-ordered pool
+// ---------------------------------------------------------------------------
+static std::once_flag g_pool_once[64];
+
+static void keep_pool_memory()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::call_once(g_pool_once[dev], [dev]() {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;  // keep freed blocks in the pool between calls
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+Scratch::Scratch(cudaStream_t st) : st_(st) { keep_pool_memory(); }
+
+Scratch::~Scratch()
+{
+    for (int k = 0; k < n_; ++k) cudaFreeAsync(ptrs_[k], st_);
+}
+
+void* Scratch::alloc(size_t bytes)
+{
+    if (n_ >= 16) {
+        rc_ = LISA_ENOMEM;
+        set_error("too many scratch buffers");
+        return nullptr;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes < 256 ? 256 : bytes, st_);
+    if (e != cudaSuccess) {
+        rc_ = cuda_status(e, "cudaMallocAsync");
+        return nullptr;
+    }
+    ptrs_[n_++] = p;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+static int check_grid(const lisa_grid& g, const char* name)
+{
+    if (!(g.dt > 0.0) || !isfinite(g.dt) || !isfinite(g.t0) || g.n < 0) {
+        set_error("%s: need dt > 0, finite t0 and n >= 0 (t0=%g dt=%g n=%lld)", name, g.t0, g.dt, (long long)g.n);
+        return LISA_EINVAL;
+    }
+    if (g.n > ((int64_t)1 << 40)) {
+        set_error("%s: n=%lld too large", name, (long long)g.n);
+        return LISA_EINVAL;
+    }
+    return LISA_OK;
+}
+
+static int check_orbit(const lisa_orbit* o)
+{
+    if (!o) { set_error("orbit is NULL"); return LISA_EINVAL; }
+    if (o->kind < LISA_ORB_KEPLER1 || o->kind > LISA_ORB_STATIC) { set_error("orbit kind %d unknown", o->kind); return LISA_EINVAL; }
+    if (o->delay < LISA_DELAY_LIGHTTIME || o->delay > LISA_DELAY_LINEAR) { set_error("delay model %d unknown", o->delay); return LISA_EINVAL; }
+    if (!(o->L_m > 0.0) || !isfinite(o->L_m)) { set_error("L_m must be positive"); return LISA_EINVAL; }
+    if (o->kind == LISA_ORB_KEPLER2) {
+        const double si = sqrt(3.0) * o->L_m / (2.0 * sqrt(3.0) * kAU) * o->kepler_tilt;
+        if (!(si > -1.0 && si < 1.0)) { set_error("kepler_tilt gives |sin(inclination)| >= 1"); return LISA_EINVAL; }
+    }
+    return LISA_OK;
+}
+
+static int check_common(int precision, int gen, int channels)
+{
+    if (precision != LISA_F64 && precision != LISA_MIXED) { set_error("precision %d unknown", precision); return LISA_EINVAL; }
+    if (gen != LISA_TDI15 && gen != LISA_TDI20) { set_error("tdi_gen must be 15 or 20 (got %d)", gen); return LISA_EINVAL; }
+    if (channels != LISA_XYZ && channels != LISA_AET) { set_error("channels %d unknown", channels); return LISA_EINVAL; }
+    return LISA_OK;
+}
+
+#define LISA_TRY(x)                  \
+    do {                             \
+        int _rc = (x);               \
+        if (_rc != LISA_OK) return _rc; \
+    } while (0)
+
+static size_t real_size(int precision) { return precision == LISA_MIXED ? sizeof(float) : sizeof(double); }
+
+// Orbit polynomial table on grid g, in scratch.
+static int make_table(const lisa_orbit* orbit, const lisa_grid& g, Scratch& sc, SegTable& tab, cudaStream_t st)
+{
+    const int S = kSegSamples;
+    const int64_t nseg = seg_count(g.n > 0 ? g.n : 1, S);
+    double* coef = (double*)sc.alloc(sizeof(double) * (size_t)nseg * kNQ * kNC);
+    if (!coef) return sc.status();
+    LISA_TRY(build_seg_table(make_orbit_dev(*orbit), g, S, coef, nseg, st));
+    tab = SegTable{coef, nseg, S, g.t0, g.dt};
+    return LISA_OK;
+}
+
+// Upper bound of any single light time (for halo sizing).
+static double max_light_time(const lisa_orbit* o, const lisa_grid& g)
+{
+    if (o->delay == LISA_DELAY_LINEAR) {
+        const double span = fmax(fabs(g.t0 - o->t_ref), fabs(g.t0 + g.n * g.dt - o->t_ref)) + 1e3;
+        double m = 0.0;
+        for (int q = 0; q < 6; ++q) m = fmax(m, fabs(o->lin_T0[q]) + fabs(o->lin_Tdot[q]) * span);
+        return m;
+    }
+    double flex = 1.0 + 3.0 * fmax(fabs(o->kepler_tilt - 1.0), 0.0) * 60.0 + 0.05 * fabs(o->flex_scale);
+    return 1.5 * flex * o->L_m / kC;
+}
+
+}  // namespace lisa
+
+using namespace lisa;
+
+extern "C" {
+
+int lisa_version(void) { return 10000; }
+
+const char* lisa_strerror(int status)
+{
+    switch (status) {
+    case LISA_OK: return "ok";
+    case LISA_EINVAL: return "invalid argument";
+    case LISA_ERANGE: return "time outside the valid range";
+    case LISA_ECUDA: return "CUDA error";
+    case LISA_ETIMEOUT: return "bounded device wait timed out";
+    case LISA_ENOMEM: return "out of device memory";
+    case LISA_ECORRECTOR: return "corrector spot check failed; full-response fallback used";
+    default: return "unknown status";
+    }
+}
+
+const char* lisa_last_error_message(void) { return last_error(); }
+
+double lisa_t_hyb_from_f(double f_hyb, double mc_s, double tc)
+{
+    return tc - pow(f_hyb, -8.0 / 3.0) * 5.0 / pow(8.0 * kPi, 8.0 / 3.0) * pow(mc_s, -5.0 / 3.0);
+}
+
+int lisa_orbits(const lisa_orbit* orbit, lisa_grid g, double* R, double* T, double* nhat, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(g, "grid"));
+    if (g.n == 0) return LISA_OK;
+    return run_orbits(orbit, g, R, T, nhat, (cudaStream_t)stream);
+}
+
+int lisa_links_full(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid, const void* hp, const void* hc,
+                    int precision, lisa_grid y_grid, void* y, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(h_grid, "h_grid"));
+    LISA_TRY(check_grid(y_grid, "y_grid"));
+    LISA_TRY(check_common(precision, LISA_TDI15, LISA_XYZ));
+    if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
+    if (y_grid.n == 0) return LISA_OK;
+    if (!y || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, y_grid, sc, tab, st));
+    return launch_links_full(tab, make_sky_dev(*sky), h_grid, hp, hc, precision, y_grid, y, 0, y_grid.n, st);
+}
+
+int lisa_tdi(const lisa_orbit* orbit, lisa_grid y_grid, const void* y, int precision, int tdi_gen, int delay_mode,
+             int channels, lisa_grid out, void* xyz, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(y_grid, "y_grid"));
+    LISA_TRY(check_grid(out, "out"));
+    LISA_TRY(check_common(precision, tdi_gen, channels));
+    if (delay_mode != LISA_FROZEN && delay_mode != LISA_NESTED) { set_error("delay_mode %d unknown", delay_mode); return LISA_EINVAL; }
+    if (out.n == 0) return LISA_OK;
+    if (!xyz || (y_grid.n > 0 && !y)) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, out, sc, tab, st));
+    BlendSpec bl{};
+    return launch_tdi(tab, y_grid, y, precision, tdi_gen, delay_mode, channels, out, xyz, 0, out.n, bl, st);
+}
+
+int lisa_response_full(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid, const void* hp, const void* hc,
+                       int precision, int tdi_gen, int channels, lisa_grid out, void* xyz, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(h_grid, "h_grid"));
+    LISA_TRY(check_grid(out, "out"));
+    LISA_TRY(check_common(precision, tdi_gen, channels));
+    if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
+    if (out.n == 0) return LISA_OK;
+    if (!xyz || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, out, sc, tab, st));
+    void* y = sc.alloc(6 * (size_t)out.n * real_size(precision));
+    if (!y) return sc.status();
+    LISA_TRY(launch_links_full(tab, make_sky_dev(*sky), h_grid, hp, hc, precision, out, y, 0, out.n, st));
+    BlendSpec bl{};
+    return launch_tdi(tab, out, y, precision, tdi_gen, LISA_FROZEN, channels, out, xyz, 0, out.n, bl, st);
+}
+
+int lisa_links_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid, const void* hp, const void* hc,
+                   int precision, int tdi_gen, int lfa_kind, lisa_grid out, void* z, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(h_grid, "h_grid"));
+    LISA_TRY(check_grid(out, "out"));
+    LISA_TRY(check_common(precision, tdi_gen, LISA_XYZ));
+    if (lfa_kind != LISA_LFA_UNEQUAL && lfa_kind != LISA_LFA_EQUAL) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
+    if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
+    if (out.n == 0) return LISA_OK;
+    if (!z || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, out, sc, tab, st));
+    BlendSpec bl{};
+    return launch_lfa(tab, make_sky_dev(*sky), orbit->L_m, h_grid, hp, hc, precision, tdi_gen, lfa_kind, LISA_XYZ, out,
+                      z, nullptr, 0, out.n, bl, st);
+}
+
+int lisa_tdi_lfa(const lisa_orbit* orbit, lisa_grid z_grid, const void* z, int precision, int tdi_gen, int lfa_kind,
+                 int channels, void* xyz, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(z_grid, "z_grid"));
+    LISA_TRY(check_common(precision, tdi_gen, channels));
+    if (lfa_kind != LISA_LFA_UNEQUAL && lfa_kind != LISA_LFA_EQUAL) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
+    if (z_grid.n == 0) return LISA_OK;
+    if (!z || !xyz) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, z_grid, sc, tab, st));
+    return launch_tdi_lfa(tab, orbit->L_m, z_grid, z, precision, tdi_gen, lfa_kind, channels, xyz, st);
+}
+
+int lisa_response_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid, const void* hp, const void* hc,
+                      int precision, int tdi_gen, int lfa_kind, int channels, lisa_grid out, void* xyz, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(h_grid, "h_grid"));
+    LISA_TRY(check_grid(out, "out"));
+    LISA_TRY(check_common(precision, tdi_gen, channels));
+    if (lfa_kind != LISA_LFA_UNEQUAL && lfa_kind != LISA_LFA_EQUAL) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
+    if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
+    if (out.n == 0) return LISA_OK;
+    if (!xyz || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, out, sc, tab, st));
+    BlendSpec bl{};
+    return launch_lfa(tab, make_sky_dev(*sky), orbit->L_m, h_grid, hp, hc, precision, tdi_gen, lfa_kind, channels, out,
+                      nullptr, xyz, 0, out.n, bl, st);
+}
+
+int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid, const void* hp, const void* hc,
+                         int precision, int tdi_gen, int lfa_kind, int channels, double t_hyb, double T_win,
+                         double sigma, lisa_grid out, void* xyz, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(h_grid, "h_grid"));
+    LISA_TRY(check_grid(out, "out"));
+    LISA_TRY(check_common(precision, tdi_gen, channels));
+    if (lfa_kind != LISA_LFA_UNEQUAL && lfa_kind != LISA_LFA_EQUAL) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
+    if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
+    if (!isfinite(t_hyb)) { set_error("t_hyb must be finite"); return LISA_EINVAL; }
+    if (out.n == 0) return LISA_OK;
+    if (!xyz || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    const double Tw = T_win > 0.0 ? T_win : 800.0 * out.dt;
+    const double sg = sigma > 0.0 ? sigma : Tw / 40.0;
+    const int64_t n = out.n;
+    // LFA samples: t_i <= t_hyb + Tw/2; full samples: t_i >= t_hyb - Tw/2
+    // (the same FP64 comparisons as the definition).
+    volatile double hi_thr = t_hyb + 0.5 * Tw, lo_thr = t_hyb - 0.5 * Tw;
+    auto t_at = [&](int64_t i) { volatile double p = (double)i * out.dt; return out.t0 + p; };
+    int64_t iL = (int64_t)floor((hi_thr - out.t0) / out.dt);
+    iL = iL < -1 ? -1 : (iL > n - 1 ? n - 1 : iL);
+    while (iL + 1 <= n - 1 && t_at(iL + 1) <= hi_thr) ++iL;
+    while (iL >= 0 && !(t_at(iL) <= hi_thr)) --iL;
+    int64_t iF = (int64_t)ceil((lo_thr - out.t0) / out.dt);
+    iF = iF < 0 ? 0 : (iF > n ? n : iF);
+    while (iF - 1 >= 0 && t_at(iF - 1) >= lo_thr) --iF;
+    while (iF < n && !(t_at(iF) >= lo_thr)) ++iF;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, out, sc, tab, st));
+    const SkyDev skyd = make_sky_dev(*sky);
+    const size_t rs = real_size(precision);
+    // samples covered by neither part are zero
+    if (iF > iL + 1) {
+        for (int c = 0; c < 3; ++c) {
+            LISA_TRY(cuda_status(cudaMemsetAsync((char*)xyz + ((size_t)c * n + (size_t)(iL + 1)) * rs, 0,
+                                                 (size_t)(iF - iL - 1) * rs, st), "cudaMemsetAsync"));
+        }
+    }
+    if (iL >= 0) {
+        BlendSpec bl{1, t_hyb, sg, +1.0, 0, 0};
+        LISA_TRY(launch_lfa(tab, skyd, orbit->L_m, h_grid, hp, hc, precision, tdi_gen, lfa_kind, channels, out, nullptr,
+                            xyz, 0, iL + 1, bl, st));
+    }
+    if (iF < n) {
+        // links from the earliest sample the TDI delays of [iF, n) can reach
+        const double Dmax = 8.0 * max_light_time(orbit, out);
+        int64_t lo = iF - (int64_t)ceil(Dmax / out.dt) - 40;
+        lo = lo < 0 ? 0 : lo;
+        void* y = sc.alloc(6 * (size_t)n * rs);
+        if (!y) return sc.status();
+        LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, precision, out, y, lo, n, st));
+        BlendSpec bl{1, t_hyb, sg, -1.0, iF, iL + 1};
+        LISA_TRY(launch_tdi(tab, out, y, precision, tdi_gen, LISA_FROZEN, channels, out, xyz, iF, n, bl, st));
+    }
+    return LISA_OK;
+}
+
+}  // extern "C"

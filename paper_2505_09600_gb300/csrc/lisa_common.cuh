@@ -1,0 +1,158 @@
+// Shared device code of liblisa: orbit model, per-segment orbit polynomials,
+// tile-local geometry, 32-point Lagrange weights and retarded-time splitting.
+//
+// Design (GB300, sm_103a):
+//  * The orbit quantities R_s(t), T_l(t) = L_l(t)/c and n_l(t) vary on the
+//    orbital time scale (1 yr).  They are evaluated exactly (FP64) only at 7
+//    Chebyshev nodes per segment of S output samples, by a separate kernel,
+//    and stored as degree-6 monomial coefficients in the segment coordinate
+//    x in [-1, 1].  Every response kernel re-expands its segment's polynomial
+//    around its tile centre and evaluates it per sample (Horner), so per
+//    sample there is no trigonometry, no Kepler solve and no light-time
+//    iteration.  The truncation error of the degree-6 fit over a 512-sample
+//    segment is < 1e-20 s, far below FP64 rounding.
+//  * LISA_F64 kernels keep every step in FP64.  LISA_MIXED kernels keep the
+//    tile-centre values of delays in FP64, split once per tile into an
+//    integer sample and a fraction, and evaluate the in-tile variation
+//    (|dt| < ~0.5 s) and everything downstream in FP32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lisa.h"
+
+namespace lisa {
+
+constexpr double kC = 299792458.0;
+constexpr double kAU = 1.495978707e11;
+constexpr double kYear = 31557600.0;  // 365.25 d
+constexpr double kPi = 3.14159265358979323846;
+
+// Orbit table quantities: R (3 spacecraft x 3), T (6 links), n (6 links x 3).
+constexpr int kNQ = 33;
+constexpr int kQR = 0;
+constexpr int kQT = 9;
+constexpr int kQN = 15;
+constexpr int kDeg = 6;      // polynomial degree per segment
+constexpr int kNodes = 7;    // Chebyshev nodes per segment
+constexpr int kNC = 8;       // stored coefficients per quantity (7 used)
+constexpr int kSegSamples = 512;
+
+// Link index li = 0..5 <-> l = +1,-1,+2,-2,+3,-3 (y_312, y_2-13, y_123, y_3-21,
+// y_231, y_1-32); 0-based spacecraft of sender and receiver.
+__host__ __device__ constexpr int link_sender(int li) { return li == 0 ? 2 : li == 1 ? 1 : li == 2 ? 0 : li == 3 ? 2 : li == 4 ? 1 : 0; }
+__host__ __device__ constexpr int link_receiver(int li) { return li == 0 ? 1 : li == 1 ? 2 : li == 2 ? 2 : li == 3 ? 0 : li == 4 ? 0 : 1; }
+// Cyclic relabelling |l| -> |l| mod 3 + 1 applied `times` times (Y, Z from X).
+__host__ __device__ constexpr int link_cycle(int li, int times)
+{
+    return times == 0 ? li : link_cycle((((li >> 1) + 1) % 3) * 2 + (li & 1), times - 1);
+}
+
+// Orbit parameters as the kernels use them (derived constants included).
+struct OrbitDev {
+    int kind, delay;
+    double L, kappa0, lambda0, tilt, t_static, xi0, delta[3], flex, t_ref, T0[6], Tdot[6];
+    double e, omega, sin_inc, cos_inc, sqrt1me2;
+};
+
+OrbitDev make_orbit_dev(const lisa_orbit& o);
+
+// Source geometry on the host, copied by value into kernel arguments.
+struct SkyDev {
+    double k[3], u[3], v[3];
+    double c2p, s2p;
+};
+SkyDev make_sky_dev(const lisa_sky& s);
+
+// Polynomial segments of the orbit quantities on an output grid: segment s
+// covers samples [s*S, (s+1)*S) of the grid, coordinate x = (q - mid)/half
+// with q the (fractional) sample index, mid = s*S + S/2, half = S/2.
+struct SegTable {
+    const double* coef;  // [nseg][kNQ][kNC]
+    int64_t nseg;
+    int S;
+    double t0, dt;
+};
+
+// Position of the time t_i - d of grid `out` on grid `in`, split into an
+// integer sample j and a fraction eps in [0, 1):  x = i*rho + b0 - d/dt_in.
+struct GridMap {
+    double rho;      // dt_out / dt_in
+    int64_t jb;      // floor(b0), b0 = (t0_out - t0_in) / dt_in
+    double fb;       // b0 - jb
+    double dt_in;
+    int64_t n_in;
+    int unit_rho;    // rho == 1 exactly
+};
+GridMap make_grid_map(const lisa_grid& out, const lisa_grid& in);
+
+__device__ __forceinline__ void split_f64(const GridMap& m, int64_t i, double d, int64_t& j, double& eps)
+{
+    double A = (double)i * m.rho;
+    double jA = floor(A);
+    double fA = __dsub_rn(A, jA);
+    double u = __dsub_rn(__dadd_rn(fA, m.fb), __ddiv_rn(d, m.dt_in));
+    double fu = floor(u);
+    j = (int64_t)jA + m.jb + (int64_t)fu;
+    eps = __dsub_rn(u, fu);
+}
+
+// 32-point Lagrange weights, stencil k = -15..16 (index p = k + 15):
+//   w_p = A_p B_p,  A_p = prod_{m=-15}^{p-16}(eps - m) / p!,
+//   B_p = prod_{m=p-14}^{16}(m - eps) / (31 - p)!,
+// which equals prod_{m != k}(eps - m)/(k - m).  Built by a backward then a
+// forward running product (about five operations per weight).
+template <typename Real>
+__device__ __forceinline__ void lagrange32_weights(Real eps, Real (&w)[32])
+{
+    // fully unrolled: every 1/n below is a compile-time constant
+    w[31] = Real(1);
+#pragma unroll
+    for (int p = 31; p >= 1; --p) w[p - 1] = w[p] * ((Real(p - 15) - eps) * (Real(1) / Real(32 - p)));
+    Real A = Real(1);
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        w[p] *= A;
+        A *= (eps - Real(p - 15)) * (Real(1) / Real(p + 1));
+    }
+}
+
+// Monomial -> re-expansion around xc: b_m = sum_{p>=m} C(p,m) a_p xc^(p-m).
+__device__ __forceinline__ void taylor_shift7(const double* a, double xc, double* b)
+{
+    double t[7];
+#pragma unroll
+    for (int p = 0; p < 7; ++p) t[p] = a[p];
+    // repeated synthetic division by (x - xc)
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+#pragma unroll
+        for (int p = 5; p >= m; --p) t[p] = fma(t[p + 1], xc, t[p]);
+        b[m] = t[m];
+    }
+}
+
+template <int N>
+__device__ __forceinline__ double horner_d(const double* b, double u)
+{
+    double r = b[N - 1];
+#pragma unroll
+    for (int p = N - 2; p >= 0; --p) r = fma(r, u, b[p]);
+    return r;
+}
+
+// Orbit state of spacecraft sc at time t: position, velocity, acceleration.
+__device__ void sc_state(const OrbitDev& o, int sc, double t, double R[3], double V[3], double A[3]);
+// Exact geometry at time t: 33 quantities (R, T, n) in table order.
+__device__ void geometry_exact(const OrbitDev& o, double t, double* q);
+
+// Host-side helpers ----------------------------------------------------------
+int build_seg_table(const OrbitDev& orb, const lisa_grid& g, int S, double* coef_dev, int64_t nseg, cudaStream_t st);
+int64_t seg_count(int64_t n, int S);
+
+// Error plumbing.
+void set_error(const char* fmt, ...);
+int cuda_status(cudaError_t e, const char* what);
+
+}  // namespace lisa

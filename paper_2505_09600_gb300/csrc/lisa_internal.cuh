@@ -1,0 +1,63 @@
+// Host-side internals shared by the translation units of liblisa.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lisa_common.cuh"
+
+namespace lisa {
+
+const char* last_error();
+
+// Every kernel launch is bracketed by these (launch counter; optional timing).
+void prof_before(const char* name, cudaStream_t st);
+void prof_after(cudaStream_t st);
+
+// Stream-ordered scratch: every allocation is released on the same stream
+// (cudaFreeAsync) when the owner goes out of scope, i.e. after the kernels
+// already enqueued have consumed it.
+class Scratch {
+public:
+    explicit Scratch(cudaStream_t st);
+    ~Scratch();
+    void* alloc(size_t bytes);
+    int status() const { return rc_; }
+
+private:
+    cudaStream_t st_;
+    void* ptrs_[16];
+    int n_ = 0;
+    int rc_ = 0;
+};
+
+// Tile size (output samples per CTA) of the response kernels.
+constexpr int kTile = 256;
+
+int run_orbits(const lisa_orbit* orbit, lisa_grid g, double* R, double* T, double* nh, cudaStream_t st);
+
+// Full links on y-grid samples [i_begin, i_end) using a segment table built
+// on the y grid.
+int launch_links_full(const SegTable& tab, const SkyDev& sky, const lisa_grid& hg, const void* hp, const void* hc,
+                      int precision, const lisa_grid& yg, void* y, int64_t i_begin, int64_t i_end, cudaStream_t st);
+
+// TDI on out-grid samples [i_begin, i_end).  Hybrid support: each output is
+// multiplied by the sigmoid weight S(t; t_hyb, sigma, -1) if `blend` is set,
+// and the value already in xyz is added where `accumulate_until` > i.
+struct BlendSpec {
+    int enabled;        // 0: plain output
+    double t_hyb, sigma, eps;   // weight S(t; t_hyb, sigma, eps)
+    int64_t acc_begin, acc_end; // samples where the existing output is added
+};
+int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int precision, int gen, int mode, int channels,
+               const lisa_grid& og, void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st);
+
+// LFA: z series (optional) and channels (optional) on out-grid samples
+// [i_begin, i_end), z recomputed with its 2-sample halo inside each tile.
+int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,
+               const void* hc, int precision, int gen, int kind, int channels, const lisa_grid& og, void* z,
+               void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st);
+int launch_tdi_lfa(const SegTable& tab, double L_nominal, const lisa_grid& zg, const void* z, int precision, int gen,
+                   int kind, int channels, void* xyz, cudaStream_t st);
+
+}  // namespace lisa

@@ -1,0 +1,283 @@
+"""ctypes binding of liblisa.so (include/lisa.h).
+
+Argument marshalling only: every step of the response runs in the CUDA
+library.  Series are torch CUDA tensors (device memory owned by the caller);
+calls are asynchronous on the current torch stream unless `stream` is given.
+If the library is missing or cannot be loaded, every call raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblisa.so")
+
+LISA_OK, LISA_EINVAL, LISA_ERANGE, LISA_ECUDA, LISA_ETIMEOUT, LISA_ENOMEM, LISA_ECORRECTOR = 0, -1, -2, -3, -4, -5, -6
+ORB_KEPLER1, ORB_KEPLER2, ORB_STATIC = 0, 1, 2
+DELAY_LIGHTTIME, DELAY_ANALYTIC, DELAY_EQUAL, DELAY_LINEAR = 0, 1, 2, 3
+F64, MIXED = 0, 1
+TDI15, TDI20 = 15, 20
+XYZ, AET = 0, 1
+FROZEN, NESTED = 0, 1
+LFA_UNEQUAL, LFA_EQUAL = 0, 1
+
+
+class LisaError(RuntimeError):
+    def __init__(self, status, where, detail):
+        super().__init__("%s failed with status %d: %s" % (where, status, detail))
+        self.status = status
+
+
+class lisa_grid(C.Structure):
+    _fields_ = [("t0", C.c_double), ("dt", C.c_double), ("n", C.c_int64)]
+
+
+class lisa_orbit(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("delay", C.c_int32), ("L_m", C.c_double),
+                ("kappa0", C.c_double), ("lambda0", C.c_double), ("kepler_tilt", C.c_double),
+                ("t_static", C.c_double), ("xi0", C.c_double), ("delta_l", C.c_double * 3),
+                ("flex_scale", C.c_double), ("t_ref", C.c_double), ("lin_T0", C.c_double * 6),
+                ("lin_Tdot", C.c_double * 6)]
+
+
+class lisa_sky(C.Structure):
+    _fields_ = [("beta", C.c_double), ("lam", C.c_double), ("psi", C.c_double)]
+
+
+@dataclass
+class Orbit:
+    """Orbit and light-time model (fields of lisa_orbit)."""
+    kind: int = ORB_KEPLER1
+    delay: int = DELAY_LIGHTTIME
+    L_m: float = 2.5e9
+    kappa0: float = 0.0
+    lambda0: float = 0.0
+    kepler_tilt: float = 1.0
+    t_static: float = 0.0
+    xi0: float = 0.0
+    delta_l: tuple = (0.0, 2.0943951023931953, 4.1887902047863905)
+    flex_scale: float = 1.0
+    t_ref: float = 0.0
+    lin_T0: tuple = (0.0,) * 6
+    lin_Tdot: tuple = (0.0,) * 6
+
+    def c(self):
+        o = lisa_orbit()
+        o.kind, o.delay, o.L_m = self.kind, self.delay, self.L_m
+        o.kappa0, o.lambda0, o.kepler_tilt, o.t_static = self.kappa0, self.lambda0, self.kepler_tilt, self.t_static
+        o.xi0, o.flex_scale, o.t_ref = self.xi0, self.flex_scale, self.t_ref
+        for q in range(3):
+            o.delta_l[q] = self.delta_l[q]
+        for q in range(6):
+            o.lin_T0[q] = self.lin_T0[q]
+            o.lin_Tdot[q] = self.lin_Tdot[q]
+        return o
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = C.c_void_p
+_SIGS = {
+    "lisa_version": (C.c_int, []),
+    "lisa_strerror": (C.c_char_p, [C.c_int]),
+    "lisa_last_error_message": (C.c_char_p, []),
+    "lisa_t_hyb_from_f": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+    "lisa_orbits": (C.c_int, [C.POINTER(lisa_orbit), lisa_grid, _P, _P, _P, _P]),
+    "lisa_links_full": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
+                                  lisa_grid, _P, _P]),
+    "lisa_tdi": (C.c_int, [C.POINTER(lisa_orbit), lisa_grid, _P, C.c_int, C.c_int, C.c_int, C.c_int,
+                           lisa_grid, _P, _P]),
+    "lisa_response_full": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
+                                     C.c_int, C.c_int, lisa_grid, _P, _P]),
+    "lisa_links_lfa": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
+                                 C.c_int, C.c_int, lisa_grid, _P, _P]),
+    "lisa_tdi_lfa": (C.c_int, [C.POINTER(lisa_orbit), lisa_grid, _P, C.c_int, C.c_int, C.c_int, C.c_int,
+                               _P, _P]),
+    "lisa_response_lfa": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
+                                    C.c_int, C.c_int, C.c_int, lisa_grid, _P, _P]),
+    "lisa_profile_enable": (C.c_int, [C.c_int]),
+    "lisa_profile_query": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "lisa_launch_count": (C.c_int64, []),
+    "lisa_response_hybrid": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
+                                       C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                       lisa_grid, _P, _P]),
+}
+
+
+def exported_symbols():
+    """Names this binding expects the library to export."""
+    return list(_SIGS)
+
+
+def load(path=None):
+    """Load liblisa.so (build it first with paper_2505_09600_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError("liblisa.so not found at %s: run paper_2505_09600_gb300.build.build() "
+                                   "(there is no CPU fallback)" % p)
+            lib = C.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc, where):
+    if rc != LISA_OK:
+        lib = load()
+        raise LisaError(rc, where, lib.lisa_last_error_message().decode(errors="replace"))
+
+
+def _grid(g):
+    if isinstance(g, lisa_grid):
+        return g
+    t0, dt, n = g
+    return lisa_grid(float(t0), float(dt), int(n))
+
+
+def _sky(s):
+    return lisa_sky(float(s[0]), float(s[1]), float(s[2]))
+
+
+def _orb(o):
+    return (o if isinstance(o, Orbit) else Orbit()).c()
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s (got %s)" % (name, dtype, t.dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements (got %d)" % (name, numel, t.numel()))
+    return C.c_void_p(t.data_ptr())
+
+
+def _rdtype(precision):
+    import torch
+    return torch.float32 if precision == MIXED else torch.float64
+
+
+# ---------------------------------------------------------------------------
+# calls (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def lisa_version():
+    return load().lisa_version()
+
+
+def lisa_t_hyb_from_f(f_hyb, mc_s, tc):
+    return load().lisa_t_hyb_from_f(float(f_hyb), float(mc_s), float(tc))
+
+
+def lisa_orbits(orbit, grid, R=None, T=None, nhat=None, stream=None):
+    import torch
+    g = _grid(grid)
+    o = _orb(orbit)
+    rc = load().lisa_orbits(C.byref(o), g, _ptr(R, torch.float64, 9 * g.n, "R"), _ptr(T, torch.float64, 6 * g.n, "T"),
+                            _ptr(nhat, torch.float64, 18 * g.n, "nhat"), _stream(stream))
+    _check(rc, "lisa_orbits")
+
+
+def lisa_links_full(orbit, sky, h_grid, hp, hc, precision, y_grid, y, stream=None):
+    hg, yg = _grid(h_grid), _grid(y_grid)
+    dt = _rdtype(precision)
+    o, s = _orb(orbit), _sky(sky)
+    rc = load().lisa_links_full(C.byref(o), C.byref(s), hg, _ptr(hp, dt, hg.n, "hp"), _ptr(hc, dt, hg.n, "hc"),
+                                precision, yg, _ptr(y, dt, 6 * yg.n, "y"), _stream(stream))
+    _check(rc, "lisa_links_full")
+
+
+def lisa_tdi(orbit, y_grid, y, precision, tdi_gen, delay_mode, channels, out_grid, xyz, stream=None):
+    yg, og = _grid(y_grid), _grid(out_grid)
+    dt = _rdtype(precision)
+    o = _orb(orbit)
+    rc = load().lisa_tdi(C.byref(o), yg, _ptr(y, dt, 6 * yg.n, "y"), precision, tdi_gen, delay_mode, channels, og,
+                         _ptr(xyz, dt, 3 * og.n, "xyz"), _stream(stream))
+    _check(rc, "lisa_tdi")
+
+
+def lisa_response_full(orbit, sky, h_grid, hp, hc, precision, tdi_gen, channels, out_grid, xyz, stream=None):
+    hg, og = _grid(h_grid), _grid(out_grid)
+    dt = _rdtype(precision)
+    o, s = _orb(orbit), _sky(sky)
+    rc = load().lisa_response_full(C.byref(o), C.byref(s), hg, _ptr(hp, dt, hg.n, "hp"), _ptr(hc, dt, hg.n, "hc"),
+                                   precision, tdi_gen, channels, og, _ptr(xyz, dt, 3 * og.n, "xyz"), _stream(stream))
+    _check(rc, "lisa_response_full")
+
+
+def lisa_links_lfa(orbit, sky, h_grid, hp, hc, precision, tdi_gen, lfa_kind, out_grid, z, stream=None):
+    hg, og = _grid(h_grid), _grid(out_grid)
+    dt = _rdtype(precision)
+    o, s = _orb(orbit), _sky(sky)
+    rc = load().lisa_links_lfa(C.byref(o), C.byref(s), hg, _ptr(hp, dt, hg.n, "hp"), _ptr(hc, dt, hg.n, "hc"),
+                               precision, tdi_gen, lfa_kind, og, _ptr(z, dt, 6 * og.n, "z"), _stream(stream))
+    _check(rc, "lisa_links_lfa")
+
+
+def lisa_tdi_lfa(orbit, z_grid, z, precision, tdi_gen, lfa_kind, channels, xyz, stream=None):
+    zg = _grid(z_grid)
+    dt = _rdtype(precision)
+    o = _orb(orbit)
+    rc = load().lisa_tdi_lfa(C.byref(o), zg, _ptr(z, dt, 6 * zg.n, "z"), precision, tdi_gen, lfa_kind, channels,
+                             _ptr(xyz, dt, 3 * zg.n, "xyz"), _stream(stream))
+    _check(rc, "lisa_tdi_lfa")
+
+
+def lisa_response_lfa(orbit, sky, h_grid, hp, hc, precision, tdi_gen, lfa_kind, channels, out_grid, xyz, stream=None):
+    hg, og = _grid(h_grid), _grid(out_grid)
+    dt = _rdtype(precision)
+    o, s = _orb(orbit), _sky(sky)
+    rc = load().lisa_response_lfa(C.byref(o), C.byref(s), hg, _ptr(hp, dt, hg.n, "hp"), _ptr(hc, dt, hg.n, "hc"),
+                                  precision, tdi_gen, lfa_kind, channels, og, _ptr(xyz, dt, 3 * og.n, "xyz"),
+                                  _stream(stream))
+    _check(rc, "lisa_response_lfa")
+
+
+def lisa_response_hybrid(orbit, sky, h_grid, hp, hc, precision, tdi_gen, lfa_kind, channels, t_hyb, T_win, sigma,
+                         out_grid, xyz, stream=None):
+    hg, og = _grid(h_grid), _grid(out_grid)
+    dt = _rdtype(precision)
+    o, s = _orb(orbit), _sky(sky)
+    rc = load().lisa_response_hybrid(C.byref(o), C.byref(s), hg, _ptr(hp, dt, hg.n, "hp"), _ptr(hc, dt, hg.n, "hc"),
+                                     precision, tdi_gen, lfa_kind, channels, float(t_hyb), float(T_win), float(sigma),
+                                     og, _ptr(xyz, dt, 3 * og.n, "xyz"), _stream(stream))
+    _check(rc, "lisa_response_hybrid")
+
+
+def lisa_profile_enable(enable=True):
+    _check(load().lisa_profile_enable(1 if enable else 0), "lisa_profile_enable")
+
+
+def lisa_profile_query(name=None):
+    """(total device ms, launches) of recorded launches whose kernel name contains `name`."""
+    ms, cnt = C.c_double(), C.c_int64()
+    _check(load().lisa_profile_query(name.encode() if name else None, C.byref(ms), C.byref(cnt)),
+           "lisa_profile_query")
+    return ms.value, cnt.value
+
+
+def lisa_launch_count():
+    return load().lisa_launch_count()

@@ -1,0 +1,60 @@
+"""Helpers shared by the GPU parity tests (no arithmetic of the method here)."""
+import math
+
+import numpy as np
+
+import synth
+
+F64_TOL = 1e-12
+
+# Orbits used by the parity cases: first-order Kepler (config 1) and exact
+# Keplerian ellipses with 1% peak-to-peak arm flexing (config 2).
+ORBITS = {
+    "kepler1": dict(kind=0, delay=0),
+    "kepler2_flex": dict(kind=1, delay=0, kepler_tilt=1.01),
+    "analytic": dict(kind=0, delay=1, flex_scale=2.0, xi0=0.3),
+    "equal": dict(kind=0, delay=2),
+    "linear": dict(kind=0, delay=3, t_ref=2.0e7, lin_T0=(8.3, 8.31, 8.35, 8.33, 8.29, 8.30),
+                   lin_Tdot=(1e-7, -2e-7, 3e-7, 1e-7, -1e-7, 2e-7)),
+    "static": dict(kind=2, delay=0, t_static=2.2e7),
+}
+
+
+def orbit_pair(name):
+    import oracle
+    import paper_2505_09600_gb300 as L
+    kw = ORBITS[name]
+    return oracle.Orbit(**kw), L.Orbit(**kw)
+
+
+def rel_err(got, want):
+    """Per channel: max |got - want| / max |want|."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    scale = np.abs(want).max(axis=-1)
+    scale = np.where(scale > 0, scale, 1.0)
+    return np.abs(got - want).max(axis=-1) / scale
+
+
+def to_dev(a, precision):
+    import torch
+    dt = torch.float32 if precision == 1 else torch.float64
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda").to(dt).contiguous()
+
+
+def empty(shape, precision):
+    import torch
+    dt = torch.float32 if precision == 1 else torch.float64
+    return torch.full(shape, float("nan"), device="cuda", dtype=dt)
+
+
+def host_inputs(src, precision):
+    """h as the GPU sees it, returned as FP64 for the oracle (the oracle is fed
+    exactly the values the kernel reads)."""
+    if precision == 1:
+        return src.hp.astype(np.float32).astype(np.float64), src.hc.astype(np.float32).astype(np.float64)
+    return src.hp, src.hc
+
+
+def sky_of(src):
+    return (src.beta, src.lam, src.psi)

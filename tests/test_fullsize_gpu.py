@@ -1,0 +1,75 @@
+"""Full-size workload (one year at 5 s, 6,311,520 samples, chirp + ringdown,
+flexing Keplerian orbits), run exactly as bench.py launches it, checked
+against the oracle at sampled outputs that the oracle evaluates one by one
+(links and z are recomputed around each sampled output)."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import F64_TOL, host_inputs, orbit_pair, sky_of, to_dev
+from tolerances import MIXED_TOL
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_09600_gb300 import build
+    build.build()
+    import paper_2505_09600_gb300 as L
+    L.load()
+    return L
+
+
+@pytest.fixture(scope="module")
+def src():
+    return synth.cfg2_source()
+
+
+def _sample_indices(s, tH, Tw):
+    rng = np.random.default_rng(20250960)
+    n = s.n
+    iH = int((tH - s.t0) / s.dt)
+    w = int(Tw / s.dt)
+    idx = set(rng.integers(0, n, 24).tolist())
+    idx |= {0, 1, 2, n - 3, n - 2, n - 1}
+    idx |= set(range(iH - w // 2 - 3, iH - w // 2 + 3)) | set(range(iH + w // 2 - 3, iH + w // 2 + 3))
+    idx |= set(rng.integers(iH - w, n, 12).tolist())          # window, merger, ringdown
+    return np.array(sorted(i for i in idx if 0 <= i < n), dtype=np.int64)
+
+
+def _oracle_hybrid_sampled(oracle_mod, oo, s, hp, hc, tH, Tw, sig, idx):
+    hd = (oracle_mod.hdot(s.grid, hp), oracle_mod.hdot(s.grid, hc))
+    lfa = oracle_mod.tdi_lfa_direct(oo, sky_of(s), s.grid, hp, hc, 20, 0, s.grid, idx, hd=hd)
+    full = np.zeros_like(lfa)
+    t = s.t0 + idx * s.dt
+    need = t >= tH - 0.5 * Tw
+    if need.any():
+        full[:, need] = oracle_mod.tdi_full_direct(oo, sky_of(s), s.grid, hp, hc, s.grid, 20, 0, s.grid, idx[need])
+    xyz = oracle_mod.hybrid_blend(s.grid, tH, Tw, sig, lfa, full, idx)
+    return oracle_mod.aet(xyz), lfa
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fullsize_hybrid_sampled(L, oracle_mod, src, precision):
+    s = src
+    oo, lo = orbit_pair("kepler2_flex")
+    tH = oracle_mod.t_hyb(1e-3, s.mc_s, s.tc)
+    Tw, sig = 800 * s.dt, 20 * s.dt
+    hp, hc = host_inputs(s, precision)
+    out = torch.empty((3, s.n), device="cuda", dtype=torch.float32 if precision else torch.float64)
+    L.lisa_response_hybrid(lo, sky_of(s), s.grid, to_dev(hp, precision), to_dev(hc, precision), precision, 20, 0,
+                           L.AET, tH, Tw, sig, s.grid, out)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.isfinite(got).all()
+    idx = _sample_indices(s, tH, Tw)
+    want, _ = _oracle_hybrid_sampled(oracle_mod, oo, s, hp, hc, tH, Tw, sig, idx)
+    # normalise by the channel's largest value over the whole series (GPU side;
+    # the sampled set contains the merger region)
+    scale = np.abs(got).max(axis=1)
+    err = np.abs(got[:, idx] - want).max(axis=1) / scale
+    tol = F64_TOL if precision == 0 else np.array(MIXED_TOL["hybrid20"]["aet"])
+    assert np.all(err <= tol), (err, tol)
