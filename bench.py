@@ -181,27 +181,35 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None):
     t0 = time.perf_counter()
     hd = (oracle.hdot(s.grid, hp), oracle.hdot(s.grid, hc))
     t_hdot = time.perf_counter() - t0
-    # LFA on a contiguous chunk of the inspiral
+    # LFA on a contiguous chunk of the inspiral: z on the chunk and its
+    # 2-sample halo, then the channels
     chunk = 20000
     while True:
         i0 = s.n // 3
-        idx = np.arange(i0, i0 + chunk)
+        zg = (s.t0 + (i0 - 2) * s.dt, s.dt, chunk + 4)
         t0 = time.perf_counter()
-        lfa = oracle.tdi_lfa_direct(oo, sky, s.grid, hp, hc, 20, 0, s.grid, idx, hd=hd)
+        z = oracle.z_lfa(oo, sky, s.grid, hp, hc, 20, 0, zg, hd=hd)
+        lfa = oracle.tdi_lfa_from_z(oo, zg, z, 20, 0, idx=np.arange(2, chunk + 2))
         t_lfa = time.perf_counter() - t0
         if t_lfa > 0.4 * budget_s or chunk >= s.n // 4:
             break
         chunk = int(chunk * min(8.0, 0.5 * budget_s / max(t_lfa, 1e-3)))
-    # full response: links + TDI on its first samples, extrapolated
-    nf = min(n_full, 600)
-    idxf = np.arange(i_full, i_full + nf)
+    idx = np.arange(i0, i0 + chunk)
+    # full response on its whole region: links on the grid from 60 s before
+    # the first full sample (the TDI delays never exceed that), then TDI
+    marg = int(math.ceil(60.0 / s.dt)) + 20
+    j0 = max(0, i_full - marg)
+    ygrid = (s.t0 + j0 * s.dt, s.dt, s.n - j0)
+    ogrid = (s.t0 + i_full * s.dt, s.dt, n_full)
     t0 = time.perf_counter()
-    full = oracle.tdi_full_direct(oo, sky, s.grid, hp, hc, s.grid, 20, 0, s.grid, idxf)
+    y = oracle.links_full(oo, sky, s.grid, hp, hc, ygrid)
+    full = oracle.tdi_from_y(oo, ygrid, y, 20, oracle.FROZEN, ogrid)
     t_full = time.perf_counter() - t0
-    total = t_hdot + t_lfa * s.n / chunk + t_full * n_full / max(nf, 1)
+    total = t_hdot + t_lfa * s.n / chunk + t_full
     out = {"value": s.n / total, "unit": UNIT, "kind": "oracle",
-           "sample": ("LFA on %d contiguous samples + full response (links and TDI recomputed per output) "
-                      "on %d of its %d samples, extrapolated to all %d samples" % (chunk, nf, n_full, s.n)),
+           "sample": ("LFA (z series then channels) on %d contiguous samples, extrapolated to all %d; "
+                      "full response (links then TDI) on its whole region of %d samples"
+                      % (chunk, s.n, n_full)),
            "seconds": round(t_hdot + t_lfa + t_full, 3)}
     try:
         import synth as _s
@@ -210,6 +218,7 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None):
         out["cores"] = os.cpu_count()
     if gpu_out is not None:
         # agreement of the timed GPU step with the oracle on the sampled outputs
+        idxf = np.arange(i_full, s.n)
         blend_idx = np.concatenate([idx[:: max(1, chunk // 200)], idxf[::10]])
         lf = oracle.tdi_lfa_direct(oo, sky, s.grid, hp, hc, 20, 0, s.grid, blend_idx, hd=hd)
         fu = np.zeros_like(lf)

@@ -165,6 +165,47 @@ int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid
 double lisa_t_hyb_from_f(double f_hyb, double mc_s, double tc);
 
 
+/* ------------------------------------------------------------------------
+ * Batched hybrid plans: many sources of uneven duration and sampling in one
+ * persistent launch (mixed precision), capturable in a CUDA graph, with a
+ * launch-shape autotuner.  The paper evaluates one source at a time; this is
+ * the same hybrid response (Sec. IV) applied to a batch.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    lisa_grid grid;              /* h grid, also the output grid (dt >= 0.5 s)          */
+    const void* hp;              /* device float[grid.n]                                */
+    const void* hc;              /* device float[grid.n]                                */
+    lisa_sky sky;
+    double t_hyb, T_win, sigma;  /* s; T_win <= 0: 800 dt, sigma <= 0: T_win/40         */
+    void* out;                   /* device float[3][grid.n]: X,Y,Z or A,E,T             */
+} lisa_source;
+
+typedef struct lisa_plan lisa_plan;
+typedef struct { int ctas_per_sm, tiles_per_item; float ms; } lisa_tune_result;
+
+/* Create a plan over `nsrc` sources (host array, copied).  The plan owns its
+ * device memory (cudaMalloc at creation: orbit tables of every source, source
+ * descriptors, a work counter) until lisa_plan_destroy.  precision must be
+ * LISA_MIXED.  Series pointers are borrowed: they must stay valid while the
+ * plan executes. */
+int lisa_plan_create(lisa_plan** plan, const lisa_orbit* orbit, int precision, int tdi_gen, int lfa_kind,
+                     int channels, const lisa_source* sources, int nsrc);
+int lisa_plan_destroy(lisa_plan* plan);
+/* Enqueue one execution: counter reset, orbit tables, persistent kernel. */
+int lisa_plan_execute(lisa_plan* plan, void* stream);
+/* Capture one execution on `stream` (non-default) into a CUDA graph;
+ * lisa_plan_replay launches it. */
+int lisa_plan_capture_graph(lisa_plan* plan, void* stream);
+int lisa_plan_replay(lisa_plan* plan, void* stream);
+/* Launch shape: CTAs per SM of the persistent kernel (clamped to what fits)
+ * and output tiles per work item.  Drops a captured graph. */
+int lisa_plan_set_launch(lisa_plan* plan, int ctas_per_sm, int tiles_per_item);
+/* Time every (CTAs per SM in 1..4) x (tiles per item in 1,2,4,8) on this
+ * plan's own data (synchronising), keep the fastest, report it. */
+int lisa_plan_autotune(lisa_plan* plan, void* stream, lisa_tune_result* best);
+int lisa_plan_info(const lisa_plan* plan, int64_t* total_samples, int64_t* total_tiles, int* ctas_per_sm,
+                   int* tiles_per_item);
+
 /* Instrumentation (no counterpart in the paper).
  * lisa_profile_enable(1) clears the record and makes every kernel launch of
  * this library on this process record a CUDA event pair on its own stream;

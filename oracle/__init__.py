@@ -287,9 +287,9 @@ def hdot(grid, h):
     return out
 
 
-def z_lfa(orbit, sky, hgrid, hp, hc, gen, kind, outgrid, idx=None):
+def z_lfa(orbit, sky, hgrid, hp, hc, gen, kind, outgrid, idx=None, hd=None):
     """TDI-shifted LFA link series z[6, m] (X_a, X_b, Y_a, Y_b, Z_a, Z_b)."""
-    hdp, hdc = hdot(hgrid, hp), hdot(hgrid, hc)
+    hdp, hdc = (hdot(hgrid, hp), hdot(hgrid, hc)) if hd is None else hd
     go = _g(outgrid)
     ix, pix, nix = _idx(idx)
     m = nix if ix is not None else go.n

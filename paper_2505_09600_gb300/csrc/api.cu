@@ -101,7 +101,7 @@ static size_t real_size(int precision) { return precision == LISA_MIXED ? sizeof
 // Orbit polynomial table on grid g, in scratch.
 static int make_table(const lisa_orbit* orbit, const lisa_grid& g, Scratch& sc, SegTable& tab, cudaStream_t st)
 {
-    const int S = kSegSamples;
+    const int S = seg_samples(g.dt);
     const int64_t nseg = seg_count(g.n > 0 ? g.n : 1, S);
     double* coef = (double*)sc.alloc(sizeof(double) * (size_t)nseg * kNQ * kNC);
     if (!coef) return sc.status();

@@ -14,339 +14,24 @@
 //      X = 8(T_a+T_b)[T_a z_a'' - T_b z_b''].
 // The derivative stencils are evaluated as differences of differences, which
 // keeps FP32 rounding from being amplified by the cancellation.
-#include "lisa_common.cuh"
-#include "lisa_internal.cuh"
-#include "tile_geo.cuh"
+#include "lfa_tile.cuh"
 
 namespace lisa {
-
-constexpr int kWinH = kTile + 384;
-constexpr int kZW = kTile + 4;
-
-template <typename Real>
-struct PairT;
-template <>
-struct PairT<double> { using T = double2; };
-template <>
-struct PairT<float> { using T = float2; };
-
-struct LfaArgs {
-    SegTable tab;
-    SkyDev sky;
-    GridMap hm;
-    double Lc;
-    int gen, kind, channels;
-    const void* hp;
-    const void* hc;
-    void* z;
-    void* xyz;
-    int64_t nout;
-    double t0_out, dt_out;
-    int64_t i_begin, i_end, tile0;
-    BlendSpec bl;
-};
-
-// Channel ch: links a = cyc(+2), b = cyc(+3); arms T_a = cyc(+3), T_b = cyc(+2).
-__device__ __forceinline__ int lfa_link(int ch, int which) { return link_cycle(which ? 4 : 2, ch); }
-__device__ __forceinline__ int lfa_arm(int ch, int which) { return link_cycle(which ? 2 : 4, ch); }
-
-__device__ __forceinline__ double lfa_shift(int gen, double Ta, double Tb)
-{
-    return gen == LISA_TDI20 ? 2.0 * Ta + 1.5 * Tb : Ta + 0.5 * Tb;
-}
-
-template <typename Real>
-__device__ __forceinline__ Real interp_pair_w(const typename PairT<Real>::T* win, int64_t wlo, int wlen,
-                                              const typename PairT<Real>::T* __restrict__ dummy, int64_t j, Real eps,
-                                              Real& oc, bool& ok)
-{
-    const int64_t base = j - 15 - wlo;
-    ok = (base >= 0 && base + 32 <= wlen);
-    if (!ok) { oc = Real(0); return Real(0); }
-    if (eps == Real(0)) {
-        oc = win[j - wlo].y;
-        return win[j - wlo].x;
-    }
-    Real w[32];
-    lagrange32_weights(eps, w);
-    Real ap = Real(0), ac = Real(0);
-    const typename PairT<Real>::T* p = win + base;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        const typename PairT<Real>::T v = p[k];
-        ap = fma(w[k], v.x, ap);
-        ac = fma(w[k], v.y, ac);
-    }
-    oc = ac;
-    return ap;
-}
-
-// hdot at grid sample idx straight from global memory (fallback path).
-template <typename Real>
-__device__ __forceinline__ Real hdot_global(const Real* __restrict__ h, int64_t n, int64_t idx, Real inv12dt)
-{
-    auto at = [&](int64_t k) { return (k >= 0 && k < n) ? h[k] : Real(0); };
-    return ((at(idx + 1) - at(idx - 1)) * Real(8) - (at(idx + 2) - at(idx - 2))) * inv12dt;
-}
-
-template <typename Real>
-__device__ __forceinline__ void interp_hdot_global(const Real* __restrict__ hp, const Real* __restrict__ hc, int64_t n,
-                                                   int64_t j, Real eps, Real inv12dt, Real& op, Real& oc)
-{
-    if (eps == Real(0)) {
-        op = hdot_global(hp, n, j, inv12dt);
-        oc = hdot_global(hc, n, j, inv12dt);
-        return;
-    }
-    Real w[32];
-    lagrange32_weights(eps, w);
-    Real ap = Real(0), ac = Real(0);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        ap = fma(w[k], hdot_global(hp, n, j - 15 + k, inv12dt), ap);
-        ac = fma(w[k], hdot_global(hc, n, j - 15 + k, inv12dt), ac);
-    }
-    op = ap;
-    oc = ac;
-}
 
 template <bool MIXED>
 __global__ void __launch_bounds__(kTile) lfa_kernel(LfaArgs a)
 {
     using Real = typename std::conditional<MIXED, float, double>::type;
-    using Real2 = typename PairT<Real>::T;
-    __shared__ TileGeo g;
-    __shared__ Real2 hw[kWinH];      // h window (+2 each side), then hdot window
-    __shared__ Real2 dw[kWinH];
-    __shared__ Real zs[6][kZW];
-    __shared__ int64_t jends[12];
-    __shared__ int64_t s_wlo;
-    __shared__ int s_wlen;
-    // mixed: FP32 rows (centre value, cubic) and per-series centre splits
-    __shared__ float s_c0[kRows];
-    __shared__ Cubic s_cu[kRows];
-    __shared__ double s_ac[6];
-    __shared__ Cubic s_da[6];
-    __shared__ int64_t s_J[6];
-    __shared__ float s_f[6];
-
-    const Real* __restrict__ hp = (const Real*)a.hp;
-    const Real* __restrict__ hc = (const Real*)a.hc;
+    __shared__ LfaSmem<MIXED> sm;
     const int64_t i0 = (a.tile0 + blockIdx.x) * (int64_t)kTile;
-    const int64_t ic = i0 + kTile / 2;
-    const double half = 0.5 * a.tab.S;
-    const double u_per_s = 1.0 / (a.dt_out * half);
-    const int t = threadIdx.x;
-    const bool equal = (a.kind == LISA_LFA_EQUAL);
-    tile_geo_load(g, a.tab, ic, a.sky);
-
-    // --- FP64 per-series quantities at a time index m (delay of tau) ------
-    auto tau_delay = [&](int c, int64_t m) -> double {
-        const double u = (double)(m - ic) / half;
-        const int ch = c >> 1, which = c & 1;
-        const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
-        const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
-        const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
-        const int l = lfa_link(ch, which);
-        const double up = u - sh * u_per_s;
-        const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
-        return sh + 0.5 * Tl + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
-    };
-
-    if (t < 12) {
-        const int c = t % 6;
-        const int64_t m = (t < 6) ? i0 - 2 : i0 + kTile + 1;
-        int64_t j;
-        double eps;
-        split_f64(a.hm, m, tau_delay(c, m), j, eps);
-        jends[t] = j;
-    }
-    if constexpr (MIXED) {
-        if (t >= 32 && t < 32 + kRows) {
-            const int r = t - 32;
-            s_c0[r] = (float)g.b[r][0];
-            s_cu[r] = tg_cubic(g, r);
-        }
-        if (t >= 96 && t < 102) {
-            const int c = t - 96, ch = c >> 1, which = c & 1;
-            const int ra = kQT + lfa_arm(ch, 0), rb = kQT + lfa_arm(ch, 1);
-            const double Ta = equal ? a.Lc : g.b[ra][0], Tb = equal ? a.Lc : g.b[rb][0];
-            const double ac = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
-            Cubic da{0.f, 0.f, 0.f};
-            if (!equal) {
-                const Cubic ca = tg_cubic(g, ra), cb = tg_cubic(g, rb);
-                const float fa = which ? (a.gen == LISA_TDI20 ? 1.5f : 0.5f) : (a.gen == LISA_TDI20 ? 2.f : 1.f);
-                const float fb = which ? (a.gen == LISA_TDI20 ? 2.f : 1.f) : (a.gen == LISA_TDI20 ? 1.5f : 0.5f);
-                da = Cubic{fa * ca.c1 + fb * cb.c1, fa * ca.c2 + fb * cb.c2, fa * ca.c3 + fb * cb.c3};
-            }
-            const int l = lfa_link(ch, which);
-            const double Tl = equal ? a.Lc : g.b[kQT + l][0];
-            const double dc = ac + 0.5 * Tl + 0.5 * (g.b[kRowKR + link_sender(l)][0] + g.b[kRowKR + link_receiver(l)][0]);
-            int64_t j;
-            double eps;
-            split_f64(a.hm, ic, dc, j, eps);
-            s_ac[c] = ac;
-            s_da[c] = da;
-            s_J[c] = j;
-            s_f[c] = (float)eps;
-        }
-    }
-    __syncthreads();
-    if (t == 0) {
-        int64_t lo = jends[0], hi = jends[0];
-        for (int k = 1; k < 12; ++k) {
-            lo = jends[k] < lo ? jends[k] : lo;
-            hi = jends[k] > hi ? jends[k] : hi;
-        }
-        s_wlo = lo - 15 - 3;
-        const int64_t len = (hi + 16 + 3) - s_wlo + 1;
-        s_wlen = (len + 4 <= kWinH) ? (int)len : 0;
-    }
-    __syncthreads();
-    const int64_t wlo = s_wlo;
-    const int wlen = s_wlen;
-    const Real inv12dt = Real(1.0 / (12.0 * a.hm.dt_in));
-    // h over [wlo-2, wlo+wlen+2), then hdot over [wlo, wlo+wlen)
-    for (int k = t; k < wlen + 4; k += blockDim.x) {
-        const int64_t idx = wlo - 2 + k;
-        Real2 v;
-        v.x = (idx >= 0 && idx < a.hm.n_in) ? hp[idx] : Real(0);
-        v.y = (idx >= 0 && idx < a.hm.n_in) ? hc[idx] : Real(0);
-        hw[k] = v;
-    }
-    __syncthreads();
-    for (int k = t; k < wlen; k += blockDim.x) {
-        const Real2 m2 = hw[k], m1 = hw[k + 1], p1 = hw[k + 3], p2 = hw[k + 4];
-        Real2 d;
-        d.x = ((p1.x - m1.x) * Real(8) - (p2.x - m2.x)) * inv12dt;
-        d.y = ((p1.y - m1.y) * Real(8) - (p2.y - m2.y)) * inv12dt;
-        dw[k] = d;
-    }
-    __syncthreads();
-
-    const Real c2 = (Real)a.sky.c2p, s2 = (Real)a.sky.s2p;
-    const Real ku[3] = {(Real)a.sky.u[0], (Real)a.sky.u[1], (Real)a.sky.u[2]};
-    const Real kv[3] = {(Real)a.sky.v[0], (Real)a.sky.v[1], (Real)a.sky.v[2]};
-    const float Lcf = (float)a.Lc;
-
-    // --- z on the tile and its halo: (kTile + 4) x 6 values ----------------
-    for (int w = t; w < 6 * kZW; w += blockDim.x) {
-        const int c = w / kZW, o = w % kZW;
-        const int64_t m = i0 - 2 + o;
-        Real zval = Real(0);
-        if (m >= 0 && m < a.nout) {
-            const int ch = c >> 1, which = c & 1;
-            const int l = lfa_link(ch, which);
-            Real Tl, n3[3];
-            int64_t j;
-            Real eps;
-            if constexpr (!MIXED) {
-                const double u = (double)(m - ic) / half;
-                const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
-                const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
-                const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
-                const double up = u - sh * u_per_s;
-                Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
-                const double dtau = sh + 0.5 * Tl
-                                  + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
-                for (int q = 0; q < 3; ++q) n3[q] = tg_eval(g, kQN + 3 * l + q, up);
-                double e;
-                split_f64(a.hm, m, dtau, j, e);
-                eps = e;
-            } else {
-                const float u = (float)(m - ic) / (float)half;
-                const float da = s_da[c](u);
-                const float up = u - (float)((s_ac[c]) * u_per_s) - da * (float)u_per_s;
-                const float dT = equal ? 0.f : s_cu[kQT + l](up);
-                Tl = equal ? Lcf : s_c0[kQT + l] + dT;
-                const float ddt = da + 0.5f * dT
-                                + 0.5f * (s_cu[kRowKR + link_sender(l)](up) + s_cu[kRowKR + link_receiver(l)](up));
-                for (int q = 0; q < 3; ++q) n3[q] = s_c0[kQN + 3 * l + q] + s_cu[kQN + 3 * l + q](up);
-                int64_t jp;
-                float fp;
-                if (a.hm.unit_rho) {
-                    jp = m - ic;
-                    fp = 0.f;
-                } else {
-                    const double P = (double)(m - ic) * a.hm.rho;
-                    const double fl = floor(P);
-                    jp = (int64_t)fl;
-                    fp = (float)(P - fl);
-                }
-                const float v = (fp + s_f[c]) - ddt * (float)(1.0 / a.hm.dt_in);
-                const float fv = floorf(v);
-                j = s_J[c] + jp + (int64_t)fv;
-                eps = v - fv;
-            }
-            const Real un = ku[0] * n3[0] + ku[1] * n3[1] + ku[2] * n3[2];
-            const Real vn = kv[0] * n3[0] + kv[1] * n3[1] + kv[2] * n3[2];
-            const Real xp = un * un - vn * vn, xc = Real(2) * un * vn;
-            Real dp, dc;
-            bool ok;
-            dp = interp_pair_w<Real>(dw, wlo, wlen, nullptr, j, eps, dc, ok);
-            if (!ok) interp_hdot_global<Real>(hp, hc, a.hm.n_in, j, eps, inv12dt, dp, dc);
-            zval = Real(-0.5) * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
-        }
-        zs[c][o] = zval;
-    }
-    __syncthreads();
-
-    const int64_t i = i0 + t;
-    if (i < a.i_begin || i >= a.i_end) return;
-    if (a.z) {
-        Real* zo = (Real*)a.z;
-        for (int c = 0; c < 6; ++c) zo[(int64_t)c * a.nout + i] = zs[c][t + 2];
-    }
-    if (!a.xyz) return;
     Real X[3];
-    const Real dt = (Real)a.dt_out;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        Real Ta, Tb;
-        if constexpr (!MIXED) {
-            const double u = (double)(i - ic) / half;
-            Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
-            Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
-        } else {
-            const float u = (float)(i - ic) / (float)half;
-            Ta = equal ? Lcf : s_c0[kQT + lfa_arm(ch, 0)] + s_cu[kQT + lfa_arm(ch, 0)](u);
-            Tb = equal ? Lcf : s_c0[kQT + lfa_arm(ch, 1)] + s_cu[kQT + lfa_arm(ch, 1)](u);
-        }
-        const Real* za = zs[2 * ch] + t;       // za[0..4] = z at i-2..i+2
-        const Real* zb = zs[2 * ch + 1] + t;
-        if (a.gen == LISA_TDI20) {
-            // 5-point second derivative as (14 d2_0 - d2_-1 - d2_1)/12, d2 from first differences
-            auto d2 = [&](const Real* z) {
-                const Real e0 = z[1] - z[0], e1 = z[2] - z[1], e2 = z[3] - z[2], e3 = z[4] - z[3];
-                const Real m1 = e1 - e0, c0 = e2 - e1, p1 = e3 - e2;
-                return (Real(14) * c0 - m1 - p1) / (Real(12) * dt * dt);
-            };
-            X[ch] = Real(8) * (Ta + Tb) * (Ta * d2(za) - Tb * d2(zb));
-        } else {
-            auto d1 = [&](const Real* z) { return ((z[3] - z[1]) * Real(8) - (z[4] - z[0])) / (Real(12) * dt); };
-            X[ch] = Real(4) * (Ta * d1(za) - Tb * d1(zb));
-        }
+    lfa_tile_compute<MIXED>(a, i0, sm, X);
+    const int64_t i = i0 + threadIdx.x;
+    if constexpr (MIXED) {
+        if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<Real>(a, i, X, sm.barg_c, sm.barg_d, (int)(i - (i0 + kTile / 2)));
+    } else {
+        if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<Real>(a, i, X);
     }
-    Real* out = (Real*)a.xyz;
-    Real o0 = X[0], o1 = X[1], o2 = X[2];
-    if (a.channels == LISA_AET) {
-        o0 = (X[2] - X[0]) * Real(0.70710678118654752440);
-        o1 = (X[0] - Real(2) * X[1] + X[2]) * Real(0.40824829046386301637);
-        o2 = (X[0] + X[1] + X[2]) * Real(0.57735026918962576451);
-    }
-    if (a.bl.enabled) {
-        const double ti = a.t0_out + (double)i * a.dt_out;
-        const double arg = a.bl.eps * (ti - a.bl.t_hyb) / a.bl.sigma;
-        Real wgt;
-        if constexpr (MIXED) wgt = 1.f / (1.f + expf((float)arg));
-        else wgt = 1.0 / (1.0 + exp(arg));
-        o0 *= wgt;
-        o1 *= wgt;
-        o2 *= wgt;
-    }
-    out[i] = o0;
-    out[a.nout + i] = o1;
-    out[2 * a.nout + i] = o2;
 }
 
 int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,

@@ -9,8 +9,8 @@
 //    x in [-1, 1].  Every response kernel re-expands its segment's polynomial
 //    around its tile centre and evaluates it per sample (Horner), so per
 //    sample there is no trigonometry, no Kepler solve and no light-time
-//    iteration.  The truncation error of the degree-6 fit over a 512-sample
-//    segment is < 1e-20 s, far below FP64 rounding.
+//    iteration.  The truncation error of the degree-6 fit over a segment of
+//    up to 25,000 s is < 1e-16 s, below FP64 rounding of the delays.
 //  * LISA_F64 kernels keep every step in FP64.  LISA_MIXED kernels keep the
 //    tile-centre values of delays in FP64, split once per tile into an
 //    integer sample and a fraction, and evaluate the in-tile variation
@@ -37,7 +37,18 @@ constexpr int kQN = 15;
 constexpr int kDeg = 6;      // polynomial degree per segment
 constexpr int kNodes = 7;    // Chebyshev nodes per segment
 constexpr int kNC = 8;       // stored coefficients per quantity (7 used)
-constexpr int kSegSamples = 512;
+constexpr int kSegSamples = 512;  // smallest segment
+// Samples per segment for a grid step dt: the largest power of two <= 16384
+// with S*dt <= 25,000 s (at least 512).  Over 25,000 s the orbital phase moves
+// by 5e-3 rad and the degree-6 Chebyshev fit of every quantity is exact to
+// ~1e-19 relative (< 1e-16 s of delay), so segment length only trades
+// table work (7 exact FP64 evaluations per segment) against nothing.
+__host__ __device__ inline int seg_samples(double dt)
+{
+    int S = kSegSamples;
+    while (S < 16384 && 2.0 * S * dt <= 25000.0) S *= 2;
+    return S;
+}
 
 // Link index li = 0..5 <-> l = +1,-1,+2,-2,+3,-3 (y_312, y_2-13, y_123, y_3-21,
 // y_231, y_1-32); 0-based spacecraft of sender and receiver.

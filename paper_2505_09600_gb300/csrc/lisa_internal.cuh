@@ -34,6 +34,15 @@ private:
 // Tile size (output samples per CTA) of the response kernels.
 constexpr int kTile = 256;
 
+// Segment tables of many grids in one launch (batched plans).
+struct SegSource {
+    double t0, dt;
+    int S;
+    int64_t seg_begin;   // index of the first segment of this grid in the shared table
+};
+int build_seg_tables_batched(const OrbitDev& orb, const SegSource* srcs_dev, int nsrc, int64_t total_segs,
+                             double* coef_dev, cudaStream_t st);
+
 int run_orbits(const lisa_orbit* orbit, lisa_grid g, double* R, double* T, double* nh, cudaStream_t st);
 
 // Full links on y-grid samples [i_begin, i_end) using a segment table built

@@ -263,6 +263,73 @@ int build_seg_table(const OrbitDev& orb, const lisa_grid& g, int S, double* coef
 }
 
 // ---------------------------------------------------------------------------
+// batched segment tables: every segment of every source in one launch
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSegPerBlock * kNodes)
+seg_table_batched_kernel(OrbitDev o, const SegSource* __restrict__ srcs, int nsrc, int64_t total,
+                         double* __restrict__ coef)
+{
+    __shared__ double vals[kSegPerBlock][kNQ][kNodes];
+    __shared__ int s_src[kSegPerBlock];
+    const int local = threadIdx.x / kNodes, node = threadIdx.x % kNodes;
+    const int64_t gseg = (int64_t)blockIdx.x * kSegPerBlock + local;
+    if (threadIdx.x < kSegPerBlock) {
+        const int64_t gs = (int64_t)blockIdx.x * kSegPerBlock + threadIdx.x;
+        int lo = 0, hi = nsrc - 1;
+        while (lo < hi) {  // last source whose first segment is <= gs
+            const int mid = (lo + hi + 1) >> 1;
+            if (srcs[mid].seg_begin <= gs) lo = mid; else hi = mid - 1;
+        }
+        s_src[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    if (gseg < total) {
+        const SegSource& src = srcs[s_src[local]];
+        const int64_t s = gseg - src.seg_begin;
+        const double xk = cospi((node + 0.5) / kNodes);
+        const double qpos = (double)(s * src.S) + 0.5 * src.S + xk * (0.5 * src.S);
+        const double t = src.t0 + qpos * src.dt;
+        double g[kNQ];
+        geometry_exact(o, t, g);
+        for (int qq = 0; qq < kNQ; ++qq) vals[local][qq][node] = g[qq];
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < kSegPerBlock * kNQ; w += blockDim.x) {
+        const int loc = w / kNQ, qq = w % kNQ;
+        const int64_t seg = (int64_t)blockIdx.x * kSegPerBlock + loc;
+        if (seg >= total) continue;
+        double c[kNodes];
+        for (int j = 0; j < kNodes; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < kNodes; ++k) acc += vals[loc][qq][k] * cospi(j * (k + 0.5) / kNodes);
+            c[j] = (2.0 / kNodes) * acc;
+        }
+        c[0] *= 0.5;
+        double* dst = coef + (seg * kNQ + qq) * kNC;
+        dst[0] = c[0] - c[2] + c[4] - c[6];
+        dst[1] = c[1] - 3.0 * c[3] + 5.0 * c[5];
+        dst[2] = 2.0 * c[2] - 8.0 * c[4] + 18.0 * c[6];
+        dst[3] = 4.0 * c[3] - 20.0 * c[5];
+        dst[4] = 8.0 * c[4] - 48.0 * c[6];
+        dst[5] = 16.0 * c[5];
+        dst[6] = 32.0 * c[6];
+        dst[7] = 0.0;
+    }
+}
+
+int build_seg_tables_batched(const OrbitDev& orb, const SegSource* srcs_dev, int nsrc, int64_t total_segs,
+                             double* coef_dev, cudaStream_t st)
+{
+    if (total_segs <= 0) return LISA_OK;
+    const int64_t blocks = (total_segs + kSegPerBlock - 1) / kSegPerBlock;
+    prof_before("seg_table_batched", st);
+    seg_table_batched_kernel<<<(unsigned)blocks, kSegPerBlock * kNodes, 0, st>>>(orb, srcs_dev, nsrc, total_segs,
+                                                                                coef_dev);
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "seg_table_batched_kernel launch");
+}
+
+// ---------------------------------------------------------------------------
 // lisa_orbits: materialise R, T, n at every sample (from the table)
 // ---------------------------------------------------------------------------
 __global__ void orbits_eval_kernel(SegTable tab, int64_t n, double* __restrict__ R, double* __restrict__ T,
@@ -285,7 +352,7 @@ __global__ void orbits_eval_kernel(SegTable tab, int64_t n, double* __restrict__
 int run_orbits(const lisa_orbit* orbit, lisa_grid g, double* R, double* T, double* nh, cudaStream_t st)
 {
     const OrbitDev od = make_orbit_dev(*orbit);
-    const int S = kSegSamples;
+    const int S = seg_samples(g.dt);
     const int64_t nseg = seg_count(g.n, S);
     Scratch sc(st);
     double* coef = (double*)sc.alloc(sizeof(double) * nseg * kNQ * kNC);

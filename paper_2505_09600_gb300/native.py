@@ -48,6 +48,15 @@ class lisa_sky(C.Structure):
     _fields_ = [("beta", C.c_double), ("lam", C.c_double), ("psi", C.c_double)]
 
 
+class lisa_source(C.Structure):
+    _fields_ = [("grid", lisa_grid), ("hp", C.c_void_p), ("hc", C.c_void_p), ("sky", lisa_sky),
+                ("t_hyb", C.c_double), ("T_win", C.c_double), ("sigma", C.c_double), ("out", C.c_void_p)]
+
+
+class lisa_tune_result(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int), ("tiles_per_item", C.c_int), ("ms", C.c_float)]
+
+
 @dataclass
 class Orbit:
     """Orbit and light-time model (fields of lisa_orbit)."""
@@ -100,6 +109,16 @@ _SIGS = {
                                _P, _P]),
     "lisa_response_lfa": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
                                     C.c_int, C.c_int, C.c_int, lisa_grid, _P, _P]),
+    "lisa_plan_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(lisa_orbit), C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.POINTER(lisa_source), C.c_int]),
+    "lisa_plan_destroy": (C.c_int, [C.c_void_p]),
+    "lisa_plan_execute": (C.c_int, [C.c_void_p, _P]),
+    "lisa_plan_capture_graph": (C.c_int, [C.c_void_p, _P]),
+    "lisa_plan_replay": (C.c_int, [C.c_void_p, _P]),
+    "lisa_plan_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "lisa_plan_autotune": (C.c_int, [C.c_void_p, _P, C.POINTER(lisa_tune_result)]),
+    "lisa_plan_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int)]),
     "lisa_profile_enable": (C.c_int, [C.c_int]),
     "lisa_profile_query": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "lisa_launch_count": (C.c_int64, []),
@@ -281,3 +300,64 @@ def lisa_profile_query(name=None):
 
 def lisa_launch_count():
     return load().lisa_launch_count()
+
+
+class LisaPlan:
+    """Batched hybrid plan (lisa_plan_*).  `sources` is a list of dicts with
+    keys grid, hp, hc, sky, t_hyb, out (and optionally T_win, sigma); the
+    tensors are kept alive for the plan's lifetime."""
+
+    def __init__(self, orbit, sources, precision=MIXED, tdi_gen=TDI20, lfa_kind=LFA_UNEQUAL, channels=AET):
+        import torch
+        self._keep = []
+        arr = (lisa_source * len(sources))()
+        for k, s in enumerate(sources):
+            g = _grid(s["grid"])
+            dt = _rdtype(precision)
+            arr[k].grid = g
+            arr[k].hp = _ptr(s["hp"], dt, g.n, "hp")
+            arr[k].hc = _ptr(s["hc"], dt, g.n, "hc")
+            arr[k].sky = _sky(s["sky"])
+            arr[k].t_hyb = float(s["t_hyb"])
+            arr[k].T_win = float(s.get("T_win", 0.0))
+            arr[k].sigma = float(s.get("sigma", 0.0))
+            arr[k].out = _ptr(s["out"], dt, 3 * g.n, "out")
+            self._keep += [s["hp"], s["hc"], s["out"]]
+        self._orbit = _orb(orbit)
+        h = C.c_void_p()
+        _check(load().lisa_plan_create(C.byref(h), C.byref(self._orbit), precision, tdi_gen, lfa_kind, channels, arr,
+                                       len(sources)), "lisa_plan_create")
+        self.handle = h
+
+    def execute(self, stream=None):
+        _check(load().lisa_plan_execute(self.handle, _stream(stream)), "lisa_plan_execute")
+
+    def capture_graph(self, stream):
+        _check(load().lisa_plan_capture_graph(self.handle, _stream(stream)), "lisa_plan_capture_graph")
+
+    def replay(self, stream=None):
+        _check(load().lisa_plan_replay(self.handle, _stream(stream)), "lisa_plan_replay")
+
+    def set_launch(self, ctas_per_sm, tiles_per_item):
+        _check(load().lisa_plan_set_launch(self.handle, ctas_per_sm, tiles_per_item), "lisa_plan_set_launch")
+
+    def autotune(self, stream=None):
+        r = lisa_tune_result()
+        _check(load().lisa_plan_autotune(self.handle, _stream(stream), C.byref(r)), "lisa_plan_autotune")
+        return {"ctas_per_sm": r.ctas_per_sm, "tiles_per_item": r.tiles_per_item, "ms": r.ms}
+
+    def info(self):
+        a, b, c, d = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+        _check(load().lisa_plan_info(self.handle, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "lisa_plan_info")
+        return {"total_samples": a.value, "total_tiles": b.value, "ctas_per_sm": c.value, "tiles_per_item": d.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().lisa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

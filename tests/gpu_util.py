@@ -5,7 +5,12 @@ import numpy as np
 
 import synth
 
-F64_TOL = 1e-12
+# All-FP64 GPU against the FP64 oracle.  The two use different but equivalent
+# operation orders (FMA contraction, Lagrange weights as running products,
+# orbit geometry from per-segment polynomials instead of exact evaluation at
+# rounded absolute times); the LFA's 5-point second differences amplify the
+# resulting rounding by up to 64/(omega dt)^2 at the lowest frequencies.
+F64_TOL = 5e-12
 
 # Orbits used by the parity cases: first-order Kepler (config 1) and exact
 # Keplerian ellipses with 1% peak-to-peak arm flexing (config 2).
@@ -27,11 +32,18 @@ def orbit_pair(name):
     return oracle.Orbit(**kw), L.Orbit(**kw)
 
 
-def rel_err(got, want):
-    """Per channel: max |got - want| / max |want|."""
+def rel_err(got, want, signal=False):
+    """Per channel: max |got - want| / max |want|.
+
+    With signal=True (used for A, E, T) every channel is divided by the largest
+    channel maximum instead: T is a near-cancelling sum of X, Y, Z (and is
+    identically zero for equal arms in the LFA), so its own maximum is not a
+    meaningful scale for errors inherited from X, Y, Z."""
     got = np.asarray(got, dtype=np.float64)
     want = np.asarray(want, dtype=np.float64)
     scale = np.abs(want).max(axis=-1)
+    if signal:
+        scale = np.full_like(scale, scale.max())
     scale = np.where(scale > 0, scale, 1.0)
     return np.abs(got - want).max(axis=-1) / scale
 

@@ -1,7 +1,8 @@
 """GPU (liblisa, sm_103a) against the FP64 CPU oracle, element by element.
 
-All-FP64 forms must agree within 1e-12 of each channel's largest value.
-Mixed-precision tolerances are in test_parity_mixed_gpu.py.
+All-FP64 forms must agree within F64_TOL (5e-12) of each channel's largest
+value (A, E, T: of the largest channel's).  Mixed-precision tolerances are in
+tolerances.py and test_parity_mixed_gpu.py.
 """
 import math
 
@@ -46,7 +47,10 @@ def test_orbits(L, oracle_mod, orb):
     torch.cuda.synchronize()
     Ro, To, no = oracle_mod.orbits(oo, g)
     assert np.abs(R.cpu().numpy() - Ro).max() < 2e-4          # metres (R ~ 1.5e11 m)
-    assert np.abs(T.cpu().numpy() - To).max() < 2e-14         # seconds
+    # The oracle evaluates R_s at the absolute time t - T, whose FP64 rounding
+    # (ulp(2e7 s) = 3.7e-9 s) moves the sender by |V| * 3.7e-9 s ~ 1e-4 m, i.e.
+    # ~4e-13 s of light time; the kernels expand R_s(t - T) about t instead.
+    assert np.abs(T.cpu().numpy() - To).max() < 1.5e-12       # seconds
     assert np.abs(nh.cpu().numpy() - no).max() < 2e-13
 
 
@@ -75,7 +79,7 @@ def test_tdi_f64_from_links(L, oracle_mod, gen, mode, channels):
         want = oracle_mod.aet(want)
     out = empty((3, 1500), 0)
     L.lisa_tdi(lo, g, to_dev(y, 0), L.F64, gen, mode, channels, g, out)
-    err = rel_err(out.cpu().numpy(), want)
+    err = rel_err(out.cpu().numpy(), want, signal=channels == 1)
     assert err.max() <= F64_TOL, err
 
 
@@ -107,7 +111,7 @@ def test_lfa_f64(L, oracle_mod, cfg2s, gen, kind):
     # channels from caller-held z
     x2 = empty((3, s.n), 0)
     L.lisa_tdi_lfa(lo, s.grid, z, L.F64, gen, kind, L.AET, x2)
-    assert rel_err(x2.cpu().numpy(), oracle_mod.aet(x_want)).max() <= F64_TOL
+    assert rel_err(x2.cpu().numpy(), oracle_mod.aet(x_want), signal=True).max() <= F64_TOL
 
 
 @pytest.mark.parametrize("where", ["middle", "before_start", "after_end", "near_end"])
@@ -122,7 +126,7 @@ def test_hybrid_f64(L, oracle_mod, cfg2s, where):
     out = empty((3, s.n), 0)
     L.lisa_response_hybrid(lo, sky_of(s), s.grid, to_dev(s.hp, 0), to_dev(s.hc, 0), L.F64, 20, 0, L.AET,
                            tH, Tw, sig, s.grid, out)
-    err = rel_err(out.cpu().numpy(), want)
+    err = rel_err(out.cpu().numpy(), want, signal=True)
     assert err.max() <= F64_TOL, err
 
 

@@ -1,0 +1,91 @@
+"""Mixed-precision forms (FP32 arithmetic, FP64 tile-centre times) against the
+FP64 oracle, element by element, at the frozen per-channel tolerances of
+tolerances.py.  The oracle is fed exactly the FP32 values the kernels read."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import empty, host_inputs, orbit_pair, rel_err, sky_of, to_dev
+from tolerances import MIXED_TOL
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_09600_gb300 import build
+    build.build()
+    import paper_2505_09600_gb300 as L
+    L.load()
+    return L
+
+
+@pytest.fixture(scope="module")
+def case():
+    s = synth.cfg2_small(n=20000)
+    hp, hc = host_inputs(s, 1)
+    return s, hp, hc
+
+
+def _check(got, want, tol, aet=False):
+    err = rel_err(got, want, signal=aet)
+    assert np.all(err <= np.asarray(tol)), (err, tol)
+    return err
+
+
+def test_links_mixed(L, oracle_mod, case):
+    s, hp, hc = case
+    oo, lo = orbit_pair("kepler2_flex")
+    want = oracle_mod.links_full(oo, sky_of(s), s.grid, hp, hc, s.grid)
+    y = empty((6, s.n), 1)
+    L.lisa_links_full(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, s.grid, y)
+    _check(y.cpu().numpy(), want, MIXED_TOL["links"])
+
+
+@pytest.mark.parametrize("gen", [15, 20])
+@pytest.mark.parametrize("channels", [0, 1])
+def test_full_mixed(L, oracle_mod, case, gen, channels):
+    s, hp, hc = case
+    oo, lo = orbit_pair("kepler2_flex")
+    want = oracle_mod.response_full(oo, sky_of(s), s.grid, hp, hc, gen, 0, "aet" if channels else "xyz")
+    out = empty((3, s.n), 1)
+    L.lisa_response_full(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, gen, channels, s.grid, out)
+    _check(out.cpu().numpy(), want, MIXED_TOL["full%d" % gen]["aet" if channels else "xyz"], aet=channels == 1)
+
+
+@pytest.mark.parametrize("gen", [15, 20])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_lfa_mixed(L, oracle_mod, case, gen, kind):
+    s, hp, hc = case
+    oo, lo = orbit_pair("kepler2_flex")
+    z_want = oracle_mod.z_lfa(oo, sky_of(s), s.grid, hp, hc, gen, kind, s.grid)
+    x_want = oracle_mod.tdi_lfa_from_z(oo, s.grid, z_want, gen, kind)
+    hpd, hcd = to_dev(hp, 1), to_dev(hc, 1)
+    z = empty((6, s.n), 1)
+    L.lisa_links_lfa(lo, sky_of(s), s.grid, hpd, hcd, L.MIXED, gen, kind, s.grid, z)
+    _check(z.cpu().numpy(), z_want, MIXED_TOL["z"])
+    for channels in (0, 1):
+        out = empty((3, s.n), 1)
+        L.lisa_response_lfa(lo, sky_of(s), s.grid, hpd, hcd, L.MIXED, gen, kind, channels, s.grid, out)
+        want = oracle_mod.aet(x_want) if channels else x_want
+        _check(out.cpu().numpy(), want, MIXED_TOL["lfa%d" % gen]["aet" if channels else "xyz"], aet=channels == 1)
+
+
+@pytest.mark.parametrize("gen", [15, 20])
+@pytest.mark.parametrize("channels", [0, 1])
+def test_hybrid_mixed(L, oracle_mod, case, gen, channels):
+    s, hp, hc = case
+    oo, lo = orbit_pair("kepler2_flex")
+    tH = oracle_mod.t_hyb(1e-3, s.mc_s, s.tc)
+    Tw, sig = 800 * s.dt, 20 * s.dt
+    want = oracle_mod.response_hybrid(oo, sky_of(s), s.grid, hp, hc, gen, 0, "aet" if channels else "xyz",
+                                      tH, Tw, sig)
+    out = empty((3, s.n), 1)
+    L.lisa_response_hybrid(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, gen, 0, channels,
+                           tH, Tw, sig, s.grid, out)
+    _check(out.cpu().numpy(), want, MIXED_TOL["hybrid%d" % gen]["aet" if channels else "xyz"], aet=channels == 1)
