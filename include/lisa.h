@@ -160,6 +160,32 @@ int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid
                          int channels, double t_hyb, double T_win, double sigma,
                          lisa_grid out, void* xyz, void* stream);
 
+/* No-allocation variant of lisa_response_hybrid (the paper has no
+ * counterpart; this is an integration aid).  Some callers may not allocate
+ * device memory while they run: an application that gives all device memory
+ * to its own pool at start-up and forbids later driver allocations, a
+ * latency-bound loop that must not wait on an allocator, or a platform
+ * without the stream-ordered allocator.  This call computes exactly what
+ * lisa_response_hybrid computes, with the same arguments, but takes its
+ * scratch (orbit tables and link series) from one fixed device array of
+ * LISA_STATIC_SCRATCH_BYTES inside the library and calls no cudaMalloc,
+ * cudaFree or allocating routine.
+ *  - The array is resident on every GPU that loads the library until exit.
+ *  - A call whose scratch does not fit returns LISA_EINVAL and says how many
+ *    bytes it needed (a one-year series at 5 s needs under 4 MB).
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture on the device.
+ *  - All calls share the array and leave the last call's contents in it:
+ *    calls that overlap on the GPU (other streams, other host threads) race
+ *    and must be serialised by the caller.  Nothing in it needs clearing;
+ *    every call writes all it reads. */
+#define LISA_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int lisa_response_hybrid_static(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                                const void* hp, const void* hc, int precision, int tdi_gen, int lfa_kind,
+                                int channels, double t_hyb, double T_win, double sigma,
+                                lisa_grid out, void* xyz, void* stream);
+
 /* Hybridisation time at leading PN order (Sec. IV, Eq. thyb):
  * t_hyb = tc - f^(-8/3) * 5/(8 pi)^(8/3) * (G Mc/c^3)^(-5/3); mc_s = G Mc/c^3 in s. */
 double lisa_t_hyb_from_f(double f_hyb, double mc_s, double tc);

@@ -109,6 +109,9 @@ _SIGS = {
                                _P, _P]),
     "lisa_response_lfa": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
                                     C.c_int, C.c_int, C.c_int, lisa_grid, _P, _P]),
+    "lisa_response_hybrid_static": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
+                                              C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                              lisa_grid, _P, _P]),
     "lisa_plan_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(lisa_orbit), C.c_int, C.c_int, C.c_int, C.c_int,
                                    C.POINTER(lisa_source), C.c_int]),
     "lisa_plan_destroy": (C.c_int, [C.c_void_p]),
@@ -300,6 +303,20 @@ def lisa_profile_query(name=None):
 
 def lisa_launch_count():
     return load().lisa_launch_count()
+
+
+def lisa_response_hybrid_static(orbit, sky, h_grid, hp, hc, precision, tdi_gen, lfa_kind, channels, t_hyb, T_win,
+                                sigma, out_grid, xyz, stream=None):
+    """lisa_response_hybrid with its scratch in the library's fixed device
+    array instead of allocated memory (see include/lisa.h)."""
+    hg, og = _grid(h_grid), _grid(out_grid)
+    dt = _rdtype(precision)
+    o, s = _orb(orbit), _sky(sky)
+    rc = load().lisa_response_hybrid_static(C.byref(o), C.byref(s), hg, _ptr(hp, dt, hg.n, "hp"),
+                                            _ptr(hc, dt, hg.n, "hc"), precision, tdi_gen, lfa_kind, channels,
+                                            float(t_hyb), float(T_win), float(sigma), og,
+                                            _ptr(xyz, dt, 3 * og.n, "xyz"), _stream(stream))
+    _check(rc, "lisa_response_hybrid_static")
 
 
 class LisaPlan:
