@@ -161,9 +161,44 @@ __device__ void sc_state(const OrbitDev& o, int sc, double t, double R[3], doubl
     A[2] = W * W * r3 * c1;
 }
 
-// Geometry at time t: R_s (9), T_l (6), n_l (18).  The sender's emission
-// position R_s(t - T) comes from a second-order Taylor expansion about t
-// (the dropped third-order term is ~1e-7 m, i.e. ~3e-16 s of light time).
+// Light time and unit vector of link li at time t from the receiver's
+// position and the sender's position, velocity and acceleration at t.  The
+// sender's emission position R_s(t - T) comes from a second-order Taylor
+// expansion about t (the dropped third-order term is ~1e-7 m, i.e. ~3e-16 s
+// of light time).
+__device__ void link_geometry(const OrbitDev& o, int li, double t, const double* Rr, const double* Rs,
+                              const double* Vs, const double* As, double* T_out, double* n_out)
+{
+    double T;
+    if (o.delay == LISA_DELAY_EQUAL) {
+        T = o.L / kC;
+    } else if (o.delay == LISA_DELAY_LINEAR) {
+        T = o.T0[li] + o.Tdot[li] * (t - o.t_ref);
+    } else if (o.delay == LISA_DELAY_ANALYTIC) {
+        const double sg = (li & 1) ? -1.0 : 1.0;
+        const double L = o.L, e = o.e, W = o.omega;
+        const double Lt = L + (1.0 / 32.0) * e * L * o.flex * sin(3.0 * W * t - 3.0 * o.xi0)
+                        + ((kAU * W * L / kC) * sg - (15.0 / 32.0) * e * L * o.flex) * sin(W * t - o.delta[li >> 1]);
+        T = Lt / kC;
+    } else {
+        double d0 = Rr[0] - Rs[0], d1 = Rr[1] - Rs[1], d2 = Rr[2] - Rs[2];
+        T = sqrt(d0 * d0 + d1 * d1 + d2 * d2) / kC;
+#pragma unroll 1
+        for (int it = 0; it < 4; ++it) {
+            d0 = Rr[0] - (Rs[0] - T * Vs[0] + 0.5 * T * T * As[0]);
+            d1 = Rr[1] - (Rs[1] - T * Vs[1] + 0.5 * T * T * As[1]);
+            d2 = Rr[2] - (Rs[2] - T * Vs[2] + 0.5 * T * T * As[2]);
+            T = sqrt(d0 * d0 + d1 * d1 + d2 * d2) / kC;
+        }
+    }
+    *T_out = T;
+    double d[3];
+    for (int c = 0; c < 3; ++c) d[c] = Rr[c] - (Rs[c] - T * Vs[c] + 0.5 * T * T * As[c]);
+    const double nrm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int c = 0; c < 3; ++c) n_out[c] = d[c] / nrm;
+}
+
+// Geometry at time t: R_s (9), T_l (6), n_l (18).
 __device__ void geometry_exact(const OrbitDev& o, double t, double* q)
 {
     double R[3][3], V[3][3], A[3][3];
@@ -175,89 +210,87 @@ __device__ void geometry_exact(const OrbitDev& o, double t, double* q)
 #pragma unroll 1
     for (int li = 0; li < 6; ++li) {
         const int s = link_sender(li), r = link_receiver(li);
-        double T;
-        if (o.delay == LISA_DELAY_EQUAL) {
-            T = o.L / kC;
-        } else if (o.delay == LISA_DELAY_LINEAR) {
-            T = o.T0[li] + o.Tdot[li] * (t - o.t_ref);
-        } else if (o.delay == LISA_DELAY_ANALYTIC) {
-            const double sg = (li & 1) ? -1.0 : 1.0;
-            const double L = o.L, e = o.e, W = o.omega;
-            const double Lt = L + (1.0 / 32.0) * e * L * o.flex * sin(3.0 * W * t - 3.0 * o.xi0)
-                            + ((kAU * W * L / kC) * sg - (15.0 / 32.0) * e * L * o.flex) * sin(W * t - o.delta[li >> 1]);
-            T = Lt / kC;
-        } else {
-            double d0 = R[r][0] - R[s][0], d1 = R[r][1] - R[s][1], d2 = R[r][2] - R[s][2];
-            T = sqrt(d0 * d0 + d1 * d1 + d2 * d2) / kC;
-#pragma unroll 1
-            for (int it = 0; it < 4; ++it) {
-                d0 = R[r][0] - (R[s][0] - T * V[s][0] + 0.5 * T * T * A[s][0]);
-                d1 = R[r][1] - (R[s][1] - T * V[s][1] + 0.5 * T * T * A[s][1]);
-                d2 = R[r][2] - (R[s][2] - T * V[s][2] + 0.5 * T * T * A[s][2]);
-                T = sqrt(d0 * d0 + d1 * d1 + d2 * d2) / kC;
-            }
-        }
-        q[kQT + li] = T;
-        double d[3];
-        for (int c = 0; c < 3; ++c) d[c] = R[r][c] - (R[s][c] - T * V[s][c] + 0.5 * T * T * A[s][c]);
-        const double nrm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        for (int c = 0; c < 3; ++c) q[kQN + 3 * li + c] = d[c] / nrm;
+        link_geometry(o, li, t, R[r], R[s], V[s], A[s], &q[kQT + li], &q[kQN + 3 * li]);
     }
 }
 
-// ---------------------------------------------------------------------------
-// segment table: 16 segments per block, one thread per (segment, node)
-// ---------------------------------------------------------------------------
-constexpr int kSegPerBlock = 16;
-
-__global__ void __launch_bounds__(kSegPerBlock * kNodes)
-seg_table_kernel(OrbitDev o, double t0, double dt, int S, int64_t nseg, double* __restrict__ coef)
+// Chebyshev fit of one quantity from its values at the 7 first-kind nodes,
+// stored as degree-6 monomial coefficients in x in [-1, 1].
+__device__ void cheb_fit_store(const double* v, double* dst)
 {
-    __shared__ double vals[kSegPerBlock][kNQ][kNodes];
-    const int local = threadIdx.x / kNodes, node = threadIdx.x % kNodes;
-    const int64_t s = (int64_t)blockIdx.x * kSegPerBlock + local;
-    if (s < nseg) {
+    double c[kNodes];
+    for (int j = 0; j < kNodes; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < kNodes; ++k) acc += v[k] * cospi(j * (k + 0.5) / kNodes);
+        c[j] = (2.0 / kNodes) * acc;
+    }
+    c[0] *= 0.5;
+    dst[0] = c[0] - c[2] + c[4] - c[6];
+    dst[1] = c[1] - 3.0 * c[3] + 5.0 * c[5];
+    dst[2] = 2.0 * c[2] - 8.0 * c[4] + 18.0 * c[6];
+    dst[3] = 4.0 * c[3] - 20.0 * c[5];
+    dst[4] = 8.0 * c[4] - 48.0 * c[6];
+    dst[5] = 16.0 * c[5];
+    dst[6] = 32.0 * c[6];
+    dst[7] = 0.0;
+}
+
+// One segment per block of 64 threads: spacecraft states at the 7 nodes (21
+// threads), light times and link vectors (42 threads), then the 33 fits.
+// Returns after writing coef[0 .. kNQ*kNC) of this segment.
+__device__ void seg_fit_block(const OrbitDev& o, double t0, double dt, int S, int64_t s, double* coef)
+{
+    __shared__ double st[kNodes][3][9];       // R, V, A per node and spacecraft
+    __shared__ double vals[kNQ][kNodes];
+    const int t = threadIdx.x;
+    auto node_time = [&](int node) {
         const double xk = cospi((node + 0.5) / kNodes);
-        const double qpos = (double)(s * S) + 0.5 * S + xk * (0.5 * S);
-        const double t = t0 + qpos * dt;
-        double g[kNQ];
-        geometry_exact(o, t, g);
-        for (int qq = 0; qq < kNQ; ++qq) vals[local][qq][node] = g[qq];
+        return t0 + ((double)(s * S) + 0.5 * S + xk * (0.5 * S)) * dt;
+    };
+    if (t < 3 * kNodes) {
+        const int node = t / 3, sc = t % 3;
+        double R[3], V[3], A[3];
+        sc_state(o, sc, node_time(node), R, V, A);
+        for (int c = 0; c < 3; ++c) {
+            st[node][sc][c] = R[c];
+            st[node][sc][3 + c] = V[c];
+            st[node][sc][6 + c] = A[c];
+            vals[kQR + 3 * sc + c][node] = R[c];
+        }
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < kSegPerBlock * kNQ; w += blockDim.x) {
-        const int loc = w / kNQ, qq = w % kNQ;
-        const int64_t seg = (int64_t)blockIdx.x * kSegPerBlock + loc;
-        if (seg >= nseg) continue;
-        // Chebyshev coefficients from values at the first-kind nodes
-        double c[kNodes];
-        for (int j = 0; j < kNodes; ++j) {
-            double acc = 0.0;
-            for (int k = 0; k < kNodes; ++k) acc += vals[loc][qq][k] * cospi(j * (k + 0.5) / kNodes);
-            c[j] = (2.0 / kNodes) * acc;
-        }
-        c[0] *= 0.5;
-        // T_0..T_6 in the monomial basis
-        double a[kNC];
-        a[0] = c[0] - c[2] + c[4] - c[6];
-        a[1] = c[1] - 3.0 * c[3] + 5.0 * c[5];
-        a[2] = 2.0 * c[2] - 8.0 * c[4] + 18.0 * c[6];
-        a[3] = 4.0 * c[3] - 20.0 * c[5];
-        a[4] = 8.0 * c[4] - 48.0 * c[6];
-        a[5] = 16.0 * c[5];
-        a[6] = 32.0 * c[6];
-        a[7] = 0.0;
-        double* dst = coef + (seg * kNQ + qq) * kNC;
-        for (int p = 0; p < kNC; ++p) dst[p] = a[p];
+    if (t < 6 * kNodes) {
+        const int node = t / 6, li = t % 6;
+        const int sd = link_sender(li), rc = link_receiver(li);
+        double T, n[3];
+        link_geometry(o, li, node_time(node), &st[node][rc][0], &st[node][sd][0], &st[node][sd][3], &st[node][sd][6],
+                      &T, n);
+        vals[kQT + li][node] = T;
+        for (int c = 0; c < 3; ++c) vals[kQN + 3 * li + c][node] = n[c];
     }
+    __syncthreads();
+    if (t < kNQ) cheb_fit_store(vals[t], coef + (int64_t)t * kNC);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// segment table: one block (64 threads) per segment
+// ---------------------------------------------------------------------------
+constexpr int kSegThreads = 64;
+
+__global__ void __launch_bounds__(kSegThreads)
+seg_table_kernel(OrbitDev o, double t0, double dt, int S, int64_t nseg, double* __restrict__ coef)
+{
+    const int64_t s = blockIdx.x;
+    if (s >= nseg) return;
+    seg_fit_block(o, t0, dt, S, s, coef + s * kNQ * kNC);
 }
 
 int build_seg_table(const OrbitDev& orb, const lisa_grid& g, int S, double* coef_dev, int64_t nseg, cudaStream_t st)
 {
     if (nseg <= 0) return LISA_OK;
-    const int64_t blocks = (nseg + kSegPerBlock - 1) / kSegPerBlock;
     prof_before("seg_table", st);
-    seg_table_kernel<<<(unsigned)blocks, kSegPerBlock * kNodes, 0, st>>>(orb, g.t0, g.dt, S, nseg, coef_dev);
+    seg_table_kernel<<<(unsigned)nseg, kSegThreads, 0, st>>>(orb, g.t0, g.dt, S, nseg, coef_dev);
     prof_after(st);
     return cuda_status(cudaGetLastError(), "seg_table_kernel launch");
 }
@@ -265,66 +298,27 @@ int build_seg_table(const OrbitDev& orb, const lisa_grid& g, int S, double* coef
 // ---------------------------------------------------------------------------
 // batched segment tables: every segment of every source in one launch
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSegPerBlock * kNodes)
+__global__ void __launch_bounds__(kSegThreads)
 seg_table_batched_kernel(OrbitDev o, const SegSource* __restrict__ srcs, int nsrc, int64_t total,
                          double* __restrict__ coef)
 {
-    __shared__ double vals[kSegPerBlock][kNQ][kNodes];
-    __shared__ int s_src[kSegPerBlock];
-    const int local = threadIdx.x / kNodes, node = threadIdx.x % kNodes;
-    const int64_t gseg = (int64_t)blockIdx.x * kSegPerBlock + local;
-    if (threadIdx.x < kSegPerBlock) {
-        const int64_t gs = (int64_t)blockIdx.x * kSegPerBlock + threadIdx.x;
-        int lo = 0, hi = nsrc - 1;
-        while (lo < hi) {  // last source whose first segment is <= gs
-            const int mid = (lo + hi + 1) >> 1;
-            if (srcs[mid].seg_begin <= gs) lo = mid; else hi = mid - 1;
-        }
-        s_src[threadIdx.x] = lo;
+    const int64_t gs = blockIdx.x;
+    if (gs >= total) return;
+    int lo = 0, hi = nsrc - 1;
+    while (lo < hi) {  // last source whose first segment is <= gs
+        const int mid = (lo + hi + 1) >> 1;
+        if (srcs[mid].seg_begin <= gs) lo = mid; else hi = mid - 1;
     }
-    __syncthreads();
-    if (gseg < total) {
-        const SegSource& src = srcs[s_src[local]];
-        const int64_t s = gseg - src.seg_begin;
-        const double xk = cospi((node + 0.5) / kNodes);
-        const double qpos = (double)(s * src.S) + 0.5 * src.S + xk * (0.5 * src.S);
-        const double t = src.t0 + qpos * src.dt;
-        double g[kNQ];
-        geometry_exact(o, t, g);
-        for (int qq = 0; qq < kNQ; ++qq) vals[local][qq][node] = g[qq];
-    }
-    __syncthreads();
-    for (int w = threadIdx.x; w < kSegPerBlock * kNQ; w += blockDim.x) {
-        const int loc = w / kNQ, qq = w % kNQ;
-        const int64_t seg = (int64_t)blockIdx.x * kSegPerBlock + loc;
-        if (seg >= total) continue;
-        double c[kNodes];
-        for (int j = 0; j < kNodes; ++j) {
-            double acc = 0.0;
-            for (int k = 0; k < kNodes; ++k) acc += vals[loc][qq][k] * cospi(j * (k + 0.5) / kNodes);
-            c[j] = (2.0 / kNodes) * acc;
-        }
-        c[0] *= 0.5;
-        double* dst = coef + (seg * kNQ + qq) * kNC;
-        dst[0] = c[0] - c[2] + c[4] - c[6];
-        dst[1] = c[1] - 3.0 * c[3] + 5.0 * c[5];
-        dst[2] = 2.0 * c[2] - 8.0 * c[4] + 18.0 * c[6];
-        dst[3] = 4.0 * c[3] - 20.0 * c[5];
-        dst[4] = 8.0 * c[4] - 48.0 * c[6];
-        dst[5] = 16.0 * c[5];
-        dst[6] = 32.0 * c[6];
-        dst[7] = 0.0;
-    }
+    const SegSource& src = srcs[lo];
+    seg_fit_block(o, src.t0, src.dt, src.S, gs - src.seg_begin, coef + gs * kNQ * kNC);
 }
 
 int build_seg_tables_batched(const OrbitDev& orb, const SegSource* srcs_dev, int nsrc, int64_t total_segs,
                              double* coef_dev, cudaStream_t st)
 {
     if (total_segs <= 0) return LISA_OK;
-    const int64_t blocks = (total_segs + kSegPerBlock - 1) / kSegPerBlock;
     prof_before("seg_table_batched", st);
-    seg_table_batched_kernel<<<(unsigned)blocks, kSegPerBlock * kNodes, 0, st>>>(orb, srcs_dev, nsrc, total_segs,
-                                                                                coef_dev);
+    seg_table_batched_kernel<<<(unsigned)total_segs, kSegThreads, 0, st>>>(orb, srcs_dev, nsrc, total_segs, coef_dev);
     prof_after(st);
     return cuda_status(cudaGetLastError(), "seg_table_batched_kernel launch");
 }

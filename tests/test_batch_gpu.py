@@ -1,0 +1,101 @@
+"""Batched hybrid plan (one persistent launch over many sources) against the
+per-source hybrid call and the oracle; graph replay and autotuned launch
+shapes give the same outputs."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import host_inputs, orbit_pair, rel_err, sky_of, to_dev
+from tolerances import MIXED_TOL
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_09600_gb300 import build
+    build.build()
+    import paper_2505_09600_gb300 as L
+    L.load()
+    return L
+
+
+@pytest.fixture(scope="module")
+def batch(L):
+    params = synth.batch_params(nsrc=14, seed=synth.SEED_BASE + 33)
+    srcs, descs = [], []
+    for k, p in enumerate(params):
+        p = dict(p, dur=(0.25 + 0.3 * k) * synth.DAY)      # short, uneven durations
+        s = synth.batch_source(p)
+        hp, hc = host_inputs(s, 1)
+        tH = L.lisa_t_hyb_from_f(1e-3, s.mc_s, s.tc)
+        out = torch.full((3, s.n), float("nan"), device="cuda")
+        descs.append(dict(grid=s.grid, hp=to_dev(hp, 1), hc=to_dev(hc, 1), sky=sky_of(s), t_hyb=tH, out=out))
+        srcs.append((s, hp, hc, tH))
+    return srcs, descs
+
+
+def _per_source(L, lo, d):
+    out = torch.empty_like(d["out"])
+    L.lisa_response_hybrid(lo, d["sky"], d["grid"], d["hp"], d["hc"], L.MIXED, 20, 0, L.AET, d["t_hyb"], 0.0, 0.0,
+                           d["grid"], out)
+    return out.cpu().numpy().astype(np.float64)
+
+
+def test_batch_matches_single_calls_and_oracle(L, oracle_mod, batch):
+    srcs, descs = batch
+    oo, lo = orbit_pair("kepler2_flex")
+    plan = L.LisaPlan(lo, descs)
+    plan.execute()
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert info["total_samples"] == sum(s.n for s, *_ in srcs)
+    regimes = set()
+    for k, (d, (s, hp, hc, tH)) in enumerate(zip(descs, srcs)):
+        got = d["out"].cpu().numpy().astype(np.float64)
+        assert np.isfinite(got).all(), k
+        ref = _per_source(L, lo, d)
+        # same arithmetic per sample; only AET-before/after-blend rounding differs
+        assert rel_err(got, ref, signal=True).max() < 2e-6, k
+        t_end = s.t0 + s.n * s.dt
+        regimes.add("full" if tH < s.t0 else "lfa" if tH > t_end else "mixed")
+        if k in (0, 5, 13):
+            want = oracle_mod.response_hybrid(oo, sky_of(s), s.grid, hp, hc, 20, 0, "aet", tH, 800 * s.dt,
+                                              20 * s.dt)
+            tol = np.array(MIXED_TOL["hybrid20"]["aet"])
+            assert np.all(rel_err(got, want, signal=True) <= tol), (k, rel_err(got, want, signal=True))
+    assert len(regimes) >= 2, regimes
+    plan.close()
+
+
+def test_batch_graph_replay_and_autotune(L, batch):
+    srcs, descs = batch
+    _, lo = orbit_pair("kepler2_flex")
+    plan = L.LisaPlan(lo, descs)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        plan.execute(stream=st.cuda_stream)
+    st.synchronize()
+    first = [d["out"].clone() for d in descs]
+    for d in descs:
+        d["out"].fill_(float("nan"))
+    torch.cuda.synchronize()
+    plan.capture_graph(st.cuda_stream)
+    for _ in range(2):
+        plan.replay(stream=st.cuda_stream)
+    st.synchronize()
+    for a, d in zip(first, descs):
+        assert torch.equal(a, d["out"])
+    best = plan.autotune(stream=st.cuda_stream)
+    assert best["ctas_per_sm"] >= 1 and best["tiles_per_item"] >= 1 and best["ms"] > 0
+    for d in descs:
+        d["out"].fill_(float("nan"))
+    torch.cuda.synchronize()
+    plan.execute(stream=st.cuda_stream)
+    st.synchronize()
+    for a, d in zip(first, descs):
+        assert torch.equal(a, d["out"])
+    plan.close()
