@@ -137,6 +137,15 @@ int lisa_links_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_gri
                    const void* hp, const void* hc, int precision, int tdi_gen, int lfa_kind,
                    lisa_grid out, void* z, void* stream);
 
+/* The LFA single links at their own reception time t (Sec. III, the LFA
+ * link formula applied to each of the six links:
+ * y_l(t) = -(T_l/2) [xi+_l hdot+ + xix_l hdotx](tau_l),
+ * tau_l = t - T_l/2 - k.(R_s + R_r)/(2c), hdot from the 5-point central
+ * stencil of h; the paper's LFA channels need only l = +1, +2, +3).
+ * y: device [6][out.n] in link order.  lfa_kind EQUAL uses L/c for T_l. */
+int lisa_links_lfa_own(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid, const void* hp, const void* hc,
+                       int precision, int lfa_kind, lisa_grid out, void* y, void* stream);
+
 /* a10. LFA Michelson variables from z (same passages):
  *   1.5: X = 4 [T_a dz_a/dt - T_b dz_b/dt],
  *   2.0: X = 8 (T_a + T_b) [T_a d2z_a/dt2 - T_b d2z_b/dt2],
@@ -231,6 +240,88 @@ int lisa_plan_set_launch(lisa_plan* plan, int ctas_per_sm, int tiles_per_item);
 int lisa_plan_autotune(lisa_plan* plan, void* stream, lisa_tune_result* best);
 int lisa_plan_info(const lisa_plan* plan, int64_t* total_samples, int64_t* total_tiles, int* ctas_per_sm,
                    int* tiles_per_item);
+
+/* ------------------------------------------------------------------------
+ * Learned corrector of the LFA links (no counterpart in the paper).
+ *
+ * An MLP 46 -> 64 -> 64 -> 64 -> 6 (GELU, tanh form; BF16 weights and
+ * activations on the tensor cores, FP32 accumulation and FP32 master weights)
+ * predicts the residuals between the six full single links (Sec. II) and the
+ * base links z_l (1 + eps_l) at each output sample, where z_l are the LFA
+ * links at their own time (lisa_links_lfa_own) and
+ * eps_l = k.v_s / (c (1 - k.n_l)) is the O(v/c) term by which the full
+ * formula (positions at the reception time) differs from T_l (1 - k.n_l)
+ * (v_s: sender velocity).  Features per sample (46, stored as rows of 48
+ * floats, the last two zero):
+ *   [ 0,30) q_k,l / M_k: the 5-point stencil of z_l re-based as
+ *           q_k = Tbar^k d^k z_l/dt^k, k = 0..4 (feature k*6 + l),
+ *           M_k = max_l |q_k,l|;
+ *   [30,34) clamp(log10(M_{k+1}/M_k), -8, 8) / 4;
+ *   [34,40) (T_l/Tbar - 1) * 100;   [40,46) 1 - k.n_l;   Tbar = L/c.
+ * Scale s = M_2 / 8; corrected link l = z_l (1 + eps_l) + s * MLP_l.  Local
+ * frequency f = sqrt(M_2/M_0) / (2 pi Tbar): below the band [f_lo, f_hi] the
+ * base link is used (s = 0), above it the full link (per 256-sample tile).
+ * Parameters: a flat FP32 vector, per layer W [n_out][n_in] row-major then b.
+ * ---------------------------------------------------------------------- */
+typedef struct lisa_corrector lisa_corrector;
+
+int64_t lisa_corrector_num_params(void);     /* 11718 */
+int lisa_corrector_num_features(void);       /* 46 */
+/* Create on the current device (cudaMalloc of its parameters, Adam state and
+ * counters; synchronising).  host_params: n_params FP32 values, or NULL for
+ * W ~ U(-1/sqrt(n_in), 1/sqrt(n_in)) drawn from SplitMix64(seed), b = 0.
+ * Defaults: band [1e-4, 2e-2] Hz, a spot check every 64th tile, tolerance 0.05. */
+int lisa_corrector_create(lisa_corrector** c, const float* host_params, int64_t n_params, uint64_t seed);
+int lisa_corrector_destroy(lisa_corrector* c);
+/* Trained band (Hz), spot-check period in tiles (0 = none) and tolerance
+ * (max |full - corrected| / max |full| over a tile). */
+int lisa_corrector_configure(lisa_corrector* c, double f_lo, double f_hi, int spot_every, double spot_tol);
+/* Checkpoint/resume: parameters, Adam moments and step count (host buffers of
+ * n_params floats; any pointer may be NULL).  Synchronising. */
+int lisa_corrector_get_state(const lisa_corrector* c, float* params, float* adam_m, float* adam_v, int64_t* step,
+                             int64_t n_params);
+int lisa_corrector_set_state(lisa_corrector* c, const float* params, const float* adam_m, const float* adam_v,
+                             int64_t step, int64_t n_params);
+/* Features, scale, base links and training targets on grid g from the LFA
+ * links z (FP32, [6][g.n], lisa_links_lfa_own with LISA_MIXED).
+ * feats: [g.n][48] (16-byte aligned), scale: [g.n], ybase ([6][g.n] or
+ * NULL): z_l (1 + eps_l).  If target ([g.n][6]) is given, y_full ([6][g.n]
+ * FP64 full links, required) and z_ref ([6][g.n] FP64 LFA links; NULL = z)
+ * give target_l = (y_full_l - z_ref_l (1 + eps_l)) / s (0 where s = 0).
+ * f_lo/f_hi: band for s (pass 0 and INFINITY for no band). */
+int lisa_corrector_features(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid g, const float* z,
+                            const double* y_full, const double* z_ref, double f_lo, double f_hi, float* feats,
+                            float* scale, float* ybase, float* target, void* stream);
+/* out[r][6] = MLP(feats[r]) for r < M. */
+int lisa_corrector_forward(const lisa_corrector* c, const float* feats, int64_t M, float* out, void* stream);
+/* grad (device, n_params floats, overwritten) and loss (device float or
+ * NULL) of L = mean_r sum_l (MLP(x_r)_l - target_r,l)^2 over either all
+ * n_data rows (batch = 0) or `batch` rows drawn as SplitMix64(seed + r) mod n_data. */
+int lisa_corrector_gradient(lisa_corrector* c, const float* feats, const float* target, int64_t n_data,
+                            int64_t batch, uint64_t seed, float* grad, float* loss, void* stream);
+/* One Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected) with rate lr. */
+int lisa_corrector_adam_step(lisa_corrector* c, const float* grad, float lr, void* stream);
+/* `steps` minibatch Adam steps, rate cosine-decayed from lr_max to lr_min;
+ * losses (device, `steps` floats, or NULL) receives each step's loss. */
+int lisa_corrector_train(lisa_corrector* c, const float* feats, const float* target, int64_t n_data, int64_t steps,
+                         int64_t batch, float lr_max, float lr_min, uint64_t seed, float* losses, void* stream);
+/* Corrected links (FP32, [6][out.n]) on every sample of `out`: LFA links,
+ * features, network, then full links on tiles above the band and on the
+ * spot-checked tiles; if a spot check fails, on every tile (decided on the
+ * device).  hp/hc are FP32 (LISA_MIXED). */
+int lisa_corrector_links(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                         const void* hp, const void* hc, lisa_grid out, void* y, void* stream);
+/* Hybrid with the corrector (LISA_MIXED, frozen TDI): as lisa_response_hybrid,
+ * but the LFA side is the full TDI combine of the corrected links. */
+int lisa_response_hybrid_corrected(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                                   const void* hp, const void* hc, int tdi_gen, int channels, double t_hyb,
+                                   double T_win, double sigma, lisa_grid out, void* xyz, void* stream);
+/* Counters since the last reset (synchronises the device): spot-checked
+ * tiles, failed spot checks, tiles above the band, tiles recomputed after a
+ * failure, largest spot-check error.  Returns LISA_ECORRECTOR if any spot
+ * check failed (the outputs were still computed from full links there). */
+int lisa_corrector_report(lisa_corrector* c, int64_t* spot_tiles, int64_t* spot_failed, int64_t* band_tiles,
+                          int64_t* fallback_tiles, float* max_spot_err, int reset);
 
 /* Instrumentation (no counterpart in the paper).
  * lisa_profile_enable(1) clears the record and makes every kernel launch of

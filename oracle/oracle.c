@@ -632,9 +632,10 @@ void og_tdi_lfa_direct(const og_orbit* o, const og_sky* sky, og_grid gh, const d
     }
 }
 
-/* LFA links at their own time t (no TDI shift): y_+1, y_+2, y_+3 from
- * Eq. yslr_strain_derivatives; the reversed links are set to zero
- * (Sec. IV: only three links are computed in the LFA). */
+/* LFA links at their own time t (no TDI shift) from the LFA link formula
+ * (Sec. III, Eq. yslr_strain_derivatives) applied to each of the six links
+ * with its own T_l, n_l and end positions.  (The paper's LFA channels only
+ * need y_+1, y_+2, y_+3; the formula itself holds for every link.) */
 void og_links_lfa_own(const og_orbit* o, const og_sky* sky, og_grid gh, const double* hdp, const double* hdc,
                       int kind, og_grid gy, double* y, const int64_t* idx, int64_t nidx)
 {
@@ -645,7 +646,7 @@ void og_links_lfa_own(const og_orbit* o, const og_sky* sky, og_grid gh, const do
     for (int64_t q = 0; q < m; ++q) {
         const int64_t i = idx ? idx[q] : q;
         for (int li = 0; li < 6; ++li)
-            y[li * m + q] = (li % 2 == 0) ? og_link_lfa_at(&S, gy, i, 0.0, li, kind) : 0.0;
+            y[li * m + q] = og_link_lfa_at(&S, gy, i, 0.0, li, kind);
     }
 }
 

@@ -6,10 +6,10 @@ The Python side only marshals arguments (``native``); build the library with
 ``paper_2505_09600_gb300.build.build()``.
 """
 from .native import *  # noqa: F401,F403
-from .native import Orbit, LisaError, LisaPlan, load, exported_symbols  # noqa: F401
+from .native import Orbit, LisaError, LisaPlan, LisaCorrector, load, exported_symbols  # noqa: F401
 
 __all__ = [n for n in dir() if n.startswith("lisa_")] + [
-    "Orbit", "LisaError", "LisaPlan", "load", "exported_symbols",
+    "Orbit", "LisaError", "LisaPlan", "LisaCorrector", "load", "exported_symbols",
     "ORB_KEPLER1", "ORB_KEPLER2", "ORB_STATIC", "DELAY_LIGHTTIME", "DELAY_ANALYTIC", "DELAY_EQUAL",
     "DELAY_LINEAR", "F64", "MIXED", "TDI15", "TDI20", "XYZ", "AET", "FROZEN", "NESTED", "LFA_UNEQUAL",
     "LFA_EQUAL"]

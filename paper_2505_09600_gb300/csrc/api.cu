@@ -56,7 +56,7 @@ void* Scratch::alloc(size_t bytes)
 // ---------------------------------------------------------------------------
 // validation
 // ---------------------------------------------------------------------------
-static int check_grid(const lisa_grid& g, const char* name)
+int check_grid(const lisa_grid& g, const char* name)
 {
     if (!(g.dt > 0.0) || !isfinite(g.dt) || !isfinite(g.t0) || g.n < 0) {
         set_error("%s: need dt > 0, finite t0 and n >= 0 (t0=%g dt=%g n=%lld)", name, g.t0, g.dt, (long long)g.n);
@@ -69,7 +69,7 @@ static int check_grid(const lisa_grid& g, const char* name)
     return LISA_OK;
 }
 
-static int check_orbit(const lisa_orbit* o)
+int check_orbit(const lisa_orbit* o)
 {
     if (!o) { set_error("orbit is NULL"); return LISA_EINVAL; }
     if (o->kind < LISA_ORB_KEPLER1 || o->kind > LISA_ORB_STATIC) { set_error("orbit kind %d unknown", o->kind); return LISA_EINVAL; }
@@ -82,7 +82,7 @@ static int check_orbit(const lisa_orbit* o)
     return LISA_OK;
 }
 
-static int check_common(int precision, int gen, int channels)
+int check_common(int precision, int gen, int channels)
 {
     if (precision != LISA_F64 && precision != LISA_MIXED) { set_error("precision %d unknown", precision); return LISA_EINVAL; }
     if (gen != LISA_TDI15 && gen != LISA_TDI20) { set_error("tdi_gen must be 15 or 20 (got %d)", gen); return LISA_EINVAL; }
@@ -90,16 +90,10 @@ static int check_common(int precision, int gen, int channels)
     return LISA_OK;
 }
 
-#define LISA_TRY(x)                  \
-    do {                             \
-        int _rc = (x);               \
-        if (_rc != LISA_OK) return _rc; \
-    } while (0)
-
-static size_t real_size(int precision) { return precision == LISA_MIXED ? sizeof(float) : sizeof(double); }
+size_t real_size(int precision) { return precision == LISA_MIXED ? sizeof(float) : sizeof(double); }
 
 // Orbit polynomial table on grid g, in scratch.
-static int make_table(const lisa_orbit* orbit, const lisa_grid& g, Scratch& sc, SegTable& tab, cudaStream_t st)
+int make_table(const lisa_orbit* orbit, const lisa_grid& g, Scratch& sc, SegTable& tab, cudaStream_t st)
 {
     const int S = seg_samples(g.dt);
     const int64_t nseg = seg_count(g.n > 0 ? g.n : 1, S);
@@ -111,7 +105,7 @@ static int make_table(const lisa_orbit* orbit, const lisa_grid& g, Scratch& sc, 
 }
 
 // Upper bound of any single light time (for halo sizing).
-static double max_light_time(const lisa_orbit* o, const lisa_grid& g)
+double max_light_time(const lisa_orbit* o, const lisa_grid& g)
 {
     if (o->delay == LISA_DELAY_LINEAR) {
         const double span = fmax(fabs(g.t0 - o->t_ref), fabs(g.t0 + g.n * g.dt - o->t_ref)) + 1e3;
@@ -121,6 +115,25 @@ static double max_light_time(const lisa_orbit* o, const lisa_grid& g)
     }
     double flex = 1.0 + 3.0 * fmax(fabs(o->kepler_tilt - 1.0), 0.0) * 60.0 + 0.05 * fabs(o->flex_scale);
     return 1.5 * flex * o->L_m / kC;
+}
+
+// LFA samples: t_i <= t_hyb + Tw/2 -> [0, iL]; full samples: t_i >= t_hyb - Tw/2
+// -> [iF, n) (the same FP64 comparisons as the definition).
+void hybrid_split(const lisa_grid& out, double t_hyb, double Tw, int64_t& iL_out, int64_t& iF_out)
+{
+    const int64_t n = out.n;
+    volatile double hi_thr = t_hyb + 0.5 * Tw, lo_thr = t_hyb - 0.5 * Tw;
+    auto t_at = [&](int64_t i) { volatile double p = (double)i * out.dt; return out.t0 + p; };
+    int64_t iL = (int64_t)floor((hi_thr - out.t0) / out.dt);
+    iL = iL < -1 ? -1 : (iL > n - 1 ? n - 1 : iL);
+    while (iL + 1 <= n - 1 && t_at(iL + 1) <= hi_thr) ++iL;
+    while (iL >= 0 && !(t_at(iL) <= hi_thr)) --iL;
+    int64_t iF = (int64_t)ceil((lo_thr - out.t0) / out.dt);
+    iF = iF < 0 ? 0 : (iF > n ? n : iF);
+    while (iF - 1 >= 0 && t_at(iF - 1) >= lo_thr) --iF;
+    while (iF < n && !(t_at(iF) >= lo_thr)) ++iF;
+    iL_out = iL;
+    iF_out = iF;
 }
 
 }  // namespace lisa
@@ -236,6 +249,26 @@ int lisa_links_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_gri
                       z, nullptr, 0, out.n, bl, st);
 }
 
+int lisa_links_lfa_own(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid, const void* hp, const void* hc,
+                       int precision, int lfa_kind, lisa_grid out, void* y, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(h_grid, "h_grid"));
+    LISA_TRY(check_grid(out, "out"));
+    LISA_TRY(check_common(precision, LISA_TDI15, LISA_XYZ));
+    if (lfa_kind != LISA_LFA_UNEQUAL && lfa_kind != LISA_LFA_EQUAL) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
+    if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
+    if (out.n == 0) return LISA_OK;
+    if (!y || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, out, sc, tab, st));
+    BlendSpec bl{};
+    return launch_lfa(tab, make_sky_dev(*sky), orbit->L_m, h_grid, hp, hc, precision, kLfaOwnTime, lfa_kind, LISA_XYZ,
+                      out, y, nullptr, 0, out.n, bl, st);
+}
+
 int lisa_tdi_lfa(const lisa_orbit* orbit, lisa_grid z_grid, const void* z, int precision, int tdi_gen, int lfa_kind,
                  int channels, void* xyz, void* stream)
 {
@@ -288,18 +321,8 @@ int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid
     const double Tw = T_win > 0.0 ? T_win : 800.0 * out.dt;
     const double sg = sigma > 0.0 ? sigma : Tw / 40.0;
     const int64_t n = out.n;
-    // LFA samples: t_i <= t_hyb + Tw/2; full samples: t_i >= t_hyb - Tw/2
-    // (the same FP64 comparisons as the definition).
-    volatile double hi_thr = t_hyb + 0.5 * Tw, lo_thr = t_hyb - 0.5 * Tw;
-    auto t_at = [&](int64_t i) { volatile double p = (double)i * out.dt; return out.t0 + p; };
-    int64_t iL = (int64_t)floor((hi_thr - out.t0) / out.dt);
-    iL = iL < -1 ? -1 : (iL > n - 1 ? n - 1 : iL);
-    while (iL + 1 <= n - 1 && t_at(iL + 1) <= hi_thr) ++iL;
-    while (iL >= 0 && !(t_at(iL) <= hi_thr)) --iL;
-    int64_t iF = (int64_t)ceil((lo_thr - out.t0) / out.dt);
-    iF = iF < 0 ? 0 : (iF > n ? n : iF);
-    while (iF - 1 >= 0 && t_at(iF - 1) >= lo_thr) --iF;
-    while (iF < n && !(t_at(iF) >= lo_thr)) ++iF;
+    int64_t iL, iF;
+    hybrid_split(out, t_hyb, Tw, iL, iF);
 
     cudaStream_t st = (cudaStream_t)stream;
     Scratch sc(st);

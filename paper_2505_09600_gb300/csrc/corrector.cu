@@ -1,0 +1,1077 @@
+// Learned corrector of the LFA links (an addition to the paper's method: the
+// paper has no learned component).
+//
+// The LFA link z_l at its own reception time (the LFA link formula of
+// Sec. III applied to each of the six links) differs from the full link y_l
+// (Sec. II, positions taken at the reception time t) by
+//   y_l - z_l = eps_l z_l + (1 - k.n_l)^2/24 * T_l^2 d^2 z_l/dt^2 + ...,
+//   eps_l = k.(R_s(t) - R_s(t - T_l)) / (c T_l (1 - k.n_l)) ~ k.v_s / (c (1 - k.n_l)):
+// the full formula's delta_s - delta_r equals T_l (1 - k.n_l) only up to the
+// sender's motion over T_l, a frequency-independent O(v/c) term that is
+// applied analytically (base link z_l (1 + eps_l), v_s from the derivative of
+// the orbit polynomial).  A multilayer perceptron 46 -> 64 -> 64 -> 64 -> 6
+// (GELU, tanh form) predicts the rest at each output sample from:
+//   [ 0,30) the 5-point stencils of z_l re-based as q_k = Tbar^k d^k z/dt^k
+//           (k = 0..4; feature k*6 + l), each order divided by
+//           M_k = max_l |q_k,l|;
+//   [30,34) log10(M_{k+1}/M_k) / 4, clamped to [-2, 2] (a local frequency);
+//   [34,40) (T_l/Tbar - 1) * 100 (arm flexing);
+//   [40,46) 1 - k.n_l;
+// with Tbar = L/c.  Inputs and outputs are O(1) in BF16: the network output is
+// scaled by s = M_2 / 8, so that the corrected link is
+// z_l (1 + eps_l) + s * MLP_l.  The full TDI combine then runs on the
+// corrected links.
+//
+// Band and checks.  The local frequency f = sqrt(M_2/M_0) / (2 pi Tbar) (exact
+// for a sinusoid) selects, per sample: below the trained band the plain LFA
+// link (no correction: the LFA is already closer than at the band's lower
+// edge); above it the full link (the whole 256-sample tile is recomputed by
+// the full links kernel).  Every spot_every-th tile is also recomputed with
+// full links and compared; if any compared tile differs by more than
+// spot_tol (max abs difference / max abs full link over the tile), every
+// remaining tile is recomputed with full links in the same call (device-side
+// decision, no host synchronisation) and the failure is counted.
+//
+// Kernels (BF16 tensor-core MMA through nvcuda::wmma, FP32 accumulation):
+//   corr_features_kernel  features, scale, band flags, optional targets
+//   mlp_forward_kernel    inference, one warp per 16 rows, all layers fused;
+//                         optional epilogue y = z + s * MLP
+//   mlp_train_kernel      forward + MSE + backward fused; weight gradients are
+//                         accumulated per block in shared memory and added to
+//                         the global FP32 gradient once per block
+//   adam_kernel           Adam on FP32 master weights
+//   publish_kernel        padded BF16 copies of the weights for the MMAs
+//   corr_fallback_kernel  full links on flagged / spot / failed tiles
+#include <cuda_bf16.h>
+#include <math.h>
+#include <mma.h>
+#include <string.h>
+
+#include <new>
+
+#include "lisa_common.cuh"
+#include "lisa_internal.cuh"
+#include "links_tile.cuh"
+#include "tile_geo.cuh"
+
+using namespace nvcuda;
+
+namespace lisa {
+
+constexpr int kIn = 46, kInP = 48, kWid = 64, kOut = 6, kOutP = 16;
+constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + kWid * kIn, kOffW2 = kOffB1 + kWid, kOffB2 = kOffW2 + kWid * kWid,
+                  kOffW3 = kOffB2 + kWid, kOffB3 = kOffW3 + kWid * kWid, kOffW4 = kOffB3 + kWid,
+                  kOffB4 = kOffW4 + kOut * kWid, kNParams = kOffB4 + kOut;
+
+struct MlpDev {
+    const __nv_bfloat16 *W1, *W2, *W3, *W4;   // padded: [64][48], [64][64], [64][64], [16][64]
+    const float *b1, *b2, *b3, *b4;           // padded: 64, 64, 64, 16
+};
+
+struct CorrStats {
+    unsigned spot_tiles, spot_failed, band_tiles, fallback_tiles, call_failed, max_err_bits;
+};
+
+// GELU, tanh form, with the hardware tanh approximation (|rel err| ~ 2^-11,
+// below BF16 resolution).
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float gelu_f(float x)
+{
+    const float c = 0.7978845608028654f;
+    return 0.5f * x * (1.f + tanh_fast(c * fmaf(0.044715f * x, x * x, x)));
+}
+__device__ __forceinline__ float gelu_grad_f(float x)
+{
+    const float c = 0.7978845608028654f;
+    const float t = tanh_fast(c * fmaf(0.044715f * x, x * x, x));
+    return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * c * fmaf(3.f * 0.044715f, x * x, 1.f);
+}
+
+using FragA = wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::row_major>;
+using FragAc = wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::col_major>;
+using FragBc = wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::col_major>;
+using FragBr = wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::row_major>;
+using FragC = wmma::fragment<wmma::accumulator, 16, 16, 16, float>;
+
+// acc[16][ldc] = act[16][K] . W[N][K]^T  (W row-major = B column-major)
+__device__ __forceinline__ void layer_mma(const __nv_bfloat16* act, int lda, const __nv_bfloat16* W, int K, int N,
+                                          float* acc, int ldc)
+{
+    for (int j = 0; j < N / 16; ++j) {
+        FragC c;
+        wmma::fill_fragment(c, 0.f);
+        for (int q = 0; q < K / 16; ++q) {
+            FragA a;
+            FragBc b;
+            wmma::load_matrix_sync(a, act + q * 16, lda);
+            wmma::load_matrix_sync(b, W + (size_t)j * 16 * K + q * 16, K);
+            wmma::mma_sync(c, a, b, c);
+        }
+        wmma::store_matrix_sync(acc + j * 16, c, ldc, wmma::mem_row_major);
+    }
+}
+
+// Load 16 input rows (stride kInP floats) as BF16 into act[16][lda].
+__device__ __forceinline__ void load_rows(const float* __restrict__ x, int64_t r0, int64_t M, __nv_bfloat16* act,
+                                          int lda, int lane)
+{
+    for (int e = lane; e < 16 * (kInP / 4); e += 32) {
+        const int r = e / (kInP / 4), c4 = e % (kInP / 4);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r0 + r < M) v = *reinterpret_cast<const float4*>(x + (r0 + r) * kInP + 4 * c4);
+        __nv_bfloat16* d = act + r * lda + 4 * c4;
+        d[0] = __float2bfloat16(v.x);
+        d[1] = __float2bfloat16(v.y);
+        d[2] = __float2bfloat16(v.z);
+        d[3] = __float2bfloat16(v.w);
+    }
+}
+
+// --------------------------------------------------------------------------
+// inference
+// --------------------------------------------------------------------------
+struct __align__(128) FwdWarp {
+    __nv_bfloat16 act[16][kWid];
+    float acc[16][kWid];
+};
+constexpr int kFwdWarps = 4;
+
+// y = MLP(x) for rows [0, M).  Epilogue: if `links` is set, out[l*n + r] +=
+// scale[r] * y_l (corrections added to the base links, rows = samples);
+// otherwise out[r*kOut + l] = y_l.
+__global__ void __launch_bounds__(32 * kFwdWarps) mlp_forward_kernel(MlpDev m, const float* __restrict__ x, int64_t M,
+                                                                     int links, const float* __restrict__ scale,
+                                                                     int64_t n, float* __restrict__ out)
+{
+    __shared__ FwdWarp wsm[kFwdWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    FwdWarp& W = wsm[warp];
+    const int64_t r0 = ((int64_t)blockIdx.x * kFwdWarps + warp) * 16;
+    if (r0 >= M) return;
+    load_rows(x, r0, M, &W.act[0][0], kWid, lane);
+    __syncwarp();
+    const __nv_bfloat16* Ws[3] = {m.W1, m.W2, m.W3};
+    const float* bs[3] = {m.b1, m.b2, m.b3};
+    for (int l = 0; l < 3; ++l) {
+        layer_mma(&W.act[0][0], kWid, Ws[l], l == 0 ? kInP : kWid, kWid, &W.acc[0][0], kWid);
+        __syncwarp();
+        for (int e = lane; e < 16 * kWid; e += 32) {
+            const int r = e / kWid, c = e % kWid;
+            W.act[r][c] = __float2bfloat16(gelu_f(W.acc[r][c] + bs[l][c]));
+        }
+        __syncwarp();
+    }
+    layer_mma(&W.act[0][0], kWid, m.W4, kWid, kOutP, &W.acc[0][0], kWid);
+    __syncwarp();
+    if (links) {
+        for (int e = lane; e < 16 * kOut; e += 32) {
+            const int l = e / 16, r = e % 16;
+            const int64_t i = r0 + r;
+            if (i < M) out[l * n + i] = fmaf(scale[i], W.acc[r][l] + m.b4[l], out[l * n + i]);
+        }
+    } else {
+        for (int e = lane; e < 16 * kOut; e += 32) {
+            const int r = e / kOut, c = e % kOut;
+            if (r0 + r < M) out[(r0 + r) * kOut + c] = W.acc[r][c] + m.b4[c];
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// training: forward + MSE + backward
+// --------------------------------------------------------------------------
+struct __align__(128) TrainWarp {
+    __nv_bfloat16 a0[16][kInP];         // input (bf16)
+    __nv_bfloat16 a[3][16][kWid];       // hidden activations
+    float z[3][16][kWid];               // hidden pre-activations
+    __nv_bfloat16 dz[16][kWid];         // current dZ (bf16 operand of the MMAs)
+    float tmp[16][kWid];                // accumulator staging
+};
+struct __align__(128) TrainBlock {
+    float gW1[kWid][kInP], gW2[kWid][kWid], gW3[kWid][kWid], gW4[kOutP][kWid];
+    float gb1[kWid], gb2[kWid], gb3[kWid], gb4[kOutP];
+    float loss;
+};
+constexpr int kTrainWarps = 2;
+constexpr size_t kTrainSmem = sizeof(TrainBlock) + kTrainWarps * sizeof(TrainWarp);
+static_assert(sizeof(TrainBlock) % 128 == 0 && sizeof(TrainWarp) % 128 == 0, "WMMA pointers need 32-byte alignment");
+
+// g[N][K] += dz[16][N]^T . act[16][K]  (block accumulator, shared atomics)
+__device__ __forceinline__ void accum_weight_grad(const __nv_bfloat16* dz, int ldz, const __nv_bfloat16* act, int lda,
+                                                  int N, int K, float* g, int ldg, float* tmp)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = 0; i < N / 16; ++i) {
+        for (int j = 0; j < K / 16; ++j) {
+            FragC c;
+            wmma::fill_fragment(c, 0.f);
+            FragAc a;   // dz^T: element (n, m) at dz[m*ldz + n]
+            FragBr b;   // act: element (m, k) at act[m*lda + k]
+            wmma::load_matrix_sync(a, dz + i * 16, ldz);
+            wmma::load_matrix_sync(b, act + j * 16, lda);
+            wmma::mma_sync(c, a, b, c);
+            wmma::store_matrix_sync(tmp, c, 16, wmma::mem_row_major);
+            __syncwarp();
+            for (int e = lane; e < 256; e += 32) atomicAdd(&g[(i * 16 + e / 16) * ldg + j * 16 + e % 16], tmp[e]);
+            __syncwarp();
+        }
+    }
+}
+
+// dA[16][K] = dz[16][N] . W[N][K]
+__device__ __forceinline__ void input_grad(const __nv_bfloat16* dz, int ldz, const __nv_bfloat16* W, int N, int K,
+                                           float* dA, int ldd)
+{
+    for (int j = 0; j < K / 16; ++j) {
+        FragC c;
+        wmma::fill_fragment(c, 0.f);
+        for (int q = 0; q < N / 16; ++q) {
+            FragA a;
+            FragBr b;
+            wmma::load_matrix_sync(a, dz + q * 16, ldz);
+            wmma::load_matrix_sync(b, W + (size_t)q * 16 * K + j * 16, K);
+            wmma::mma_sync(c, a, b, c);
+        }
+        wmma::store_matrix_sync(dA + j * 16, c, ldd, wmma::mem_row_major);
+    }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): minibatch row selection.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+struct TrainArgs {
+    MlpDev m;
+    const float* x;        // [n_data][kInP]
+    const float* tgt;      // [n_data][kOut]
+    int64_t n_data;
+    int64_t M;             // rows of this pass (batch size, or n_data)
+    int sampled;           // 1: row r is data row splitmix64(seed + r) % n_data
+    uint64_t seed;
+    int rows_per_block;
+    float* grad;           // [kNParams], accumulated
+    float* loss;           // accumulated (optional)
+};
+
+__device__ __forceinline__ int64_t data_row(const TrainArgs& A, int64_t r)
+{
+    return A.sampled ? (int64_t)(splitmix64(A.seed + (uint64_t)r) % (uint64_t)A.n_data) : r;
+}
+
+__global__ void __launch_bounds__(32 * kTrainWarps) mlp_train_kernel(TrainArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TrainBlock& B = *reinterpret_cast<TrainBlock*>(smem_raw);
+    TrainWarp* warps = reinterpret_cast<TrainWarp*>(smem_raw + sizeof(TrainBlock));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    TrainWarp& W = warps[warp];
+    const MlpDev& m = A.m;
+    float* gb = &B.gW1[0][0];
+    for (int e = threadIdx.x; e < (int)(sizeof(TrainBlock) / sizeof(float)); e += blockDim.x) gb[e] = 0.f;
+    __syncthreads();
+    const float inv_m = 1.f / (float)A.M;
+    const __nv_bfloat16* Ws[3] = {m.W1, m.W2, m.W3};
+    const float* bs[3] = {m.b1, m.b2, m.b3};
+    const int64_t row_begin = (int64_t)blockIdx.x * A.rows_per_block;
+    const int64_t row_end = row_begin + A.rows_per_block < A.M ? row_begin + A.rows_per_block : A.M;
+    for (int64_t r0 = row_begin + warp * 16; r0 < row_end; r0 += 16 * kTrainWarps) {
+        // ---- forward
+        for (int e = lane; e < 16 * (kInP / 4); e += 32) {
+            const int r = e / (kInP / 4), c4 = e % (kInP / 4);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r0 + r < row_end) v = *reinterpret_cast<const float4*>(A.x + data_row(A, r0 + r) * kInP + 4 * c4);
+            W.a0[r][4 * c4] = __float2bfloat16(v.x);
+            W.a0[r][4 * c4 + 1] = __float2bfloat16(v.y);
+            W.a0[r][4 * c4 + 2] = __float2bfloat16(v.z);
+            W.a0[r][4 * c4 + 3] = __float2bfloat16(v.w);
+        }
+        __syncwarp();
+        for (int l = 0; l < 3; ++l) {
+            if (l == 0) layer_mma(&W.a0[0][0], kInP, Ws[0], kInP, kWid, &W.z[0][0][0], kWid);
+            else layer_mma(&W.a[l - 1][0][0], kWid, Ws[l], kWid, kWid, &W.z[l][0][0], kWid);
+            __syncwarp();
+            for (int e = lane; e < 16 * kWid; e += 32) {
+                const int r = e / kWid, c = e % kWid;
+                const float zz = W.z[l][r][c] + bs[l][c];
+                W.z[l][r][c] = zz;
+                W.a[l][r][c] = __float2bfloat16(gelu_f(zz));
+            }
+            __syncwarp();
+        }
+        layer_mma(&W.a[2][0][0], kWid, m.W4, kWid, kOutP, &W.tmp[0][0], kWid);
+        __syncwarp();
+        // ---- loss = mean over rows of the squared error summed over outputs
+        float lsum = 0.f;
+        for (int e = lane; e < 16 * kOutP; e += 32) {
+            const int r = e / kOutP, c = e % kOutP;
+            float d = 0.f;
+            if (c < kOut && r0 + r < row_end) {
+                const float yhat = W.tmp[r][c] + m.b4[c];
+                const float diff = yhat - A.tgt[data_row(A, r0 + r) * kOut + c];
+                lsum = fmaf(diff, diff, lsum);
+                d = 2.f * diff * inv_m;
+                atomicAdd(&B.gb4[c], d);
+            }
+            W.dz[r][c] = __float2bfloat16(d);
+        }
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if (lane == 0) atomicAdd(&B.loss, lsum * inv_m);
+        __syncwarp();
+        // ---- output layer
+        accum_weight_grad(&W.dz[0][0], kWid, &W.a[2][0][0], kWid, kOutP, kWid, &B.gW4[0][0], kWid, &W.tmp[0][0]);
+        input_grad(&W.dz[0][0], kWid, m.W4, kOutP, kWid, &W.tmp[0][0], kWid);
+        __syncwarp();
+        // ---- hidden layers, top down
+        for (int l = 2; l >= 0; --l) {
+            float s0 = 0.f, s1 = 0.f;   // bias gradients of columns lane, lane + 32
+            for (int e = lane; e < 16 * kWid; e += 32) {
+                const int r = e / kWid, c = e % kWid;
+                const float d = W.tmp[r][c] * gelu_grad_f(W.z[l][r][c]);
+                if (c < 32) s0 += d; else s1 += d;
+                W.dz[r][c] = __float2bfloat16(d);
+            }
+            float* gbl = l == 2 ? B.gb3 : l == 1 ? B.gb2 : B.gb1;
+            atomicAdd(&gbl[lane], s0);
+            atomicAdd(&gbl[lane + 32], s1);
+            __syncwarp();
+            if (l > 0) {
+                float* gWl = l == 2 ? &B.gW3[0][0] : &B.gW2[0][0];
+                accum_weight_grad(&W.dz[0][0], kWid, &W.a[l - 1][0][0], kWid, kWid, kWid, gWl, kWid, &W.tmp[0][0]);
+                input_grad(&W.dz[0][0], kWid, Ws[l], kWid, kWid, &W.tmp[0][0], kWid);
+            } else {
+                accum_weight_grad(&W.dz[0][0], kWid, &W.a0[0][0], kInP, kWid, kInP, &B.gW1[0][0], kInP, &W.tmp[0][0]);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // ---- one global add per parameter per block (flat, unpadded layout)
+    for (int e = threadIdx.x; e < kNParams; e += blockDim.x) {
+        float v;
+        int64_t k = e;
+        if (k < kOffB1) v = B.gW1[k / kIn][k % kIn];
+        else if (k < kOffW2) v = B.gb1[k - kOffB1];
+        else if (k < kOffB2) { k -= kOffW2; v = B.gW2[k / kWid][k % kWid]; }
+        else if (k < kOffW3) v = B.gb2[k - kOffB2];
+        else if (k < kOffB3) { k -= kOffW3; v = B.gW3[k / kWid][k % kWid]; }
+        else if (k < kOffW4) v = B.gb3[k - kOffB3];
+        else if (k < kOffB4) { k -= kOffW4; v = B.gW4[k / kWid][k % kWid]; }
+        else v = B.gb4[k - kOffB4];
+        atomicAdd(&A.grad[e], v);
+    }
+    if (threadIdx.x == 0 && A.loss) atomicAdd(A.loss, B.loss);
+}
+
+// --------------------------------------------------------------------------
+// parameters: padded BF16 copies; Adam
+// --------------------------------------------------------------------------
+struct MlpBuf {
+    __nv_bfloat16 *W1, *W2, *W3, *W4;
+    float *b1, *b2, *b3, *b4;
+};
+
+__global__ void publish_kernel(const float* __restrict__ p, MlpBuf m)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid < kWid * kInP) {
+        const int r = tid / kInP, c = tid % kInP;
+        m.W1[tid] = __float2bfloat16(c < kIn ? p[kOffW1 + r * kIn + c] : 0.f);
+    }
+    if (tid < kWid * kWid) {
+        m.W2[tid] = __float2bfloat16(p[kOffW2 + tid]);
+        m.W3[tid] = __float2bfloat16(p[kOffW3 + tid]);
+    }
+    if (tid < kOutP * kWid) {
+        const int r = tid / kWid;
+        m.W4[tid] = __float2bfloat16(r < kOut ? p[kOffW4 + tid] : 0.f);
+    }
+    if (tid < kWid) {
+        m.b1[tid] = p[kOffB1 + tid];
+        m.b2[tid] = p[kOffB2 + tid];
+        m.b3[tid] = p[kOffB3 + tid];
+    }
+    if (tid < kOutP) m.b4[tid] = tid < kOut ? p[kOffB4 + tid] : 0.f;
+}
+
+// Default initialisation: W ~ U(-1/sqrt(n_in), 1/sqrt(n_in)) from SplitMix64
+// of (seed, index), biases zero.
+__global__ void init_params_kernel(float* __restrict__ p, uint64_t seed)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNParams) return;
+    int fan_in = 0;
+    if (i < kOffB1) fan_in = kIn;
+    else if (i >= kOffW2 && i < kOffB2) fan_in = kWid;
+    else if (i >= kOffW3 && i < kOffB3) fan_in = kWid;
+    else if (i >= kOffW4 && i < kOffB4) fan_in = kWid;
+    if (!fan_in) { p[i] = 0.f; return; }
+    const uint64_t r = splitmix64(seed * 0x100000000ull + (uint64_t)i);
+    const float u = (float)(r >> 40) * (1.f / 16777216.f);        // [0, 1)
+    p[i] = (2.f * u - 1.f) * rsqrtf((float)fan_in);
+}
+
+// Adam (Kingma & Ba 2015) with bias correction; c1 = 1 - beta1^t, c2 = 1 - beta2^t.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ mom,
+                            float* __restrict__ vel, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * mom[i] + (1.f - b1) * gi;
+    const float vi = b2 * vel[i] + (1.f - b2) * gi * gi;
+    mom[i] = mi;
+    vel[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// --------------------------------------------------------------------------
+// features
+// --------------------------------------------------------------------------
+struct FeatArgs {
+    SegTable tab;
+    SkyDev sky;
+    const float* z;        // [6][stride] LFA links at their own time, valid on [0, nz), zero outside
+    int64_t stride, nz;
+    int64_t rows;          // features for samples [0, rows)
+    float r1;              // Tbar / dt
+    float Tbar;
+    float vfac;            // d/dt of the segment coordinate over c: 2 / (S dt c)
+    float w_lo, w_hi;      // band as limits of (omega Tbar)^2 = M2/M0
+    float* feats;          // [rows][kInP]
+    float* scale;          // [rows]
+    float* ybase;          // [6][stride] base links z (1 + eps), or null
+    int* tile_flag;        // [ceil(rows / kTile)] or null: set where above the band
+    const double* y_full;  // [6][stride] full links, or null (targets)
+    const double* z_ref;   // [6][stride] or null (targets; default z)
+    float* target;         // [rows][kOut] or null
+};
+
+__global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.rows) return;
+    const float r1 = a.r1, r2 = r1 * r1;
+    float q[5][6];
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+        float v[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const int64_t k = i - 2 + m;
+            v[m] = (k >= 0 && k < a.nz) ? a.z[(int64_t)l * a.stride + k] : 0.f;
+        }
+        // differences first: the stencils of slowly varying series cancel less
+        const float d0 = v[1] - v[0], d1 = v[2] - v[1], d2 = v[3] - v[2], d3 = v[4] - v[3];
+        q[0][l] = v[2];
+        q[1][l] = r1 * (8.f * (d1 + d2) - (d0 + d1 + d2 + d3)) * (1.f / 12.f);
+        q[2][l] = r2 * (14.f * (d2 - d1) - (d1 - d0) - (d3 - d2)) * (1.f / 12.f);
+        q[3][l] = r2 * r1 * ((d0 + d1 + d2 + d3) - 2.f * (d1 + d2)) * 0.5f;
+        q[4][l] = r2 * r2 * ((d3 - d2) - 2.f * (d2 - d1) + (d1 - d0));
+    }
+    float ft[kInP];
+    float mk[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float mx = 0.f;
+#pragma unroll
+        for (int l = 0; l < 6; ++l) mx = fmaxf(mx, fabsf(q[k][l]));
+        mk[k] = mx;
+        const float inv = mx > 0.f ? 1.f / mx : 0.f;
+#pragma unroll
+        for (int l = 0; l < 6; ++l) ft[k * 6 + l] = q[k][l] * inv;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float lr = (mk[k] > 0.f && mk[k + 1] > 0.f) ? log10f(mk[k + 1] / mk[k]) : -8.f;
+        ft[30 + k] = fminf(fmaxf(lr, -8.f), 8.f) * 0.25f;
+    }
+    // geometry at sample i from the orbit table (FP32 evaluation suffices here)
+    int64_t s = i / a.tab.S;
+    if (s >= a.tab.nseg) s = a.tab.nseg - 1;
+    const float x = (float)(i - s * a.tab.S) * (2.f / (float)a.tab.S) - 1.f;
+    const double* cf = a.tab.coef + s * kNQ * kNC;
+    auto ev = [&](int row) {
+        const double* b = cf + row * kNC;
+        float r = (float)b[6];
+#pragma unroll
+        for (int p = 5; p >= 0; --p) r = fmaf(r, x, (float)b[p]);
+        return r;
+    };
+    // k.v / c of each spacecraft from the derivative of its position polynomial
+    auto evd = [&](int row) {
+        const double* b = cf + row * kNC;
+        float r = 6.f * (float)b[6];
+#pragma unroll
+        for (int p = 5; p >= 1; --p) r = fmaf(r, x, (float)p * (float)b[p]);
+        return r;
+    };
+    float kv[3];
+#pragma unroll
+    for (int sc3 = 0; sc3 < 3; ++sc3)
+        kv[sc3] = ((float)a.sky.k[0] * evd(kQR + 3 * sc3) + (float)a.sky.k[1] * evd(kQR + 3 * sc3 + 1)
+                   + (float)a.sky.k[2] * evd(kQR + 3 * sc3 + 2)) * a.vfac;
+    float eps[6];
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+        ft[34 + l] = (ev(kQT + l) / a.Tbar - 1.f) * 100.f;
+        const float kn = (float)a.sky.k[0] * ev(kQN + 3 * l) + (float)a.sky.k[1] * ev(kQN + 3 * l + 1)
+                       + (float)a.sky.k[2] * ev(kQN + 3 * l + 2);
+        ft[40 + l] = 1.f - kn;
+        eps[l] = (1.f - kn) > 1e-6f ? kv[link_sender(l)] / (1.f - kn) : 0.f;
+    }
+    ft[46] = 0.f;
+    ft[47] = 0.f;
+    float4* fo = reinterpret_cast<float4*>(a.feats + i * kInP);
+#pragma unroll
+    for (int c = 0; c < kInP / 4; ++c) fo[c] = make_float4(ft[4 * c], ft[4 * c + 1], ft[4 * c + 2], ft[4 * c + 3]);
+
+    // band: (omega Tbar)^2 ~ M2/M0
+    float sc = 0.125f * mk[2];
+    const float w2 = mk[0] > 0.f ? mk[2] / mk[0] : 0.f;
+    if (!(w2 >= a.w_lo)) sc = 0.f;                    // below the band (or no signal): plain LFA link
+    if (w2 > a.w_hi && a.tile_flag) atomicOr(&a.tile_flag[i / kTile], 1);
+    a.scale[i] = sc;
+    if (a.ybase) {
+#pragma unroll
+        for (int l = 0; l < 6; ++l) {
+            const int64_t zi = (int64_t)l * a.stride + i;
+            a.ybase[zi] = fmaf(eps[l], a.z[zi], a.z[zi]);
+        }
+    }
+    if (a.target) {
+#pragma unroll
+        for (int l = 0; l < 6; ++l) {
+            float t = 0.f;
+            if (sc > 0.f && a.y_full) {
+                const int64_t zi = (int64_t)l * a.stride + i;
+                const double zr = a.z_ref ? a.z_ref[zi] : (double)a.z[zi];
+                t = (float)((a.y_full[zi] - zr * (1.0 + (double)eps[l])) / (double)sc);
+            }
+            a.target[i * kOut + l] = t;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// full-link fallback and spot checks
+// --------------------------------------------------------------------------
+struct FallbackArgs {
+    LinksArgs la;          // y = the corrected links, overwritten where recomputed
+    const int* tile_flag;  // per tile: nonzero = above the band
+    int spot_every;        // 0: no spot checks
+    float spot_tol;
+    int global_pass;       // 0: flagged and spot tiles; 1: all others if this call failed a spot check
+    CorrStats* stats;
+};
+
+__global__ void __launch_bounds__(kTile) corr_fallback_kernel(FallbackArgs A)
+{
+    __shared__ TileGeo g;
+    __shared__ LinksTile<true> s;
+    __shared__ float red[2][kTile / 32];
+    const LinksArgs& a = A.la;
+    const int64_t tile = a.tile0 + blockIdx.x;
+    const int flag = A.tile_flag[tile];
+    const bool spot = A.spot_every > 0 && (tile % A.spot_every) == 0;
+    if (A.global_pass) {
+        if (flag || spot || A.stats->call_failed == 0) return;
+    } else if (!flag && !spot) {
+        return;
+    }
+    const int64_t i0 = tile * (int64_t)kTile;
+    const int64_t ic = i0 + kTile / 2;
+    tile_geo_load(g, a.tab, ic, a.sky);
+    links_tile_prologue<true>(a, g, ic, i0, i0 + kTile - 1, s);
+    const int64_t i = i0 + threadIdx.x;
+    const bool valid = i >= a.i_begin && i < a.i_end;
+    float* y = (float*)a.y;
+    const bool check = !A.global_pass && spot && !flag;
+    float old[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid && check) {
+#pragma unroll
+        for (int l = 0; l < 6; ++l) old[l] = y[l * a.ny + i];
+    }
+    if (valid) links_sample<true>(a, g, ic, i, s, y + i, a.ny);
+    if (!check) {
+        if (threadIdx.x == 0) atomicAdd(A.global_pass ? &A.stats->fallback_tiles : &A.stats->band_tiles, 1u);
+        return;
+    }
+    float num = 0.f, den = 0.f;
+    if (valid) {
+#pragma unroll
+        for (int l = 0; l < 6; ++l) {
+            const float v = y[l * a.ny + i];
+            num = fmaxf(num, fabsf(v - old[l]));
+            den = fmaxf(den, fabsf(v));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        num = fmaxf(num, __shfl_xor_sync(0xffffffffu, num, o));
+        den = fmaxf(den, __shfl_xor_sync(0xffffffffu, den, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = num;
+        red[1][threadIdx.x >> 5] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kTile / 32; ++w) {
+            num = fmaxf(num, red[0][w]);
+            den = fmaxf(den, red[1][w]);
+        }
+        const float rel = den > 0.f ? num / den : 0.f;
+        atomicAdd(&A.stats->spot_tiles, 1u);
+        atomicMax(&A.stats->max_err_bits, __float_as_uint(rel));
+        if (!(rel <= A.spot_tol)) {
+            atomicAdd(&A.stats->spot_failed, 1u);
+            atomicAdd(&A.stats->call_failed, 1u);
+        }
+    }
+}
+
+}  // namespace lisa
+
+using namespace lisa;
+
+struct lisa_corrector {
+    float* p = nullptr;       // FP32 master parameters
+    float* mom = nullptr;     // Adam moments
+    float* vel = nullptr;
+    void* wbuf = nullptr;     // padded BF16 weights + FP32 biases
+    MlpBuf buf{};
+    CorrStats* stats = nullptr;
+    float* grad = nullptr;    // gradient buffer of lisa_corrector_train
+    int64_t step = 0;
+    double f_lo = 1e-4, f_hi = 2e-2;
+    int spot_every = 64;
+    float spot_tol = 0.05f;
+};
+
+namespace lisa {
+
+static MlpDev mlp_dev(const lisa_corrector* c)
+{
+    return MlpDev{c->buf.W1, c->buf.W2, c->buf.W3, c->buf.W4, c->buf.b1, c->buf.b2, c->buf.b3, c->buf.b4};
+}
+
+static int publish(lisa_corrector* c, cudaStream_t st)
+{
+    prof_before("corr_publish", st);
+    publish_kernel<<<(kWid * kWid + 255) / 256, 256, 0, st>>>(c->p, c->buf);
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "publish_kernel launch");
+}
+
+static void free_corrector(lisa_corrector* c)
+{
+    cudaFree(c->p);
+    cudaFree(c->mom);
+    cudaFree(c->vel);
+    cudaFree(c->wbuf);
+    cudaFree(c->stats);
+    cudaFree(c->grad);
+    delete c;
+}
+
+static int run_forward(const lisa_corrector* c, const float* x, int64_t M, int links, const float* scale,
+                       int64_t n, float* out, cudaStream_t st)
+{
+    if (M <= 0) return LISA_OK;
+    const int64_t rows_per_block = 16 * kFwdWarps;
+    const int64_t blocks = (M + rows_per_block - 1) / rows_per_block;
+    prof_before("mlp_forward", st);
+    mlp_forward_kernel<<<(unsigned)blocks, 32 * kFwdWarps, 0, st>>>(mlp_dev(c), x, M, links, scale, n, out);
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "mlp_forward_kernel launch");
+}
+
+static int run_features(const SegTable& tab, const SkyDev& sky, double Tbar, double dt, const float* z,
+                        int64_t stride, int64_t nz, int64_t rows, double f_lo, double f_hi, float* feats,
+                        float* scale, float* ybase, int* tile_flag, const double* y_full, const double* z_ref,
+                        float* target, cudaStream_t st)
+{
+    if (rows <= 0) return LISA_OK;
+    const double two_pi_T = 2.0 * M_PI * Tbar;
+    FeatArgs a;
+    a.tab = tab;
+    a.sky = sky;
+    a.z = z;
+    a.stride = stride;
+    a.nz = nz;
+    a.rows = rows;
+    a.r1 = (float)(Tbar / dt);
+    a.Tbar = (float)Tbar;
+    a.vfac = (float)(2.0 / ((double)tab.S * dt * kC));
+    a.w_lo = (float)(two_pi_T * f_lo * two_pi_T * f_lo);
+    a.w_hi = isfinite(f_hi) ? (float)(two_pi_T * f_hi * two_pi_T * f_hi) : INFINITY;
+    a.feats = feats;
+    a.scale = scale;
+    a.ybase = ybase;
+    a.tile_flag = tile_flag;
+    a.y_full = y_full;
+    a.z_ref = z_ref;
+    a.target = target;
+    prof_before("corr_features", st);
+    corr_features_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "corr_features_kernel launch");
+}
+
+// Corrected links on out-grid samples [0, rows) into y ([6][out.n], FP32):
+// LFA z, features, MLP with the y = z + s*MLP epilogue, then full links on
+// tiles above the band, spot checks, and the all-tile fallback pass.
+static int corrected_links(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, const lisa_grid& h_grid,
+                           const void* hp, const void* hc, const lisa_grid& out, const SegTable& tab,
+                           int64_t rows, float* y, Scratch& sc, cudaStream_t st)
+{
+    const int64_t n = out.n;
+    if (rows <= 0) return LISA_OK;
+    const int64_t nz = rows + 2 < n ? rows + 2 : n;
+    const int64_t ntile = (rows + kTile - 1) / kTile;
+    float* z = (float*)sc.alloc(sizeof(float) * 6 * (size_t)n);
+    float* feats = (float*)sc.alloc(sizeof(float) * kInP * (size_t)rows);
+    float* scale = (float*)sc.alloc(sizeof(float) * (size_t)rows);
+    int* flags = (int*)sc.alloc(sizeof(int) * (size_t)ntile);
+    if (!z || !feats || !scale || !flags) return sc.status();
+    const SkyDev skyd = make_sky_dev(*sky);
+    BlendSpec none{};
+    LISA_TRY(launch_lfa(tab, skyd, orbit->L_m, h_grid, hp, hc, LISA_MIXED, kLfaOwnTime, LISA_LFA_UNEQUAL, LISA_XYZ,
+                        out, z, nullptr, 0, nz, none, st));
+    LISA_TRY(cuda_status(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)ntile, st), "cudaMemsetAsync"));
+    LISA_TRY(cuda_status(cudaMemsetAsync(&c->stats->call_failed, 0, sizeof(unsigned), st), "cudaMemsetAsync"));
+    const double Tbar = orbit->L_m / kC;
+    LISA_TRY(run_features(tab, skyd, Tbar, out.dt, z, n, nz, rows, c->f_lo, c->f_hi, feats, scale, y, flags,
+                          nullptr, nullptr, nullptr, st));
+    LISA_TRY(run_forward(c, feats, rows, 1, scale, n, y, st));
+    FallbackArgs A;
+    A.la.tab = tab;
+    A.la.sky = skyd;
+    A.la.hm = make_grid_map(out, h_grid);
+    A.la.hp = hp;
+    A.la.hc = hc;
+    A.la.y = y;
+    A.la.ny = n;
+    A.la.i_begin = 0;
+    A.la.i_end = rows;
+    A.la.tile0 = 0;
+    A.tile_flag = flags;
+    A.spot_every = c->spot_every;
+    A.spot_tol = c->spot_tol;
+    A.stats = c->stats;
+    for (int pass = 0; pass < 2; ++pass) {
+        A.global_pass = pass;
+        prof_before(pass ? "corr_fallback_all" : "corr_fallback", st);
+        corr_fallback_kernel<<<(unsigned)ntile, kTile, 0, st>>>(A);
+        prof_after(st);
+        LISA_TRY(cuda_status(cudaGetLastError(), "corr_fallback_kernel launch"));
+    }
+    return LISA_OK;
+}
+
+}  // namespace lisa
+
+extern "C" {
+
+int64_t lisa_corrector_num_params(void) { return kNParams; }
+int lisa_corrector_num_features(void) { return kIn; }
+
+int lisa_corrector_create(lisa_corrector** out, const float* host_params, int64_t n_params, uint64_t seed)
+{
+    if (!out) { set_error("lisa_corrector_create: out is NULL"); return LISA_EINVAL; }
+    if (host_params && n_params != kNParams) {
+        set_error("lisa_corrector_create: need %lld FP32 parameters (got %lld)", (long long)kNParams,
+                  (long long)n_params);
+        return LISA_EINVAL;
+    }
+    lisa_corrector* c = new (std::nothrow) lisa_corrector();
+    if (!c) { set_error("lisa_corrector_create: out of host memory"); return LISA_ENOMEM; }
+    const size_t pb = sizeof(float) * kNParams;
+    const size_t wb = sizeof(__nv_bfloat16) * (kWid * kInP + 2 * kWid * kWid + kOutP * kWid);
+    const size_t bb = sizeof(float) * (3 * kWid + kOutP);
+    int rc = cuda_status(cudaMalloc(&c->p, pb), "cudaMalloc");
+    if (!rc) rc = cuda_status(cudaMalloc(&c->mom, pb), "cudaMalloc");
+    if (!rc) rc = cuda_status(cudaMalloc(&c->vel, pb), "cudaMalloc");
+    if (!rc) rc = cuda_status(cudaMalloc(&c->wbuf, wb + bb), "cudaMalloc");
+    if (!rc) rc = cuda_status(cudaMalloc(&c->stats, sizeof(CorrStats)), "cudaMalloc");
+    if (!rc) rc = cuda_status(cudaMalloc(&c->grad, pb), "cudaMalloc");
+    if (rc) { free_corrector(c); return rc; }
+    __nv_bfloat16* w = (__nv_bfloat16*)c->wbuf;
+    c->buf.W1 = w;
+    c->buf.W2 = c->buf.W1 + kWid * kInP;
+    c->buf.W3 = c->buf.W2 + kWid * kWid;
+    c->buf.W4 = c->buf.W3 + kWid * kWid;
+    float* b = (float*)((char*)c->wbuf + wb);
+    c->buf.b1 = b;
+    c->buf.b2 = b + kWid;
+    c->buf.b3 = b + 2 * kWid;
+    c->buf.b4 = b + 3 * kWid;
+    if (host_params) {
+        rc = cuda_status(cudaMemcpy(c->p, host_params, pb, cudaMemcpyHostToDevice), "cudaMemcpy");
+    } else {
+        prof_before("corr_init", 0);
+        init_params_kernel<<<(unsigned)((kNParams + 255) / 256), 256>>>(c->p, seed);
+        prof_after(0);
+        rc = cuda_status(cudaGetLastError(), "init_params_kernel launch");
+    }
+    if (!rc) rc = cuda_status(cudaMemset(c->mom, 0, pb), "cudaMemset");
+    if (!rc) rc = cuda_status(cudaMemset(c->vel, 0, pb), "cudaMemset");
+    if (!rc) rc = cuda_status(cudaMemset(c->stats, 0, sizeof(CorrStats)), "cudaMemset");
+    if (!rc) rc = publish(c, 0);
+    if (!rc) rc = cuda_status(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if (rc) { free_corrector(c); return rc; }
+    *out = c;
+    return LISA_OK;
+}
+
+int lisa_corrector_destroy(lisa_corrector* c)
+{
+    if (c) free_corrector(c);
+    return LISA_OK;
+}
+
+int lisa_corrector_configure(lisa_corrector* c, double f_lo, double f_hi, int spot_every, double spot_tol)
+{
+    if (!c || !(f_lo >= 0.0) || !(f_hi > f_lo) || spot_every < 0 || !(spot_tol > 0.0)) {
+        set_error("lisa_corrector_configure: need 0 <= f_lo < f_hi, spot_every >= 0, spot_tol > 0");
+        return LISA_EINVAL;
+    }
+    c->f_lo = f_lo;
+    c->f_hi = f_hi;
+    c->spot_every = spot_every;
+    c->spot_tol = (float)spot_tol;
+    return LISA_OK;
+}
+
+int lisa_corrector_get_state(const lisa_corrector* c, float* params, float* adam_m, float* adam_v, int64_t* step,
+                             int64_t n_params)
+{
+    if (!c || n_params != kNParams) { set_error("lisa_corrector_get_state: bad arguments"); return LISA_EINVAL; }
+    const size_t pb = sizeof(float) * kNParams;
+    int rc = cuda_status(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if (!rc && params) rc = cuda_status(cudaMemcpy(params, c->p, pb, cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (!rc && adam_m) rc = cuda_status(cudaMemcpy(adam_m, c->mom, pb, cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (!rc && adam_v) rc = cuda_status(cudaMemcpy(adam_v, c->vel, pb, cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (!rc && step) *step = c->step;
+    return rc;
+}
+
+int lisa_corrector_set_state(lisa_corrector* c, const float* params, const float* adam_m, const float* adam_v,
+                             int64_t step, int64_t n_params)
+{
+    if (!c || n_params != kNParams || step < 0) { set_error("lisa_corrector_set_state: bad arguments"); return LISA_EINVAL; }
+    const size_t pb = sizeof(float) * kNParams;
+    int rc = cuda_status(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if (!rc && params) rc = cuda_status(cudaMemcpy(c->p, params, pb, cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (!rc && adam_m) rc = cuda_status(cudaMemcpy(c->mom, adam_m, pb, cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (!rc && adam_v) rc = cuda_status(cudaMemcpy(c->vel, adam_v, pb, cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (!rc) c->step = step;
+    if (!rc) rc = publish(c, 0);
+    if (!rc) rc = cuda_status(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    return rc;
+}
+
+int lisa_corrector_forward(const lisa_corrector* c, const float* feats, int64_t M, float* out, void* stream)
+{
+    if (!c || M < 0 || (M > 0 && (!feats || !out))) { set_error("lisa_corrector_forward: bad arguments"); return LISA_EINVAL; }
+    if (((uintptr_t)feats & 15) != 0) { set_error("lisa_corrector_forward: feats must be 16-byte aligned"); return LISA_EINVAL; }
+    return run_forward(c, feats, M, 0, nullptr, 0, out, (cudaStream_t)stream);
+}
+
+int lisa_corrector_gradient(lisa_corrector* c, const float* feats, const float* target, int64_t n_data,
+                            int64_t batch, uint64_t seed, float* grad, float* loss, void* stream)
+{
+    if (!c || n_data <= 0 || batch < 0 || !feats || !target || !grad) {
+        set_error("lisa_corrector_gradient: bad arguments");
+        return LISA_EINVAL;
+    }
+    if (((uintptr_t)feats & 15) != 0) { set_error("lisa_corrector_gradient: feats must be 16-byte aligned"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    LISA_TRY(cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * kNParams, st), "cudaMemsetAsync"));
+    if (loss) LISA_TRY(cuda_status(cudaMemsetAsync(loss, 0, sizeof(float), st), "cudaMemsetAsync"));
+    static int attr_dev = -1;
+    int dev = 0;
+    LISA_TRY(cuda_status(cudaGetDevice(&dev), "cudaGetDevice"));
+    if (attr_dev != dev) {
+        LISA_TRY(cuda_status(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)kTrainSmem), "cudaFuncSetAttribute"));
+        attr_dev = dev;
+    }
+    TrainArgs A;
+    A.m = mlp_dev(c);
+    A.x = feats;
+    A.tgt = target;
+    A.n_data = n_data;
+    A.M = batch > 0 ? batch : n_data;
+    A.sampled = batch > 0;
+    A.seed = seed;
+    // about two blocks of 32 rows or more per SM (fewer global flushes for large passes)
+    int64_t rpb = (A.M + 303) / 304;
+    rpb = (rpb + 31) / 32 * 32;
+    A.rows_per_block = (int)(rpb < 32 ? 32 : rpb > 1024 ? 1024 : rpb);
+    A.grad = grad;
+    A.loss = loss;
+    const int64_t blocks = (A.M + A.rows_per_block - 1) / A.rows_per_block;
+    prof_before("mlp_train", st);
+    mlp_train_kernel<<<(unsigned)blocks, 32 * kTrainWarps, kTrainSmem, st>>>(A);
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "mlp_train_kernel launch");
+}
+
+int lisa_corrector_adam_step(lisa_corrector* c, const float* grad, float lr, void* stream)
+{
+    if (!c || !grad || !(lr > 0.f)) { set_error("lisa_corrector_adam_step: bad arguments"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    c->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - pow(b1, (double)c->step)), c2 = (float)(1.0 - pow(b2, (double)c->step));
+    prof_before("mlp_adam", st);
+    adam_kernel<<<(unsigned)((kNParams + 255) / 256), 256, 0, st>>>(c->p, grad, c->mom, c->vel, kNParams, lr,
+                                                                   (float)b1, (float)b2, 1e-8f, c1, c2);
+    prof_after(st);
+    LISA_TRY(cuda_status(cudaGetLastError(), "adam_kernel launch"));
+    return publish(c, st);
+}
+
+int lisa_corrector_train(lisa_corrector* c, const float* feats, const float* target, int64_t n_data, int64_t steps,
+                         int64_t batch, float lr_max, float lr_min, uint64_t seed, float* losses, void* stream)
+{
+    if (!c || !feats || !target || n_data <= 0 || steps < 0 || batch <= 0 || !(lr_max > 0.f) || !(lr_min > 0.f) ||
+        lr_min > lr_max) {
+        set_error("lisa_corrector_train: bad arguments");
+        return LISA_EINVAL;
+    }
+    for (int64_t k = 0; k < steps; ++k) {
+        // cosine decay from lr_max to lr_min
+        const double lr = lr_min + 0.5 * (lr_max - lr_min) * (1.0 + cos(M_PI * (double)k / (double)steps));
+        LISA_TRY(lisa_corrector_gradient(c, feats, target, n_data, batch, seed + ((uint64_t)k << 32), c->grad,
+                                         losses ? losses + k : nullptr, stream));
+        LISA_TRY(lisa_corrector_adam_step(c, c->grad, (float)lr, stream));
+    }
+    return LISA_OK;
+}
+
+int lisa_corrector_features(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid g, const float* z,
+                            const double* y_full, const double* z_ref, double f_lo, double f_hi, float* feats,
+                            float* scale, float* ybase, float* target, void* stream)
+{
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(g, "grid"));
+    if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
+    if (!(f_lo >= 0.0) || !(f_hi > f_lo)) { set_error("need 0 <= f_lo < f_hi"); return LISA_EINVAL; }
+    if (g.n == 0) return LISA_OK;
+    if (!z || !feats || !scale || (target && !y_full)) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    if (((uintptr_t)feats & 15) != 0) { set_error("feats must be 16-byte aligned"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, g, sc, tab, st));
+    return run_features(tab, make_sky_dev(*sky), orbit->L_m / kC, g.dt, z, g.n, g.n, g.n, f_lo, f_hi, feats, scale,
+                        ybase, nullptr, y_full, z_ref, target, st);
+}
+
+int lisa_corrector_links(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                         const void* hp, const void* hc, lisa_grid out, void* y, void* stream)
+{
+    if (!c) { set_error("corrector is NULL"); return LISA_EINVAL; }
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(h_grid, "h_grid"));
+    LISA_TRY(check_grid(out, "out"));
+    LISA_TRY(check_common(LISA_MIXED, LISA_TDI15, LISA_XYZ));
+    if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
+    if (out.n == 0) return LISA_OK;
+    if (!y || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, out, sc, tab, st));
+    return corrected_links(c, orbit, sky, h_grid, hp, hc, out, tab, out.n, (float*)y, sc, st);
+}
+
+int lisa_response_hybrid_corrected(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
+                                   const void* hp, const void* hc, int tdi_gen, int channels, double t_hyb,
+                                   double T_win, double sigma, lisa_grid out, void* xyz, void* stream)
+{
+    if (!c) { set_error("corrector is NULL"); return LISA_EINVAL; }
+    LISA_TRY(check_orbit(orbit));
+    LISA_TRY(check_grid(h_grid, "h_grid"));
+    LISA_TRY(check_grid(out, "out"));
+    LISA_TRY(check_common(LISA_MIXED, tdi_gen, channels));
+    if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
+    if (!isfinite(t_hyb)) { set_error("t_hyb must be finite"); return LISA_EINVAL; }
+    if (out.n == 0) return LISA_OK;
+    if (!xyz || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
+    const double Tw = T_win > 0.0 ? T_win : 800.0 * out.dt;
+    const double sg = sigma > 0.0 ? sigma : Tw / 40.0;
+    const int64_t n = out.n;
+    int64_t iL, iF;
+    hybrid_split(out, t_hyb, Tw, iL, iF);
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
+    SegTable tab;
+    LISA_TRY(make_table(orbit, out, sc, tab, st));
+    const SkyDev skyd = make_sky_dev(*sky);
+    if (iF > iL + 1) {
+        for (int ch = 0; ch < 3; ++ch) {
+            LISA_TRY(cuda_status(cudaMemsetAsync((float*)xyz + (size_t)ch * n + (size_t)(iL + 1), 0,
+                                                 sizeof(float) * (size_t)(iF - iL - 1), st), "cudaMemsetAsync"));
+        }
+    }
+    if (iL >= 0) {
+        // corrected links up to the forward reach of the TDI stencil (16 samples)
+        const int64_t rows = iL + 1 + 32 < n ? iL + 1 + 32 : n;
+        float* yc = (float*)sc.alloc(sizeof(float) * 6 * (size_t)n);
+        if (!yc) return sc.status();
+        LISA_TRY(corrected_links(c, orbit, sky, h_grid, hp, hc, out, tab, rows, yc, sc, st));
+        BlendSpec bl{1, t_hyb, sg, +1.0, 0, 0};
+        LISA_TRY(launch_tdi(tab, out, yc, LISA_MIXED, tdi_gen, LISA_FROZEN, channels, out, xyz, 0, iL + 1, bl, st));
+    }
+    if (iF < n) {
+        const double Dmax = 8.0 * max_light_time(orbit, out);
+        int64_t lo = iF - (int64_t)ceil(Dmax / out.dt) - 40;
+        lo = lo < 0 ? 0 : lo;
+        float* y = (float*)sc.alloc(sizeof(float) * 6 * (size_t)n);
+        if (!y) return sc.status();
+        LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, LISA_MIXED, out, y, lo, n, st));
+        BlendSpec bl{1, t_hyb, sg, -1.0, iF, iL + 1};
+        LISA_TRY(launch_tdi(tab, out, y, LISA_MIXED, tdi_gen, LISA_FROZEN, channels, out, xyz, iF, n, bl, st));
+    }
+    return LISA_OK;
+}
+
+int lisa_corrector_report(lisa_corrector* c, int64_t* spot_tiles, int64_t* spot_failed, int64_t* band_tiles,
+                          int64_t* fallback_tiles, float* max_spot_err, int reset)
+{
+    if (!c) { set_error("corrector is NULL"); return LISA_EINVAL; }
+    CorrStats h;
+    LISA_TRY(cuda_status(cudaDeviceSynchronize(), "cudaDeviceSynchronize"));
+    LISA_TRY(cuda_status(cudaMemcpy(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost), "cudaMemcpy"));
+    if (spot_tiles) *spot_tiles = h.spot_tiles;
+    if (spot_failed) *spot_failed = h.spot_failed;
+    if (band_tiles) *band_tiles = h.band_tiles;
+    if (fallback_tiles) *fallback_tiles = h.fallback_tiles;
+    if (max_spot_err) {
+        float e;
+        memcpy(&e, &h.max_err_bits, sizeof(e));
+        *max_spot_err = e;
+    }
+    if (reset) LISA_TRY(cuda_status(cudaMemset(c->stats, 0, sizeof(CorrStats)), "cudaMemset"));
+    if (h.spot_failed > 0) {
+        set_error("%u of %u spot-checked tiles exceeded the tolerance: the full links were used instead",
+                  h.spot_failed, h.spot_tiles);
+        return LISA_ECORRECTOR;
+    }
+    return LISA_OK;
+}
+
+}  // extern "C"

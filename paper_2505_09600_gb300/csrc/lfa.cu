@@ -59,7 +59,8 @@ int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const l
     a.tile0 = i_begin / kTile;
     a.bl = bl;
     const int64_t tiles = (i_end - 1) / kTile - a.tile0 + 1;
-    prof_before(precision == LISA_MIXED ? "lfa_mixed" : "lfa_f64", st);
+    prof_before(gen == kLfaOwnTime ? (precision == LISA_MIXED ? "lfa_own_mixed" : "lfa_own_f64")
+                                   : (precision == LISA_MIXED ? "lfa_mixed" : "lfa_f64"), st);
     if (precision == LISA_MIXED) lfa_kernel<true><<<(unsigned)tiles, kTile, 0, st>>>(a);
     else lfa_kernel<false><<<(unsigned)tiles, kTile, 0, st>>>(a);
     prof_after(st);

@@ -36,13 +36,14 @@ struct LfaArgs {
     BlendSpec bl;
 };
 
+
 // Channel ch: links a = cyc(+2), b = cyc(+3); arms T_a = cyc(+3), T_b = cyc(+2).
 __device__ __forceinline__ int lfa_link(int ch, int which) { return link_cycle(which ? 4 : 2, ch); }
 __device__ __forceinline__ int lfa_arm(int ch, int which) { return link_cycle(which ? 2 : 4, ch); }
 
 __device__ __forceinline__ double lfa_shift(int gen, double Ta, double Tb)
 {
-    return gen == LISA_TDI20 ? 2.0 * Ta + 1.5 * Tb : Ta + 0.5 * Tb;
+    return gen == LISA_TDI20 ? 2.0 * Ta + 1.5 * Tb : gen == LISA_TDI15 ? Ta + 0.5 * Tb : 0.0;
 }
 
 template <typename Real>
@@ -151,7 +152,7 @@ __device__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& s
         const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
         const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
         const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
-        const int l = lfa_link(ch, which);
+        const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
         const double up = u - sh * u_per_s;
         const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
         return sh + 0.5 * Tl + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
@@ -187,11 +188,12 @@ __device__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& s
             Cubic da{0.f, 0.f, 0.f};
             if (!equal) {
                 const Cubic ca = tg_cubic(g, ra), cb = tg_cubic(g, rb);
-                const float fa = which ? (a.gen == LISA_TDI20 ? 1.5f : 0.5f) : (a.gen == LISA_TDI20 ? 2.f : 1.f);
-                const float fb = which ? (a.gen == LISA_TDI20 ? 2.f : 1.f) : (a.gen == LISA_TDI20 ? 1.5f : 0.5f);
+                float fa = which ? (a.gen == LISA_TDI20 ? 1.5f : 0.5f) : (a.gen == LISA_TDI20 ? 2.f : 1.f);
+                float fb = which ? (a.gen == LISA_TDI20 ? 2.f : 1.f) : (a.gen == LISA_TDI20 ? 1.5f : 0.5f);
+                if (a.gen == kLfaOwnTime) fa = fb = 0.f;
                 da = Cubic{fa * ca.c1 + fb * cb.c1, fa * ca.c2 + fb * cb.c2, fa * ca.c3 + fb * cb.c3};
             }
-            const int l = lfa_link(ch, which);
+            const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
             const double Tl = equal ? a.Lc : g.b[kQT + l][0];
             const double dc = ac + 0.5 * Tl + 0.5 * (g.b[kRowKR + link_sender(l)][0] + g.b[kRowKR + link_receiver(l)][0]);
             int64_t j;
@@ -252,7 +254,7 @@ __device__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& s
         Real zval = Real(0);
         if (m >= 0 && m < a.nout) {
             const int ch = c >> 1, which = c & 1;
-            const int l = lfa_link(ch, which);
+            const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
             Real Tl, n3[3];
             int64_t j;
             Real eps;

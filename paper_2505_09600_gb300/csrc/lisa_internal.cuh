@@ -63,10 +63,32 @@ int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int prec
 
 // LFA: z series (optional) and channels (optional) on out-grid samples
 // [i_begin, i_end), z recomputed with its 2-sample halo inside each tile.
+// gen = kLfaOwnTime evaluates the LFA link formula for each of the six links
+// at its own reception time (no TDI shift): z[6][og.n] in link order (xyz
+// must be null).
+constexpr int kLfaOwnTime = 0;
 int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,
                const void* hc, int precision, int gen, int kind, int channels, const lisa_grid& og, void* z,
                void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st);
 int launch_tdi_lfa(const SegTable& tab, double L_nominal, const lisa_grid& zg, const void* z, int precision, int gen,
                    int kind, int channels, void* xyz, cudaStream_t st);
+
+// Shared host helpers of the C ABI (validation and orchestration).
+#define LISA_TRY(x)                     \
+    do {                                \
+        int _rc = (x);                  \
+        if (_rc != LISA_OK) return _rc; \
+    } while (0)
+int check_grid(const lisa_grid& g, const char* name);
+int check_orbit(const lisa_orbit* o);
+int check_common(int precision, int gen, int channels);
+size_t real_size(int precision);
+// Orbit polynomial table on grid g, in scratch.
+int make_table(const lisa_orbit* orbit, const lisa_grid& g, Scratch& sc, SegTable& tab, cudaStream_t st);
+// Upper bound of any single light time (halo sizing).
+double max_light_time(const lisa_orbit* o, const lisa_grid& g);
+// Hybrid regions on grid `out`: LFA samples [0, iL] (t <= t_hyb + Tw/2), full
+// samples [iF, n) (t >= t_hyb - Tw/2).
+void hybrid_split(const lisa_grid& out, double t_hyb, double Tw, int64_t& iL, int64_t& iF);
 
 }  // namespace lisa

@@ -128,6 +128,29 @@ _SIGS = {
     "lisa_response_hybrid": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
                                        C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                        lisa_grid, _P, _P]),
+    "lisa_corrector_num_params": (C.c_int64, []),
+    "lisa_corrector_num_features": (C.c_int, []),
+    "lisa_corrector_create": (C.c_int, [C.POINTER(C.c_void_p), _P, C.c_int64, C.c_uint64]),
+    "lisa_corrector_destroy": (C.c_int, [C.c_void_p]),
+    "lisa_corrector_configure": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_double]),
+    "lisa_corrector_get_state": (C.c_int, [C.c_void_p, _P, _P, _P, C.POINTER(C.c_int64), C.c_int64]),
+    "lisa_corrector_set_state": (C.c_int, [C.c_void_p, _P, _P, _P, C.c_int64, C.c_int64]),
+    "lisa_corrector_features": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, _P,
+                                          C.c_double, C.c_double, _P, _P, _P, _P, _P]),
+    "lisa_corrector_forward": (C.c_int, [C.c_void_p, _P, C.c_int64, _P, _P]),
+    "lisa_corrector_gradient": (C.c_int, [C.c_void_p, _P, _P, C.c_int64, C.c_int64, C.c_uint64, _P, _P, _P]),
+    "lisa_corrector_adam_step": (C.c_int, [C.c_void_p, _P, C.c_float, _P]),
+    "lisa_corrector_train": (C.c_int, [C.c_void_p, _P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_float, C.c_float,
+                                       C.c_uint64, _P, _P]),
+    "lisa_corrector_links": (C.c_int, [C.c_void_p, C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P,
+                                       lisa_grid, _P, _P]),
+    "lisa_links_lfa_own": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int, C.c_int,
+                                     lisa_grid, _P, _P]),
+    "lisa_response_hybrid_corrected": (C.c_int, [C.c_void_p, C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid,
+                                                 _P, _P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                                 lisa_grid, _P, _P]),
+    "lisa_corrector_report": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_float), C.c_int]),
 }
 
 
@@ -259,6 +282,15 @@ def lisa_links_lfa(orbit, sky, h_grid, hp, hc, precision, tdi_gen, lfa_kind, out
     _check(rc, "lisa_links_lfa")
 
 
+def lisa_links_lfa_own(orbit, sky, h_grid, hp, hc, precision, lfa_kind, out_grid, y, stream=None):
+    hg, og = _grid(h_grid), _grid(out_grid)
+    dt = _rdtype(precision)
+    o, s = _orb(orbit), _sky(sky)
+    rc = load().lisa_links_lfa_own(C.byref(o), C.byref(s), hg, _ptr(hp, dt, hg.n, "hp"), _ptr(hc, dt, hg.n, "hc"),
+                                   precision, lfa_kind, og, _ptr(y, dt, 6 * og.n, "y"), _stream(stream))
+    _check(rc, "lisa_links_lfa_own")
+
+
 def lisa_tdi_lfa(orbit, z_grid, z, precision, tdi_gen, lfa_kind, channels, xyz, stream=None):
     zg = _grid(z_grid)
     dt = _rdtype(precision)
@@ -378,3 +410,145 @@ class LisaPlan:
             self.close()
         except Exception:
             pass
+
+
+class LisaCorrector:
+    """The learned LFA-link corrector (lisa_corrector_*).  `params` is a flat
+    FP32 vector (numpy) or None for the library's seeded initialisation."""
+
+    def __init__(self, params=None, seed=0):
+        import numpy as np
+        lib = load()
+        self.n_params = lib.lisa_corrector_num_params()
+        self.n_features = lib.lisa_corrector_num_features()
+        h = C.c_void_p()
+        if params is None:
+            rc = lib.lisa_corrector_create(C.byref(h), None, self.n_params, int(seed))
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            if p.size != self.n_params:
+                raise ValueError("need %d parameters (got %d)" % (self.n_params, p.size))
+            rc = lib.lisa_corrector_create(C.byref(h), p.ctypes.data_as(C.c_void_p), self.n_params, int(seed))
+        _check(rc, "lisa_corrector_create")
+        self.handle = h
+
+    def configure(self, f_lo=1e-4, f_hi=2e-2, spot_every=64, spot_tol=0.05):
+        _check(load().lisa_corrector_configure(self.handle, float(f_lo), float(f_hi), int(spot_every),
+                                               float(spot_tol)), "lisa_corrector_configure")
+
+    def get_state(self):
+        import numpy as np
+        p, m, v = (np.empty(self.n_params, dtype=np.float32) for _ in range(3))
+        step = C.c_int64()
+        _check(load().lisa_corrector_get_state(self.handle, p.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
+                                               v.ctypes.data_as(C.c_void_p), C.byref(step), self.n_params),
+               "lisa_corrector_get_state")
+        return {"params": p, "adam_m": m, "adam_v": v, "step": step.value}
+
+    def set_state(self, state):
+        import numpy as np
+        arrs = [np.ascontiguousarray(state[k], dtype=np.float32) if state.get(k) is not None else None
+                for k in ("params", "adam_m", "adam_v")]
+        ptrs = [a.ctypes.data_as(C.c_void_p) if a is not None else None for a in arrs]
+        _check(load().lisa_corrector_set_state(self.handle, ptrs[0], ptrs[1], ptrs[2], int(state.get("step", 0)),
+                                               self.n_params), "lisa_corrector_set_state")
+
+    def save(self, path):
+        """Checkpoint (parameters, Adam moments, step) as .npz."""
+        import numpy as np
+        st = self.get_state()
+        np.savez(path, params=st["params"], adam_m=st["adam_m"], adam_v=st["adam_v"], step=np.int64(st["step"]))
+
+    def load_checkpoint(self, path):
+        import numpy as np
+        with np.load(path) as d:
+            self.set_state({"params": d["params"], "adam_m": d["adam_m"], "adam_v": d["adam_v"],
+                            "step": int(d["step"])})
+
+    def forward(self, feats, out, stream=None):
+        import torch
+        M = feats.shape[0]
+        _check(load().lisa_corrector_forward(self.handle, _ptr(feats, torch.float32, M * 48, "feats"), M,
+                                             _ptr(out, torch.float32, M * 6, "out"), _stream(stream)),
+               "lisa_corrector_forward")
+
+    def gradient(self, feats, target, grad, loss=None, batch=0, seed=0, stream=None):
+        import torch
+        n = feats.shape[0]
+        _check(load().lisa_corrector_gradient(self.handle, _ptr(feats, torch.float32, n * 48, "feats"),
+                                              _ptr(target, torch.float32, n * 6, "target"), n, int(batch), int(seed),
+                                              _ptr(grad, torch.float32, self.n_params, "grad"),
+                                              _ptr(loss, torch.float32, 1, "loss"), _stream(stream)),
+               "lisa_corrector_gradient")
+
+    def adam_step(self, grad, lr, stream=None):
+        import torch
+        _check(load().lisa_corrector_adam_step(self.handle, _ptr(grad, torch.float32, self.n_params, "grad"),
+                                               float(lr), _stream(stream)), "lisa_corrector_adam_step")
+
+    def train(self, feats, target, steps, batch, lr_max=3e-3, lr_min=3e-5, seed=0, losses=None, stream=None):
+        import torch
+        n = feats.shape[0]
+        _check(load().lisa_corrector_train(self.handle, _ptr(feats, torch.float32, n * 48, "feats"),
+                                           _ptr(target, torch.float32, n * 6, "target"), n, int(steps), int(batch),
+                                           float(lr_max), float(lr_min), int(seed),
+                                           _ptr(losses, torch.float32, int(steps), "losses"), _stream(stream)),
+               "lisa_corrector_train")
+
+    def links(self, orbit, sky, h_grid, hp, hc, out_grid, y, stream=None):
+        import torch
+        hg, og = _grid(h_grid), _grid(out_grid)
+        o, s = _orb(orbit), _sky(sky)
+        _check(load().lisa_corrector_links(self.handle, C.byref(o), C.byref(s), hg,
+                                           _ptr(hp, torch.float32, hg.n, "hp"), _ptr(hc, torch.float32, hg.n, "hc"),
+                                           og, _ptr(y, torch.float32, 6 * og.n, "y"), _stream(stream)),
+               "lisa_corrector_links")
+
+    def hybrid(self, orbit, sky, h_grid, hp, hc, tdi_gen, channels, t_hyb, T_win, sigma, out_grid, xyz, stream=None):
+        import torch
+        hg, og = _grid(h_grid), _grid(out_grid)
+        o, s = _orb(orbit), _sky(sky)
+        _check(load().lisa_response_hybrid_corrected(self.handle, C.byref(o), C.byref(s), hg,
+                                                     _ptr(hp, torch.float32, hg.n, "hp"),
+                                                     _ptr(hc, torch.float32, hg.n, "hc"), tdi_gen, channels,
+                                                     float(t_hyb), float(T_win), float(sigma), og,
+                                                     _ptr(xyz, torch.float32, 3 * og.n, "xyz"), _stream(stream)),
+               "lisa_response_hybrid_corrected")
+
+    def report(self, reset=True):
+        """Counters and status (LISA_ECORRECTOR if a spot check failed since the last reset)."""
+        a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        e = C.c_float()
+        rc = load().lisa_corrector_report(self.handle, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e),
+                                          1 if reset else 0)
+        out = {"spot_tiles": a.value, "spot_failed": b.value, "band_tiles": c.value, "fallback_tiles": d.value,
+               "max_spot_err": e.value, "status": rc}
+        if rc not in (LISA_OK, LISA_ECORRECTOR):
+            _check(rc, "lisa_corrector_report")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().lisa_corrector_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lisa_corrector_features(orbit, sky, grid, z, y_full, z_ref, f_lo, f_hi, feats, scale, ybase=None, target=None,
+                            stream=None):
+    import torch
+    g = _grid(grid)
+    o, s = _orb(orbit), _sky(sky)
+    _check(load().lisa_corrector_features(C.byref(o), C.byref(s), g, _ptr(z, torch.float32, 6 * g.n, "z"),
+                                          _ptr(y_full, torch.float64, 6 * g.n, "y_full"),
+                                          _ptr(z_ref, torch.float64, 6 * g.n, "z_ref"), float(f_lo), float(f_hi),
+                                          _ptr(feats, torch.float32, 48 * g.n, "feats"),
+                                          _ptr(scale, torch.float32, g.n, "scale"),
+                                          _ptr(ybase, torch.float32, 6 * g.n, "ybase"),
+                                          _ptr(target, torch.float32, 6 * g.n, "target"), _stream(stream)),
+           "lisa_corrector_features")

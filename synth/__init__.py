@@ -261,6 +261,73 @@ def pe_source(p, n=3155760, dt=10.0, t0=2.0e7):
     return Source(t0, dt, n, hp, hc, p["beta"], p["lam"], p["psi"], tc, mc_s, info)
 
 
+
+def corrector_params(nsrc=4096, seed=SEED_BASE + 4, n=4883, fmin=1e-4, fmax=2e-2):
+    """Sources of the corrector's training and held-out sets: chirps whose GW
+    frequency stays inside [fmin, fmax] over their grid.  Start frequency
+    log-U[fmin, fmax/1.02], sweep ratio f_end/f_start log-U[1.001, min(3,
+    fmax/f_start)], dt in {5, 10} s, n samples, isotropic sky, cos(iota)
+    U[-1, 1], t0 U[1e7, 4e7] s (orbit phase), distance 10 Gpc."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nsrc):
+        f0 = math.exp(rng.uniform(math.log(fmin), math.log(fmax / 1.02)))
+        rmax = min(3.0, fmax / f0)
+        r = math.exp(rng.uniform(math.log(1.001), math.log(rmax)))
+        dt = 5.0 if rng.uniform() < 0.5 else 10.0
+        beta, lam, psi = draw_sky(rng)
+        iota = math.acos(rng.uniform(-1.0, 1.0))
+        phi_c = rng.uniform(0.0, 2.0 * math.pi)
+        t0 = rng.uniform(1.0e7, 4.0e7)
+        out.append(dict(f0=f0, ratio=r, dt=dt, n=n, beta=beta, lam=lam, psi=psi, iota=iota, phi_c=phi_c, t0=t0))
+    return out
+
+
+def corrector_source(p, dist_gpc=10.0):
+    """Materialise a corrector source: the 0PN chirp whose frequency goes from
+    f0 at the first sample to f0*ratio at the end of the grid (chirp mass and
+    coalescence time solved from the two frequencies)."""
+    n, dt = p["n"], p["dt"]
+    dur = n * dt
+    f_end = p["f0"] * p["ratio"]
+    tau_end = dur / (p["ratio"] ** (8.0 / 3.0) - 1.0)
+    # f = (1/pi)(5/256)^(3/8) M^(-5/8) tau^(-3/8)  ->  M from (f_end, tau_end)
+    mc_s = (math.pi * f_end * tau_end ** 0.375 / (5.0 / 256.0) ** 0.375) ** -1.6
+    t0 = p["t0"]
+    tc = t0 + dur + tau_end
+    t = t0 + np.arange(n) * dt
+    hp, hc = chirp_0pn(t, tc, mc_s, dist_gpc * GPC, p["iota"], p["phi_c"])
+    return Source(t0, dt, n, hp, hc, p["beta"], p["lam"], p["psi"], tc, mc_s, dict(p))
+
+
+
+def sweep_params(nsrc=256, seed=SEED_BASE + 40, f_start=5e-4, f_end=2e-2, dt=5.0):
+    """Held-out chirps of the corrector's hybrid test: Newtonian chirps that
+    sweep from f_start to f_end over their grid (Mc log-U[3e5, 1e6] Msun,
+    tc U[2e7, 5e7] s, isotropic sky, cos(iota) U[-1, 1])."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nsrc):
+        mc = 10.0 ** rng.uniform(math.log10(3e5), 6.0)
+        beta, lam, psi = draw_sky(rng)
+        iota = math.acos(rng.uniform(-1.0, 1.0))
+        out.append(dict(mc=mc, tc=rng.uniform(2.0e7, 5.0e7), beta=beta, lam=lam, psi=psi, iota=iota,
+                        phi_c=rng.uniform(0.0, 2.0 * math.pi), f_start=f_start, f_end=f_end, dt=dt))
+    return out
+
+
+def sweep_source(p, dist_gpc=10.0):
+    mc_s = p["mc"] * T_SUN
+    tau0 = chirp_tau_of_f(p["f_start"], mc_s)
+    tau1 = chirp_tau_of_f(p["f_end"], mc_s)
+    dt = p["dt"]
+    n = int((tau0 - tau1) // dt)
+    t0 = p["tc"] - tau0
+    t = t0 + np.arange(n) * dt
+    hp, hc = chirp_0pn(t, p["tc"], mc_s, dist_gpc * GPC, p["iota"], p["phi_c"])
+    return Source(t0, dt, n, hp, hc, p["beta"], p["lam"], p["psi"], p["tc"], mc_s, dict(p))
+
+
 def monochromatic(t0, dt, n, f, amp_p=1.0, amp_c=1.0, phase=0.0):
     """h+ = amp_p cos(2 pi f t + phase), hx = amp_c sin(2 pi f t + phase)."""
     t = t0 + np.arange(n) * dt

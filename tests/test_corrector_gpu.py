@@ -1,0 +1,380 @@
+"""The learned LFA-link corrector on the GPU, through the C ABI.
+
+* own-time LFA links, features, forward pass and gradients against the FP64
+  references (oracle/__init__.links_lfa_own, oracle/corrector.py,
+  oracle/mlp.py);
+* Adam against its textbook definition; checkpoint round trip;
+* the full-link fallbacks (above the band, failed spot check) and the
+  below-band base link;
+* training on the GPU and what the trained network gains over the plain LFA,
+  per link and in the hybrid (the switch frequency it allows at the error of
+  the plain hybrid switched at 1e-3 Hz).
+
+BF16-scaled tolerances: the network runs with BF16 weights and activations
+(unit roundoff u = 2^-8) and FP32 accumulation; a forward pass rounds four
+times and a backward pass four more, so errors of a few u, i.e. ~1e-2 of the
+output scale, are the expected size.  Relative L2 errors per parameter block
+are held to 5e-2 (~13 u) and the loss to 1e-2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import F64_TOL, ORBITS, orbit_pair, rel_err, to_dev
+from tolerances import MIXED_TOL
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_09600_gb300 import build
+    build.build()
+    import paper_2505_09600_gb300 as L
+    L.load()
+    return L
+
+
+def _dev_source(s):
+    return dict(grid=s.grid, sky=(s.beta, s.lam, s.psi), hp32=to_dev(s.hp, 1), hc32=to_dev(s.hc, 1),
+                hp64=to_dev(s.hp, 0), hc64=to_dev(s.hc, 0))
+
+
+def _small_source(n=900, f0=3e-3, ratio=1.5, dt=5.0, seed=1):
+    p = synth.corrector_params(nsrc=1, seed=synth.SEED_BASE + 400 + seed, n=n)[0]
+    p.update(f0=f0, ratio=ratio, dt=dt)
+    return synth.corrector_source(p)
+
+
+# ---------------------------------------------------------------------------
+# parity of the building blocks
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_links_lfa_own(L, oracle_mod, precision):
+    s = _small_source(n=1300)
+    oo, lo = orbit_pair("kepler2_flex")
+    sky = (s.beta, s.lam, s.psi)
+    hp = s.hp.astype(np.float32).astype(np.float64) if precision == 1 else s.hp
+    hc = s.hc.astype(np.float32).astype(np.float64) if precision == 1 else s.hc
+    z = torch.full((6, s.n), float("nan"), device="cuda", dtype=torch.float64 if precision == 0 else torch.float32)
+    L.lisa_links_lfa_own(lo, sky, s.grid, to_dev(hp, precision), to_dev(hc, precision), precision, L.LFA_UNEQUAL,
+                         s.grid, z)
+    want = oracle_mod.links_lfa_own(oo, sky, s.grid, hp, hc, oracle_mod.LFA_UNEQUAL, s.grid)
+    got = z.cpu().numpy().astype(np.float64)
+    tol = np.full(6, F64_TOL) if precision == 0 else np.array(MIXED_TOL["z"])
+    assert np.all(rel_err(got, want) <= tol), rel_err(got, want)
+
+
+def test_features_match_oracle(L, oracle_mod):
+    from oracle import corrector as OC
+    s = _small_source(n=700, f0=4e-3)
+    oo, lo = orbit_pair("kepler2_flex")
+    d = _dev_source(s)
+    n = s.n
+    z = torch.empty((6, n), device="cuda", dtype=torch.float32)
+    L.lisa_links_lfa_own(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, L.LFA_UNEQUAL, s.grid, z)
+    y = torch.empty((6, n), device="cuda", dtype=torch.float64)
+    L.lisa_links_full(lo, d["sky"], s.grid, d["hp64"], d["hc64"], L.F64, s.grid, y)
+    feats = torch.full((n, 48), float("nan"), device="cuda")
+    scale = torch.empty(n, device="cuda")
+    ybase = torch.empty((6, n), device="cuda")
+    target = torch.empty((n, 6), device="cuda")
+    f_lo, f_hi = 1e-4, 2e-2
+    L.lisa_corrector_features(lo, d["sky"], s.grid, z, y, None, f_lo, f_hi, feats, scale, ybase, target)
+    zh = z.cpu().numpy().astype(np.float64)
+    yh = y.cpu().numpy()
+    T, kn = OC.link_geometry(oracle_mod, oo, s.grid, s.beta, s.lam)
+    eps = OC.link_eps(oracle_mod, oo, s.grid, s.beta, s.lam)
+    wf, ws, _, wt = OC.features(zh, T, kn, oo.L_m, s.dt, f_lo=f_lo, f_hi=f_hi, y_full=yh, eps=eps)
+    gf = feats.cpu().numpy().astype(np.float64)
+    # FP32 stencils of the same FP32 series (differences first), FP32
+    # evaluation of the orbit polynomial for the geometry columns
+    assert np.abs(gf[:, :34] - wf[:, :34]).max() < 2e-5
+    assert np.abs(gf[:, 34:40] - wf[:, 34:40]).max() < 2e-4
+    assert np.abs(gf[:, 40:46] - wf[:, 40:46]).max() < 2e-6
+    assert np.all(gf[:, 46:] == 0)
+    gs = scale.cpu().numpy()
+    assert np.allclose(gs, ws, rtol=2e-5, atol=0)
+    gb = ybase.cpu().numpy().astype(np.float64)
+    assert np.abs(gb - zh * (1 + eps)).max() <= 1e-7 * np.abs(zh).max()
+    m = 150
+    gt = target.cpu().numpy()[m:n - m]
+    assert np.abs(gt - wt[m:n - m]).max() < 2e-3 * max(1.0, np.abs(wt[m:n - m]).max())
+
+
+def _params(seed):
+    from oracle import mlp
+    return mlp.init_params(mlp.layer_shapes(), seed).astype(np.float32)
+
+
+def test_forward_matches_fp64_mlp(L):
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    p = _params(21)
+    x = np.zeros((1000, 48), dtype=np.float32)
+    x[:, :46] = rng.normal(size=(1000, 46))
+    c = L.LisaCorrector(p)
+    out = torch.empty((1000, 6), device="cuda")
+    c.forward(torch.as_tensor(x, device="cuda"), out)
+    got = out.cpu().numpy().astype(np.float64)
+    want, _, _ = mlp.forward(p.astype(np.float64), x[:, :46].astype(np.float64), mlp.layer_shapes())
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err < 3e-2, err
+    c.close()
+
+
+def test_gradient_matches_fp64_backprop(L):
+    from oracle import mlp
+    rng = np.random.default_rng(9)
+    shapes = mlp.layer_shapes()
+    p = _params(33)
+    M = 2000
+    x = np.zeros((M, 48), dtype=np.float32)
+    x[:, :46] = rng.normal(size=(M, 46))
+    want_out, _, _ = mlp.forward(p.astype(np.float64), x[:, :46].astype(np.float64), shapes)
+    t = (want_out + 0.5 * rng.normal(size=want_out.shape)).astype(np.float32)
+    c = L.LisaCorrector(p)
+    grad = torch.empty(c.n_params, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    c.gradient(torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda"), grad, loss)
+    g = grad.cpu().numpy().astype(np.float64)
+    ref = mlp.backward(p.astype(np.float64), x[:, :46].astype(np.float64), t.astype(np.float64), shapes)
+    lref = mlp.loss(p.astype(np.float64), x[:, :46].astype(np.float64), t.astype(np.float64), shapes)
+    assert loss.item() == pytest.approx(lref, rel=1e-2)
+    off = 0
+    for o, i in shapes:
+        for size in (o * i, o):
+            a, b = g[off:off + size], ref[off:off + size]
+            off += size
+            assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b), (o, i, size)
+            assert a @ b >= 0.998 * np.linalg.norm(a) * np.linalg.norm(b)
+    assert off == c.n_params
+    # a minibatch of the whole set (all rows drawn with replacement) has the
+    # same expected gradient; check only that it is finite and runs
+    c.gradient(torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda"), grad, loss, batch=512, seed=3)
+    assert torch.isfinite(grad).all()
+    c.close()
+
+
+def test_adam_step_is_textbook(L):
+    rng = np.random.default_rng(2)
+    p = _params(4)
+    c = L.LisaCorrector(p)
+    m = np.zeros_like(p, dtype=np.float64)
+    v = np.zeros_like(p, dtype=np.float64)
+    w = p.astype(np.float64)
+    for step in range(1, 4):
+        g = rng.normal(size=p.size).astype(np.float32)
+        c.adam_step(torch.as_tensor(g, device="cuda"), 1e-2)
+        m = 0.9 * m + 0.1 * g
+        v = 0.999 * v + 0.001 * g.astype(np.float64) ** 2
+        w = w - 1e-2 * (m / (1 - 0.9 ** step)) / (np.sqrt(v / (1 - 0.999 ** step)) + 1e-8)
+    st = c.get_state()
+    assert st["step"] == 3
+    assert np.abs(st["params"] - w).max() < 1e-5
+    c.close()
+
+
+def test_checkpoint_round_trip(L, tmp_path):
+    rng = np.random.default_rng(8)
+    x = torch.as_tensor(rng.normal(size=(300, 48)).astype(np.float32), device="cuda")
+    x[:, 46:] = 0
+    c = L.LisaCorrector(None, seed=77)
+    g = torch.as_tensor(rng.normal(size=c.n_params).astype(np.float32), device="cuda")
+    c.adam_step(g, 1e-3)
+    path = str(tmp_path / "corr.npz")
+    c.save(path)
+    a = torch.empty((300, 6), device="cuda")
+    c.forward(x, a)
+    d = L.LisaCorrector(None, seed=1)
+    d.load_checkpoint(path)
+    b = torch.empty((300, 6), device="cuda")
+    d.forward(x, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert d.get_state()["step"] == 1
+    # the library's own initialisation is seeded and bounded by 1/sqrt(n_in)
+    p = L.LisaCorrector(None, seed=77).get_state()["params"]
+    q = L.LisaCorrector(None, seed=77).get_state()["params"]
+    assert np.array_equal(p, q)
+    assert np.abs(p[:64 * 46]).max() <= 1 / math.sqrt(46) + 1e-7
+    c.close()
+    d.close()
+
+
+# ---------------------------------------------------------------------------
+# fallbacks
+# ---------------------------------------------------------------------------
+
+def _fallback_case(L):
+    s = _small_source(n=3000, f0=3e-3)
+    _, lo = orbit_pair("kepler2_flex")
+    d = _dev_source(s)
+    full = torch.empty((6, s.n), device="cuda")
+    L.lisa_links_full(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, s.grid, full)
+    return s, lo, d, full
+
+
+def test_above_band_tiles_use_full_links(L):
+    s, lo, d, full = _fallback_case(L)
+    c = L.LisaCorrector(None, seed=5)
+    c.configure(f_lo=0.0, f_hi=1e-5, spot_every=0)
+    y = torch.full((6, s.n), float("nan"), device="cuda")
+    c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
+    r = c.report()
+    assert torch.equal(y, full)
+    assert r["band_tiles"] == (s.n + 255) // 256 and r["status"] == 0
+    c.close()
+
+
+def test_below_band_uses_base_links(L):
+    s, lo, d, _ = _fallback_case(L)
+    c = L.LisaCorrector(None, seed=5)
+    c.configure(f_lo=1.0, f_hi=2.0, spot_every=0)
+    y = torch.full((6, s.n), float("nan"), device="cuda")
+    c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
+    z = torch.empty((6, s.n), device="cuda")
+    L.lisa_links_lfa_own(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, L.LFA_UNEQUAL, s.grid, z)
+    feats = torch.empty((s.n, 48), device="cuda")
+    scale = torch.empty(s.n, device="cuda")
+    ybase = torch.empty((6, s.n), device="cuda")
+    L.lisa_corrector_features(lo, d["sky"], s.grid, z, None, None, 1.0, 2.0, feats, scale, ybase)
+    torch.cuda.synchronize()
+    assert torch.equal(y, ybase)
+    assert float(scale.abs().max()) == 0.0
+    c.close()
+
+
+def test_failed_spot_check_recomputes_every_tile(L):
+    s, lo, d, full = _fallback_case(L)
+    c = L.LisaCorrector(None, seed=5)          # untrained network
+    c.configure(f_lo=0.0, f_hi=1.0, spot_every=4, spot_tol=1e-9)
+    y = torch.full((6, s.n), float("nan"), device="cuda")
+    c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
+    r = c.report()
+    ntile = (s.n + 255) // 256
+    assert r["status"] == L.LISA_ECORRECTOR
+    assert r["spot_tiles"] == (ntile + 3) // 4 and r["spot_failed"] >= 1
+    assert r["fallback_tiles"] == ntile - r["spot_tiles"]
+    assert torch.equal(y, full)
+    # counters were reset by the report; a lenient tolerance passes
+    c.configure(f_lo=0.0, f_hi=1.0, spot_every=1, spot_tol=10.0)
+    c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
+    r = c.report()
+    assert r["status"] == 0 and r["spot_tiles"] == ntile and r["spot_failed"] == 0
+    c.close()
+
+
+# ---------------------------------------------------------------------------
+# training and gain
+# ---------------------------------------------------------------------------
+
+N_TRAIN, N_HELD = 128, 24
+
+
+@pytest.fixture(scope="module")
+def trained(L):
+    from paper_2505_09600_gb300 import corrector as CT
+    _, lo = orbit_pair("kepler2_flex")
+    params = synth.corrector_params(nsrc=N_TRAIN + N_HELD, seed=synth.SEED_BASE + 4, n=4096)
+    srcs = [synth.corrector_source(p) for p in params]
+    feats, target = CT.training_set(lo, [_dev_source(s) for s in srcs[:N_TRAIN]])
+    c = L.LisaCorrector(None, seed=2505)
+    steps = 4000
+    losses = torch.empty(steps, device="cuda")
+    c.train(feats, target, steps=steps, batch=8192, lr_max=2e-3, lr_min=2e-5, seed=11, losses=losses)
+    torch.cuda.synchronize()
+    return c, lo, srcs[N_TRAIN:], losses.cpu().numpy(), float(target.square().sum(1).mean())
+
+
+def test_training_reduces_the_loss(trained):
+    _, _, _, losses, var = trained
+    assert np.isfinite(losses).all()
+    first, last = losses[:50].mean(), losses[-200:].mean()
+    print("corrector loss: first %.4g last %.4g (target mean square %.4g)" % (first, last, var))
+    assert last < 0.02 * var
+
+
+def test_link_gain_on_held_out_sources(L, trained):
+    from paper_2505_09600_gb300 import corrector as CT
+    c, lo, held, _, _ = trained
+    c.configure(f_lo=1e-4, f_hi=2e-2, spot_every=64, spot_tol=0.05)
+    rows = []
+    for s in held:
+        d = _dev_source(s)
+        n, m = s.n, CT.edge_margin(s.dt)
+        yref = torch.empty((6, n), device="cuda", dtype=torch.float64)
+        L.lisa_links_full(lo, d["sky"], s.grid, d["hp64"], d["hc64"], L.F64, s.grid, yref)
+        z = torch.empty((6, n), device="cuda")
+        L.lisa_links_lfa_own(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, L.LFA_UNEQUAL, s.grid, z)
+        y = torch.empty((6, n), device="cuda")
+        c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
+        ref = yref.cpu().numpy()[:, m:n - m]
+        scale = np.abs(ref).max()
+        e_lfa = np.abs(z.cpu().numpy()[:, m:n - m] - ref).max() / scale
+        e_cor = np.abs(y.cpu().numpy()[:, m:n - m] - ref).max() / scale
+        rows.append((s.meta["f0"], s.meta["f0"] * s.meta["ratio"], e_lfa, e_cor))
+    r = c.report()
+    assert r["status"] == 0, r
+    rows = np.array(rows)
+    for f0, f1, a, b in rows:
+        print("held-out f %.2e..%.2e  LFA %.2e  corrected %.2e  gain %.1f" % (f0, f1, a, b, a / b))
+    # where the LFA error is well above the FP32 floor of the mixed links
+    sel = rows[:, 2] > 2e-4
+    assert sel.sum() >= 8
+    gains = rows[sel, 2] / rows[sel, 3]
+    assert np.median(gains) >= 10.0, gains
+    assert np.all(rows[:, 3] <= np.maximum(rows[:, 2], 2e-5))
+
+
+F_H = (1e-3, 1.5e-3, 2e-3, 3e-3, 4e-3, 5e-3, 6e-3, 8e-3, 1e-2)
+
+
+def _lfa_side_error(got, ref, i_end, m):
+    g, r = got[:, m:i_end], ref[:, m:i_end]
+    return np.abs(g - r).max() / np.abs(r).max()
+
+
+def test_hybrid_switch_frequency_gain(L, trained):
+    from paper_2505_09600_gb300 import corrector as CT
+    c, lo, _, _, _ = trained
+    c.configure(f_lo=1e-4, f_hi=2e-2, spot_every=64, spot_tol=0.05)
+    ratios = []
+    for p in synth.sweep_params(nsrc=6, seed=synth.SEED_BASE + 41):
+        s = synth.sweep_source(p)
+        d = _dev_source(s)
+        n, m = s.n, CT.edge_margin(s.dt)
+        ref = torch.empty((3, n), device="cuda", dtype=torch.float64)
+        L.lisa_response_full(lo, d["sky"], s.grid, d["hp64"], d["hc64"], L.F64, L.TDI20, L.AET, s.grid, ref)
+        ref = ref.cpu().numpy()
+        Tw = 800 * s.dt
+        out = torch.empty((3, n), device="cuda")
+
+        def i_end(tH):
+            return int(min(n, max(0, math.floor((tH + Tw / 2 - s.t0) / s.dt) + 1)))
+
+        tH = L.lisa_t_hyb_from_f(1e-3, s.mc_s, s.tc)
+        L.lisa_response_hybrid(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, L.TDI20, L.LFA_UNEQUAL, L.AET,
+                               tH, 0.0, 0.0, s.grid, out)
+        e0 = _lfa_side_error(out.cpu().numpy(), ref, i_end(tH), m)
+        best = 1e-3
+        errs = []
+        for fH in F_H:
+            tH = L.lisa_t_hyb_from_f(fH, s.mc_s, s.tc)
+            c.hybrid(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.TDI20, L.AET, tH, 0.0, 0.0, s.grid, out)
+            e = _lfa_side_error(out.cpu().numpy(), ref, i_end(tH), m)
+            errs.append(e)
+            if e <= e0:
+                best = fH
+        print("Mc %.3g: plain hybrid at 1e-3 Hz err %.2e; corrected %s -> f_H %.3g" %
+              (p["mc"], e0, " ".join("%.1e" % e for e in errs), best))
+        ratios.append(best / 1e-3)
+    assert c.report()["status"] == 0
+    print("switch-frequency ratio R per source:", ratios)
+    assert np.median(ratios) >= 3.0
