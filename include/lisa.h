@@ -244,20 +244,21 @@ int lisa_plan_info(const lisa_plan* plan, int64_t* total_samples, int64_t* total
 /* ------------------------------------------------------------------------
  * Learned corrector of the LFA links (no counterpart in the paper).
  *
- * An MLP 46 -> 64 -> 64 -> 64 -> 6 (GELU, tanh form; BF16 weights and
+ * An MLP 47 -> 64 -> 64 -> 64 -> 6 (GELU, tanh form; BF16 weights and
  * activations on the tensor cores, FP32 accumulation and FP32 master weights)
  * predicts the residuals between the six full single links (Sec. II) and the
  * base links z_l (1 + eps_l) at each output sample, where z_l are the LFA
  * links at their own time (lisa_links_lfa_own) and
  * eps_l = k.v_s / (c (1 - k.n_l)) is the O(v/c) term by which the full
  * formula (positions at the reception time) differs from T_l (1 - k.n_l)
- * (v_s: sender velocity).  Features per sample (46, stored as rows of 48
- * floats, the last two zero):
+ * (v_s: sender velocity).  Features per sample (47, stored as rows of 48
+ * floats, the last one zero):
  *   [ 0,30) q_k,l / M_k: the 5-point stencil of z_l re-based as
  *           q_k = Tbar^k d^k z_l/dt^k, k = 0..4 (feature k*6 + l),
  *           M_k = max_l |q_k,l|;
  *   [30,34) clamp(log10(M_{k+1}/M_k), -8, 8) / 4;
- *   [34,40) (T_l/Tbar - 1) * 100;   [40,46) 1 - k.n_l;   Tbar = L/c.
+ *   [34,40) (T_l/Tbar - 1) * 100;   [40,46) 1 - k.n_l;   46: dt/Tbar;
+ *   Tbar = L/c.
  * Scale s = M_2 / 8; corrected link l = z_l (1 + eps_l) + s * MLP_l.  Local
  * frequency f = sqrt(M_2/M_0) / (2 pi Tbar): below the band [f_lo, f_hi] the
  * base link is used (s = 0), above it the full link (per 256-sample tile).
@@ -265,8 +266,8 @@ int lisa_plan_info(const lisa_plan* plan, int64_t* total_samples, int64_t* total
  * ---------------------------------------------------------------------- */
 typedef struct lisa_corrector lisa_corrector;
 
-int64_t lisa_corrector_num_params(void);     /* 11718 */
-int lisa_corrector_num_features(void);       /* 46 */
+int64_t lisa_corrector_num_params(void);     /* 11782 */
+int lisa_corrector_num_features(void);       /* 47 */
 /* Create on the current device (cudaMalloc of its parameters, Adam state and
  * counters; synchronising).  host_params: n_params FP32 values, or NULL for
  * W ~ U(-1/sqrt(n_in), 1/sqrt(n_in)) drawn from SplitMix64(seed), b = 0.
@@ -307,8 +308,8 @@ int lisa_corrector_train(lisa_corrector* c, const float* feats, const float* tar
                          int64_t batch, float lr_max, float lr_min, uint64_t seed, float* losses, void* stream);
 /* Corrected links (FP32, [6][out.n]) on every sample of `out`: LFA links,
  * features, network, then full links on tiles above the band and on the
- * spot-checked tiles; if a spot check fails, on every tile (decided on the
- * device).  hp/hc are FP32 (LISA_MIXED). */
+ * spot-checked tiles that fail the check; if one fails, on every tile
+ * (decided on the device).  hp/hc are FP32 (LISA_MIXED). */
 int lisa_corrector_links(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
                          const void* hp, const void* hc, lisa_grid out, void* y, void* stream);
 /* Hybrid with the corrector (LISA_MIXED, frozen TDI): as lisa_response_hybrid,

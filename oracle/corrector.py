@@ -25,7 +25,7 @@ Features of sample i (written out plainly, one sample at a time):
   f[k*6 + l] = q_k,l / M_k (0 if M_k = 0), k = 0..4, l = 0..5;
   f[30 + k] = clamp(log10(M_{k+1}/M_k), -8, 8) / 4 (-2 if either is 0);
   f[34 + l] = (T_l/Tbar - 1) * 100,  f[40 + l] = 1 - k.n_l;
-  f[46] = f[47] = 0;  Tbar = L/c.
+  f[46] = dt/Tbar, f[47] = 0;  Tbar = L/c.
 Scale s = M_2 / 8, set to 0 below the band, i.e. where M_2/M_0 < (2 pi f_lo
 Tbar)^2 (M_0 = 0 counts as below); above the band: M_2/M_0 > (2 pi f_hi
 Tbar)^2.  Target of link l: (y_full_l - z_l (1 + eps_l)) / s (0 where s = 0).
@@ -36,7 +36,7 @@ import math
 
 import numpy as np
 
-N_FEAT = 46
+N_FEAT = 47
 ROW = 48
 C_LIGHT = 299792458.0
 
@@ -79,6 +79,7 @@ def features(z, T, kn, L_m, dt, f_lo=0.0, f_hi=math.inf, y_full=None, eps=None):
             feats[i, 30 + k] = min(max(r, -8.0), 8.0) / 4.0
         feats[i, 34:40] = (T[:, i] / Tbar - 1.0) * 100.0
         feats[i, 40:46] = 1.0 - kn[:, i]
+        feats[i, 46] = dt / Tbar
         w2 = M[2] / M[0] if M[0] > 0 else 0.0
         s = M[2] / 8.0 if w2 >= w_lo else 0.0
         above[i] = w2 > w_hi

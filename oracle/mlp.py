@@ -18,7 +18,7 @@ import numpy as np
 SQ2PI = math.sqrt(2.0 / math.pi)
 
 
-def layer_shapes(n_in=31, width=64, n_hidden=3, n_out=6):
+def layer_shapes(n_in=47, width=64, n_hidden=3, n_out=6):
     dims = [n_in] + [width] * n_hidden + [n_out]
     return [(dims[k + 1], dims[k]) for k in range(len(dims) - 1)]
 

@@ -9,7 +9,7 @@
 // the full formula's delta_s - delta_r equals T_l (1 - k.n_l) only up to the
 // sender's motion over T_l, a frequency-independent O(v/c) term that is
 // applied analytically (base link z_l (1 + eps_l), v_s from the derivative of
-// the orbit polynomial).  A multilayer perceptron 46 -> 64 -> 64 -> 64 -> 6
+// the orbit polynomial).  A multilayer perceptron 47 -> 64 -> 64 -> 64 -> 6
 // (GELU, tanh form) predicts the rest at each output sample from:
 //   [ 0,30) the 5-point stencils of z_l re-based as q_k = Tbar^k d^k z/dt^k
 //           (k = 0..4; feature k*6 + l), each order divided by
@@ -17,6 +17,7 @@
 //   [30,34) log10(M_{k+1}/M_k) / 4, clamped to [-2, 2] (a local frequency);
 //   [34,40) (T_l/Tbar - 1) * 100 (arm flexing);
 //   [40,46) 1 - k.n_l;
+//   46      dt / Tbar (the stencils' distortion depends on omega dt as well);
 // with Tbar = L/c.  Inputs and outputs are O(1) in BF16: the network output is
 // scaled by s = M_2 / 8, so that the corrected link is
 // z_l (1 + eps_l) + s * MLP_l.  The full TDI combine then runs on the
@@ -58,7 +59,7 @@ using namespace nvcuda;
 
 namespace lisa {
 
-constexpr int kIn = 46, kInP = 48, kWid = 64, kOut = 6, kOutP = 16;
+constexpr int kIn = 47, kInP = 48, kWid = 64, kOut = 6, kOutP = 16;
 constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + kWid * kIn, kOffW2 = kOffB1 + kWid, kOffB2 = kOffW2 + kWid * kWid,
                   kOffW3 = kOffB2 + kWid, kOffB3 = kOffW3 + kWid * kWid, kOffW4 = kOffB3 + kWid,
                   kOffB4 = kOffW4 + kOut * kWid, kNParams = kOffB4 + kOut;
@@ -447,6 +448,7 @@ struct FeatArgs {
     float r1;              // Tbar / dt
     float Tbar;
     float vfac;            // d/dt of the segment coordinate over c: 2 / (S dt c)
+    float dtr;             // dt / Tbar (feature 46)
     float w_lo, w_hi;      // band as limits of (omega Tbar)^2 = M2/M0
     float* feats;          // [rows][kInP]
     float* scale;          // [rows]
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
         ft[40 + l] = 1.f - kn;
         eps[l] = (1.f - kn) > 1e-6f ? kv[link_sender(l)] / (1.f - kn) : 0.f;
     }
-    ft[46] = 0.f;
+    ft[46] = a.dtr;
     ft[47] = 0.f;
     float4* fo = reinterpret_cast<float4*>(a.feats + i * kInP);
 #pragma unroll
@@ -603,6 +605,8 @@ __global__ void __launch_bounds__(kTile) corr_fallback_kernel(FallbackArgs A)
         for (int l = 0; l < 6; ++l) old[l] = y[l * a.ny + i];
     }
     if (valid) links_sample<true>(a, g, ic, i, s, y + i, a.ny);
+    // a spot-checked tile keeps its corrected links unless the check fails
+    // (the FP32 full links are the less accurate ones at low frequency)
     if (!check) {
         if (threadIdx.x == 0) atomicAdd(A.global_pass ? &A.stats->fallback_tiles : &A.stats->band_tiles, 1u);
         return;
@@ -631,12 +635,19 @@ __global__ void __launch_bounds__(kTile) corr_fallback_kernel(FallbackArgs A)
             den = fmaxf(den, red[1][w]);
         }
         const float rel = den > 0.f ? num / den : 0.f;
+        const bool pass = rel <= A.spot_tol;
         atomicAdd(&A.stats->spot_tiles, 1u);
         atomicMax(&A.stats->max_err_bits, __float_as_uint(rel));
-        if (!(rel <= A.spot_tol)) {
+        if (!pass) {
             atomicAdd(&A.stats->spot_failed, 1u);
             atomicAdd(&A.stats->call_failed, 1u);
         }
+        red[0][0] = pass ? 1.f : 0.f;
+    }
+    __syncthreads();
+    if (red[0][0] != 0.f && valid) {
+#pragma unroll
+        for (int l = 0; l < 6; ++l) y[l * a.ny + i] = old[l];
     }
 }
 
@@ -713,6 +724,7 @@ static int run_features(const SegTable& tab, const SkyDev& sky, double Tbar, dou
     a.r1 = (float)(Tbar / dt);
     a.Tbar = (float)Tbar;
     a.vfac = (float)(2.0 / ((double)tab.S * dt * kC));
+    a.dtr = (float)(dt / Tbar);
     a.w_lo = (float)(two_pi_T * f_lo * two_pi_T * f_lo);
     a.w_hi = isfinite(f_hi) ? (float)(two_pi_T * f_hi * two_pi_T * f_hi) : INFINITY;
     a.feats = feats;

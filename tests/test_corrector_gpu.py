@@ -93,19 +93,26 @@ def test_features_match_oracle(L, oracle_mod):
     eps = OC.link_eps(oracle_mod, oo, s.grid, s.beta, s.lam)
     wf, ws, _, wt = OC.features(zh, T, kn, oo.L_m, s.dt, f_lo=f_lo, f_hi=f_hi, y_full=yh, eps=eps)
     gf = feats.cpu().numpy().astype(np.float64)
-    # FP32 stencils of the same FP32 series (differences first), FP32
-    # evaluation of the orbit polynomial for the geometry columns
-    assert np.abs(gf[:, :34] - wf[:, :34]).max() < 2e-5
-    assert np.abs(gf[:, 34:40] - wf[:, 34:40]).max() < 2e-4
+    assert np.isfinite(gf).all()
+    # Interior samples (away from the ends, where h switches on abruptly and
+    # the stencils of z are ill-conditioned in FP32): FP32 stencils of the
+    # same FP32 series (differences first), FP32 evaluation of the orbit
+    # polynomial for the geometry columns.
+    from paper_2505_09600_gb300.corrector import edge_margin
+    m = edge_margin(s.dt)
+    sl = slice(m, n - m)
+    d = np.abs(gf[sl, :34] - wf[sl, :34])
+    k = np.unravel_index(np.argmax(d), d.shape)
+    assert d.max() < 2e-5, (d.max(), k[0] + m, k[1])
+    assert np.abs(gf[sl, 34:40] - wf[sl, 34:40]).max() < 2e-4
     assert np.abs(gf[:, 40:46] - wf[:, 40:46]).max() < 2e-6
-    assert np.all(gf[:, 46:] == 0)
+    assert np.allclose(gf[:, 46], wf[:, 46], rtol=1e-6) and np.all(gf[:, 47] == 0)
     gs = scale.cpu().numpy()
-    assert np.allclose(gs, ws, rtol=2e-5, atol=0)
+    assert np.allclose(gs[sl], ws[sl], rtol=2e-5, atol=0)
     gb = ybase.cpu().numpy().astype(np.float64)
     assert np.abs(gb - zh * (1 + eps)).max() <= 1e-7 * np.abs(zh).max()
-    m = 150
-    gt = target.cpu().numpy()[m:n - m]
-    assert np.abs(gt - wt[m:n - m]).max() < 2e-3 * max(1.0, np.abs(wt[m:n - m]).max())
+    gt = target.cpu().numpy()[sl]
+    assert np.abs(gt - wt[sl]).max() < 2e-3 * max(1.0, np.abs(wt[sl]).max())
 
 
 def _params(seed):
@@ -118,12 +125,12 @@ def test_forward_matches_fp64_mlp(L):
     rng = np.random.default_rng(5)
     p = _params(21)
     x = np.zeros((1000, 48), dtype=np.float32)
-    x[:, :46] = rng.normal(size=(1000, 46))
+    x[:, :47] = rng.normal(size=(1000, 47))
     c = L.LisaCorrector(p)
     out = torch.empty((1000, 6), device="cuda")
     c.forward(torch.as_tensor(x, device="cuda"), out)
     got = out.cpu().numpy().astype(np.float64)
-    want, _, _ = mlp.forward(p.astype(np.float64), x[:, :46].astype(np.float64), mlp.layer_shapes())
+    want, _, _ = mlp.forward(p.astype(np.float64), x[:, :47].astype(np.float64), mlp.layer_shapes())
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err < 3e-2, err
     c.close()
@@ -136,16 +143,16 @@ def test_gradient_matches_fp64_backprop(L):
     p = _params(33)
     M = 2000
     x = np.zeros((M, 48), dtype=np.float32)
-    x[:, :46] = rng.normal(size=(M, 46))
-    want_out, _, _ = mlp.forward(p.astype(np.float64), x[:, :46].astype(np.float64), shapes)
+    x[:, :47] = rng.normal(size=(M, 47))
+    want_out, _, _ = mlp.forward(p.astype(np.float64), x[:, :47].astype(np.float64), shapes)
     t = (want_out + 0.5 * rng.normal(size=want_out.shape)).astype(np.float32)
     c = L.LisaCorrector(p)
     grad = torch.empty(c.n_params, device="cuda")
     loss = torch.empty(1, device="cuda")
     c.gradient(torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda"), grad, loss)
     g = grad.cpu().numpy().astype(np.float64)
-    ref = mlp.backward(p.astype(np.float64), x[:, :46].astype(np.float64), t.astype(np.float64), shapes)
-    lref = mlp.loss(p.astype(np.float64), x[:, :46].astype(np.float64), t.astype(np.float64), shapes)
+    ref = mlp.backward(p.astype(np.float64), x[:, :47].astype(np.float64), t.astype(np.float64), shapes)
+    lref = mlp.loss(p.astype(np.float64), x[:, :47].astype(np.float64), t.astype(np.float64), shapes)
     assert loss.item() == pytest.approx(lref, rel=1e-2)
     off = 0
     for o, i in shapes:
@@ -184,7 +191,7 @@ def test_adam_step_is_textbook(L):
 def test_checkpoint_round_trip(L, tmp_path):
     rng = np.random.default_rng(8)
     x = torch.as_tensor(rng.normal(size=(300, 48)).astype(np.float32), device="cuda")
-    x[:, 46:] = 0
+    x[:, 47:] = 0
     c = L.LisaCorrector(None, seed=77)
     g = torch.as_tensor(rng.normal(size=c.n_params).astype(np.float32), device="cuda")
     c.adam_step(g, 1e-3)
@@ -203,7 +210,7 @@ def test_checkpoint_round_trip(L, tmp_path):
     p = L.LisaCorrector(None, seed=77).get_state()["params"]
     q = L.LisaCorrector(None, seed=77).get_state()["params"]
     assert np.array_equal(p, q)
-    assert np.abs(p[:64 * 46]).max() <= 1 / math.sqrt(46) + 1e-7
+    assert np.abs(p[:64 * 47]).max() <= 1 / math.sqrt(47) + 1e-7
     c.close()
     d.close()
 
@@ -260,7 +267,7 @@ def test_failed_spot_check_recomputes_every_tile(L):
     r = c.report()
     ntile = (s.n + 255) // 256
     assert r["status"] == L.LISA_ECORRECTOR
-    assert r["spot_tiles"] == (ntile + 3) // 4 and r["spot_failed"] >= 1
+    assert r["spot_tiles"] == (ntile + 3) // 4 and r["spot_failed"] == r["spot_tiles"]
     assert r["fallback_tiles"] == ntile - r["spot_tiles"]
     assert torch.equal(y, full)
     # counters were reset by the report; a lenient tolerance passes
@@ -286,7 +293,7 @@ def trained(L):
     srcs = [synth.corrector_source(p) for p in params]
     feats, target = CT.training_set(lo, [_dev_source(s) for s in srcs[:N_TRAIN]])
     c = L.LisaCorrector(None, seed=2505)
-    steps = 4000
+    steps = 6000
     losses = torch.empty(steps, device="cuda")
     c.train(feats, target, steps=steps, batch=8192, lr_max=2e-3, lr_min=2e-5, seed=11, losses=losses)
     torch.cuda.synchronize()
@@ -333,7 +340,7 @@ def test_link_gain_on_held_out_sources(L, trained):
     assert np.all(rows[:, 3] <= np.maximum(rows[:, 2], 2e-5))
 
 
-F_H = (1e-3, 1.5e-3, 2e-3, 3e-3, 4e-3, 5e-3, 6e-3, 8e-3, 1e-2)
+F_H = (1e-3, 1.5e-3, 2e-3, 3e-3, 4e-3, 6e-3, 8e-3, 1e-2, 1.4e-2, 2e-2)
 
 
 def _lfa_side_error(got, ref, i_end, m):
@@ -377,4 +384,4 @@ def test_hybrid_switch_frequency_gain(L, trained):
         ratios.append(best / 1e-3)
     assert c.report()["status"] == 0
     print("switch-frequency ratio R per source:", ratios)
-    assert np.median(ratios) >= 3.0
+    assert np.median(ratios) >= 5.0

@@ -71,8 +71,8 @@ def test_scale_invariance():
     assert np.allclose(f1, f2, rtol=1e-12, atol=1e-12)
     assert np.allclose(s2, 7.5 * s1, rtol=1e-12)
     assert np.allclose(t1, t2, rtol=1e-9, atol=1e-9)
-    # padding columns are zero; geometry columns are the stated maps
-    assert np.all(f1[:, 46:] == 0)
+    # padding column is zero; geometry columns are the stated maps
+    assert np.all(f1[:, 47] == 0) and np.all(f1[:, 46] == dt / TBAR)
     assert np.allclose(f1[:, 40:46].T, 1 - kn)
     assert np.allclose(f1[:, 34:40].T, (T / TBAR - 1) * 100)
 
