@@ -4,8 +4,10 @@ kernels; torch provides the device buffers).
 
 Each source contributes the samples that are at least `edge_margin` samples
 away from both ends of its grid: nearer the ends the retarded times
-t - k.R/c (|k.R/c| <= 1 AU/c ~ 500 s) reach outside the sampled waveform,
-where h is zero by convention and neither link form is meaningful.
+t - k.R/c (|k.R/c| <= 1 AU/c ~ 500 s) and their 32-point stencils reach
+outside the sampled waveform, where h is zero by convention and neither link
+form is meaningful.  The library itself takes the full links there (at most
+1 AU/c + 2 T_max + 20 dt from either end, T_max < 50 s for the orbits here).
 """
 from __future__ import annotations
 
@@ -14,9 +16,12 @@ import math
 from . import native as N
 
 
-def edge_margin(dt, L_m=2.5e9):
+AU_LIGHT_S = 1.495978707e11 / 299792458.0
+
+
+def edge_margin(dt):
     """Samples near either grid end excluded from training and from errors."""
-    return int(math.ceil((600.0 + 8.0 * L_m / 299792458.0) / dt)) + 8
+    return int(math.ceil((AU_LIGHT_S + 100.0 + 20.0 * dt) / dt)) + 4
 
 
 def training_rows(sources):

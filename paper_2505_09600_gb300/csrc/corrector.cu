@@ -28,7 +28,10 @@
 // link (no correction: the LFA is already closer than at the band's lower
 // edge); above it the full link (the whole 256-sample tile is recomputed by
 // the full links kernel).  Every spot_every-th tile is also recomputed with
-// full links and compared; if any compared tile differs by more than
+// full links and compared (band flags and spot checks only where the retarded
+// times stay on the h grid; samples whose retarded times leave it, at the grid
+// ends, take the full links, the form whose boundary convention the reference
+// results follow); if any compared tile differs by more than
 // spot_tol (max abs difference / max abs full link over the tile), every
 // remaining tile is recomputed with full links in the same call (device-side
 // decision, no host synchronisation) and the failure is counted.
@@ -454,6 +457,7 @@ struct FeatArgs {
     float* scale;          // [rows]
     float* ybase;          // [6][stride] base links z (1 + eps), or null
     int* tile_flag;        // [ceil(rows / kTile)] or null: set where above the band
+    int64_t safe_lo, safe_hi;  // samples whose retarded times stay on the h grid (flags only there)
     const double* y_full;  // [6][stride] full links, or null (targets)
     const double* z_ref;   // [6][stride] or null (targets; default z)
     float* target;         // [rows][kOut] or null
@@ -542,7 +546,7 @@ __global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
     float sc = 0.125f * mk[2];
     const float w2 = mk[0] > 0.f ? mk[2] / mk[0] : 0.f;
     if (!(w2 >= a.w_lo)) sc = 0.f;                    // below the band (or no signal): plain LFA link
-    if (w2 > a.w_hi && a.tile_flag) atomicOr(&a.tile_flag[i / kTile], 1);
+    if (w2 > a.w_hi && a.tile_flag && i >= a.safe_lo && i < a.safe_hi) atomicOr(&a.tile_flag[i / kTile], 1);
     a.scale[i] = sc;
     if (a.ybase) {
 #pragma unroll
@@ -574,6 +578,7 @@ struct FallbackArgs {
     int spot_every;        // 0: no spot checks
     float spot_tol;
     int global_pass;       // 0: flagged and spot tiles; 1: all others if this call failed a spot check
+    int64_t safe_lo, safe_hi;  // spot checks only on tiles inside [safe_lo, safe_hi)
     CorrStats* stats;
 };
 
@@ -585,10 +590,11 @@ __global__ void __launch_bounds__(kTile) corr_fallback_kernel(FallbackArgs A)
     const LinksArgs& a = A.la;
     const int64_t tile = a.tile0 + blockIdx.x;
     const int flag = A.tile_flag[tile];
-    const bool spot = A.spot_every > 0 && (tile % A.spot_every) == 0;
+    const bool inside = tile * kTile >= A.safe_lo && (tile + 1) * kTile <= A.safe_hi;
+    const bool spot = A.spot_every > 0 && (tile % A.spot_every) == 0 && inside;
     if (A.global_pass) {
         if (flag || spot || A.stats->call_failed == 0) return;
-    } else if (!flag && !spot) {
+    } else if (!flag && !spot && inside) {
         return;
     }
     const int64_t i0 = tile * (int64_t)kTile;
@@ -604,19 +610,38 @@ __global__ void __launch_bounds__(kTile) corr_fallback_kernel(FallbackArgs A)
 #pragma unroll
         for (int l = 0; l < 6; ++l) old[l] = y[l * a.ny + i];
     }
-    if (valid) links_sample<true>(a, g, ic, i, s, y + i, a.ny);
+    // edge tiles outside the band and the checks: full links only on the
+    // samples whose retarded times leave the h grid
+    const bool whole = A.global_pass || flag || spot;
+    if (valid && (whole || i < A.safe_lo || i >= A.safe_hi)) links_sample<true>(a, g, ic, i, s, y + i, a.ny);
     // a spot-checked tile keeps its corrected links unless the check fails
     // (the FP32 full links are the less accurate ones at low frequency)
     if (!check) {
-        if (threadIdx.x == 0) atomicAdd(A.global_pass ? &A.stats->fallback_tiles : &A.stats->band_tiles, 1u);
+        if (threadIdx.x == 0 && (A.global_pass || flag))
+            atomicAdd(A.global_pass ? &A.stats->fallback_tiles : &A.stats->band_tiles, 1u);
         return;
     }
+    // The FP32 full link is itself uncertain by about its interpolation
+    // rounding (~5e-7 of |h|) divided by 2 (1 - k.n_l): differences within
+    // that bound (1e-6 |h|max / (1 - k.n_l)) are not counted.
+    float hmax = 0.f;
+    for (int k = threadIdx.x; k < s.wlen; k += blockDim.x) hmax = fmaxf(hmax, fmaxf(fabsf(s.win[k].x), fabsf(s.win[k].y)));
+    for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = hmax;
+    __syncthreads();
+    hmax = red[0][0];
+    for (int w = 1; w < kTile / 32; ++w) hmax = fmaxf(hmax, red[0][w]);
+    if (s.wlen == 0) hmax = 0.f;
+    __syncthreads();
     float num = 0.f, den = 0.f;
     if (valid) {
 #pragma unroll
         for (int l = 0; l < 6; ++l) {
+            const float kn = (float)(a.sky.k[0] * g.b[kQN + 3 * l][0] + a.sky.k[1] * g.b[kQN + 3 * l + 1][0]
+                                     + a.sky.k[2] * g.b[kQN + 3 * l + 2][0]);
+            const float eb = 1e-6f * hmax / fmaxf(1.f - kn, 1e-6f);
             const float v = y[l * a.ny + i];
-            num = fmaxf(num, fabsf(v - old[l]));
+            num = fmaxf(num, fabsf(v - old[l]) - eb);
             den = fmaxf(den, fabsf(v));
         }
     }
@@ -634,7 +659,7 @@ __global__ void __launch_bounds__(kTile) corr_fallback_kernel(FallbackArgs A)
             num = fmaxf(num, red[0][w]);
             den = fmaxf(den, red[1][w]);
         }
-        const float rel = den > 0.f ? num / den : 0.f;
+        const float rel = den > 0.f ? fmaxf(num, 0.f) / den : 0.f;
         const bool pass = rel <= A.spot_tol;
         atomicAdd(&A.stats->spot_tiles, 1u);
         atomicMax(&A.stats->max_err_bits, __float_as_uint(rel));
@@ -709,8 +734,8 @@ static int run_forward(const lisa_corrector* c, const float* x, int64_t M, int l
 
 static int run_features(const SegTable& tab, const SkyDev& sky, double Tbar, double dt, const float* z,
                         int64_t stride, int64_t nz, int64_t rows, double f_lo, double f_hi, float* feats,
-                        float* scale, float* ybase, int* tile_flag, const double* y_full, const double* z_ref,
-                        float* target, cudaStream_t st)
+                        float* scale, float* ybase, int* tile_flag, int64_t safe_lo, int64_t safe_hi,
+                        const double* y_full, const double* z_ref, float* target, cudaStream_t st)
 {
     if (rows <= 0) return LISA_OK;
     const double two_pi_T = 2.0 * M_PI * Tbar;
@@ -731,6 +756,8 @@ static int run_features(const SegTable& tab, const SkyDev& sky, double Tbar, dou
     a.scale = scale;
     a.ybase = ybase;
     a.tile_flag = tile_flag;
+    a.safe_lo = safe_lo;
+    a.safe_hi = safe_hi;
     a.y_full = y_full;
     a.z_ref = z_ref;
     a.target = target;
@@ -738,6 +765,20 @@ static int run_features(const SegTable& tab, const SkyDev& sky, double Tbar, dou
     corr_features_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
     prof_after(st);
     return cuda_status(cudaGetLastError(), "corr_features_kernel launch");
+}
+
+// Output samples [lo, hi) whose retarded times t - k.R/c - T (|k.R/c| <= 1 AU/c)
+// and their 32-point stencils stay on the h grid.  Nearer the ends both link
+// forms see the zero padding of h, and neither band flags nor spot checks
+// are meaningful there.
+static void safe_range(const lisa_grid& out, const lisa_grid& hg, double Tmax, int64_t& lo, int64_t& hi)
+{
+    const double reach = kAU / kC + 2.0 * Tmax + 20.0 * hg.dt;
+    const double a = (hg.t0 + reach - out.t0) / out.dt;
+    const double b = (hg.t0 + (double)hg.n * hg.dt - reach - out.t0) / out.dt;
+    lo = a <= 0.0 ? 0 : (a >= (double)out.n ? out.n : (int64_t)ceil(a));
+    hi = b <= 0.0 ? 0 : (b >= (double)out.n ? out.n : (int64_t)floor(b));
+    if (hi < lo) hi = lo;
 }
 
 // Corrected links on out-grid samples [0, rows) into y ([6][out.n], FP32):
@@ -763,8 +804,10 @@ static int corrected_links(lisa_corrector* c, const lisa_orbit* orbit, const lis
     LISA_TRY(cuda_status(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)ntile, st), "cudaMemsetAsync"));
     LISA_TRY(cuda_status(cudaMemsetAsync(&c->stats->call_failed, 0, sizeof(unsigned), st), "cudaMemsetAsync"));
     const double Tbar = orbit->L_m / kC;
+    int64_t safe_lo, safe_hi;
+    safe_range(out, h_grid, max_light_time(orbit, out), safe_lo, safe_hi);
     LISA_TRY(run_features(tab, skyd, Tbar, out.dt, z, n, nz, rows, c->f_lo, c->f_hi, feats, scale, y, flags,
-                          nullptr, nullptr, nullptr, st));
+                          safe_lo, safe_hi, nullptr, nullptr, nullptr, st));
     LISA_TRY(run_forward(c, feats, rows, 1, scale, n, y, st));
     FallbackArgs A;
     A.la.tab = tab;
@@ -781,6 +824,8 @@ static int corrected_links(lisa_corrector* c, const lisa_orbit* orbit, const lis
     A.spot_every = c->spot_every;
     A.spot_tol = c->spot_tol;
     A.stats = c->stats;
+    A.safe_lo = safe_lo;
+    A.safe_hi = safe_hi;
     for (int pass = 0; pass < 2; ++pass) {
         A.global_pass = pass;
         prof_before(pass ? "corr_fallback_all" : "corr_fallback", st);
@@ -989,7 +1034,7 @@ int lisa_corrector_features(const lisa_orbit* orbit, const lisa_sky* sky, lisa_g
     SegTable tab;
     LISA_TRY(make_table(orbit, g, sc, tab, st));
     return run_features(tab, make_sky_dev(*sky), orbit->L_m / kC, g.dt, z, g.n, g.n, g.n, f_lo, f_hi, feats, scale,
-                        ybase, nullptr, y_full, z_ref, target, st);
+                        ybase, nullptr, 0, g.n, y_full, z_ref, target, st);
 }
 
 int lisa_corrector_links(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,

@@ -101,9 +101,29 @@ def test_features_match_oracle(L, oracle_mod):
     from paper_2505_09600_gb300.corrector import edge_margin
     m = edge_margin(s.dt)
     sl = slice(m, n - m)
-    d = np.abs(gf[sl, :34] - wf[sl, :34])
-    k = np.unravel_index(np.argmax(d), d.shape)
-    assert d.max() < 2e-5, (d.max(), k[0] + m, k[1])
+    # Stencil columns: each FP32 operation rounds by u = 2^-24 relative to
+    # operands of size |z| (T/dt)^k S_k (S_k = sum of the stencil's |weights|:
+    # 1, 1.5, 16/3, 3, 16), so the normalised q_k,l may differ by
+    # 4 u (T/dt)^k S_k max|z| / M_k (ill-conditioned only where the z series
+    # cross zero); the ratio columns by that over ln 10 / 4 per order.
+    u = 2.0 ** -24
+    r1 = (oo.L_m / OC.C_LIGHT) / s.dt
+    S = [1.0, 1.5, 16.0 / 3.0, 3.0, 16.0]
+    zpad = np.pad(zh, ((0, 0), (2, 2)))
+    zmax = np.max([np.abs(zpad[:, j:j + n]).max(axis=0) for j in range(5)], axis=0)
+    q = np.stack([np.array([OC.stencils(zh[l], i, s.dt, oo.L_m / OC.C_LIGHT)
+                            for i in range(n)]) for l in range(6)], 0)                   # [6][n][5]
+    Mk = np.abs(q).max(axis=0)                                                           # [n][5]
+    tol = np.zeros((n, 34))
+    for k in range(5):
+        tk = 4 * u * r1 ** k * S[k] * zmax / np.where(Mk[:, k] > 0, Mk[:, k], np.inf) + 1e-6
+        tol[:, 6 * k:6 * k + 6] = tk[:, None]
+    for k in range(4):
+        tol[:, 30 + k] = (tol[:, 6 * k] + tol[:, 6 * (k + 1)]) / math.log(10) / 4 + 1e-6
+    d = np.abs(gf[:, :34] - wf[:, :34])
+    bad = d[sl] > tol[sl]
+    assert not bad.any(), (d[sl][bad][:5], tol[sl][bad][:5], np.argwhere(bad)[:5] + [m, 0])
+    assert np.median(d[sl, :30]) < 1e-6
     assert np.abs(gf[sl, 34:40] - wf[sl, 34:40]).max() < 2e-4
     assert np.abs(gf[:, 40:46] - wf[:, 40:46]).max() < 2e-6
     assert np.allclose(gf[:, 46], wf[:, 46], rtol=1e-6) and np.all(gf[:, 47] == 0)
@@ -252,8 +272,15 @@ def test_below_band_uses_base_links(L):
     scale = torch.empty(s.n, device="cuda")
     ybase = torch.empty((6, s.n), device="cuda")
     L.lisa_corrector_features(lo, d["sky"], s.grid, z, None, None, 1.0, 2.0, feats, scale, ybase)
+    full = torch.empty((6, s.n), device="cuda")
+    L.lisa_links_full(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, s.grid, full)
     torch.cuda.synchronize()
-    assert torch.equal(y, ybase)
+    # interior: the base links; within ~670 s of either end (retarded times
+    # off the h grid): the full links
+    from paper_2505_09600_gb300.corrector import edge_margin
+    m = edge_margin(s.dt)
+    assert torch.equal(y[:, m:s.n - m], ybase[:, m:s.n - m])
+    assert torch.equal(y[:, :120], full[:, :120]) and torch.equal(y[:, s.n - 120:], full[:, s.n - 120:])
     assert float(scale.abs().max()) == 0.0
     c.close()
 
@@ -266,15 +293,17 @@ def test_failed_spot_check_recomputes_every_tile(L):
     c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
     r = c.report()
     ntile = (s.n + 255) // 256
+    # spot checks only on tiles whose retarded times stay on the h grid
+    # (tiles 4 and 8 of 12 here: about 670 s = 134 samples lost at each end)
     assert r["status"] == L.LISA_ECORRECTOR
-    assert r["spot_tiles"] == (ntile + 3) // 4 and r["spot_failed"] == r["spot_tiles"]
+    assert r["spot_tiles"] == 2 and r["spot_failed"] == r["spot_tiles"]
     assert r["fallback_tiles"] == ntile - r["spot_tiles"]
     assert torch.equal(y, full)
     # counters were reset by the report; a lenient tolerance passes
     c.configure(f_lo=0.0, f_hi=1.0, spot_every=1, spot_tol=10.0)
     c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
     r = c.report()
-    assert r["status"] == 0 and r["spot_tiles"] == ntile and r["spot_failed"] == 0
+    assert r["status"] == 0 and r["spot_tiles"] == ntile - 2 and r["spot_failed"] == 0
     c.close()
 
 
@@ -326,12 +355,14 @@ def test_link_gain_on_held_out_sources(L, trained):
         scale = np.abs(ref).max()
         e_lfa = np.abs(z.cpu().numpy()[:, m:n - m] - ref).max() / scale
         e_cor = np.abs(y.cpu().numpy()[:, m:n - m] - ref).max() / scale
-        rows.append((s.meta["f0"], s.meta["f0"] * s.meta["ratio"], e_lfa, e_cor))
-    r = c.report()
-    assert r["status"] == 0, r
+        r = c.report()
+        rows.append((s.meta["f0"], s.meta["f0"] * s.meta["ratio"], e_lfa, e_cor, r["status"], r["max_spot_err"],
+                     r["band_tiles"]))
     rows = np.array(rows)
-    for f0, f1, a, b in rows:
-        print("held-out f %.2e..%.2e  LFA %.2e  corrected %.2e  gain %.1f" % (f0, f1, a, b, a / b))
+    for f0, f1, a, b, st, se, bt in rows:
+        print("held-out f %.2e..%.2e  LFA %.2e  corrected %.2e  gain %.1f  (spot err %.1e%s, %d tiles above band)"
+              % (f0, f1, a, b, a / b, se, " FAILED" if st else "", bt))
+    assert np.all(rows[:, 4] == 0)
     # where the LFA error is well above the FP32 floor of the mixed links
     sel = rows[:, 2] > 2e-4
     assert sel.sum() >= 8
