@@ -125,47 +125,19 @@ struct LfaSmem {
     float barg_c, barg_d;         // sigmoid argument at the tile centre and per sample
 };
 
-// One tile of LFA channels: on return thread t holds X, Y, Z of sample
-// i0 + t (before AET, blend and store) and z has been written if requested.
-// Every thread of the block must call it; it ends with all z in shared memory
-// and does not return early, so it can run inside a persistent loop.
+// FP64 per-tile set-up around the centre sample ic: the orbit geometry
+// (Taylor shift of the segment polynomials) and, for the mixed form, the FP32
+// constants of every z series (centre delay split, in-tile cubics).  Every
+// thread of the block must call it (it synchronises).
 template <bool MIXED>
-__device__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& sm,
-                                 typename std::conditional<MIXED, float, double>::type (&X)[3])
+__device__ void lfa_tile_prologue(const LfaArgs& a, int64_t ic, LfaSmem<MIXED>& sm)
 {
-    using Real = typename std::conditional<MIXED, float, double>::type;
-    using Real2 = typename PairT<Real>::T;
     TileGeo& g = sm.g;
-    const Real* __restrict__ hp = (const Real*)a.hp;
-    const Real* __restrict__ hc = (const Real*)a.hc;
-    const int64_t ic = i0 + kTile / 2;
     const double half = 0.5 * a.tab.S;
     const double u_per_s = 1.0 / (a.dt_out * half);
     const int t = threadIdx.x;
     const bool equal = (a.kind == LISA_LFA_EQUAL);
     tile_geo_load(g, a.tab, ic, a.sky);
-
-    // --- FP64 per-series quantities at a time index m (delay of tau) ------
-    auto tau_delay = [&](int c, int64_t m) -> double {
-        const double u = (double)(m - ic) / half;
-        const int ch = c >> 1, which = c & 1;
-        const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
-        const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
-        const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
-        const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
-        const double up = u - sh * u_per_s;
-        const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
-        return sh + 0.5 * Tl + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
-    };
-
-    if (t < 12) {
-        const int c = t % 6;
-        const int64_t m = (t < 6) ? i0 - 2 : i0 + kTile + 1;
-        int64_t j;
-        double eps;
-        split_f64(a.hm, m, tau_delay(c, m), j, eps);
-        sm.jends[t] = j;
-    }
     if constexpr (MIXED) {
         if (t == 12) {
             sm.inv_half = (float)(2.0 / a.tab.S);
@@ -205,6 +177,96 @@ __device__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& s
             sm.J[c] = j;
             sm.f[c] = (float)eps;
         }
+    }
+    __syncthreads();
+}
+
+// Mixed form: integer sample and fraction of the retarded time of series c
+// at output sample m, from the FP32 constants of the tile centre ic.
+__device__ __forceinline__ void lfa_locate_f32(const LfaArgs& a, const LfaSmem<true>& sm, int c, int64_t m,
+                                               int64_t ic, bool equal, int64_t& j, float& eps, float& Tl,
+                                               float (&n3)[3])
+{
+    const int ch = c >> 1, which = c & 1;
+    const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
+    // in-tile offsets are 32-bit: no 64-bit conversions (FP64 pipe) per sample
+    const float u = (float)(int)(m - ic) * sm.inv_half;
+    const float da = sm.da[c](u);
+    const float up = u - sm.acu[c] - da * sm.u_per_s;
+    const float dT = equal ? 0.f : sm.cu[kQT + l](up);
+    Tl = equal ? (float)a.Lc : sm.c0[kQT + l] + dT;
+    const float ddt = da + 0.5f * dT + 0.5f * (sm.cu[kRowKR + link_sender(l)](up) + sm.cu[kRowKR + link_receiver(l)](up));
+    for (int q = 0; q < 3; ++q) n3[q] = sm.c0[kQN + 3 * l + q] + sm.cu[kQN + 3 * l + q](up);
+    int64_t jp;
+    float fp;
+    if (a.hm.unit_rho) {
+        jp = m - ic;
+        fp = 0.f;
+    } else {
+        const double P = (double)(m - ic) * a.hm.rho;
+        const double fl = floor(P);
+        jp = (int64_t)fl;
+        fp = (float)(P - fl);
+    }
+    const float v = (fp + sm.f[c]) - ddt * sm.inv_dt;
+    const float fv = floorf(v);
+    j = sm.J[c] + jp + (int)fv;
+    eps = v - fv;
+}
+
+// One tile [i0, i0 + kTile) of LFA channels, after lfa_tile_prologue at the
+// centre ic (the tile's own centre, or that of a group of tiles sharing one
+// prologue): on return thread t holds X, Y, Z of sample i0 + t (before AET,
+// blend and store) and z has been written if requested.  With reuse_halo the
+// previous tile [i0 - kTile, i0) was the last one computed in this block, and
+// its last four z values are this tile's leading halo: the block then
+// computes exactly kTile values per series (no straggling round for the
+// halo).  Every thread of the block must call it; it does not return early,
+// so it can run inside a persistent loop.
+template <bool MIXED>
+__device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MIXED>& sm,
+                              typename std::conditional<MIXED, float, double>::type (&X)[3], bool reuse_halo = false)
+{
+    using Real = typename std::conditional<MIXED, float, double>::type;
+    using Real2 = typename PairT<Real>::T;
+    TileGeo& g = sm.g;
+    const Real* __restrict__ hp = (const Real*)a.hp;
+    const Real* __restrict__ hc = (const Real*)a.hc;
+    const double half = 0.5 * a.tab.S;
+    const double u_per_s = 1.0 / (a.dt_out * half);
+    const int t = threadIdx.x;
+    const bool equal = (a.kind == LISA_LFA_EQUAL);
+    __syncthreads();   // the previous tile's readers of the windows are done
+    // z of samples i0-2 .. i0+1 were computed as the previous tile's i0'+256 .. i0'+259
+    if (reuse_halo && t < 24) {
+        const int c = t >> 2, o = t & 3;
+        sm.zs[c][o] = sm.zs[c][kTile + o];
+    }
+
+    // --- window of h this tile reaches: the retarded samples of the 6 series
+    //     at the tile's two ends (2-sample halo included)
+    if (t < 12) {
+        const int c = t % 6;
+        const int64_t m = (t < 6) ? i0 - 2 : i0 + kTile + 1;
+        int64_t j;
+        if constexpr (MIXED) {
+            float eps, Tl, n3[3];
+            lfa_locate_f32(a, sm, c, m, ic, equal, j, eps, Tl, n3);
+        } else {
+            const double u = (double)(m - ic) / half;
+            const int ch = c >> 1, which = c & 1;
+            const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
+            const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
+            const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
+            const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
+            const double up = u - sh * u_per_s;
+            const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
+            const double d = sh + 0.5 * Tl
+                           + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
+            double eps;
+            split_f64(a.hm, m, d, j, eps);
+        }
+        sm.jends[t] = j;
     }
     __syncthreads();
     if (t == 0) {
@@ -248,8 +310,11 @@ __device__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& s
     const float Lcf = (float)a.Lc;
 
     // --- z on the tile and its halo: (kTile + 4) x 6 values ----------------
-    for (int w = t; w < 6 * kZW; w += blockDim.x) {
-        const int c = w / kZW, o = w % kZW;
+    const int per = reuse_halo ? kTile : kZW;
+    for (int w = t; w < 6 * per; w += blockDim.x) {
+        // constant divisors: kTile values per series after a reused halo, else kZW
+        const int c = reuse_halo ? w / kTile : w / kZW;
+        const int o = reuse_halo ? 4 + w % kTile : w % kZW;
         const int64_t m = i0 - 2 + o;
         Real zval = Real(0);
         if (m >= 0 && m < a.nout) {
@@ -272,30 +337,13 @@ __device__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& s
                 split_f64(a.hm, m, dtau, j, e);
                 eps = e;
             } else {
-                // in-tile offsets are 32-bit: no 64-bit conversions (FP64 pipe) per sample
-                const float u = (float)(int)(m - ic) * sm.inv_half;
-                const float da = sm.da[c](u);
-                const float up = u - sm.acu[c] - da * sm.u_per_s;
-                const float dT = equal ? 0.f : sm.cu[kQT + l](up);
-                Tl = equal ? Lcf : sm.c0[kQT + l] + dT;
-                const float ddt = da + 0.5f * dT
-                                + 0.5f * (sm.cu[kRowKR + link_sender(l)](up) + sm.cu[kRowKR + link_receiver(l)](up));
-                for (int q = 0; q < 3; ++q) n3[q] = sm.c0[kQN + 3 * l + q] + sm.cu[kQN + 3 * l + q](up);
-                int64_t jp;
-                float fp;
-                if (a.hm.unit_rho) {
-                    jp = m - ic;
-                    fp = 0.f;
-                } else {
-                    const double P = (double)(m - ic) * a.hm.rho;
-                    const double fl = floor(P);
-                    jp = (int64_t)fl;
-                    fp = (float)(P - fl);
-                }
-                const float v = (fp + sm.f[c]) - ddt * sm.inv_dt;
-                const float fv = floorf(v);
-                j = sm.J[c] + jp + (int)fv;
-                eps = v - fv;
+                float e, T32, n32[3];
+                lfa_locate_f32(a, sm, c, m, ic, equal, j, e, T32, n32);
+                eps = e;
+                Tl = T32;
+                n3[0] = n32[0];
+                n3[1] = n32[1];
+                n3[2] = n32[2];
             }
             const Real un = ku[0] * n3[0] + ku[1] * n3[1] + ku[2] * n3[2];
             const Real vn = kv[0] * n3[0] + kv[1] * n3[1] + kv[2] * n3[2];
@@ -343,6 +391,16 @@ __device__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& s
             X[ch] = Real(4) * (Ta * d1(za) - Tb * d1(zb));
         }
     }
+}
+
+// Prologue and body of one tile around its own centre.
+template <bool MIXED>
+__device__ __forceinline__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& sm,
+                                                 typename std::conditional<MIXED, float, double>::type (&X)[3])
+{
+    const int64_t ic = i0 + kTile / 2;
+    lfa_tile_prologue<MIXED>(a, ic, sm);
+    lfa_tile_body<MIXED>(a, i0, ic, sm, X);
 }
 
 // AET, sigmoid weight (LFA side: eps = +1) and store of one sample.

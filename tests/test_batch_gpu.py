@@ -58,8 +58,11 @@ def test_batch_matches_single_calls_and_oracle(L, oracle_mod, batch):
         got = d["out"].cpu().numpy().astype(np.float64)
         assert np.isfinite(got).all(), k
         ref = _per_source(L, lo, d)
-        # same arithmetic per sample; only AET-before/after-blend rounding differs
-        assert rel_err(got, ref, signal=True).max() < 2e-6, k
+        # Same formulas; FP32 rounding differs: the single call's LFA shares one
+        # FP64 tile-centre set-up among 8 tiles, the batch sets up every tile,
+        # and the blend is applied before or after AET.  Both forms are held to
+        # the oracle below; against each other, to twice the LFA tolerance.
+        assert rel_err(got, ref, signal=True).max() < 2 * MIXED_TOL["lfa20"]["aet"][0], k
         t_end = s.t0 + s.n * s.dt
         regimes.add("full" if tH < s.t0 else "lfa" if tH > t_end else "mixed")
         if k in (0, 5, 13):
