@@ -44,6 +44,7 @@ struct BatchSrc {
     int64_t n;
     double t0, dt;
     double t_hyb, sigma;
+    float dtf, inv12dtf;  // FP32 copies of dt and 1/(12 dt)
     int64_t iL, iF;      // LFA on samples <= iL, full response on samples >= iF
     int64_t tile_begin;  // first work tile of this source
     int64_t ntiles;
@@ -57,6 +58,7 @@ struct BatchKernelArgs {
     unsigned long long* counter;
     int gen, kind, channels;
     double Lc;
+    float Lcf;
 };
 
 struct BatchSmem {
@@ -173,6 +175,9 @@ __global__ void __launch_bounds__(kTile) batch_hybrid_kernel(BatchKernelArgs ka)
                 a.i_end = b.n;
                 a.tile0 = 0;
                 a.bl = BlendSpec{};
+                a.Lcf = ka.Lcf;
+                a.dtf = b.dtf;
+                a.inv12dtf = b.inv12dtf;
                 lfa_tile_compute<true>(a, i0, sm.lfa, Xl);
             } else {
                 tile_geo_load(sm.lfa.g, b.tab, i0 + kTile / 2, b.sky);
@@ -248,6 +253,7 @@ static int plan_enqueue(lisa_plan* p, cudaStream_t st)
     ka.kind = p->kind;
     ka.channels = p->channels;
     ka.Lc = p->orbit.L_m / kC;
+    ka.Lcf = (float)ka.Lc;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_hybrid_kernel, kTile, 0);
     const int cps = per_sm > 0 && p->ctas_per_sm > per_sm ? per_sm : p->ctas_per_sm;
@@ -335,6 +341,8 @@ int lisa_plan_create(lisa_plan** out, const lisa_orbit* orbit, int precision, in
         b.n = g.n;
         b.t0 = g.t0;
         b.dt = g.dt;
+        b.dtf = (float)g.dt;
+        b.inv12dtf = (float)(1.0 / (12.0 * g.dt));
         const double Tw = s.T_win > 0.0 ? s.T_win : 800.0 * g.dt;
         b.sigma = s.sigma > 0.0 ? s.sigma : Tw / 40.0;
         b.t_hyb = s.t_hyb;

@@ -451,6 +451,7 @@ struct FeatArgs {
     float r1;              // Tbar / dt
     float Tbar;
     float vfac;            // d/dt of the segment coordinate over c: 2 / (S dt c)
+    float inv_half;        // 2 / S
     float dtr;             // dt / Tbar (feature 46)
     float w_lo, w_hi;      // band as limits of (omega Tbar)^2 = M2/M0
     float* feats;          // [rows][kInP]
@@ -465,7 +466,17 @@ struct FeatArgs {
 
 __global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // The block's 256 samples lie in one orbit segment (segments are whole
+    // multiples of 512 samples): its coefficients are converted to FP32 once
+    // (conversions from FP64 run on the FP64 pipe).
+    __shared__ float cfs[kNQ][7];
+    const int64_t b0 = (int64_t)blockIdx.x * blockDim.x;
+    int64_t s = b0 / a.tab.S;
+    if (s >= a.tab.nseg) s = a.tab.nseg - 1;
+    for (int e = threadIdx.x; e < kNQ * 7; e += blockDim.x)
+        cfs[e / 7][e % 7] = (float)a.tab.coef[(s * kNQ + e / 7) * kNC + e % 7];
+    __syncthreads();
+    const int64_t i = b0 + threadIdx.x;
     if (i >= a.rows) return;
     const float r1 = a.r1, r2 = r1 * r1;
     float q[5][6];
@@ -503,36 +514,32 @@ __global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
         ft[30 + k] = fminf(fmaxf(lr, -8.f), 8.f) * 0.25f;
     }
     // geometry at sample i from the orbit table (FP32 evaluation suffices here)
-    int64_t s = i / a.tab.S;
-    if (s >= a.tab.nseg) s = a.tab.nseg - 1;
-    const float x = (float)(i - s * a.tab.S) * (2.f / (float)a.tab.S) - 1.f;
-    const double* cf = a.tab.coef + s * kNQ * kNC;
+    const float x = (float)(int)(i - s * a.tab.S) * a.inv_half - 1.f;
     auto ev = [&](int row) {
-        const double* b = cf + row * kNC;
-        float r = (float)b[6];
+        const float* b = cfs[row];
+        float r = b[6];
 #pragma unroll
-        for (int p = 5; p >= 0; --p) r = fmaf(r, x, (float)b[p]);
+        for (int p = 5; p >= 0; --p) r = fmaf(r, x, b[p]);
         return r;
     };
     // k.v / c of each spacecraft from the derivative of its position polynomial
     auto evd = [&](int row) {
-        const double* b = cf + row * kNC;
-        float r = 6.f * (float)b[6];
+        const float* b = cfs[row];
+        float r = 6.f * b[6];
 #pragma unroll
-        for (int p = 5; p >= 1; --p) r = fmaf(r, x, (float)p * (float)b[p]);
+        for (int p = 5; p >= 1; --p) r = fmaf(r, x, (float)p * b[p]);
         return r;
     };
+    const float k0 = a.sky.kf[0], k1 = a.sky.kf[1], k2 = a.sky.kf[2];
     float kv[3];
 #pragma unroll
     for (int sc3 = 0; sc3 < 3; ++sc3)
-        kv[sc3] = ((float)a.sky.k[0] * evd(kQR + 3 * sc3) + (float)a.sky.k[1] * evd(kQR + 3 * sc3 + 1)
-                   + (float)a.sky.k[2] * evd(kQR + 3 * sc3 + 2)) * a.vfac;
+        kv[sc3] = (k0 * evd(kQR + 3 * sc3) + k1 * evd(kQR + 3 * sc3 + 1) + k2 * evd(kQR + 3 * sc3 + 2)) * a.vfac;
     float eps[6];
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
         ft[34 + l] = (ev(kQT + l) / a.Tbar - 1.f) * 100.f;
-        const float kn = (float)a.sky.k[0] * ev(kQN + 3 * l) + (float)a.sky.k[1] * ev(kQN + 3 * l + 1)
-                       + (float)a.sky.k[2] * ev(kQN + 3 * l + 2);
+        const float kn = k0 * ev(kQN + 3 * l) + k1 * ev(kQN + 3 * l + 1) + k2 * ev(kQN + 3 * l + 2);
         ft[40 + l] = 1.f - kn;
         eps[l] = (1.f - kn) > 1e-6f ? kv[link_sender(l)] / (1.f - kn) : 0.f;
     }
@@ -749,6 +756,7 @@ static int run_features(const SegTable& tab, const SkyDev& sky, double Tbar, dou
     a.r1 = (float)(Tbar / dt);
     a.Tbar = (float)Tbar;
     a.vfac = (float)(2.0 / ((double)tab.S * dt * kC));
+    a.inv_half = (float)(2.0 / (double)tab.S);
     a.dtr = (float)(dt / Tbar);
     a.w_lo = (float)(two_pi_T * f_lo * two_pi_T * f_lo);
     a.w_hi = isfinite(f_hi) ? (float)(two_pi_T * f_hi * two_pi_T * f_hi) : INFINITY;

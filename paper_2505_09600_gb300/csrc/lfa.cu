@@ -76,6 +76,7 @@ int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const l
     a.i_end = i_end;
     a.tile0 = i_begin / kTile;
     a.bl = bl;
+    lfa_args_f32(a);
     const int64_t tiles = (i_end - 1) / kTile - a.tile0 + 1;
     const int64_t tile_end = a.tile0 + tiles;
     prof_before(gen == kLfaOwnTime ? (precision == LISA_MIXED ? "lfa_own_mixed" : "lfa_own_f64")

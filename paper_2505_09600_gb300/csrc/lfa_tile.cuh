@@ -34,7 +34,16 @@ struct LfaArgs {
     double t0_out, dt_out;
     int64_t i_begin, i_end, tile0;
     BlendSpec bl;
+    float Lcf, dtf, inv12dtf;   // FP32 copies of Lc, dt_out and 1/(12 dt_in) (mixed form)
 };
+
+// Fill the FP32 copies of LfaArgs (host side).
+inline void lfa_args_f32(LfaArgs& a)
+{
+    a.Lcf = (float)a.Lc;
+    a.dtf = (float)a.dt_out;
+    a.inv12dtf = (float)(1.0 / (12.0 * a.hm.dt_in));
+}
 
 
 // Channel ch: links a = cyc(+2), b = cyc(+3); arms T_a = cyc(+3), T_b = cyc(+2).
@@ -194,7 +203,7 @@ __device__ __forceinline__ void lfa_locate_f32(const LfaArgs& a, const LfaSmem<t
     const float da = sm.da[c](u);
     const float up = u - sm.acu[c] - da * sm.u_per_s;
     const float dT = equal ? 0.f : sm.cu[kQT + l](up);
-    Tl = equal ? (float)a.Lc : sm.c0[kQT + l] + dT;
+    Tl = equal ? a.Lcf : sm.c0[kQT + l] + dT;
     const float ddt = da + 0.5f * dT + 0.5f * (sm.cu[kRowKR + link_sender(l)](up) + sm.cu[kRowKR + link_receiver(l)](up));
     for (int q = 0; q < 3; ++q) n3[q] = sm.c0[kQN + 3 * l + q] + sm.cu[kQN + 3 * l + q](up);
     int64_t jp;
@@ -282,7 +291,9 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
     __syncthreads();
     const int64_t wlo = sm.wlo;
     const int wlen = sm.wlen;
-    const Real inv12dt = Real(1.0 / (12.0 * a.hm.dt_in));
+    Real inv12dt;
+    if constexpr (MIXED) inv12dt = a.inv12dtf;
+    else inv12dt = 1.0 / (12.0 * a.hm.dt_in);
     // h over [wlo-2, wlo+wlen+2), then hdot over [wlo, wlo+wlen)
     for (int k = t; k < wlen + 4; k += blockDim.x) {
         const int64_t idx = wlo - 2 + k;
@@ -304,10 +315,15 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
     }
     __syncthreads();
 
-    const Real c2 = (Real)a.sky.c2p, s2 = (Real)a.sky.s2p;
-    const Real ku[3] = {(Real)a.sky.u[0], (Real)a.sky.u[1], (Real)a.sky.u[2]};
-    const Real kv[3] = {(Real)a.sky.v[0], (Real)a.sky.v[1], (Real)a.sky.v[2]};
-    const float Lcf = (float)a.Lc;
+    Real c2, s2, ku[3], kv[3];
+    if constexpr (MIXED) {
+        c2 = a.sky.c2f; s2 = a.sky.s2f;
+        for (int q = 0; q < 3; ++q) { ku[q] = a.sky.uf[q]; kv[q] = a.sky.vf[q]; }
+    } else {
+        c2 = a.sky.c2p; s2 = a.sky.s2p;
+        for (int q = 0; q < 3; ++q) { ku[q] = a.sky.u[q]; kv[q] = a.sky.v[q]; }
+    }
+    const float Lcf = a.Lcf;
 
     // --- z on the tile and its halo: (kTile + 4) x 6 values ----------------
     const int per = reuse_halo ? kTile : kZW;
@@ -363,7 +379,9 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
         Real* zo = (Real*)a.z;
         for (int c = 0; c < 6; ++c) zo[(int64_t)c * a.nout + i] = sm.zs[c][t + 2];
     }
-    const Real dt = (Real)a.dt_out;
+    Real dt;
+    if constexpr (MIXED) dt = a.dtf;
+    else dt = a.dt_out;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         Real Ta, Tb;

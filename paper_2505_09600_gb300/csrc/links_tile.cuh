@@ -183,9 +183,14 @@ __device__ __forceinline__ void links_sample(const LinksArgs& a, const TileGeo& 
     const double half = 0.5 * a.tab.S;
     const int64_t wlo = s.wlo;
     const int wlen = s.wlen;
-    const Real c2 = (Real)a.sky.c2p, s2 = (Real)a.sky.s2p;
-    const Real ku[3] = {(Real)a.sky.u[0], (Real)a.sky.u[1], (Real)a.sky.u[2]};
-    const Real kv[3] = {(Real)a.sky.v[0], (Real)a.sky.v[1], (Real)a.sky.v[2]};
+    Real c2, s2, ku[3], kv[3];
+    if constexpr (MIXED) {
+        c2 = a.sky.c2f; s2 = a.sky.s2f;
+        for (int q = 0; q < 3; ++q) { ku[q] = a.sky.uf[q]; kv[q] = a.sky.vf[q]; }
+    } else {
+        c2 = a.sky.c2p; s2 = a.sky.s2p;
+        for (int q = 0; q < 3; ++q) { ku[q] = a.sky.u[q]; kv[q] = a.sky.v[q]; }
+    }
 
     if constexpr (!MIXED) {
         const double u = (double)(m - ic) / half;

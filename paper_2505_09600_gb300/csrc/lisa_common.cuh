@@ -74,6 +74,10 @@ OrbitDev make_orbit_dev(const lisa_orbit& o);
 struct SkyDev {
     double k[3], u[3], v[3];
     double c2p, s2p;
+    // FP32 copies for the mixed-precision kernels: converting FP64 values in
+    // device code runs on the FP64 pipe (2 per clock per SM on GB300)
+    float kf[3], uf[3], vf[3];
+    float c2f, s2f;
 };
 SkyDev make_sky_dev(const lisa_sky& s);
 

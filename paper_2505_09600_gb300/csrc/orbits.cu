@@ -78,6 +78,13 @@ SkyDev make_sky_dev(const lisa_sky& s)
     d.v[0] = -sb * cl; d.v[1] = -sb * sl; d.v[2] = cb;
     d.c2p = cos(2.0 * s.psi);
     d.s2p = sin(2.0 * s.psi);
+    for (int c = 0; c < 3; ++c) {
+        d.kf[c] = (float)d.k[c];
+        d.uf[c] = (float)d.u[c];
+        d.vf[c] = (float)d.v[c];
+    }
+    d.c2f = (float)d.c2p;
+    d.s2f = (float)d.s2p;
     return d;
 }
 
