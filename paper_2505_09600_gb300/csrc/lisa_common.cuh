@@ -118,19 +118,23 @@ __device__ __forceinline__ void split_f64(const GridMap& m, int64_t i, double d,
 //   w_p = A_p B_p,  A_p = prod_{m=-15}^{p-16}(eps - m) / p!,
 //   B_p = prod_{m=p-14}^{16}(m - eps) / (31 - p)!,
 // which equals prod_{m != k}(eps - m)/(k - m).  Built by a backward then a
-// forward running product (about five operations per weight).
+// forward running product (about five operations per weight, four with the
+// fused factors).
 template <typename Real>
 __device__ __forceinline__ void lagrange32_weights(Real eps, Real (&w)[32])
 {
-    // fully unrolled: every 1/n below is a compile-time constant
+    // Fully unrolled.  Each factor (c - eps)/n is one fused multiply-add with
+    // the compile-time constants -1/n and c/n (instead of a subtraction and a
+    // multiplication): the same factor up to the rounding of c/n.
     w[31] = Real(1);
 #pragma unroll
-    for (int p = 31; p >= 1; --p) w[p - 1] = w[p] * ((Real(p - 15) - eps) * (Real(1) / Real(32 - p)));
+    for (int p = 31; p >= 1; --p)
+        w[p - 1] = w[p] * fma(eps, Real(-1) / Real(32 - p), Real(p - 15) / Real(32 - p));
     Real A = Real(1);
 #pragma unroll
     for (int p = 0; p < 32; ++p) {
         w[p] *= A;
-        A *= (eps - Real(p - 15)) * (Real(1) / Real(p + 1));
+        A *= fma(eps, Real(1) / Real(p + 1), Real(15 - p) / Real(p + 1));
     }
 }
 
