@@ -45,6 +45,7 @@ struct BatchSrc {
     double t0, dt;
     double t_hyb, sigma;
     float dtf, inv12dtf;  // FP32 copies of dt and 1/(12 dt)
+    float c1f, c2f;       // 1/(12 dt), 1/(12 dt^2)
     int64_t iL, iF;      // LFA on samples <= iL, full response on samples >= iF
     int64_t tile_begin;  // first work tile of this source
     int64_t ntiles;
@@ -178,6 +179,8 @@ __global__ void __launch_bounds__(kTile) batch_hybrid_kernel(BatchKernelArgs ka)
                 a.Lcf = ka.Lcf;
                 a.dtf = b.dtf;
                 a.inv12dtf = b.inv12dtf;
+                a.c1f = b.c1f;
+                a.c2f = b.c2f;
                 lfa_tile_compute<true>(a, i0, sm.lfa, Xl);
             } else {
                 tile_geo_load(sm.lfa.g, b.tab, i0 + kTile / 2, b.sky);
@@ -343,6 +346,8 @@ int lisa_plan_create(lisa_plan** out, const lisa_orbit* orbit, int precision, in
         b.dt = g.dt;
         b.dtf = (float)g.dt;
         b.inv12dtf = (float)(1.0 / (12.0 * g.dt));
+        b.c1f = b.inv12dtf;
+        b.c2f = (float)(1.0 / (12.0 * g.dt * g.dt));
         const double Tw = s.T_win > 0.0 ? s.T_win : 800.0 * g.dt;
         b.sigma = s.sigma > 0.0 ? s.sigma : Tw / 40.0;
         b.t_hyb = s.t_hyb;

@@ -18,25 +18,25 @@
 
 namespace lisa {
 
-// Tiles per CTA: the FP64 prologue (segment polynomials shifted to the centre,
-// delay splits) is shared by LISA_LFA_GROUP consecutive tiles in the mixed
-// form; the omitted quartic terms of the in-tile cubics stay below 4e-10 s
-// over the group's +-1024 samples at dt = 10 s (k.R/c: 500 s at the orbital
-// frequency), a phase error under 1e-10 rad at 2e-2 Hz.
-#ifndef LISA_LFA_GROUP
-#define LISA_LFA_GROUP 8
-#endif
-template <bool MIXED>
-constexpr int lfa_group() { return MIXED ? LISA_LFA_GROUP : 1; }
+// Tiles per CTA (mixed form): the FP64 prologue (segment polynomials shifted
+// to the centre, the series' composed cubics) is shared by up to 8
+// consecutive tiles, as many as keep the block's half-span within 1.1e4 s:
+// the omitted quartic terms of the cubics (k.R/c: 500 s at the orbital
+// frequency) then stay below 4e-10 s, a phase error under 1e-10 rad at
+// 2e-2 Hz.
+inline int lfa_group(double dt)
+{
+    int G = (int)floor(80.0 / dt);
+    return G < 1 ? 1 : (G > 8 ? 8 : G);
+}
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kTile) lfa_kernel(LfaArgs a, int64_t tile_end)
+__global__ void __launch_bounds__(kTile) lfa_kernel(LfaArgs a, int64_t tile_end, int G)
 {
     using Real = typename std::conditional<MIXED, float, double>::type;
     __shared__ LfaSmem<MIXED> sm;
-    constexpr int G = lfa_group<MIXED>();
     const int64_t t0 = a.tile0 + (int64_t)blockIdx.x * G;
-    const int64_t ic = t0 * kTile + G * kTile / 2;
+    const int64_t ic = t0 * kTile + (int64_t)G * kTile / 2;
     lfa_tile_prologue<MIXED>(a, ic, sm);
     for (int q = 0; q < G; ++q) {
         const int64_t i0 = (t0 + q) * (int64_t)kTile;
@@ -82,10 +82,10 @@ int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const l
     prof_before(gen == kLfaOwnTime ? (precision == LISA_MIXED ? "lfa_own_mixed" : "lfa_own_f64")
                                    : (precision == LISA_MIXED ? "lfa_mixed" : "lfa_f64"), st);
     if (precision == LISA_MIXED) {
-        constexpr int G = lfa_group<true>();
-        lfa_kernel<true><<<(unsigned)((tiles + G - 1) / G), kTile, 0, st>>>(a, tile_end);
+        const int G = lfa_group(og.dt);
+        lfa_kernel<true><<<(unsigned)((tiles + G - 1) / G), kTile, 0, st>>>(a, tile_end, G);
     } else {
-        lfa_kernel<false><<<(unsigned)tiles, kTile, 0, st>>>(a, tile_end);
+        lfa_kernel<false><<<(unsigned)tiles, kTile, 0, st>>>(a, tile_end, 1);
     }
     prof_after(st);
     return cuda_status(cudaGetLastError(), "lfa_kernel launch");

@@ -35,6 +35,7 @@ struct LfaArgs {
     int64_t i_begin, i_end, tile0;
     BlendSpec bl;
     float Lcf, dtf, inv12dtf;   // FP32 copies of Lc, dt_out and 1/(12 dt_in) (mixed form)
+    float c1f, c2f;             // 1/(12 dt_out) and 1/(12 dt_out^2): the channels' stencil scales
 };
 
 // Fill the FP32 copies of LfaArgs (host side).
@@ -43,6 +44,8 @@ inline void lfa_args_f32(LfaArgs& a)
     a.Lcf = (float)a.Lc;
     a.dtf = (float)a.dt_out;
     a.inv12dtf = (float)(1.0 / (12.0 * a.hm.dt_in));
+    a.c1f = (float)(1.0 / (12.0 * a.dt_out));
+    a.c2f = (float)(1.0 / (12.0 * a.dt_out * a.dt_out));
 }
 
 
@@ -111,6 +114,17 @@ __device__ __forceinline__ void interp_hdot_global(const Real* __restrict__ hp, 
     oc = ac;
 }
 
+// Mixed form: each z series (link l evaluated at tau = t - sh - T_l/2 -
+// k.(R_s + R_r)/2c with the TDI shift sh, Sec. III) as FP32 cubics in the
+// block's coordinate u = (m - ic) * 2/S around the centre sample ic: the
+// total delay d(u) = D0 + d1 u + d2 u^2 + d3 u^3 (D0 split exactly into J, f
+// in FP64), the light time T_l and the link vector n_l at the retarded time.
+struct SerF32 {
+    float f, d1, d2, d3;      // centre fraction, in-block delay variation (s)
+    float T[4];               // T_l(u) = T[0] + T[1] u + T[2] u^2 + T[3] u^3
+    float n[3][4];            // n_l components, same form
+};
+
 template <bool MIXED>
 struct LfaSmem {
     using Real = typename std::conditional<MIXED, float, double>::type;
@@ -122,105 +136,143 @@ struct LfaSmem {
     int64_t jends[12];
     int64_t wlo;
     int wlen;
-    // mixed: FP32 rows (centre value, cubic) and per-series centre splits
+    // mixed: per-series records, arm rows (centre value, cubic) for the channels
+    SerF32 ser[6];
+    int64_t J[6];
+    int jrel[6];                  // J - wlo of the current tile
+    double comp[6][6][4];         // prologue scratch: composed rows per series
     float c0[kRows];
     Cubic cu[kRows];
-    double ac[6];
-    Cubic da[6];
-    int64_t J[6];
-    float f[6];
-    float acu[6];                 // centre shift in segment units
-    float inv_half, inv_dt, u_per_s;   // FP32 constants
-    float barg_c, barg_d;         // sigmoid argument at the tile centre and per sample
+    float inv_half, inv_dt;       // FP32 constants
+    float barg_c, barg_d;         // sigmoid argument at the centre and per sample
 };
 
-// FP64 per-tile set-up around the centre sample ic: the orbit geometry
-// (Taylor shift of the segment polynomials) and, for the mixed form, the FP32
-// constants of every z series (centre delay split, in-tile cubics).  Every
-// thread of the block must call it (it synchronises).
+// FP64 set-up around the centre sample ic: the orbit geometry (Taylor shift
+// of the segment polynomials) and, for the mixed form, the FP32 records of
+// the six z series.  Every thread of the block must call it (it
+// synchronises).
 template <bool MIXED>
 __device__ void lfa_tile_prologue(const LfaArgs& a, int64_t ic, LfaSmem<MIXED>& sm)
 {
     TileGeo& g = sm.g;
-    const double half = 0.5 * a.tab.S;
-    const double u_per_s = 1.0 / (a.dt_out * half);
     const int t = threadIdx.x;
-    const bool equal = (a.kind == LISA_LFA_EQUAL);
     tile_geo_load(g, a.tab, ic, a.sky);
     if constexpr (MIXED) {
-        if (t == 12) {
+        const bool equal = (a.kind == LISA_LFA_EQUAL);
+        const double u_per_s = 1.0 / (a.dt_out * 0.5 * a.tab.S);
+        if (t < 36) {
+            // series c, quantity r: 0 T_l, 1 k.R_s/c, 2 k.R_r/c, 3..5 n_l
+            // composed with the retarded coordinate up(u) = u - sh(u)/(dt S/2):
+            // r(up(u)) to cubic order by a Taylor shift to up(0) and the chain
+            // rule (a1, a2, a3: the u, u^2, u^3 coefficients of up).
+            const int c = t / 6, r = t % 6;
+            const int ch = c >> 1, which = c & 1;
+            const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
+            double sh[4] = {0.0, 0.0, 0.0, 0.0};
+            if (a.gen != kLfaOwnTime) {
+                const double al = which ? (a.gen == LISA_TDI20 ? 1.5 : 0.5) : (a.gen == LISA_TDI20 ? 2.0 : 1.0);
+                const double be = which ? (a.gen == LISA_TDI20 ? 2.0 : 1.0) : (a.gen == LISA_TDI20 ? 1.5 : 0.5);
+                const int ra = kQT + lfa_arm(ch, 0), rb = kQT + lfa_arm(ch, 1);
+                for (int k = 0; k < 4; ++k)
+                    sh[k] = equal ? (k == 0 ? (al + be) * a.Lc : 0.0) : al * g.b[ra][k] + be * g.b[rb][k];
+            }
+            const double a0 = -u_per_s * sh[0], a1 = 1.0 - u_per_s * sh[1], a2 = -u_per_s * sh[2],
+                         a3 = -u_per_s * sh[3];
+            double out[4];
+            if (r == 0 && equal) {
+                out[0] = a.Lc; out[1] = 0.0; out[2] = 0.0; out[3] = 0.0;
+            } else {
+                const int row = r == 0 ? kQT + l : r == 1 ? kRowKR + link_sender(l)
+                              : r == 2 ? kRowKR + link_receiver(l) : kQN + 3 * l + (r - 3);
+                double b[7];
+                taylor_shift7(g.b[row], a0, b);
+                out[0] = b[0];
+                out[1] = b[1] * a1;
+                out[2] = b[1] * a2 + b[2] * a1 * a1;
+                out[3] = b[1] * a3 + 2.0 * b[2] * a1 * a2 + b[3] * a1 * a1 * a1;
+            }
+            for (int k = 0; k < 4; ++k) sm.comp[c][r][k] = out[k];
+        }
+        if (t == 40) {
             sm.inv_half = (float)(2.0 / a.tab.S);
             sm.inv_dt = (float)(1.0 / a.hm.dt_in);
-            sm.u_per_s = (float)u_per_s;
             const double tc = a.t0_out + (double)ic * a.dt_out;
             sm.barg_c = (float)(a.bl.enabled ? a.bl.eps * (tc - a.bl.t_hyb) / a.bl.sigma : 0.0);
             sm.barg_d = (float)(a.bl.enabled ? a.bl.eps * a.dt_out / a.bl.sigma : 0.0);
         }
-        if (t >= 32 && t < 32 + kRows) {
-            const int r = t - 32;
+        if (t >= 64 && t < 64 + kRows) {
+            const int r = t - 64;
             sm.c0[r] = (float)g.b[r][0];
             sm.cu[r] = tg_cubic(g, r);
         }
-        if (t >= 96 && t < 102) {
-            const int c = t - 96, ch = c >> 1, which = c & 1;
-            const int ra = kQT + lfa_arm(ch, 0), rb = kQT + lfa_arm(ch, 1);
-            const double Ta = equal ? a.Lc : g.b[ra][0], Tb = equal ? a.Lc : g.b[rb][0];
-            const double ac = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
-            Cubic da{0.f, 0.f, 0.f};
-            if (!equal) {
-                const Cubic ca = tg_cubic(g, ra), cb = tg_cubic(g, rb);
-                float fa = which ? (a.gen == LISA_TDI20 ? 1.5f : 0.5f) : (a.gen == LISA_TDI20 ? 2.f : 1.f);
-                float fb = which ? (a.gen == LISA_TDI20 ? 2.f : 1.f) : (a.gen == LISA_TDI20 ? 1.5f : 0.5f);
-                if (a.gen == kLfaOwnTime) fa = fb = 0.f;
-                da = Cubic{fa * ca.c1 + fb * cb.c1, fa * ca.c2 + fb * cb.c2, fa * ca.c3 + fb * cb.c3};
+        __syncthreads();
+        if (t < 6) {
+            const int c = t, ch = c >> 1, which = c & 1;
+            double sh[4] = {0.0, 0.0, 0.0, 0.0};
+            if (a.gen != kLfaOwnTime) {
+                const double al = which ? (a.gen == LISA_TDI20 ? 1.5 : 0.5) : (a.gen == LISA_TDI20 ? 2.0 : 1.0);
+                const double be = which ? (a.gen == LISA_TDI20 ? 2.0 : 1.0) : (a.gen == LISA_TDI20 ? 1.5 : 0.5);
+                const int ra = kQT + lfa_arm(ch, 0), rb = kQT + lfa_arm(ch, 1);
+                for (int k = 0; k < 4; ++k)
+                    sh[k] = equal ? (k == 0 ? (al + be) * a.Lc : 0.0) : al * g.b[ra][k] + be * g.b[rb][k];
             }
-            const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
-            const double Tl = equal ? a.Lc : g.b[kQT + l][0];
-            const double dc = ac + 0.5 * Tl + 0.5 * (g.b[kRowKR + link_sender(l)][0] + g.b[kRowKR + link_receiver(l)][0]);
+            double d[4];
+            for (int k = 0; k < 4; ++k)
+                d[k] = sh[k] + 0.5 * (sm.comp[c][0][k] + sm.comp[c][1][k] + sm.comp[c][2][k]);
             int64_t j;
             double eps;
-            split_f64(a.hm, ic, dc, j, eps);
-            sm.ac[c] = ac;
-            sm.acu[c] = (float)(ac * u_per_s);
-            sm.da[c] = da;
+            split_f64(a.hm, ic, d[0], j, eps);
+            SerF32& R = sm.ser[c];
+            R.f = (float)eps;
+            R.d1 = (float)d[1];
+            R.d2 = (float)d[2];
+            R.d3 = (float)d[3];
+            for (int k = 0; k < 4; ++k) R.T[k] = (float)sm.comp[c][0][k];
+            for (int q = 0; q < 3; ++q)
+                for (int k = 0; k < 4; ++k) R.n[q][k] = (float)sm.comp[c][3 + q][k];
             sm.J[c] = j;
-            sm.f[c] = (float)eps;
         }
     }
     __syncthreads();
 }
 
-// Mixed form: integer sample and fraction of the retarded time of series c
-// at output sample m, from the FP32 constants of the tile centre ic.
-__device__ __forceinline__ void lfa_locate_f32(const LfaArgs& a, const LfaSmem<true>& sm, int c, int64_t m,
-                                               int64_t ic, bool equal, int64_t& j, float& eps, float& Tl,
-                                               float (&n3)[3])
+// Mixed form: retarded sample j (relative: jr = j - J) and fraction of series c
+// at block offset dm = m - ic.
+__device__ __forceinline__ void lfa_ser_locate(const LfaArgs& a, const SerF32& R, float inv_half, float inv_dt, int dm,
+                                               int& jr, float& eps, float& u)
 {
-    const int ch = c >> 1, which = c & 1;
-    const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
-    // in-tile offsets are 32-bit: no 64-bit conversions (FP64 pipe) per sample
-    const float u = (float)(int)(m - ic) * sm.inv_half;
-    const float da = sm.da[c](u);
-    const float up = u - sm.acu[c] - da * sm.u_per_s;
-    const float dT = equal ? 0.f : sm.cu[kQT + l](up);
-    Tl = equal ? a.Lcf : sm.c0[kQT + l] + dT;
-    const float ddt = da + 0.5f * dT + 0.5f * (sm.cu[kRowKR + link_sender(l)](up) + sm.cu[kRowKR + link_receiver(l)](up));
-    for (int q = 0; q < 3; ++q) n3[q] = sm.c0[kQN + 3 * l + q] + sm.cu[kQN + 3 * l + q](up);
-    int64_t jp;
+    u = (float)dm * inv_half;
+    const float D = u * fmaf(u, fmaf(u, R.d3, R.d2), R.d1);
+    int jp;
     float fp;
     if (a.hm.unit_rho) {
-        jp = m - ic;
+        jp = dm;
         fp = 0.f;
     } else {
-        const double P = (double)(m - ic) * a.hm.rho;
+        const double P = (double)dm * a.hm.rho;
         const double fl = floor(P);
-        jp = (int64_t)fl;
+        jp = (int)fl;
         fp = (float)(P - fl);
     }
-    const float v = (fp + sm.f[c]) - ddt * sm.inv_dt;
+    const float v = fmaf(-D, inv_dt, fp + R.f);
     const float fv = floorf(v);
-    j = sm.J[c] + jp + (int)fv;
+    jr = jp + (int)fv;
     eps = v - fv;
+}
+
+__device__ __forceinline__ float cubic4(const float (&c)[4], float u)
+{
+    return fmaf(u, fmaf(u, fmaf(u, c[3], c[2]), c[1]), c[0]);
+}
+
+// hdot interpolated straight from global memory (stencils outside the staged
+// window; kept out of line).
+static __device__ __noinline__ float2 interp_hdot_global_ool(const float* __restrict__ hp, const float* __restrict__ hc,
+                                                      int64_t n, int64_t j, float eps, float inv12dt)
+{
+    float p, q;
+    interp_hdot_global<float>(hp, hc, n, j, eps, inv12dt, p, q);
+    return make_float2(p, q);
 }
 
 // One tile [i0, i0 + kTile) of LFA channels, after lfa_tile_prologue at the
@@ -245,6 +297,7 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
     const double u_per_s = 1.0 / (a.dt_out * half);
     const int t = threadIdx.x;
     const bool equal = (a.kind == LISA_LFA_EQUAL);
+    const int dmt = (int)(i0 - ic);   // block offset of the tile's first sample
     __syncthreads();   // the previous tile's readers of the windows are done
     // z of samples i0-2 .. i0+1 were computed as the previous tile's i0'+256 .. i0'+259
     if (reuse_halo && t < 24) {
@@ -259,8 +312,10 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
         const int64_t m = (t < 6) ? i0 - 2 : i0 + kTile + 1;
         int64_t j;
         if constexpr (MIXED) {
-            float eps, Tl, n3[3];
-            lfa_locate_f32(a, sm, c, m, ic, equal, j, eps, Tl, n3);
+            int jr;
+            float eps, u;
+            lfa_ser_locate(a, sm.ser[c], sm.inv_half, sm.inv_dt, (int)(m - ic), jr, eps, u);
+            j = sm.J[c] + jr;
         } else {
             const double u = (double)(m - ic) / half;
             const int ch = c >> 1, which = c & 1;
@@ -291,6 +346,11 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
     __syncthreads();
     const int64_t wlo = sm.wlo;
     const int wlen = sm.wlen;
+    if constexpr (MIXED) {
+        // window-relative start of each series' stencils (32-bit: |J - wlo| < kWinH
+        // whenever the window is staged; otherwise unused)
+        if (t < 6) sm.jrel[t] = wlen ? (int)(sm.J[t] - wlo) - 15 : 0;
+    }
     Real inv12dt;
     if constexpr (MIXED) inv12dt = a.inv12dtf;
     else inv12dt = 1.0 / (12.0 * a.hm.dt_in);
@@ -323,7 +383,6 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
         c2 = a.sky.c2p; s2 = a.sky.s2p;
         for (int q = 0; q < 3; ++q) { ku[q] = a.sky.u[q]; kv[q] = a.sky.v[q]; }
     }
-    const float Lcf = a.Lcf;
 
     // --- z on the tile and its halo: (kTile + 4) x 6 values ----------------
     const int per = reuse_halo ? kTile : kZW;
@@ -334,41 +393,62 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
         const int64_t m = i0 - 2 + o;
         Real zval = Real(0);
         if (m >= 0 && m < a.nout) {
-            const int ch = c >> 1, which = c & 1;
-            const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
-            Real Tl, n3[3];
-            int64_t j;
-            Real eps;
-            if constexpr (!MIXED) {
+            if constexpr (MIXED) {
+                const SerF32& R = sm.ser[c];
+                int jr;
+                float eps, u;
+                lfa_ser_locate(a, R, sm.inv_half, sm.inv_dt, dmt - 2 + o, jr, eps, u);
+                const float Tl = cubic4(R.T, u);
+                const float n0 = cubic4(R.n[0], u), n1 = cubic4(R.n[1], u), n2 = cubic4(R.n[2], u);
+                const float un = ku[0] * n0 + ku[1] * n1 + ku[2] * n2;
+                const float vn = kv[0] * n0 + kv[1] * n1 + kv[2] * n2;
+                const float xp = un * un - vn * vn, xc = 2.f * un * vn;
+                const int base = sm.jrel[c] + jr;
+                float dp, dc;
+                if (base >= 0 && base + 32 <= wlen) {
+                    float w32[32];
+                    lagrange32_weights(eps, w32);
+                    const float2* pw = sm.dw + base;
+                    float ap = 0.f, ac = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const float2 v = pw[k];
+                        ap = fmaf(w32[k], v.x, ap);
+                        ac = fmaf(w32[k], v.y, ac);
+                    }
+                    dp = ap;
+                    dc = ac;
+                } else {
+                    const float2 r2 = interp_hdot_global_ool(hp, hc, a.hm.n_in, sm.J[c] + jr, eps, inv12dt);
+                    dp = r2.x;
+                    dc = r2.y;
+                }
+                zval = -0.5f * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
+            } else {
+                const int ch = c >> 1, which = c & 1;
+                const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
                 const double u = (double)(m - ic) / half;
                 const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
                 const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
                 const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
                 const double up = u - sh * u_per_s;
-                Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
+                const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
                 const double dtau = sh + 0.5 * Tl
                                   + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
+                double n3[3];
                 for (int q = 0; q < 3; ++q) n3[q] = tg_eval(g, kQN + 3 * l + q, up);
-                double e;
-                split_f64(a.hm, m, dtau, j, e);
-                eps = e;
-            } else {
-                float e, T32, n32[3];
-                lfa_locate_f32(a, sm, c, m, ic, equal, j, e, T32, n32);
-                eps = e;
-                Tl = T32;
-                n3[0] = n32[0];
-                n3[1] = n32[1];
-                n3[2] = n32[2];
+                int64_t j;
+                double eps;
+                split_f64(a.hm, m, dtau, j, eps);
+                const double un = ku[0] * n3[0] + ku[1] * n3[1] + ku[2] * n3[2];
+                const double vn = kv[0] * n3[0] + kv[1] * n3[1] + kv[2] * n3[2];
+                const double xp = un * un - vn * vn, xc = 2.0 * un * vn;
+                double dp, dc;
+                bool ok;
+                dp = interp_pair_w<double>(sm.dw, wlo, wlen, nullptr, j, eps, dc, ok);
+                if (!ok) interp_hdot_global<double>(hp, hc, a.hm.n_in, j, eps, inv12dt, dp, dc);
+                zval = -0.5 * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
             }
-            const Real un = ku[0] * n3[0] + ku[1] * n3[1] + ku[2] * n3[2];
-            const Real vn = kv[0] * n3[0] + kv[1] * n3[1] + kv[2] * n3[2];
-            const Real xp = un * un - vn * vn, xc = Real(2) * un * vn;
-            Real dp, dc;
-            bool ok;
-            dp = interp_pair_w<Real>(sm.dw, wlo, wlen, nullptr, j, eps, dc, ok);
-            if (!ok) interp_hdot_global<Real>(hp, hc, a.hm.n_in, j, eps, inv12dt, dp, dc);
-            zval = Real(-0.5) * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
         }
         sm.zs[c][o] = zval;
     }
@@ -379,9 +459,14 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
         Real* zo = (Real*)a.z;
         for (int c = 0; c < 6; ++c) zo[(int64_t)c * a.nout + i] = sm.zs[c][t + 2];
     }
-    Real dt;
-    if constexpr (MIXED) dt = a.dtf;
-    else dt = a.dt_out;
+    Real k1, k2;   // 1/(12 dt), 1/(12 dt^2)
+    if constexpr (MIXED) {
+        k1 = a.c1f;
+        k2 = a.c2f;
+    } else {
+        k1 = 1.0 / (12.0 * a.dt_out);
+        k2 = k1 / a.dt_out;
+    }
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         Real Ta, Tb;
@@ -390,9 +475,9 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
             Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
             Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
         } else {
-            const float u = (float)(int)(i - ic) * sm.inv_half;
-            Ta = equal ? Lcf : sm.c0[kQT + lfa_arm(ch, 0)] + sm.cu[kQT + lfa_arm(ch, 0)](u);
-            Tb = equal ? Lcf : sm.c0[kQT + lfa_arm(ch, 1)] + sm.cu[kQT + lfa_arm(ch, 1)](u);
+            const float u = (float)(dmt + t) * sm.inv_half;
+            Ta = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 0)] + sm.cu[kQT + lfa_arm(ch, 0)](u);
+            Tb = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 1)] + sm.cu[kQT + lfa_arm(ch, 1)](u);
         }
         const Real* za = sm.zs[2 * ch] + t;       // za[0..4] = z at i-2..i+2
         const Real* zb = sm.zs[2 * ch + 1] + t;
@@ -401,11 +486,11 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
             auto d2 = [&](const Real* z) {
                 const Real e0 = z[1] - z[0], e1 = z[2] - z[1], e2 = z[3] - z[2], e3 = z[4] - z[3];
                 const Real m1 = e1 - e0, c0 = e2 - e1, p1 = e3 - e2;
-                return (Real(14) * c0 - m1 - p1) / (Real(12) * dt * dt);
+                return (Real(14) * c0 - m1 - p1) * k2;
             };
             X[ch] = Real(8) * (Ta + Tb) * (Ta * d2(za) - Tb * d2(zb));
         } else {
-            auto d1 = [&](const Real* z) { return ((z[3] - z[1]) * Real(8) - (z[4] - z[0])) / (Real(12) * dt); };
+            auto d1 = [&](const Real* z) { return ((z[3] - z[1]) * Real(8) - (z[4] - z[0])) * k1; };
             X[ch] = Real(4) * (Ta * d1(za) - Tb * d1(zb));
         }
     }
