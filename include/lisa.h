@@ -324,6 +324,13 @@ int lisa_response_hybrid_corrected(lisa_corrector* c, const lisa_orbit* orbit, c
 int lisa_corrector_report(lisa_corrector* c, int64_t* spot_tiles, int64_t* spot_failed, int64_t* band_tiles,
                           int64_t* fallback_tiles, float* max_spot_err, int reset);
 
+/* Device status (no counterpart in the paper).  Kernels that wait on
+ * asynchronous copies bound every wait (about a second); a wait that gives up
+ * sets bit 0 of a per-device status word and its block stops.  This call
+ * synchronises the device, returns the word in *status (may be NULL), clears
+ * it if reset != 0, and returns LISA_ETIMEOUT if bit 0 was set. */
+int lisa_device_status(unsigned int* status, int reset);
+
 /* Instrumentation (no counterpart in the paper).
  * lisa_profile_enable(1) clears the record and makes every kernel launch of
  * this library on this process record a CUDA event pair on its own stream;

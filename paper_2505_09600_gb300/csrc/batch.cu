@@ -181,6 +181,8 @@ __global__ void __launch_bounds__(kTile) batch_hybrid_kernel(BatchKernelArgs ka)
                 a.inv12dtf = b.inv12dtf;
                 a.c1f = b.c1f;
                 a.c2f = b.c2f;
+                a.h_aligned = 0;
+                a.status = nullptr;
                 lfa_tile_compute<true>(a, i0, sm.lfa, Xl);
             } else {
                 tile_geo_load(sm.lfa.g, b.tab, i0 + kTile / 2, b.sky);

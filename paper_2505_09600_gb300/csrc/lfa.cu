@@ -30,24 +30,63 @@ inline int lfa_group(double dt)
     return G < 1 ? 1 : (G > 8 ? 8 : G);
 }
 
+#ifndef LISA_LFA_MINB
+#define LISA_LFA_MINB 4
+#endif
+// Mixed form: the block's tiles share one prologue; the h window of tile q+1
+// is fetched with bulk copies (two buffers) while tile q is computed.
 template <bool MIXED>
-__global__ void __launch_bounds__(kTile) lfa_kernel(LfaArgs a, int64_t tile_end, int G)
+__global__ void __launch_bounds__(kTile, MIXED ? LISA_LFA_MINB : 1) lfa_kernel(LfaArgs a, int64_t tile_end, int G)
 {
     using Real = typename std::conditional<MIXED, float, double>::type;
-    __shared__ LfaSmem<MIXED> sm;
+    constexpr int NB = MIXED ? 2 : 1;
+    __shared__ LfaSmem<MIXED, NB> sm;
     const int64_t t0 = a.tile0 + (int64_t)blockIdx.x * G;
     const int64_t ic = t0 * kTile + (int64_t)G * kTile / 2;
-    lfa_tile_prologue<MIXED>(a, ic, sm);
-    for (int q = 0; q < G; ++q) {
-        const int64_t i0 = (t0 + q) * (int64_t)kTile;
-        if (t0 + q >= tile_end) break;   // uniform over the block
-        Real X[3];
-        lfa_tile_body<MIXED>(a, i0, ic, sm, X, q > 0);
-        const int64_t i = i0 + threadIdx.x;
-        if constexpr (MIXED) {
-            if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<Real>(a, i, X, sm.barg_c, sm.barg_d, (int)(i - ic));
-        } else {
+    const int nt = (int)(tile_end - t0 < G ? tile_end - t0 : G);
+    if constexpr (MIXED) {
+        if (threadIdx.x == 0) {
+            mbar_init(&sm.bar[0], 1);
+            mbar_init(&sm.bar[1], 1);
+            mbar_init_fence();
+        }
+    }
+    lfa_tile_prologue<MIXED, NB>(a, ic, sm);   // ends with a block barrier
+    if constexpr (!MIXED) {
+        for (int q = 0; q < nt; ++q) {
+            const int64_t i0 = (t0 + q) * (int64_t)kTile;
+            Real X[3];
+            lfa_tile_body<MIXED, NB>(a, i0, ic, sm, X);
+            const int64_t i = i0 + threadIdx.x;
             if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<Real>(a, i, X);
+        }
+    } else {
+        uint32_t ph0 = 0u, ph1 = 0u;   // phase parities of the two buffers' barriers
+        lfa_window<MIXED, NB>(a, t0 * (int64_t)kTile, ic, sm, 0);
+        lfa_stage<MIXED, NB>(a, sm, 0);
+        for (int q = 0; q < nt; ++q) {
+            const int b = q & 1;
+            const int64_t i0 = (t0 + q) * (int64_t)kTile;
+            if (q + 1 < nt) {
+                lfa_window<MIXED, NB>(a, i0 + kTile, ic, sm, b ^ 1);
+                lfa_stage<MIXED, NB>(a, sm, b ^ 1);
+            }
+            if (!lfa_wait<MIXED, NB>(a, sm, b, b ? ph1 : ph0)) return;
+            if (sm.win[b].bulk) {
+                if (b) ph1 ^= 1u;
+                else ph0 ^= 1u;
+            }
+            // z of samples i0-2 .. i0+1 are the previous tile's last four values
+            if (q > 0 && threadIdx.x < 24) {
+                const int c = threadIdx.x >> 2, o = threadIdx.x & 3;
+                sm.zs[c][o] = sm.zs[c][kTile + o];
+            }
+            lfa_hdot<MIXED, NB>(a, sm, b);
+            lfa_zvalues<MIXED, NB>(a, i0, ic, sm, b, q > 0);
+            Real X[3];
+            lfa_channels<MIXED, NB>(a, i0, ic, sm, X);
+            const int64_t i = i0 + threadIdx.x;
+            if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<Real>(a, i, X, sm.barg_c, sm.barg_d, (int)(i - ic));
         }
     }
 }
@@ -77,6 +116,8 @@ int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const l
     a.tile0 = i_begin / kTile;
     a.bl = bl;
     lfa_args_f32(a);
+    a.h_aligned = ((uintptr_t)hp % 16 == 0) && ((uintptr_t)hc % 16 == 0);
+    a.status = device_status_ptr();
     const int64_t tiles = (i_end - 1) / kTile - a.tile0 + 1;
     const int64_t tile_end = a.tile0 + tiles;
     prof_before(gen == kLfaOwnTime ? (precision == LISA_MIXED ? "lfa_own_mixed" : "lfa_own_f64")

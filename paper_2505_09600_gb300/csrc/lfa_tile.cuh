@@ -4,6 +4,7 @@
 
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "lisa_common.cuh"
 #include "lisa_internal.cuh"
 #include "tile_geo.cuh"
@@ -12,6 +13,7 @@ namespace lisa {
 
 constexpr int kWinH = kTile + 384;
 constexpr int kZW = kTile + 4;
+constexpr int kWinP = kWinH + 8;   // planar h buffers: room for 16-byte alignment of the copy
 
 template <typename Real>
 struct PairT;
@@ -36,6 +38,8 @@ struct LfaArgs {
     BlendSpec bl;
     float Lcf, dtf, inv12dtf;   // FP32 copies of Lc, dt_out and 1/(12 dt_in) (mixed form)
     float c1f, c2f;             // 1/(12 dt_out) and 1/(12 dt_out^2): the channels' stencil scales
+    int h_aligned;              // hp, hc start on 16-byte boundaries (bulk copies allowed)
+    unsigned int* status;       // device status word (bounded waits)
 };
 
 // Fill the FP32 copies of LfaArgs (host side).
@@ -119,27 +123,50 @@ __device__ __forceinline__ void interp_hdot_global(const Real* __restrict__ hp, 
 // block's coordinate u = (m - ic) * 2/S around the centre sample ic: the
 // total delay d(u) = D0 + d1 u + d2 u^2 + d3 u^3 (D0 split exactly into J, f
 // in FP64), the light time T_l and the link vector n_l at the retarded time.
-struct SerF32 {
+struct __align__(16) SerF32 {
     float f, d1, d2, d3;      // centre fraction, in-block delay variation (s)
     float T[4];               // T_l(u) = T[0] + T[1] u + T[2] u^2 + T[3] u^3
     float n[3][4];            // n_l components, same form
 };
 
-template <bool MIXED>
+// A record read as five 16-byte shared-memory loads.
+__device__ __forceinline__ SerF32 load_ser(const SerF32& r)
+{
+    const float4* p = reinterpret_cast<const float4*>(&r);
+    const float4 a = p[0], b = p[1], c = p[2], d = p[3], e = p[4];
+    SerF32 o;
+    o.f = a.x; o.d1 = a.y; o.d2 = a.z; o.d3 = a.w;
+    o.T[0] = b.x; o.T[1] = b.y; o.T[2] = b.z; o.T[3] = b.w;
+    o.n[0][0] = c.x; o.n[0][1] = c.y; o.n[0][2] = c.z; o.n[0][3] = c.w;
+    o.n[1][0] = d.x; o.n[1][1] = d.y; o.n[1][2] = d.z; o.n[1][3] = d.w;
+    o.n[2][0] = e.x; o.n[2][1] = e.y; o.n[2][2] = e.z; o.n[2][3] = e.w;
+    return o;
+}
+
+// Staged window of one tile: hdot on samples [wlo, wlo + wlen) of the h grid
+// (wlen = 0: not staged, stencils read global memory), built from h on
+// [a0, a0 + nh) held in a planar buffer.
+struct LfaWin {
+    int64_t wlo, a0;
+    int wlen, nh;
+    int bulk;                 // filled by an asynchronous bulk copy
+    int jrel[6];              // mixed form: J_c - wlo - 15
+};
+
+template <bool MIXED, int NB = 1>
 struct LfaSmem {
     using Real = typename std::conditional<MIXED, float, double>::type;
     using Real2 = typename PairT<Real>::T;
     TileGeo g;
-    Real2 hw[kWinH];      // h window (+2 each side)
-    Real2 dw[kWinH];      // hdot window
+    alignas(16) Real hb[NB][2][kWinP];   // h+ and hx windows (NB buffers)
+    Real2 dw[kWinH];          // hdot window (interleaved pairs)
     Real zs[6][kZW];
+    LfaWin win[NB];
+    uint64_t bar[NB];         // completion barriers of the bulk copies
     int64_t jends[12];
-    int64_t wlo;
-    int wlen;
     // mixed: per-series records, arm rows (centre value, cubic) for the channels
     SerF32 ser[6];
     int64_t J[6];
-    int jrel[6];                  // J - wlo of the current tile
     double comp[6][6][4];         // prologue scratch: composed rows per series
     float c0[kRows];
     Cubic cu[kRows];
@@ -151,8 +178,8 @@ struct LfaSmem {
 // of the segment polynomials) and, for the mixed form, the FP32 records of
 // the six z series.  Every thread of the block must call it (it
 // synchronises).
-template <bool MIXED>
-__device__ void lfa_tile_prologue(const LfaArgs& a, int64_t ic, LfaSmem<MIXED>& sm)
+template <bool MIXED, int NB>
+__device__ void lfa_tile_prologue(const LfaArgs& a, int64_t ic, LfaSmem<MIXED, NB>& sm)
 {
     TileGeo& g = sm.g;
     const int t = threadIdx.x;
@@ -275,38 +302,15 @@ static __device__ __noinline__ float2 interp_hdot_global_ool(const float* __rest
     return make_float2(p, q);
 }
 
-// One tile [i0, i0 + kTile) of LFA channels, after lfa_tile_prologue at the
-// centre ic (the tile's own centre, or that of a group of tiles sharing one
-// prologue): on return thread t holds X, Y, Z of sample i0 + t (before AET,
-// blend and store) and z has been written if requested.  With reuse_halo the
-// previous tile [i0 - kTile, i0) was the last one computed in this block, and
-// its last four z values are this tile's leading halo: the block then
-// computes exactly kTile values per series (no straggling round for the
-// halo).  Every thread of the block must call it; it does not return early,
-// so it can run inside a persistent loop.
-template <bool MIXED>
-__device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MIXED>& sm,
-                              typename std::conditional<MIXED, float, double>::type (&X)[3], bool reuse_halo = false)
+// Window of the tile starting at i0 (prologue centre ic) into sm.win[b]: the
+// retarded samples of the six series at the tile's two ends (2-sample halo
+// included) bound the hdot window.  Every thread must call it (it
+// synchronises twice).
+template <bool MIXED, int NB>
+__device__ void lfa_window(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MIXED, NB>& sm, int b)
 {
-    using Real = typename std::conditional<MIXED, float, double>::type;
-    using Real2 = typename PairT<Real>::T;
-    TileGeo& g = sm.g;
-    const Real* __restrict__ hp = (const Real*)a.hp;
-    const Real* __restrict__ hc = (const Real*)a.hc;
-    const double half = 0.5 * a.tab.S;
-    const double u_per_s = 1.0 / (a.dt_out * half);
     const int t = threadIdx.x;
     const bool equal = (a.kind == LISA_LFA_EQUAL);
-    const int dmt = (int)(i0 - ic);   // block offset of the tile's first sample
-    __syncthreads();   // the previous tile's readers of the windows are done
-    // z of samples i0-2 .. i0+1 were computed as the previous tile's i0'+256 .. i0'+259
-    if (reuse_halo && t < 24) {
-        const int c = t >> 2, o = t & 3;
-        sm.zs[c][o] = sm.zs[c][kTile + o];
-    }
-
-    // --- window of h this tile reaches: the retarded samples of the 6 series
-    //     at the tile's two ends (2-sample halo included)
     if (t < 12) {
         const int c = t % 6;
         const int64_t m = (t < 6) ? i0 - 2 : i0 + kTile + 1;
@@ -317,6 +321,9 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
             lfa_ser_locate(a, sm.ser[c], sm.inv_half, sm.inv_dt, (int)(m - ic), jr, eps, u);
             j = sm.J[c] + jr;
         } else {
+            const TileGeo& g = sm.g;
+            const double half = 0.5 * a.tab.S;
+            const double u_per_s = 1.0 / (a.dt_out * half);
             const double u = (double)(m - ic) / half;
             const int ch = c >> 1, which = c & 1;
             const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
@@ -339,42 +346,126 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
             lo = sm.jends[k] < lo ? sm.jends[k] : lo;
             hi = sm.jends[k] > hi ? sm.jends[k] : hi;
         }
-        sm.wlo = lo - 15 - 3;
-        const int64_t len = (hi + 16 + 3) - sm.wlo + 1;
-        sm.wlen = (len + 4 <= kWinH) ? (int)len : 0;
+        LfaWin& w = sm.win[b];
+        w.wlo = lo - 15 - 3;
+        const int64_t len = (hi + 16 + 3) - w.wlo + 1;
+        w.wlen = (len + 4 <= kWinH) ? (int)len : 0;
+        // h needed on [wlo - 2, wlo + wlen + 2); a bulk copy moves whole
+        // 16-byte groups from a 16-byte boundary and must stay on the h array
+        const int64_t s0 = w.wlo - 2, s1 = w.wlo + w.wlen + 2;
+        const int64_t a0 = s0 - (((s0 % 4) + 4) % 4);
+        const int64_t a1 = s1 + (((4 - s1 % 4) % 4 + 4) % 4);
+        const bool bulk = MIXED && NB > 1 && a.h_aligned && w.wlen > 0 && a0 >= 0 && a1 <= a.hm.n_in &&
+                          a1 - a0 <= kWinP;
+        w.bulk = bulk ? 1 : 0;
+        w.a0 = bulk ? a0 : s0;
+        w.nh = bulk ? (int)(a1 - a0) : (w.wlen > 0 ? w.wlen + 4 : 0);
+        if constexpr (MIXED) {
+            // window-relative start of each series' stencils (32-bit: |J - wlo| <
+            // kWinH whenever the window is staged; otherwise unused)
+            for (int c = 0; c < 6; ++c) w.jrel[c] = w.wlen ? (int)(sm.J[c] - w.wlo) - 15 : 0;
+        }
     }
     __syncthreads();
-    const int64_t wlo = sm.wlo;
-    const int wlen = sm.wlen;
-    if constexpr (MIXED) {
-        // window-relative start of each series' stencils (32-bit: |J - wlo| < kWinH
-        // whenever the window is staged; otherwise unused)
-        if (t < 6) sm.jrel[t] = wlen ? (int)(sm.J[t] - wlo) - 15 : 0;
+}
+
+// Stage h of window b: one bulk copy per polarisation issued by thread 0
+// (completing on sm.bar[b]), or plain loads by every thread (complete at the
+// next block barrier).
+template <bool MIXED, int NB>
+__device__ void lfa_stage(const LfaArgs& a, LfaSmem<MIXED, NB>& sm, int b)
+{
+    using Real = typename std::conditional<MIXED, float, double>::type;
+    const LfaWin& w = sm.win[b];
+    const Real* __restrict__ hp = (const Real*)a.hp;
+    const Real* __restrict__ hc = (const Real*)a.hc;
+    if (w.bulk) {
+        if constexpr (MIXED && NB > 1) {
+            if (threadIdx.x == 0) {
+                const uint32_t bytes = (uint32_t)w.nh * (uint32_t)sizeof(float);
+                mbar_arrive_expect_tx(&sm.bar[b], 2u * bytes);
+                bulk_copy_g2s(sm.hb[b][0], hp + w.a0, bytes, &sm.bar[b]);
+                bulk_copy_g2s(sm.hb[b][1], hc + w.a0, bytes, &sm.bar[b]);
+            }
+        }
+    } else {
+        for (int k = threadIdx.x; k < w.nh; k += blockDim.x) {
+            const int64_t idx = w.a0 + k;
+            const bool in = idx >= 0 && idx < a.hm.n_in;
+            sm.hb[b][0][k] = in ? hp[idx] : Real(0);
+            sm.hb[b][1][k] = in ? hc[idx] : Real(0);
+        }
     }
+}
+
+// Wait until window b is staged (bounded for bulk copies).  Synchronises the
+// block.  False (for every thread) if the wait timed out: the status word
+// is flagged after a second bounded wait for the copy to land, and the block
+// must stop.
+template <bool MIXED, int NB>
+__device__ bool lfa_wait(const LfaArgs& a, LfaSmem<MIXED, NB>& sm, int b, uint32_t parity)
+{
+    bool ok = true;
+    if constexpr (MIXED && NB > 1) {
+        if (sm.win[b].bulk) ok = mbar_wait_bounded(&sm.bar[b], parity);
+    }
+    if (__syncthreads_or(ok ? 0 : 1)) {
+        if constexpr (MIXED && NB > 1) {
+            if (threadIdx.x == 0) flag_timeout(a.status);
+            if (sm.win[b].bulk) mbar_wait_bounded(&sm.bar[b], parity);
+        }
+        return false;
+    }
+    return true;
+}
+
+// hdot of window b (5-point central stencil on the staged h, zero outside the
+// h grid).  Synchronises the block at the end.
+template <bool MIXED, int NB>
+__device__ void lfa_hdot(const LfaArgs& a, LfaSmem<MIXED, NB>& sm, int b)
+{
+    using Real = typename std::conditional<MIXED, float, double>::type;
+    using Real2 = typename PairT<Real>::T;
+    const LfaWin& w = sm.win[b];
     Real inv12dt;
     if constexpr (MIXED) inv12dt = a.inv12dtf;
     else inv12dt = 1.0 / (12.0 * a.hm.dt_in);
-    // h over [wlo-2, wlo+wlen+2), then hdot over [wlo, wlo+wlen)
-    for (int k = t; k < wlen + 4; k += blockDim.x) {
-        const int64_t idx = wlo - 2 + k;
-        Real2 v;
-        v.x = (idx >= 0 && idx < a.hm.n_in) ? hp[idx] : Real(0);
-        v.y = (idx >= 0 && idx < a.hm.n_in) ? hc[idx] : Real(0);
-        sm.hw[k] = v;
-    }
-    __syncthreads();
-    for (int k = t; k < wlen; k += blockDim.x) {
-        // hdot is defined on the h grid only and is zero outside it, like h
-        const int64_t idx = wlo + k;
-        const Real2 m2 = sm.hw[k], m1 = sm.hw[k + 1], p1 = sm.hw[k + 3], p2 = sm.hw[k + 4];
-        Real2 d;
+    const int off = (int)(w.wlo - 2 - w.a0);
+    const Real* P = sm.hb[b][0] + off;
+    const Real* C = sm.hb[b][1] + off;
+    for (int k = threadIdx.x; k < w.wlen; k += blockDim.x) {
+        const int64_t idx = w.wlo + k;
         const bool in = (idx >= 0 && idx < a.hm.n_in);
-        d.x = in ? ((p1.x - m1.x) * Real(8) - (p2.x - m2.x)) * inv12dt : Real(0);
-        d.y = in ? ((p1.y - m1.y) * Real(8) - (p2.y - m2.y)) * inv12dt : Real(0);
+        Real2 d;
+        d.x = in ? ((P[k + 3] - P[k + 1]) * Real(8) - (P[k + 4] - P[k])) * inv12dt : Real(0);
+        d.y = in ? ((C[k + 3] - C[k + 1]) * Real(8) - (C[k + 4] - C[k])) * inv12dt : Real(0);
         sm.dw[k] = d;
     }
     __syncthreads();
+}
 
+// z values of the tile starting at i0 (window b staged, hdot in sm.dw): the
+// tile and its 2-sample halo, or with reuse_halo only the kTile new values
+// per series (the previous tile's last four values are this tile's leading
+// halo, copied by the caller).  Synchronises the block at the end.
+template <bool MIXED, int NB>
+__device__ void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MIXED, NB>& sm, int b, bool reuse_halo)
+{
+    using Real = typename std::conditional<MIXED, float, double>::type;
+    const Real* __restrict__ hp = (const Real*)a.hp;
+    const Real* __restrict__ hc = (const Real*)a.hc;
+    const TileGeo& g = sm.g;
+    const LfaWin& W = sm.win[b];
+    const int64_t wlo = W.wlo;
+    const int wlen = W.wlen;
+    const double half = 0.5 * a.tab.S;
+    const double u_per_s = 1.0 / (a.dt_out * half);
+    const int t = threadIdx.x;
+    const bool equal = (a.kind == LISA_LFA_EQUAL);
+    const int dmt = (int)(i0 - ic);   // block offset of the tile's first sample
+    Real inv12dt;
+    if constexpr (MIXED) inv12dt = a.inv12dtf;
+    else inv12dt = 1.0 / (12.0 * a.hm.dt_in);
     Real c2, s2, ku[3], kv[3];
     if constexpr (MIXED) {
         c2 = a.sky.c2f; s2 = a.sky.s2f;
@@ -383,8 +474,10 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
         c2 = a.sky.c2p; s2 = a.sky.s2p;
         for (int q = 0; q < 3; ++q) { ku[q] = a.sky.u[q]; kv[q] = a.sky.v[q]; }
     }
-
-    // --- z on the tile and its halo: (kTile + 4) x 6 values ----------------
+    // After a reused halo every series has exactly kTile new values (iteration
+    // c covers series c for the whole block).  On interior tiles no sample of
+    // the tile or its halo is off the grid.
+    const bool interior = i0 - 2 >= 0 && i0 + kTile + 2 <= a.nout;
     const int per = reuse_halo ? kTile : kZW;
     for (int w = t; w < 6 * per; w += blockDim.x) {
         // constant divisors: kTile values per series after a reused halo, else kZW
@@ -392,39 +485,65 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
         const int o = reuse_halo ? 4 + w % kTile : w % kZW;
         const int64_t m = i0 - 2 + o;
         Real zval = Real(0);
-        if (m >= 0 && m < a.nout) {
-            if constexpr (MIXED) {
-                const SerF32& R = sm.ser[c];
-                int jr;
-                float eps, u;
-                lfa_ser_locate(a, R, sm.inv_half, sm.inv_dt, dmt - 2 + o, jr, eps, u);
-                const float Tl = cubic4(R.T, u);
-                const float n0 = cubic4(R.n[0], u), n1 = cubic4(R.n[1], u), n2 = cubic4(R.n[2], u);
-                const float un = ku[0] * n0 + ku[1] * n1 + ku[2] * n2;
-                const float vn = kv[0] * n0 + kv[1] * n1 + kv[2] * n2;
-                const float xp = un * un - vn * vn, xc = 2.f * un * vn;
-                const int base = sm.jrel[c] + jr;
-                float dp, dc;
-                if (base >= 0 && base + 32 <= wlen) {
-                    float w32[32];
-                    lagrange32_weights(eps, w32);
-                    const float2* pw = sm.dw + base;
-                    float ap = 0.f, ac = 0.f;
+        if constexpr (MIXED) {
+            // Branch-free in the common case: off-grid samples (edge tiles only)
+            // are computed on clamped indices and masked; stencils outside the
+            // staged window are redone from global memory under a warp vote.
+            const bool valid = interior || (m >= 0 && m < a.nout);
+            const float4 r0 = reinterpret_cast<const float4*>(&sm.ser[c])[0];   // f, d1, d2, d3
+            const float u = (float)(dmt - 2 + o) * sm.inv_half;
+            const float D = u * fmaf(u, fmaf(u, r0.w, r0.z), r0.y);
+            int jp;
+            float fp;
+            if (a.hm.unit_rho) {
+                jp = dmt - 2 + o;
+                fp = 0.f;
+            } else {
+                const double P = (double)(dmt - 2 + o) * a.hm.rho;
+                const double fl = floor(P);
+                jp = (int)fl;
+                fp = (float)(P - fl);
+            }
+            const float v = fmaf(-D, sm.inv_dt, fp + r0.x);
+            const float fv = floorf(v);
+            const int jr = jp + (int)fv;
+            const float eps = v - fv;
+            const int base = W.jrel[c] + jr;
+            const bool inwin = base >= 0 && base + 32 <= wlen;
+            float dp, dc;
+            {
+                float w32[32];
+                lagrange32_weights(eps, w32);
+                const float2* pw = sm.dw + (inwin ? base : 0);
+                float ap = 0.f, ac = 0.f;
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const float2 v = pw[k];
-                        ap = fmaf(w32[k], v.x, ap);
-                        ac = fmaf(w32[k], v.y, ac);
-                    }
-                    dp = ap;
-                    dc = ac;
-                } else {
+                for (int k = 0; k < 32; ++k) {
+                    const float2 hv = pw[k];
+                    ap = fmaf(w32[k], hv.x, ap);
+                    ac = fmaf(w32[k], hv.y, ac);
+                }
+                dp = ap;
+                dc = ac;
+            }
+            if (__any_sync(__activemask(), !inwin)) {
+                if (!inwin && valid) {
                     const float2 r2 = interp_hdot_global_ool(hp, hc, a.hm.n_in, sm.J[c] + jr, eps, inv12dt);
                     dp = r2.x;
                     dc = r2.y;
                 }
-                zval = -0.5f * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
-            } else {
+            }
+            const float4* rp = reinterpret_cast<const float4*>(&sm.ser[c]);
+            const float4 rT = rp[1], rn0 = rp[2], rn1 = rp[3], rn2 = rp[4];
+            const float Tl = fmaf(u, fmaf(u, fmaf(u, rT.w, rT.z), rT.y), rT.x);
+            const float n0 = fmaf(u, fmaf(u, fmaf(u, rn0.w, rn0.z), rn0.y), rn0.x);
+            const float n1 = fmaf(u, fmaf(u, fmaf(u, rn1.w, rn1.z), rn1.y), rn1.x);
+            const float n2 = fmaf(u, fmaf(u, fmaf(u, rn2.w, rn2.z), rn2.y), rn2.x);
+            const float un = ku[0] * n0 + ku[1] * n1 + ku[2] * n2;
+            const float vn = kv[0] * n0 + kv[1] * n1 + kv[2] * n2;
+            const float xp = un * un - vn * vn, xc = 2.f * un * vn;
+            zval = valid ? -0.5f * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2)) : 0.f;
+        } else if (interior || (m >= 0 && m < a.nout)) {
+            {
                 const int ch = c >> 1, which = c & 1;
                 const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
                 const double u = (double)(m - ic) / half;
@@ -453,7 +572,20 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
         sm.zs[c][o] = zval;
     }
     __syncthreads();
+}
 
+// Channels of sample i0 + t from the z values in shared memory (and z stored
+// if requested).
+template <bool MIXED, int NB>
+__device__ void lfa_channels(const LfaArgs& a, int64_t i0, int64_t ic, const LfaSmem<MIXED, NB>& sm,
+                             typename std::conditional<MIXED, float, double>::type (&X)[3])
+{
+    using Real = typename std::conditional<MIXED, float, double>::type;
+    const TileGeo& g = sm.g;
+    const int t = threadIdx.x;
+    const bool equal = (a.kind == LISA_LFA_EQUAL);
+    const double half = 0.5 * a.tab.S;
+    const int dmt = (int)(i0 - ic);
     const int64_t i = i0 + t;
     if (a.z && i >= a.i_begin && i < a.i_end) {
         Real* zo = (Real*)a.z;
@@ -496,14 +628,32 @@ __device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<
     }
 }
 
+// One tile [i0, i0 + kTile) after lfa_tile_prologue at the centre ic, staged
+// with plain loads (one buffer): on return thread t holds X, Y, Z of sample
+// i0 + t (before AET, blend and store) and z has been written if requested.
+// Every thread of the block must call it; it does not return early, so it
+// can run inside a persistent loop.
+template <bool MIXED, int NB>
+__device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MIXED, NB>& sm,
+                              typename std::conditional<MIXED, float, double>::type (&X)[3])
+{
+    __syncthreads();   // the previous tile's readers of the shared buffers are done
+    lfa_window<MIXED, NB>(a, i0, ic, sm, 0);
+    lfa_stage<MIXED, NB>(a, sm, 0);
+    __syncthreads();
+    lfa_hdot<MIXED, NB>(a, sm, 0);
+    lfa_zvalues<MIXED, NB>(a, i0, ic, sm, 0, false);
+    lfa_channels<MIXED, NB>(a, i0, ic, sm, X);
+}
+
 // Prologue and body of one tile around its own centre.
-template <bool MIXED>
-__device__ __forceinline__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED>& sm,
+template <bool MIXED, int NB>
+__device__ __forceinline__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED, NB>& sm,
                                                  typename std::conditional<MIXED, float, double>::type (&X)[3])
 {
     const int64_t ic = i0 + kTile / 2;
-    lfa_tile_prologue<MIXED>(a, ic, sm);
-    lfa_tile_body<MIXED>(a, i0, ic, sm, X);
+    lfa_tile_prologue<MIXED, NB>(a, ic, sm);
+    lfa_tile_body<MIXED, NB>(a, i0, ic, sm, X);
 }
 
 // AET, sigmoid weight (LFA side: eps = +1) and store of one sample.

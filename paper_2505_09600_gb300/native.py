@@ -125,6 +125,7 @@ _SIGS = {
     "lisa_profile_enable": (C.c_int, [C.c_int]),
     "lisa_profile_query": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "lisa_launch_count": (C.c_int64, []),
+    "lisa_device_status": (C.c_int, [C.POINTER(C.c_uint), C.c_int]),
     "lisa_response_hybrid": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
                                        C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                        lisa_grid, _P, _P]),
@@ -335,6 +336,14 @@ def lisa_profile_query(name=None):
 
 def lisa_launch_count():
     return load().lisa_launch_count()
+
+
+def lisa_device_status(reset=True):
+    """Device status word (bit 0: a bounded device wait timed out); raises
+    LisaError(LISA_ETIMEOUT) if it was set."""
+    st = C.c_uint()
+    _check(load().lisa_device_status(C.byref(st), 1 if reset else 0), "lisa_device_status")
+    return st.value
 
 
 def lisa_response_hybrid_static(orbit, sky, h_grid, hp, hc, precision, tdi_gen, lfa_kind, channels, t_hyb, T_win,
