@@ -75,7 +75,7 @@ def fp32_peak_tflops(pk):
 
 def kernel_src_hash():
     h = hashlib.sha256()
-    for f in ("lfa.cu", "lisa_common.cuh", "tile_geo.cuh"):
+    for f in ("lfa.cu", "lfa_tile.cuh", "async_copy.cuh", "lisa_common.cuh", "tile_geo.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2505_09600_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -234,6 +234,132 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None):
 
 
 # ---------------------------------------------------------------------------
+# learned corrector and batched plan (reported next to the headline)
+# ---------------------------------------------------------------------------
+
+def _timed(torch, stream, flush, fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(np.median(ms))
+
+
+def _lfa_side_error(got, ref, i_end, m):
+    g, r = got[:, m:i_end], ref[:, m:i_end]
+    return float(np.abs(g - r).max() / np.abs(r).max())
+
+
+def bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig,
+                    n_sources=256, steps=3000, batch=8192, f_raised=5e-3):
+    """Train the LFA-link corrector on the GPU (seeded sources of the band
+    1e-4..2e-2 Hz) and time the corrected hybrid on the headline workload at
+    f_H = 1e-3 Hz and at a raised switch frequency; report its error on the
+    LFA side against the FP64 full response next to the plain hybrid's."""
+    import synth
+    from paper_2505_09600_gb300 import corrector as CT
+    t0 = time.perf_counter()
+    params = synth.corrector_params(nsrc=n_sources, seed=synth.SEED_BASE + 4, n=4096)
+    devsrc = []
+    for p in params:
+        s = synth.corrector_source(p)
+        devsrc.append(dict(grid=s.grid, sky=(s.beta, s.lam, s.psi),
+                           hp32=torch.as_tensor(s.hp.astype(np.float32), device=dev),
+                           hc32=torch.as_tensor(s.hc.astype(np.float32), device=dev),
+                           hp64=torch.as_tensor(s.hp, device=dev), hc64=torch.as_tensor(s.hc, device=dev)))
+    t_gen = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    feats, target = CT.training_set(orbit, devsrc)
+    b.record(stream)
+    b.synchronize()
+    t_set = a.elapsed_time(b)
+    c = L.LisaCorrector(None, seed=2505)
+    losses = torch.empty(steps, device=dev)
+    a.record(stream)
+    c.train(feats, target, steps=steps, batch=batch, lr_max=2e-3, lr_min=2e-5, seed=11, losses=losses)
+    b.record(stream)
+    b.synchronize()
+    t_train = a.elapsed_time(b)
+    ls = losses.cpu().numpy()
+    c.configure(f_lo=1e-4, f_hi=2e-2, spot_every=64, spot_tol=0.05)
+    n = src.n
+    hp64 = torch.as_tensor(src.hp, device=dev)
+    hc64 = torch.as_tensor(src.hc, device=dev)
+    ref = torch.empty((3, n), device=dev, dtype=torch.float64)
+    L.lisa_response_full(orbit, sky, src.grid, hp64, hc64, L.F64, 20, L.AET, src.grid, ref)
+    refh = ref.cpu().numpy()
+    del ref, hp64, hc64
+    m = CT.edge_margin(src.dt)
+    res = {"train_sources": n_sources, "train_rows": int(feats.shape[0]), "train_steps": steps, "batch": batch,
+           "train_ms": round(t_train, 1), "train_rows_per_s": steps * batch / (t_train / 1e3),
+           "training_set_ms": round(t_set, 1), "source_generation_s": round(t_gen, 2),
+           "loss_first": float(ls[:50].mean()), "loss_last": float(ls[-200:].mean()),
+           "target_mean_square": float(target.square().sum(1).mean())}
+    del feats, target
+    forms = {}
+    for fH in (F_HYB, f_raised):
+        tHx = L.lisa_t_hyb_from_f(fH, src.mc_s, src.tc)
+        i_end = int(min(n, math.floor((tHx + Tw / 2 - src.t0) / src.dt) + 1))
+        fn = (lambda tHx=tHx: c.hybrid(orbit, sky, src.grid, hp32, hc32, 20, L.AET, tHx, Tw, sig, src.grid, out32))
+        ms = _timed(torch, stream, flush, fn)
+        fn()
+        err = _lfa_side_error(out32.cpu().numpy().astype(np.float64), refh, i_end, m)
+        forms["corrected_hybrid20_f%.0e" % fH] = {"ms": round(ms, 4), "samples_per_s": n / (ms / 1e3),
+                                                   "lfa_side_err": err}
+        L.lisa_response_hybrid(orbit, sky, src.grid, hp32, hc32, L.MIXED, 20, 0, L.AET, tHx, Tw, sig, src.grid, out32)
+        torch.cuda.synchronize()
+        forms["plain_hybrid20_f%.0e" % fH] = {"lfa_side_err": _lfa_side_error(out32.cpu().numpy().astype(np.float64),
+                                                                               refh, i_end, m)}
+    rep = c.report()
+    res["forms"] = forms
+    res["spot_checks"] = {k: rep[k] for k in ("spot_tiles", "spot_failed", "band_tiles", "fallback_tiles",
+                                             "max_spot_err", "status")}
+    res["error_measure"] = ("max |X - X_FP64full| / max |X_FP64full| over the LFA side t <= t_H + T/2 "
+                            "(A, E, T together), first and last %d samples excluded" % m)
+    c.close()
+    return res
+
+
+def bench_batch(L, torch, dev, orbit, flush, stream, args):
+    """Batched hybrid plan over the seeded config-3 population (Mc log-U
+    [1e4, 1e7], q U[1, 10], 1 day to 3 months at 5 or 10 s): one persistent
+    launch, autotuned tiles, captured graph."""
+    import synth
+    params = synth.batch_params(nsrc=args.batch_sources, seed=synth.SEED_BASE + 3)
+    t0 = time.perf_counter()
+    descs = []
+    total = 0
+    for p in params:
+        s = synth.batch_source(p)
+        tHs = L.lisa_t_hyb_from_f(F_HYB, s.mc_s, s.tc)
+        descs.append(dict(grid=s.grid, hp=torch.as_tensor(s.hp.astype(np.float32), device=dev),
+                          hc=torch.as_tensor(s.hc.astype(np.float32), device=dev),
+                          sky=(s.beta, s.lam, s.psi), t_hyb=tHs, out=torch.empty((3, s.n), device=dev)))
+        total += s.n
+    t_gen = time.perf_counter() - t0
+    plan = L.LisaPlan(orbit, descs)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        tune = plan.autotune(stream=st.cuda_stream)
+        plan.capture_graph(st.cuda_stream)
+        fn = lambda: plan.replay(stream=st.cuda_stream)   # noqa: E731
+        ms = _timed(torch, st, flush, fn, reps=5)
+    plan.close()
+    return {"sources": len(descs), "samples": total, "ms": round(ms, 3), "samples_per_s": total / (ms / 1e3),
+            "autotune": tune, "source_generation_s": round(t_gen, 1),
+            "workload": "hybrid TDI2.0 AET, f_hyb=1e-3 Hz, mixed precision, one persistent launch (graph replay)"}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -369,6 +495,13 @@ def run_ours(args):
             forms[name] = {"ms": round(best, 4), "samples_per_s": n / (best / 1e3)}
         del hp64, hc64, out64
 
+    corrector = None
+    if not args.no_corrector and rank == 0:
+        corrector = bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig)
+    batched = None
+    if not args.no_batch and rank == 0:
+        batched = bench_batch(L, torch, dev, orbit, flush, stream, args)
+
     gpu_out = out32.float().cpu().numpy().astype(np.float64) if (rank == 0 and world == 1 and not args.no_cpu) else None
     if rank != 0:
         if world > 1:
@@ -407,6 +540,10 @@ def run_ours(args):
         "forms": forms,
         "gpu_name": torch.cuda.get_device_name(dev),
     }
+    if corrector is not None:
+        line["corrector"] = corrector
+    if batched is not None:
+        line["batched"] = batched
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = oracle_hybrid_rate(src, budget_s=args.cpu_budget, gpu_out=gpu_out)
     print(json.dumps(line), flush=True)
@@ -449,6 +586,9 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-corrector", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-sources", type=int, default=1024)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
