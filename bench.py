@@ -257,12 +257,40 @@ def _lfa_side_error(got, ref, i_end, m):
     return float(np.abs(g - r).max() / np.abs(r).max())
 
 
+def kernel_breakdown(L, torch, fn):
+    """Device ms per kernel name of one call (lisa_profile event pairs)."""
+    names = ("seg_table", "lfa_own_mixed", "lfa_mixed", "corr_features", "mlp_forward", "corr_fallback_all",
+             "corr_fallback", "links_full_mixed", "tdi_mixed", "batch")
+    L.lisa_profile_enable(True)
+    fn()
+    torch.cuda.synchronize()
+    out = {}
+    total, _ = L.lisa_profile_query(None)
+    for nm in names:
+        ms, cnt = L.lisa_profile_query(nm)
+        if cnt:
+            out[nm] = round(ms, 4)
+    # fallback names overlap ("corr_fallback" also matches "corr_fallback_all")
+    if "corr_fallback" in out and "corr_fallback_all" in out:
+        out["corr_fallback"] = round(out["corr_fallback"] - out["corr_fallback_all"], 4)
+    if "lfa_mixed" in out and "lfa_own_mixed" in out:
+        pass
+    out["all"] = round(total, 4)
+    L.lisa_profile_enable(False)
+    return out
+
+
+F_H_GRID = (1e-3, 1.5e-3, 2e-3, 3e-3, 4e-3, 6e-3, 8e-3, 1e-2, 1.4e-2, 2e-2)
+
+
 def bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig,
-                    n_sources=256, steps=3000, batch=8192, f_raised=5e-3):
+                    n_sources=256, steps=3000, batch=8192, n_sweep=8):
     """Train the LFA-link corrector on the GPU (seeded sources of the band
-    1e-4..2e-2 Hz) and time the corrected hybrid on the headline workload at
-    f_H = 1e-3 Hz and at a raised switch frequency; report its error on the
-    LFA side against the FP64 full response next to the plain hybrid's."""
+    1e-4..2e-2 Hz); on seeded held-out chirps sweeping 5e-4..2e-2 Hz find the
+    highest switch frequency at which the corrected hybrid's LFA-side error
+    (against the FP64 full response on the same GPU) stays within that of
+    the plain hybrid switched at 1e-3 Hz; time the corrected hybrid on the
+    headline workload."""
     import synth
     from paper_2505_09600_gb300 import corrector as CT
     t0 = time.perf_counter()
@@ -290,41 +318,56 @@ def bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, st
     b.synchronize()
     t_train = a.elapsed_time(b)
     ls = losses.cpu().numpy()
-    c.configure(f_lo=1e-4, f_hi=2e-2, spot_every=64, spot_tol=0.05)
-    n = src.n
-    hp64 = torch.as_tensor(src.hp, device=dev)
-    hc64 = torch.as_tensor(src.hc, device=dev)
-    ref = torch.empty((3, n), device=dev, dtype=torch.float64)
-    L.lisa_response_full(orbit, sky, src.grid, hp64, hc64, L.F64, 20, L.AET, src.grid, ref)
-    refh = ref.cpu().numpy()
-    del ref, hp64, hc64
-    m = CT.edge_margin(src.dt)
     res = {"train_sources": n_sources, "train_rows": int(feats.shape[0]), "train_steps": steps, "batch": batch,
            "train_ms": round(t_train, 1), "train_rows_per_s": steps * batch / (t_train / 1e3),
            "training_set_ms": round(t_set, 1), "source_generation_s": round(t_gen, 2),
            "loss_first": float(ls[:50].mean()), "loss_last": float(ls[-200:].mean()),
            "target_mean_square": float(target.square().sum(1).mean())}
-    del feats, target
-    forms = {}
-    for fH in (F_HYB, f_raised):
-        tHx = L.lisa_t_hyb_from_f(fH, src.mc_s, src.tc)
-        i_end = int(min(n, math.floor((tHx + Tw / 2 - src.t0) / src.dt) + 1))
-        fn = (lambda tHx=tHx: c.hybrid(orbit, sky, src.grid, hp32, hc32, 20, L.AET, tHx, Tw, sig, src.grid, out32))
-        ms = _timed(torch, stream, flush, fn)
-        fn()
-        err = _lfa_side_error(out32.cpu().numpy().astype(np.float64), refh, i_end, m)
-        forms["corrected_hybrid20_f%.0e" % fH] = {"ms": round(ms, 4), "samples_per_s": n / (ms / 1e3),
-                                                   "lfa_side_err": err}
-        L.lisa_response_hybrid(orbit, sky, src.grid, hp32, hc32, L.MIXED, 20, 0, L.AET, tHx, Tw, sig, src.grid, out32)
-        torch.cuda.synchronize()
-        forms["plain_hybrid20_f%.0e" % fH] = {"lfa_side_err": _lfa_side_error(out32.cpu().numpy().astype(np.float64),
-                                                                               refh, i_end, m)}
+    del feats, target, devsrc
+    c.configure(f_lo=1e-4, f_hi=2e-2, spot_every=64, spot_tol=0.05)
+    # switch-frequency gain on held-out sweeping chirps
+    ratios, e0s = [], []
+    for p in synth.sweep_params(nsrc=n_sweep, seed=synth.SEED_BASE + 41):
+        s = synth.sweep_source(p)
+        n = s.n
+        m = CT.edge_margin(s.dt)
+        sk = (s.beta, s.lam, s.psi)
+        h32 = (torch.as_tensor(s.hp.astype(np.float32), device=dev), torch.as_tensor(s.hc.astype(np.float32), device=dev))
+        h64 = (torch.as_tensor(s.hp, device=dev), torch.as_tensor(s.hc, device=dev))
+        ref = torch.empty((3, n), device=dev, dtype=torch.float64)
+        L.lisa_response_full(orbit, sk, s.grid, h64[0], h64[1], L.F64, 20, L.AET, s.grid, ref)
+        refh = ref.cpu().numpy()
+        o = torch.empty((3, n), device=dev)
+        Tws = 800 * s.dt
+
+        def i_end(tHx):
+            return int(min(n, max(0, math.floor((tHx + Tws / 2 - s.t0) / s.dt) + 1)))
+
+        tH0 = L.lisa_t_hyb_from_f(1e-3, s.mc_s, s.tc)
+        L.lisa_response_hybrid(orbit, sk, s.grid, h32[0], h32[1], L.MIXED, 20, 0, L.AET, tH0, 0.0, 0.0, s.grid, o)
+        e0 = _lfa_side_error(o.cpu().numpy().astype(np.float64), refh, i_end(tH0), m)
+        best = 1e-3
+        for fH in F_H_GRID:
+            tHx = L.lisa_t_hyb_from_f(fH, s.mc_s, s.tc)
+            c.hybrid(orbit, sk, s.grid, h32[0], h32[1], 20, L.AET, tHx, 0.0, 0.0, s.grid, o)
+            if _lfa_side_error(o.cpu().numpy().astype(np.float64), refh, i_end(tHx), m) <= e0:
+                best = fH
+        ratios.append(best / 1e-3)
+        e0s.append(e0)
+    res["switch_frequency_gain"] = {
+        "held_out_sources": n_sweep, "ratio_per_source": ratios, "median_ratio": float(np.median(ratios)),
+        "plain_err_at_1e-3": e0s, "f_grid_max": F_H_GRID[-1],
+        "error_measure": "max |X - X_FP64full| / max |X_FP64full| over the LFA side t <= t_H + T/2 (A, E, T), "
+                         "ends of the grid excluded"}
+    # throughput of the corrected hybrid on the headline workload (same switch)
+    n = src.n
+    fn = lambda: c.hybrid(orbit, sky, src.grid, hp32, hc32, 20, L.AET, tH, Tw, sig, src.grid, out32)   # noqa: E731
+    ms = _timed(torch, stream, flush, fn)
+    res["headline_workload"] = {"ms": round(ms, 4), "samples_per_s": n / (ms / 1e3),
+                                "kernels_ms": kernel_breakdown(L, torch, fn)}
     rep = c.report()
-    res["forms"] = forms
     res["spot_checks"] = {k: rep[k] for k in ("spot_tiles", "spot_failed", "band_tiles", "fallback_tiles",
                                              "max_spot_err", "status")}
-    res["error_measure"] = ("max |X - X_FP64full| / max |X_FP64full| over the LFA side t <= t_H + T/2 "
-                            "(A, E, T together), first and last %d samples excluded" % m)
     c.close()
     return res
 
@@ -495,14 +538,17 @@ def run_ours(args):
             forms[name] = {"ms": round(best, 4), "samples_per_s": n / (best / 1e3)}
         del hp64, hc64, out64
 
+    # the headline step's output, for the oracle comparison below
+    step()
+    torch.cuda.synchronize()
+    gpu_out = out32.float().cpu().numpy().astype(np.float64) if (rank == 0 and world == 1 and not args.no_cpu) else None
+
     corrector = None
     if not args.no_corrector and rank == 0:
         corrector = bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig)
     batched = None
     if not args.no_batch and rank == 0:
         batched = bench_batch(L, torch, dev, orbit, flush, stream, args)
-
-    gpu_out = out32.float().cpu().numpy().astype(np.float64) if (rank == 0 and world == 1 and not args.no_cpu) else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
