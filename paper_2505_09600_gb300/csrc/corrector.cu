@@ -36,15 +36,20 @@
 // remaining tile is recomputed with full links in the same call (device-side
 // decision, no host synchronisation) and the failure is counted.
 //
-// Kernels (BF16 tensor-core MMA through nvcuda::wmma, FP32 accumulation):
+// Kernels (BF16 operands, FP32 accumulation):
 //   corr_features_kernel  features, scale, band flags, optional targets
-//   mlp_forward_kernel    inference, one warp per 16 rows, all layers fused;
-//                         optional epilogue y = z + s * MLP
-//   mlp_train_kernel      forward + MSE + backward fused; weight gradients are
+//   corr_mlp_tc_kernel    inference on the fifth-generation tensor cores
+//                         (tcgen05.mma, accumulators in tensor memory), all
+//                         layers fused; either on given features or fused with
+//                         the features and the y = z (1 + eps) + s * MLP
+//                         epilogue
+//   mlp_train_kernel      training: forward + MSE + backward fused on the
+//                         warp-level MMAs (nvcuda::wmma); weight gradients are
 //                         accumulated per block in shared memory and added to
 //                         the global FP32 gradient once per block
 //   adam_kernel           Adam on FP32 master weights
-//   publish_kernel        padded BF16 copies of the weights for the MMAs
+//   publish_kernel        padded BF16 copies of the weights for the MMAs, and
+//   publish_tc_kernel     their image in the tensor-core operand layout
 //   corr_fallback_kernel  full links on flagged / spot / failed tiles
 #include <cuda_bf16.h>
 #include <math.h>
@@ -53,9 +58,11 @@
 
 #include <new>
 
+#include "async_copy.cuh"
 #include "lisa_common.cuh"
 #include "lisa_internal.cuh"
 #include "links_tile.cuh"
+#include "tcgen05.cuh"
 #include "tile_geo.cuh"
 
 using namespace nvcuda;
@@ -117,72 +124,6 @@ __device__ __forceinline__ void layer_mma(const __nv_bfloat16* act, int lda, con
             wmma::mma_sync(c, a, b, c);
         }
         wmma::store_matrix_sync(acc + j * 16, c, ldc, wmma::mem_row_major);
-    }
-}
-
-// Load 16 input rows (stride kInP floats) as BF16 into act[16][lda].
-__device__ __forceinline__ void load_rows(const float* __restrict__ x, int64_t r0, int64_t M, __nv_bfloat16* act,
-                                          int lda, int lane)
-{
-    for (int e = lane; e < 16 * (kInP / 4); e += 32) {
-        const int r = e / (kInP / 4), c4 = e % (kInP / 4);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r0 + r < M) v = *reinterpret_cast<const float4*>(x + (r0 + r) * kInP + 4 * c4);
-        __nv_bfloat16* d = act + r * lda + 4 * c4;
-        d[0] = __float2bfloat16(v.x);
-        d[1] = __float2bfloat16(v.y);
-        d[2] = __float2bfloat16(v.z);
-        d[3] = __float2bfloat16(v.w);
-    }
-}
-
-// --------------------------------------------------------------------------
-// inference
-// --------------------------------------------------------------------------
-struct __align__(128) FwdWarp {
-    __nv_bfloat16 act[16][kWid];
-    float acc[16][kWid];
-};
-constexpr int kFwdWarps = 4;
-
-// y = MLP(x) for rows [0, M).  Epilogue: if `links` is set, out[l*n + r] +=
-// scale[r] * y_l (corrections added to the base links, rows = samples);
-// otherwise out[r*kOut + l] = y_l.
-__global__ void __launch_bounds__(32 * kFwdWarps) mlp_forward_kernel(MlpDev m, const float* __restrict__ x, int64_t M,
-                                                                     int links, const float* __restrict__ scale,
-                                                                     int64_t n, float* __restrict__ out)
-{
-    __shared__ FwdWarp wsm[kFwdWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    FwdWarp& W = wsm[warp];
-    const int64_t r0 = ((int64_t)blockIdx.x * kFwdWarps + warp) * 16;
-    if (r0 >= M) return;
-    load_rows(x, r0, M, &W.act[0][0], kWid, lane);
-    __syncwarp();
-    const __nv_bfloat16* Ws[3] = {m.W1, m.W2, m.W3};
-    const float* bs[3] = {m.b1, m.b2, m.b3};
-    for (int l = 0; l < 3; ++l) {
-        layer_mma(&W.act[0][0], kWid, Ws[l], l == 0 ? kInP : kWid, kWid, &W.acc[0][0], kWid);
-        __syncwarp();
-        for (int e = lane; e < 16 * kWid; e += 32) {
-            const int r = e / kWid, c = e % kWid;
-            W.act[r][c] = __float2bfloat16(gelu_f(W.acc[r][c] + bs[l][c]));
-        }
-        __syncwarp();
-    }
-    layer_mma(&W.act[0][0], kWid, m.W4, kWid, kOutP, &W.acc[0][0], kWid);
-    __syncwarp();
-    if (links) {
-        for (int e = lane; e < 16 * kOut; e += 32) {
-            const int l = e / 16, r = e % 16;
-            const int64_t i = r0 + r;
-            if (i < M) out[l * n + i] = fmaf(scale[i], W.acc[r][l] + m.b4[l], out[l * n + i]);
-        }
-    } else {
-        for (int e = lane; e < 16 * kOut; e += 32) {
-            const int r = e / kOut, c = e % kOut;
-            if (r0 + r < M) out[(r0 + r) * kOut + c] = W.acc[r][c] + m.b4[c];
-        }
     }
 }
 
@@ -464,20 +405,14 @@ struct FeatArgs {
     float* target;         // [rows][kOut] or null
 };
 
-__global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
+// Features of sample i from the LFA links z and the FP32 coefficients cfs of
+// the orbit segment s holding i: the feature row ft (ft[46] = dt/Tbar,
+// ft[47] = 0), the scale s (0 below the band), eps_l, the link values z_l(i),
+// and whether the local frequency is above the band.
+__device__ __forceinline__ void corr_feature_row(const FeatArgs& a, int64_t i, const float (*cfs)[7], int64_t s,
+                                                 float (&ft)[kInP], float& sc, float (&eps)[6], float (&z0)[6],
+                                                 bool& above)
 {
-    // The block's 256 samples lie in one orbit segment (segments are whole
-    // multiples of 512 samples): its coefficients are converted to FP32 once
-    // (conversions from FP64 run on the FP64 pipe).
-    __shared__ float cfs[kNQ][7];
-    const int64_t b0 = (int64_t)blockIdx.x * blockDim.x;
-    int64_t s = b0 / a.tab.S;
-    if (s >= a.tab.nseg) s = a.tab.nseg - 1;
-    for (int e = threadIdx.x; e < kNQ * 7; e += blockDim.x)
-        cfs[e / 7][e % 7] = (float)a.tab.coef[(s * kNQ + e / 7) * kNC + e % 7];
-    __syncthreads();
-    const int64_t i = b0 + threadIdx.x;
-    if (i >= a.rows) return;
     const float r1 = a.r1, r2 = r1 * r1;
     float q[5][6];
 #pragma unroll
@@ -495,8 +430,8 @@ __global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
         q[2][l] = r2 * (14.f * (d2 - d1) - (d1 - d0) - (d3 - d2)) * (1.f / 12.f);
         q[3][l] = r2 * r1 * ((d0 + d1 + d2 + d3) - 2.f * (d1 + d2)) * 0.5f;
         q[4][l] = r2 * r2 * ((d3 - d2) - 2.f * (d2 - d1) + (d1 - d0));
+        z0[l] = v[2];
     }
-    float ft[kInP];
     float mk[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -535,7 +470,6 @@ __global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
 #pragma unroll
     for (int sc3 = 0; sc3 < 3; ++sc3)
         kv[sc3] = (k0 * evd(kQR + 3 * sc3) + k1 * evd(kQR + 3 * sc3 + 1) + k2 * evd(kQR + 3 * sc3 + 2)) * a.vfac;
-    float eps[6];
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
         ft[34 + l] = (ev(kQT + l) / a.Tbar - 1.f) * 100.f;
@@ -545,22 +479,45 @@ __global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
     }
     ft[46] = a.dtr;
     ft[47] = 0.f;
+    // band: (omega Tbar)^2 ~ M2/M0
+    sc = 0.125f * mk[2];
+    const float w2 = mk[0] > 0.f ? mk[2] / mk[0] : 0.f;
+    if (!(w2 >= a.w_lo)) sc = 0.f;                    // below the band (or no signal): plain LFA link
+    above = w2 > a.w_hi;
+}
+
+// FP32 copy of the coefficients of orbit segment s (every thread of the
+// block calls it; no barrier inside).
+__device__ __forceinline__ void load_segment_f32(const SegTable& tab, int64_t s, float (*cfs)[7])
+{
+    for (int e = threadIdx.x; e < kNQ * 7; e += blockDim.x)
+        cfs[e / 7][e % 7] = (float)tab.coef[(s * kNQ + e / 7) * kNC + e % 7];
+}
+
+__global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
+{
+    // The block's 256 samples lie in one orbit segment (segments are whole
+    // multiples of 512 samples): its coefficients are converted to FP32 once
+    // (conversions from FP64 run on the FP64 pipe).
+    __shared__ float cfs[kNQ][7];
+    const int64_t b0 = (int64_t)blockIdx.x * blockDim.x;
+    int64_t s = b0 / a.tab.S;
+    if (s >= a.tab.nseg) s = a.tab.nseg - 1;
+    load_segment_f32(a.tab, s, cfs);
+    __syncthreads();
+    const int64_t i = b0 + threadIdx.x;
+    if (i >= a.rows) return;
+    float ft[kInP], sc, eps[6], z0[6];
+    bool above;
+    corr_feature_row(a, i, cfs, s, ft, sc, eps, z0, above);
     float4* fo = reinterpret_cast<float4*>(a.feats + i * kInP);
 #pragma unroll
     for (int c = 0; c < kInP / 4; ++c) fo[c] = make_float4(ft[4 * c], ft[4 * c + 1], ft[4 * c + 2], ft[4 * c + 3]);
-
-    // band: (omega Tbar)^2 ~ M2/M0
-    float sc = 0.125f * mk[2];
-    const float w2 = mk[0] > 0.f ? mk[2] / mk[0] : 0.f;
-    if (!(w2 >= a.w_lo)) sc = 0.f;                    // below the band (or no signal): plain LFA link
-    if (w2 > a.w_hi && a.tile_flag && i >= a.safe_lo && i < a.safe_hi) atomicOr(&a.tile_flag[i / kTile], 1);
+    if (above && a.tile_flag && i >= a.safe_lo && i < a.safe_hi) atomicOr(&a.tile_flag[i / kTile], 1);
     a.scale[i] = sc;
     if (a.ybase) {
 #pragma unroll
-        for (int l = 0; l < 6; ++l) {
-            const int64_t zi = (int64_t)l * a.stride + i;
-            a.ybase[zi] = fmaf(eps[l], a.z[zi], a.z[zi]);
-        }
+        for (int l = 0; l < 6; ++l) a.ybase[(int64_t)l * a.stride + i] = fmaf(eps[l], z0[l], z0[l]);
     }
     if (a.target) {
 #pragma unroll
@@ -568,11 +525,242 @@ __global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
             float t = 0.f;
             if (sc > 0.f && a.y_full) {
                 const int64_t zi = (int64_t)l * a.stride + i;
-                const double zr = a.z_ref ? a.z_ref[zi] : (double)a.z[zi];
+                const double zr = a.z_ref ? a.z_ref[zi] : (double)z0[l];
                 t = (float)((a.y_full[zi] - zr * (1.0 + (double)eps[l])) / (double)sc);
             }
             a.target[i * kOut + l] = t;
         }
+    }
+}
+
+// --------------------------------------------------------------------------
+// inference on the fifth-generation tensor cores
+// --------------------------------------------------------------------------
+// One CTA of four warps per 128-row tile at a time (persistent over tiles):
+// thread r owns row r, which is also tensor-memory lane r of the accumulator.
+// Per layer: the BF16 operand rows are written to shared memory in the
+// K-major core-matrix layout, one thread issues the K/16 MMAs (128 x N x 16,
+// BF16 -> FP32 in tensor memory) and commits them to an mbarrier, and each
+// thread reads its accumulator row back (tcgen05.ld) for bias, GELU and the
+// next operand.  Weights: a BF16 image in the same layout, fetched once per
+// CTA with a bulk copy.
+//
+// Operand layout (bytes): element (r, k) of a K-major matrix with K/8 core
+// columns sits at (r/8) * SBO + (k/8) * 128 + (r%8) * 16 + (k%8) * 2, with
+// SBO = (K/8) * 128.
+constexpr int kTcRows = 128;
+constexpr uint32_t kTcW1 = 0, kTcW2 = 6144, kTcW3 = 14336, kTcW4 = 22528, kTcWBytes = 24576;
+constexpr uint32_t kTcActSbo = 1024;   // activation tile: 8 core columns (K up to 64)
+
+__host__ __device__ constexpr uint32_t tc_off(int r, int k, uint32_t sbo)
+{
+    return (uint32_t)(r >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+struct __align__(128) TcSmem {
+    unsigned char w[kTcWBytes];      // weights image
+    unsigned char act[16384];        // operand tile: 128 rows x 64 BF16
+    float bias[3 * kWid + kOutP];
+    float cfs[kNQ][7];               // FP32 orbit segment (fused mode)
+    int64_t cseg;
+    uint64_t bar_w, bar_mma;
+    uint32_t tmem_base;
+};
+
+// The BF16 weight image in the operand layout (W1 at kTcW1 with SBO 768,
+// W2, W3 at kTcW2, kTcW3 and W4 (16 rows, 6 used) at kTcW4 with SBO 1024).
+__global__ void publish_tc_kernel(const float* __restrict__ p, unsigned char* __restrict__ img)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    __nv_bfloat16* o = (__nv_bfloat16*)img;
+    if (t < kWid * kInP) {           // W1: 64 x 48
+        const int n = t / kInP, k = t % kInP;
+        o[(kTcW1 + tc_off(n, k, 768)) / 2] = __float2bfloat16(k < kIn ? p[kOffW1 + n * kIn + k] : 0.f);
+    }
+    if (t < kWid * kWid) {           // W2, W3: 64 x 64
+        const int n = t / kWid, k = t % kWid;
+        o[(kTcW2 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(p[kOffW2 + t]);
+        o[(kTcW3 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(p[kOffW3 + t]);
+    }
+    if (t < kOutP * kWid) {          // W4: 16 x 64
+        const int n = t / kWid, k = t % kWid;
+        o[(kTcW4 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(n < kOut ? p[kOffW4 + n * kWid + k] : 0.f);
+    }
+}
+
+struct TcArgs {
+    const unsigned char* wimg;       // 16-byte aligned
+    const float* bias;               // b1 | b2 | b3 | b4 (padded: 64, 64, 64, 16)
+    int64_t rows;
+    // raw mode: x [rows][kInP] -> out [rows][kOut]
+    const float* x;
+    float* out;
+    // fused mode (x == null): features from FeatArgs, corrected links into y [6][stride]
+    FeatArgs fa;
+    float* y;
+    unsigned int* status;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Row r of the operand tile from 8 consecutive values per 16-byte store.
+__device__ __forceinline__ void store_row_bf16(unsigned char* act, int r, int kb, const float* v8)
+{
+    uint4 u;
+    u.x = pack_bf16x2(v8[0], v8[1]);
+    u.y = pack_bf16x2(v8[2], v8[3]);
+    u.z = pack_bf16x2(v8[4], v8[5]);
+    u.w = pack_bf16x2(v8[6], v8[7]);
+    *reinterpret_cast<uint4*>(act + tc_off(r, 8 * kb, kTcActSbo)) = u;
+}
+
+// One layer: MMAs issued by thread 0 after the operand tile is complete, then
+// a bounded wait for their completion.  The result is the same in every
+// thread; on false the phase is left at the one that did not complete.
+__device__ __forceinline__ bool tc_layer(TcSmem& sm, uint32_t wofs, uint32_t wsbo, int K, int N, uint32_t& phase)
+{
+    fence_async_shared();
+    tc_fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc_fence_after_sync();
+        const uint32_t idesc = idesc_bf16_f32(kTcRows, N);
+        for (int s = 0; s < K / 16; ++s) {
+            const uint64_t ad = smem_desc(sm.act + 2 * s * 128, 128u, kTcActSbo);
+            const uint64_t bd = smem_desc(sm.w + wofs + 2 * s * 128, 128u, wsbo);
+            tc_mma_bf16(sm.tmem_base, ad, bd, idesc, s > 0 ? 1u : 0u);
+        }
+        tc_commit(&sm.bar_mma);
+    }
+    const bool ok = mbar_wait_bounded(&sm.bar_mma, phase);
+    const bool all_ok = __syncthreads_or(ok ? 0 : 1) == 0;
+    if (all_ok) phase ^= 1u;
+    tc_fence_after_sync();
+    return all_ok;
+}
+
+__global__ void __launch_bounds__(kTcRows, 1) corr_mlp_tc_kernel(TcArgs A)
+{
+    __shared__ TcSmem sm;
+    const int t = threadIdx.x, warp = t >> 5;
+    if (t == 0) {
+        mbar_init(&sm.bar_w, 1);
+        mbar_init(&sm.bar_mma, 1);
+        mbar_init_fence();
+        sm.cseg = -1;
+    }
+    if (warp == 0) tmem_alloc(&sm.tmem_base, 64);
+    for (int e = t; e < 3 * kWid + kOutP; e += blockDim.x) sm.bias[e] = A.bias[e];
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    if (t == 0) {
+        mbar_arrive_expect_tx(&sm.bar_w, kTcWBytes);
+        bulk_copy_g2s(sm.w, A.wimg, kTcWBytes, &sm.bar_w);
+    }
+    const bool okw = __syncthreads_or(mbar_wait_bounded(&sm.bar_w, 0) ? 0 : 1) == 0;
+    bool ok = okw;
+    uint32_t phase = 0;
+    const uint32_t lane_base = sm.tmem_base + ((uint32_t)(warp * 32) << 16);
+    const int64_t ntiles = (A.rows + kTcRows - 1) / kTcRows;
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int64_t i = tile * kTcRows + t;
+        const bool live = i < A.rows;
+        // ---- layer-1 operand: the feature row of sample i
+        float ft[kInP];
+        float sc = 0.f, base[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (A.x) {
+            if (live) {
+                const float4* xr = reinterpret_cast<const float4*>(A.x + i * kInP);
+#pragma unroll
+                for (int c = 0; c < kInP / 4; ++c) {
+                    const float4 v = xr[c];
+                    ft[4 * c] = v.x; ft[4 * c + 1] = v.y; ft[4 * c + 2] = v.z; ft[4 * c + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < kInP; ++c) ft[c] = 0.f;
+            }
+        } else {
+            // the tile's 128 samples lie in one orbit segment
+            int64_t s = (tile * kTcRows) / A.fa.tab.S;
+            if (s >= A.fa.tab.nseg) s = A.fa.tab.nseg - 1;
+            if (s != sm.cseg) {
+                __syncthreads();
+                load_segment_f32(A.fa.tab, s, sm.cfs);
+                __syncthreads();
+                if (t == 0) sm.cseg = s;
+            }
+            if (live) {
+                float eps[6], z0[6];
+                bool above;
+                corr_feature_row(A.fa, i, sm.cfs, s, ft, sc, eps, z0, above);
+                if (above && A.fa.tile_flag && i >= A.fa.safe_lo && i < A.fa.safe_hi)
+                    atomicOr(&A.fa.tile_flag[i / kTile], 1);
+#pragma unroll
+                for (int l = 0; l < 6; ++l) base[l] = fmaf(eps[l], z0[l], z0[l]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < kInP; ++c) ft[c] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int kb = 0; kb < kInP / 8; ++kb) store_row_bf16(sm.act, t, kb, ft + 8 * kb);
+        // ---- hidden layers
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            ok = tc_layer(sm, l == 0 ? kTcW1 : l == 1 ? kTcW2 : kTcW3, l == 0 ? 768u : 1024u, l == 0 ? kInP : kWid,
+                          kWid, phase);
+            if (!ok) break;
+#pragma unroll
+            for (int cb = 0; cb < kWid / 16; ++cb) {
+                float v[16];
+                tmem_ld16(lane_base + cb * 16, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) v[k] = gelu_f(v[k] + sm.bias[l * kWid + cb * 16 + k]);
+                store_row_bf16(sm.act, t, 2 * cb, v);
+                store_row_bf16(sm.act, t, 2 * cb + 1, v + 8);
+            }
+        }
+        if (!ok) break;
+        // ---- output layer
+        ok = tc_layer(sm, kTcW4, 1024u, kWid, kOutP, phase);
+        if (!ok) break;
+        float v[16];
+        tmem_ld16(lane_base, v);
+        tmem_wait_ld();
+        if (live) {
+            if (A.x) {
+#pragma unroll
+                for (int l = 0; l < kOut; ++l) A.out[i * kOut + l] = v[l] + sm.bias[3 * kWid + l];
+            } else {
+#pragma unroll
+                for (int l = 0; l < kOut; ++l)
+                    A.y[(int64_t)l * A.fa.stride + i] = fmaf(sc, v[l] + sm.bias[3 * kWid + l], base[l]);
+            }
+        }
+    }
+    if (!okw) {
+        // the weights copy did not complete: flag it and give the copy another
+        // bounded wait before the block leaves
+        if (t == 0) flag_timeout(A.status);
+        mbar_wait_bounded(&sm.bar_w, 0);
+    } else if (!ok) {
+        // an MMA completion wait gave up: flag it, let the MMAs finish (again
+        // bounded) before releasing tensor memory
+        if (t == 0) flag_timeout(A.status);
+        mbar_wait_bounded(&sm.bar_mma, phase);
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after_sync();
+        tmem_dealloc(sm.tmem_base, 64);
     }
 }
 
@@ -693,6 +881,7 @@ struct lisa_corrector {
     float* vel = nullptr;
     void* wbuf = nullptr;     // padded BF16 weights + FP32 biases
     MlpBuf buf{};
+    unsigned char* wimg = nullptr;   // BF16 weights in the tensor-core operand layout
     CorrStats* stats = nullptr;
     float* grad = nullptr;    // gradient buffer of lisa_corrector_train
     int64_t step = 0;
@@ -713,7 +902,49 @@ static int publish(lisa_corrector* c, cudaStream_t st)
     prof_before("corr_publish", st);
     publish_kernel<<<(kWid * kWid + 255) / 256, 256, 0, st>>>(c->p, c->buf);
     prof_after(st);
-    return cuda_status(cudaGetLastError(), "publish_kernel launch");
+    LISA_TRY(cuda_status(cudaGetLastError(), "publish_kernel launch"));
+    prof_before("corr_publish", st);
+    publish_tc_kernel<<<(kWid * kWid + 255) / 256, 256, 0, st>>>(c->p, c->wimg);
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "publish_tc_kernel launch");
+}
+
+static int sm_count()
+{
+    static int n[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!n[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        n[dev] = v > 0 ? v : 148;
+    }
+    return n[dev];
+}
+
+// The tensor-core MLP over `rows` rows: raw (x -> out) or fused with the
+// features (fa, y).  Persistent: up to 4 CTAs per SM.
+static int run_mlp_tc(const lisa_corrector* c, int64_t rows, const float* x, float* out, const FeatArgs* fa,
+                      float* y, cudaStream_t st)
+{
+    if (rows <= 0) return LISA_OK;
+    TcArgs A;
+    memset(&A, 0, sizeof(A));
+    A.wimg = c->wimg;
+    A.bias = c->buf.b1;
+    A.rows = rows;
+    A.x = x;
+    A.out = out;
+    if (fa) A.fa = *fa;
+    A.y = y;
+    A.status = device_status_ptr();
+    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
+    const int64_t cap = (int64_t)sm_count() * 4;
+    const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+    prof_before(x ? "mlp_forward_tc" : "corr_fused_tc", st);
+    corr_mlp_tc_kernel<<<grid, kTcRows, 0, st>>>(A);
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "corr_mlp_tc_kernel launch");
 }
 
 static void free_corrector(lisa_corrector* c)
@@ -722,29 +953,17 @@ static void free_corrector(lisa_corrector* c)
     cudaFree(c->mom);
     cudaFree(c->vel);
     cudaFree(c->wbuf);
+    cudaFree(c->wimg);
     cudaFree(c->stats);
     cudaFree(c->grad);
     delete c;
 }
 
-static int run_forward(const lisa_corrector* c, const float* x, int64_t M, int links, const float* scale,
-                       int64_t n, float* out, cudaStream_t st)
+static FeatArgs make_feat_args(const SegTable& tab, const SkyDev& sky, double Tbar, double dt, const float* z,
+                               int64_t stride, int64_t nz, int64_t rows, double f_lo, double f_hi, float* feats,
+                               float* scale, float* ybase, int* tile_flag, int64_t safe_lo, int64_t safe_hi,
+                               const double* y_full, const double* z_ref, float* target)
 {
-    if (M <= 0) return LISA_OK;
-    const int64_t rows_per_block = 16 * kFwdWarps;
-    const int64_t blocks = (M + rows_per_block - 1) / rows_per_block;
-    prof_before("mlp_forward", st);
-    mlp_forward_kernel<<<(unsigned)blocks, 32 * kFwdWarps, 0, st>>>(mlp_dev(c), x, M, links, scale, n, out);
-    prof_after(st);
-    return cuda_status(cudaGetLastError(), "mlp_forward_kernel launch");
-}
-
-static int run_features(const SegTable& tab, const SkyDev& sky, double Tbar, double dt, const float* z,
-                        int64_t stride, int64_t nz, int64_t rows, double f_lo, double f_hi, float* feats,
-                        float* scale, float* ybase, int* tile_flag, int64_t safe_lo, int64_t safe_hi,
-                        const double* y_full, const double* z_ref, float* target, cudaStream_t st)
-{
-    if (rows <= 0) return LISA_OK;
     const double two_pi_T = 2.0 * M_PI * Tbar;
     FeatArgs a;
     a.tab = tab;
@@ -769,6 +988,17 @@ static int run_features(const SegTable& tab, const SkyDev& sky, double Tbar, dou
     a.y_full = y_full;
     a.z_ref = z_ref;
     a.target = target;
+    return a;
+}
+
+static int run_features(const SegTable& tab, const SkyDev& sky, double Tbar, double dt, const float* z,
+                        int64_t stride, int64_t nz, int64_t rows, double f_lo, double f_hi, float* feats,
+                        float* scale, float* ybase, int* tile_flag, int64_t safe_lo, int64_t safe_hi,
+                        const double* y_full, const double* z_ref, float* target, cudaStream_t st)
+{
+    if (rows <= 0) return LISA_OK;
+    const FeatArgs a = make_feat_args(tab, sky, Tbar, dt, z, stride, nz, rows, f_lo, f_hi, feats, scale, ybase,
+                                      tile_flag, safe_lo, safe_hi, y_full, z_ref, target);
     prof_before("corr_features", st);
     corr_features_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
     prof_after(st);
@@ -801,10 +1031,8 @@ static int corrected_links(lisa_corrector* c, const lisa_orbit* orbit, const lis
     const int64_t nz = rows + 2 < n ? rows + 2 : n;
     const int64_t ntile = (rows + kTile - 1) / kTile;
     float* z = (float*)sc.alloc(sizeof(float) * 6 * (size_t)n);
-    float* feats = (float*)sc.alloc(sizeof(float) * kInP * (size_t)rows);
-    float* scale = (float*)sc.alloc(sizeof(float) * (size_t)rows);
     int* flags = (int*)sc.alloc(sizeof(int) * (size_t)ntile);
-    if (!z || !feats || !scale || !flags) return sc.status();
+    if (!z || !flags) return sc.status();
     const SkyDev skyd = make_sky_dev(*sky);
     BlendSpec none{};
     LISA_TRY(launch_lfa(tab, skyd, orbit->L_m, h_grid, hp, hc, LISA_MIXED, kLfaOwnTime, LISA_LFA_UNEQUAL, LISA_XYZ,
@@ -814,9 +1042,10 @@ static int corrected_links(lisa_corrector* c, const lisa_orbit* orbit, const lis
     const double Tbar = orbit->L_m / kC;
     int64_t safe_lo, safe_hi;
     safe_range(out, h_grid, max_light_time(orbit, out), safe_lo, safe_hi);
-    LISA_TRY(run_features(tab, skyd, Tbar, out.dt, z, n, nz, rows, c->f_lo, c->f_hi, feats, scale, y, flags,
-                          safe_lo, safe_hi, nullptr, nullptr, nullptr, st));
-    LISA_TRY(run_forward(c, feats, rows, 1, scale, n, y, st));
+    // features, network and z (1 + eps) + s * MLP in one tensor-core kernel
+    const FeatArgs fa = make_feat_args(tab, skyd, Tbar, out.dt, z, n, nz, rows, c->f_lo, c->f_hi, nullptr, nullptr,
+                                       nullptr, flags, safe_lo, safe_hi, nullptr, nullptr, nullptr);
+    LISA_TRY(run_mlp_tc(c, rows, nullptr, nullptr, &fa, y, st));
     FallbackArgs A;
     A.la.tab = tab;
     A.la.sky = skyd;
@@ -870,6 +1099,7 @@ int lisa_corrector_create(lisa_corrector** out, const float* host_params, int64_
     if (!rc) rc = cuda_status(cudaMalloc(&c->wbuf, wb + bb), "cudaMalloc");
     if (!rc) rc = cuda_status(cudaMalloc(&c->stats, sizeof(CorrStats)), "cudaMalloc");
     if (!rc) rc = cuda_status(cudaMalloc(&c->grad, pb), "cudaMalloc");
+    if (!rc) rc = cuda_status(cudaMalloc(&c->wimg, kTcWBytes), "cudaMalloc");
     if (rc) { free_corrector(c); return rc; }
     __nv_bfloat16* w = (__nv_bfloat16*)c->wbuf;
     c->buf.W1 = w;
@@ -950,7 +1180,7 @@ int lisa_corrector_forward(const lisa_corrector* c, const float* feats, int64_t 
 {
     if (!c || M < 0 || (M > 0 && (!feats || !out))) { set_error("lisa_corrector_forward: bad arguments"); return LISA_EINVAL; }
     if (((uintptr_t)feats & 15) != 0) { set_error("lisa_corrector_forward: feats must be 16-byte aligned"); return LISA_EINVAL; }
-    return run_forward(c, feats, M, 0, nullptr, 0, out, (cudaStream_t)stream);
+    return run_mlp_tc(c, M, feats, out, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 int lisa_corrector_gradient(lisa_corrector* c, const float* feats, const float* target, int64_t n_data,
