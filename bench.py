@@ -259,7 +259,7 @@ def _lfa_side_error(got, ref, i_end, m):
 
 def kernel_breakdown(L, torch, fn):
     """Device ms per kernel name of one call (lisa_profile event pairs)."""
-    names = ("seg_table", "lfa_own_mixed", "lfa_mixed", "corr_features", "mlp_forward", "corr_fallback_all",
+    names = ("seg_table", "lfa_own_mixed", "lfa_mixed", "corr_features", "corr_fused_tc", "mlp_forward", "corr_fallback_all",
              "corr_fallback", "links_full_mixed", "tdi_mixed", "batch")
     L.lisa_profile_enable(True)
     fn()
