@@ -152,6 +152,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms, world, device):
+    """Slowest rank's time: replicas run independently, so the job ends when
+    the last one does (one scalar all_reduce, outside the timed region)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, n_per_rank, steps, total_ms):
+    """Samples of all ranks per second of the slowest rank (weak scaling)."""
+    return world * n_per_rank * steps / (total_ms / 1e3)
+
+
 def make_source(rank):
     import synth
     return synth.cfg2_source(seed_offset=rank)
@@ -471,12 +488,8 @@ def run_ours(args):
     lfa_ms, lfa_launches = L.lisa_profile_query("lfa_mixed")
     all_ms, _ = L.lisa_profile_query(None)
     L.lisa_profile_enable(False)
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
+    value = whole_job_rate(world, n, args.steps, total_ms)
 
     # end to end through the public call with host buffers (pinned), copies timed
     hp_h = torch.as_tensor(src.hp.astype(np.float32)).pin_memory()
@@ -498,12 +511,8 @@ def run_ours(args):
         b.synchronize()
         if k >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_total = float(sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * n * len(e2e_ms) / (e2e_total / 1e3)
+    e2e_total = max_over_ranks(float(sum(e2e_ms)), world, dev)
+    e2e_value = whole_job_rate(world, n, len(e2e_ms), e2e_total)
 
     # other forms (same source), fewer steps
     forms = {}
