@@ -14,6 +14,10 @@ namespace lisa {
 constexpr int kWinH = kTile + 384;
 constexpr int kZW = kTile + 4;
 constexpr int kWinP = kWinH + 8;   // planar h buffers: room for 16-byte alignment of the copy
+#ifndef LISA_LFA_UNROLL
+#define LISA_LFA_UNROLL 2
+#endif
+constexpr int kLfaUnroll = LISA_LFA_UNROLL;   // series per unrolled step of the mixed z loop
 
 template <typename Real>
 struct PairT;
@@ -444,6 +448,61 @@ __device__ void lfa_hdot(const LfaArgs& a, LfaSmem<MIXED, NB>& sm, int b)
     __syncthreads();
 }
 
+// Mixed form: block offset dm of an output sample -> block coordinate u and
+// the sample's own position on the h grid (integer part jp, fraction fp).
+__device__ __forceinline__ void lfa_sample_pos(const LfaArgs& a, float inv_half, int dm, float& u, int& jp, float& fp)
+{
+    u = (float)dm * inv_half;
+    if (a.hm.unit_rho) {
+        jp = dm;
+        fp = 0.f;
+    } else {
+        const double P = (double)dm * a.hm.rho;
+        const double fl = floor(P);
+        jp = (int)fl;
+        fp = (float)(P - fl);
+    }
+}
+
+// Mixed form: z of series c at one sample (block coordinate u, own position
+// jp + fp).  With the window staged (a decision uniform over the block) every
+// stencil lies inside it: the retarded sample index is monotonic in the
+// sample (|d delay/dt| << 1) and the window spans the indices at the tile's
+// two ends plus margins; the clamp only keeps shared-memory reads in bounds.
+// Without a window the stencils read global memory.
+template <int NB>
+__device__ __forceinline__ float lfa_z_mixed(const LfaArgs& a, const LfaSmem<true, NB>& sm, const LfaWin& W, int c,
+                                             float u, int jp, float fp, float c2, float s2, const float (&ku)[3],
+                                             const float (&kv)[3])
+{
+    const float4* rp = reinterpret_cast<const float4*>(&sm.ser[c]);
+    const float4 r0 = rp[0];   // f, d1, d2, d3
+    const float D = u * fmaf(u, fmaf(u, r0.w, r0.z), r0.y);
+    const float v = fmaf(-D, sm.inv_dt, fp + r0.x);
+    const float fv = floorf(v);
+    const int jr = jp + (int)fv;
+    const float eps = v - fv;
+    float dp, dc;
+    if (W.wlen > 0) {
+        const int base = min(max(W.jrel[c] + jr, 0), W.wlen - 32);
+        lagrange32_dot2(eps, sm.dw + base, dp, dc);
+    } else {
+        const float2 r2 = interp_hdot_global_ool((const float*)a.hp, (const float*)a.hc, a.hm.n_in, sm.J[c] + jr, eps,
+                                                 a.inv12dtf);
+        dp = r2.x;
+        dc = r2.y;
+    }
+    const float4 rT = rp[1], rn0 = rp[2], rn1 = rp[3], rn2 = rp[4];
+    const float Tl = fmaf(u, fmaf(u, fmaf(u, rT.w, rT.z), rT.y), rT.x);
+    const float n0 = fmaf(u, fmaf(u, fmaf(u, rn0.w, rn0.z), rn0.y), rn0.x);
+    const float n1 = fmaf(u, fmaf(u, fmaf(u, rn1.w, rn1.z), rn1.y), rn1.x);
+    const float n2 = fmaf(u, fmaf(u, fmaf(u, rn2.w, rn2.z), rn2.y), rn2.x);
+    const float un = ku[0] * n0 + ku[1] * n1 + ku[2] * n2;
+    const float vn = kv[0] * n0 + kv[1] * n1 + kv[2] * n2;
+    const float xp = un * un - vn * vn, xc = 2.f * un * vn;
+    return -0.5f * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
+}
+
 // z values of the tile starting at i0 (window b staged, hdot in sm.dw): the
 // tile and its 2-sample halo, or with reuse_halo only the kTile new values
 // per series (the previous tile's last four values are this tile's leading
@@ -478,6 +537,33 @@ __device__ void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MI
     // c covers series c for the whole block).  On interior tiles no sample of
     // the tile or its halo is off the grid.
     const bool interior = i0 - 2 >= 0 && i0 + kTile + 2 <= a.nout;
+    if constexpr (MIXED) {
+        // One thread per sample (blockDim.x == kTile): the sample's position
+        // is shared by the six series, which are unrolled.  Off-grid samples
+        // (edge tiles only) are computed on clamped indices and masked.
+        if (!reuse_halo && t < 24) {   // leading halo, samples i0-2 .. i0+1
+            const int c = t >> 2, o = t & 3;
+            const int64_t m = i0 - 2 + o;
+            float u, fp;
+            int jp;
+            lfa_sample_pos(a, sm.inv_half, dmt - 2 + o, u, jp, fp);
+            const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp, c2, s2, ku, kv);
+            sm.zs[c][o] = (interior || (m >= 0 && m < a.nout)) ? z : 0.f;
+        }
+        {
+            const int o = 4 + t;
+            const int64_t m = i0 + 2 + t;
+            const bool valid = interior || (m >= 0 && m < a.nout);
+            float u, fp;
+            int jp;
+            lfa_sample_pos(a, sm.inv_half, dmt + 2 + t, u, jp, fp);
+#pragma unroll kLfaUnroll
+            for (int c = 0; c < 6; ++c) {
+                const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp, c2, s2, ku, kv);
+                sm.zs[c][o] = valid ? z : 0.f;
+            }
+        }
+    } else {
     const int per = reuse_halo ? kTile : kZW;
     for (int w = t; w < 6 * per; w += blockDim.x) {
         // constant divisors: kTile values per series after a reused halo, else kZW
@@ -485,64 +571,7 @@ __device__ void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MI
         const int o = reuse_halo ? 4 + w % kTile : w % kZW;
         const int64_t m = i0 - 2 + o;
         Real zval = Real(0);
-        if constexpr (MIXED) {
-            // Branch-free in the common case: off-grid samples (edge tiles only)
-            // are computed on clamped indices and masked; stencils outside the
-            // staged window are redone from global memory under a warp vote.
-            const bool valid = interior || (m >= 0 && m < a.nout);
-            const float4 r0 = reinterpret_cast<const float4*>(&sm.ser[c])[0];   // f, d1, d2, d3
-            const float u = (float)(dmt - 2 + o) * sm.inv_half;
-            const float D = u * fmaf(u, fmaf(u, r0.w, r0.z), r0.y);
-            int jp;
-            float fp;
-            if (a.hm.unit_rho) {
-                jp = dmt - 2 + o;
-                fp = 0.f;
-            } else {
-                const double P = (double)(dmt - 2 + o) * a.hm.rho;
-                const double fl = floor(P);
-                jp = (int)fl;
-                fp = (float)(P - fl);
-            }
-            const float v = fmaf(-D, sm.inv_dt, fp + r0.x);
-            const float fv = floorf(v);
-            const int jr = jp + (int)fv;
-            const float eps = v - fv;
-            const int base = W.jrel[c] + jr;
-            const bool inwin = base >= 0 && base + 32 <= wlen;
-            float dp, dc;
-            {
-                float w32[32];
-                lagrange32_weights(eps, w32);
-                const float2* pw = sm.dw + (inwin ? base : 0);
-                float ap = 0.f, ac = 0.f;
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const float2 hv = pw[k];
-                    ap = fmaf(w32[k], hv.x, ap);
-                    ac = fmaf(w32[k], hv.y, ac);
-                }
-                dp = ap;
-                dc = ac;
-            }
-            if (__any_sync(__activemask(), !inwin)) {
-                if (!inwin && valid) {
-                    const float2 r2 = interp_hdot_global_ool(hp, hc, a.hm.n_in, sm.J[c] + jr, eps, inv12dt);
-                    dp = r2.x;
-                    dc = r2.y;
-                }
-            }
-            const float4* rp = reinterpret_cast<const float4*>(&sm.ser[c]);
-            const float4 rT = rp[1], rn0 = rp[2], rn1 = rp[3], rn2 = rp[4];
-            const float Tl = fmaf(u, fmaf(u, fmaf(u, rT.w, rT.z), rT.y), rT.x);
-            const float n0 = fmaf(u, fmaf(u, fmaf(u, rn0.w, rn0.z), rn0.y), rn0.x);
-            const float n1 = fmaf(u, fmaf(u, fmaf(u, rn1.w, rn1.z), rn1.y), rn1.x);
-            const float n2 = fmaf(u, fmaf(u, fmaf(u, rn2.w, rn2.z), rn2.y), rn2.x);
-            const float un = ku[0] * n0 + ku[1] * n1 + ku[2] * n2;
-            const float vn = kv[0] * n0 + kv[1] * n1 + kv[2] * n2;
-            const float xp = un * un - vn * vn, xc = 2.f * un * vn;
-            zval = valid ? -0.5f * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2)) : 0.f;
-        } else if (interior || (m >= 0 && m < a.nout)) {
+        if (interior || (m >= 0 && m < a.nout)) {
             {
                 const int ch = c >> 1, which = c & 1;
                 const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
@@ -570,6 +599,7 @@ __device__ void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MI
             }
         }
         sm.zs[c][o] = zval;
+    }
     }
     __syncthreads();
 }

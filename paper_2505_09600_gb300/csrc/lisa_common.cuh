@@ -120,22 +120,73 @@ __device__ __forceinline__ void split_f64(const GridMap& m, int64_t i, double d,
 // which equals prod_{m != k}(eps - m)/(k - m).  Built by a backward then a
 // forward running product (about five operations per weight, four with the
 // fused factors).
+// K_p = 1 / prod_{m != p} (p - m) = (-1)^(31-p) / (p! (31-p)!), p = 0..31.
+__host__ __device__ constexpr double lagrange32_k(int p)
+{
+    double f = 1.0;
+    for (int m = 2; m <= p; ++m) f *= m;
+    for (int m = 2; m <= 31 - p; ++m) f *= m;
+    return ((31 - p) & 1 ? -1.0 : 1.0) / f;
+}
+
 template <typename Real>
 __device__ __forceinline__ void lagrange32_weights(Real eps, Real (&w)[32])
 {
-    // Fully unrolled.  Each factor (c - eps)/n is one fused multiply-add with
-    // the compile-time constants -1/n and c/n (instead of a subtraction and a
-    // multiplication): the same factor up to the rounding of c/n.
-    w[31] = Real(1);
+    if constexpr (sizeof(Real) == 4) {
+        // FP32: unnormalised differences d_m = eps - (m - 15), one addition of
+        // a constant each; w_p = K_p (prod_{m<p} d_m)(prod_{m>p} d_m), the
+        // suffix products first, then the prefix products with one constant
+        // per weight.  Every instruction takes at most one constant operand
+        // (a factor (c - eps)/n would need two).  The products stay inside
+        // the FP32 range: |prod| <= 16!^2 < 5e26, K_p >= 1/31! > 1e-34.
+        w[31] = Real(1);
 #pragma unroll
-    for (int p = 31; p >= 1; --p)
-        w[p - 1] = w[p] * fma(eps, Real(-1) / Real(32 - p), Real(p - 15) / Real(32 - p));
-    Real A = Real(1);
+        for (int p = 30; p >= 0; --p) w[p] = w[p + 1] * (eps + Real(14 - p));
+        Real P = Real(1);
+#pragma unroll
+        for (int p = 0; p < 32; ++p) {
+            w[p] = (w[p] * P) * Real(lagrange32_k(p));
+            P *= eps + Real(15 - p);
+        }
+    } else {
+        // Fully unrolled.  Each factor (c - eps)/n is one fused multiply-add
+        // with the compile-time constants -1/n and c/n (instead of a
+        // subtraction and a multiplication): the same factor up to the
+        // rounding of c/n.
+        w[31] = Real(1);
+#pragma unroll
+        for (int p = 31; p >= 1; --p)
+            w[p - 1] = w[p] * fma(eps, Real(-1) / Real(32 - p), Real(p - 15) / Real(32 - p));
+        Real A = Real(1);
+#pragma unroll
+        for (int p = 0; p < 32; ++p) {
+            w[p] *= A;
+            A *= fma(eps, Real(1) / Real(p + 1), Real(15 - p) / Real(p + 1));
+        }
+    }
+}
+
+// FP32 interpolation of an interleaved pair series: sum_p w_p(eps) v[p] for
+// both components, the weights formed as in lagrange32_weights<float> with the
+// prefix pass fused into the taps (the suffix products are the only array
+// held in registers).
+__device__ __forceinline__ void lagrange32_dot2(float eps, const float2* __restrict__ v, float& ox, float& oy)
+{
+    float s[32];
+    s[31] = 1.f;
+#pragma unroll
+    for (int p = 30; p >= 0; --p) s[p] = s[p + 1] * (eps + float(14 - p));
+    float P = 1.f, ax = 0.f, ay = 0.f;
 #pragma unroll
     for (int p = 0; p < 32; ++p) {
-        w[p] *= A;
-        A *= fma(eps, Real(1) / Real(p + 1), Real(15 - p) / Real(p + 1));
+        const float w = (s[p] * P) * float(lagrange32_k(p));
+        const float2 hv = v[p];
+        ax = fmaf(w, hv.x, ax);
+        ay = fmaf(w, hv.y, ay);
+        P *= eps + float(15 - p);
     }
+    ox = ax;
+    oy = ay;
 }
 
 // Monomial -> re-expansion around xc: b_m = sum_{p>=m} C(p,m) a_p xc^(p-m).
