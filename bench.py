@@ -533,6 +533,9 @@ def run_ours(args):
             "full20_f64": lambda: L.lisa_response_full(orbit, sky, src.grid, hp64, hc64, L.F64, 20, L.AET,
                                                        src.grid, out64),
         }
+        if args.forms:
+            keep = args.forms.split(",")
+            cases = {k: v for k, v in cases.items() if k in keep}
         for name, fn in cases.items():
             fn()
             torch.cuda.synchronize()
@@ -646,6 +649,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--forms", default="", help="comma-separated subset of the forms section (profiling aid)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-corrector", action="store_true")

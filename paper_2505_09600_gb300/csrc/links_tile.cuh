@@ -94,6 +94,22 @@ __device__ __forceinline__ void interp_pair(const typename Pair<Real>::T* win, i
     oc = ac;
 }
 
+// Both polarisations interpolated straight from global memory (zero outside
+// the grid): stencils that the staged window does not hold.  Out of line.
+static __device__ __noinline__ float2 links_interp_global_f32(const float* __restrict__ hp, const float* __restrict__ hc,
+                                                              int64_t n, int64_t j, float eps)
+{
+    float ap = 0.f, ac = 0.f;
+    lagrange32_paired_f32(eps, [&](int p, float w) {
+        const int64_t idx = j - 15 + p;
+        if (idx >= 0 && idx < n) {
+            ap = fmaf(w, hp[idx], ap);
+            ac = fmaf(w, hc[idx], ac);
+        }
+    });
+    return make_float2(ap, ac);
+}
+
 // Stage the h window reachable from samples m_lo..m_hi (tile centre ic) and
 // the mixed-precision per-tile data.  Every thread must call it (it
 // synchronises); g must already hold the tile geometry around ic.
@@ -240,7 +256,31 @@ __device__ __forceinline__ void links_sample(const LinksArgs& a, const TileGeo& 
             fp = (float)(P - fl);
         }
         const float inv_dt = s.inv_dt;
-#pragma unroll 1
+        // stencil position of link-time lt (even: sender end, odd: receiver end)
+        auto interp_lt = [&](int lt, float& op, float& oc) {
+            const float v = (fp + s.f[lt]) - s.dd[lt](u) * inv_dt;
+            const float fv = floorf(v);
+            const float eps = v - fv;
+            if (wlen > 0) {
+                // every stencil of the tile lies in the staged window (the
+                // window spans the tile's end points plus margins and the
+                // retarded index is monotonic); the clamp keeps reads in bounds
+                const int base = min(max((int)(s.J[lt] - wlo) + (int)jp + (int)fv - 15, 0), wlen - 32);
+                lagrange32_dot2(eps, reinterpret_cast<const float2*>(s.win) + base, op, oc);
+            } else {
+                const float2 r = links_interp_global_f32(hp, hc, a.hm.n_in, s.J[lt] + jp + (int)fv, eps);
+                op = r.x;
+                oc = r.y;
+            }
+        };
+        // receiver ends: k.R_r/c depends on the receiving spacecraft only, so
+        // the two links into a spacecraft share it (links 3, 0, 1 carry the
+        // receivers 0, 1, 2)
+        float rp[3], rc[3];
+        interp_lt(2 * 3 + 1, rp[0], rc[0]);
+        interp_lt(2 * 0 + 1, rp[1], rc[1]);
+        interp_lt(2 * 1 + 1, rp[2], rc[2]);
+#pragma unroll
         for (int li = 0; li < 6; ++li) {
             float d[3], dd = 0.f;
 #pragma unroll
@@ -248,26 +288,16 @@ __device__ __forceinline__ void links_sample(const LinksArgs& a, const TileGeo& 
                 d[c] = s.dk[li][c] + s.dn[li][c](u);
                 dd = fmaf(d[c], d[c], dd);
             }
-            float y = 0.f;
-            if (dd >= 2e-12f) {
-                const float un = ku[0] * d[0] + ku[1] * d[1] + ku[2] * d[2];
-                const float vn = kv[0] * d[0] + kv[1] * d[1] + kv[2] * d[2];
-                const float xp = un * un - vn * vn, xc = 2.f * un * vn;
-                const float rdd = 1.f / dd;
-                const float Fp = (xp * c2 + xc * s2) * rdd, Fc = (xc * c2 - xp * s2) * rdd;
-                float vals[4];
-#pragma unroll
-                for (int w = 0; w < 2; ++w) {
-                    const int lt = 2 * li + w;
-                    const float v = (fp + s.f[lt]) - s.dd[lt](u) * inv_dt;
-                    const float fv = floorf(v);
-                    const int64_t j = s.J[lt] + jp + (int)fv;
-                    const float eps = v - fv;
-                    interp_pair<float>(s.win, wlo, wlen, hp, hc, a.hm.n_in, j, eps, vals[2 * w], vals[2 * w + 1]);
-                }
-                y = Fp * (vals[0] - vals[2]) + Fc * (vals[1] - vals[3]);
-            }
-            out[li * stride] = y;
+            const float un = ku[0] * d[0] + ku[1] * d[1] + ku[2] * d[2];
+            const float vn = kv[0] * d[0] + kv[1] * d[1] + kv[2] * d[2];
+            const float xp = un * un - vn * vn, xc = 2.f * un * vn;
+            const float rdd = 1.f / dd;
+            const float Fp = (xp * c2 + xc * s2) * rdd, Fc = (xc * c2 - xp * s2) * rdd;
+            float ps, cs;
+            interp_lt(2 * li, ps, cs);
+            const int r = link_receiver(li);
+            const float y = Fp * (ps - rp[r]) + Fc * (cs - rc[r]);
+            out[li * stride] = dd >= 2e-12f ? y : 0.f;
         }
     }
 }

@@ -115,11 +115,10 @@ __device__ __forceinline__ void split_f64(const GridMap& m, int64_t i, double d,
 }
 
 // 32-point Lagrange weights, stencil k = -15..16 (index p = k + 15):
-//   w_p = A_p B_p,  A_p = prod_{m=-15}^{p-16}(eps - m) / p!,
-//   B_p = prod_{m=p-14}^{16}(m - eps) / (31 - p)!,
-// which equals prod_{m != k}(eps - m)/(k - m).  Built by a backward then a
-// forward running product (about five operations per weight, four with the
-// fused factors).
+//   w_p = prod_{m != k}(eps - m)/(k - m) = K_p prod_{m != p} d_m,
+//   d_m = eps - (m - 15).  The FP64 form builds A_p = prod_{m<p} d_m / p! and
+// B_p = prod_{m>p} (-d_m) / (31 - p)! by a backward then a forward running
+// product; the FP32 form pairs mirrored nodes (below).
 // K_p = 1 / prod_{m != p} (p - m) = (-1)^(31-p) / (p! (31-p)!), p = 0..31.
 __host__ __device__ constexpr double lagrange32_k(int p)
 {
@@ -129,25 +128,46 @@ __host__ __device__ constexpr double lagrange32_k(int p)
     return ((31 - p) & 1 ? -1.0 : 1.0) / f;
 }
 
+// FP32 form, pairing the nodes that mirror each other about eps = 1/2.  With
+// s = eps - 1/2, the nodes 15 - k and 16 + k (k = 0..15) sit at s = -(k + 1/2)
+// and s = k + 1/2, so their two differences multiply to
+//   e_k = (s + k + 1/2)(s - k - 1/2) = s^2 - (k + 1/2)^2
+// (e_0 = eps (eps - 1) directly: no cancellation near eps = 0 or 1), and with
+// Q_k = K_{15-k} prod_{j != k} e_j (leave-one-out products by a suffix then a
+// prefix pass) and K_{16+k} = -K_{15-k}:
+//   w_{15-k} = (s - k - 1/2) Q_k,   w_{16+k} = (-s - k - 1/2) Q_k.
+// Every instruction takes at most one constant operand (a factor (c - eps)/n
+// would need two, hence a register move each).  About 141 operations for the
+// 32 weights; the products stay inside the FP32 range (|e_j| <= 241,
+// |Q_k| <= 1).  tap(p, w_p) receives the weights in pairs.
+template <class Tap>
+__device__ __forceinline__ void lagrange32_paired_f32(float eps, Tap&& tap)
+{
+    const float s = eps - 0.5f;
+    const float sig = s * s;
+    float e[16];
+    e[0] = eps * (eps - 1.f);
+#pragma unroll
+    for (int k = 1; k < 16; ++k) e[k] = sig - float((k + 0.5) * (k + 0.5));
+    float S[16];   // S[k] = prod_{j>k} e_j
+    S[15] = 1.f;
+#pragma unroll
+    for (int k = 14; k >= 0; --k) S[k] = S[k + 1] * e[k + 1];
+    float P = 1.f;   // prod_{j<k} e_j
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float Q = (P * S[k]) * float(lagrange32_k(15 - k));
+        tap(15 - k, (s - float(k + 0.5)) * Q);
+        tap(16 + k, (-s - float(k + 0.5)) * Q);
+        P *= e[k];
+    }
+}
+
 template <typename Real>
 __device__ __forceinline__ void lagrange32_weights(Real eps, Real (&w)[32])
 {
     if constexpr (sizeof(Real) == 4) {
-        // FP32: unnormalised differences d_m = eps - (m - 15), one addition of
-        // a constant each; w_p = K_p (prod_{m<p} d_m)(prod_{m>p} d_m), the
-        // suffix products first, then the prefix products with one constant
-        // per weight.  Every instruction takes at most one constant operand
-        // (a factor (c - eps)/n would need two).  The products stay inside
-        // the FP32 range: |prod| <= 16!^2 < 5e26, K_p >= 1/31! > 1e-34.
-        w[31] = Real(1);
-#pragma unroll
-        for (int p = 30; p >= 0; --p) w[p] = w[p + 1] * (eps + Real(14 - p));
-        Real P = Real(1);
-#pragma unroll
-        for (int p = 0; p < 32; ++p) {
-            w[p] = (w[p] * P) * Real(lagrange32_k(p));
-            P *= eps + Real(15 - p);
-        }
+        lagrange32_paired_f32(eps, [&](int p, float v) { w[p] = v; });
     } else {
         // Fully unrolled.  Each factor (c - eps)/n is one fused multiply-add
         // with the compile-time constants -1/n and c/n (instead of a
@@ -167,24 +187,15 @@ __device__ __forceinline__ void lagrange32_weights(Real eps, Real (&w)[32])
 }
 
 // FP32 interpolation of an interleaved pair series: sum_p w_p(eps) v[p] for
-// both components, the weights formed as in lagrange32_weights<float> with the
-// prefix pass fused into the taps (the suffix products are the only array
-// held in registers).
+// both components, each weight used as soon as it is formed.
 __device__ __forceinline__ void lagrange32_dot2(float eps, const float2* __restrict__ v, float& ox, float& oy)
 {
-    float s[32];
-    s[31] = 1.f;
-#pragma unroll
-    for (int p = 30; p >= 0; --p) s[p] = s[p + 1] * (eps + float(14 - p));
-    float P = 1.f, ax = 0.f, ay = 0.f;
-#pragma unroll
-    for (int p = 0; p < 32; ++p) {
-        const float w = (s[p] * P) * float(lagrange32_k(p));
+    float ax = 0.f, ay = 0.f;
+    lagrange32_paired_f32(eps, [&](int p, float w) {
         const float2 hv = v[p];
         ax = fmaf(w, hv.x, ax);
         ay = fmaf(w, hv.y, ay);
-        P *= eps + float(15 - p);
-    }
+    });
     ox = ax;
     oy = ay;
 }

@@ -16,6 +16,9 @@
 
 namespace lisa {
 
+// Mixed frozen form on a common grid: per-link combined filters (tdi_comb.cu).
+int launch_tdi_comb(const TdiArgs& a, int64_t tiles, cudaStream_t st);
+
 template <bool MIXED>
 __global__ void __launch_bounds__(kTile) tdi_kernel(TdiArgs a)
 {
@@ -60,10 +63,16 @@ int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int prec
     a.dt_out = og.dt;
     const int64_t tiles = (i_end - 1) / kTile - a.tile0 + 1;
     prof_before(precision == LISA_MIXED ? "tdi_mixed" : "tdi_f64", st);
-    if (precision == LISA_MIXED) tdi_kernel<true><<<(unsigned)tiles, kTile, 0, st>>>(a);
-    else tdi_kernel<false><<<(unsigned)tiles, kTile, 0, st>>>(a);
+    int rc;
+    if (precision == LISA_MIXED && mode == LISA_FROZEN && a.ym.unit_rho) {
+        rc = launch_tdi_comb(a, tiles, st);
+    } else {
+        if (precision == LISA_MIXED) tdi_kernel<true><<<(unsigned)tiles, kTile, 0, st>>>(a);
+        else tdi_kernel<false><<<(unsigned)tiles, kTile, 0, st>>>(a);
+        rc = cuda_status(cudaGetLastError(), "tdi_kernel launch");
+    }
     prof_after(st);
-    return cuda_status(cudaGetLastError(), "tdi_kernel launch");
+    return rc;
 }
 
 }  // namespace lisa

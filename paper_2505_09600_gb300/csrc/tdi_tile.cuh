@@ -209,11 +209,11 @@ __device__ void tdi_fill_global(const TdiArgs& a, TdiTile<MIXED>& s)
     const Real* __restrict__ yg = (const Real*)a.y;
     const int64_t wlo = s.wlo;
     const int wlen = s.wlen;
-    for (int k = threadIdx.x; k < 6 * wlen; k += blockDim.x) {
-        const int li = k / wlen, o = k % wlen;
-        const int64_t idx = wlo + o;
-        s.win[li][o] = (idx >= 0 && idx < a.ym.n_in) ? yg[(int64_t)li * a.ny + idx] : Real(0);
-    }
+    for (int li = 0; li < 6; ++li)
+        for (int o = threadIdx.x; o < wlen; o += blockDim.x) {
+            const int64_t idx = wlo + o;
+            s.win[li][o] = (idx >= 0 && idx < a.ym.n_in) ? yg[(int64_t)li * a.ny + idx] : Real(0);
+        }
     __syncthreads();
 }
 
