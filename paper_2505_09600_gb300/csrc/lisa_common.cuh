@@ -10,7 +10,7 @@
 //    around its tile centre and evaluates it per sample (Horner), so per
 //    sample there is no trigonometry, no Kepler solve and no light-time
 //    iteration.  The truncation error of the degree-6 fit over a segment of
-//    up to 100,000 s is < 1e-16 s, below FP64 rounding of the delays.
+//    up to 330,000 s is ~1e-16 s, below FP64 rounding of the delays.
 //  * LISA_F64 kernels keep every step in FP64.  LISA_MIXED kernels keep the
 //    tile-centre values of delays in FP64, split once per tile into an
 //    integer sample and a fraction, and evaluate the in-tile variation
@@ -38,16 +38,17 @@ constexpr int kDeg = 6;      // polynomial degree per segment
 constexpr int kNodes = 7;    // Chebyshev nodes per segment
 constexpr int kNC = 8;       // stored coefficients per quantity (7 used)
 constexpr int kSegSamples = 512;  // smallest segment
-// Samples per segment for a grid step dt: the largest power of two <= 16384
-// with S*dt <= 100,000 s (at least 512).  Over 100,000 s the orbital phase
-// moves by 0.02 rad and the degree-6 Chebyshev fit is exact to ~5e-9 m in the
-// positions and ~1e-19 s in the light times (truncation ~ (Omega W/2)^7 /
-// (2^6 7!)), so a longer segment only saves table work (7 exact FP64
-// evaluations per segment).
+// Samples per segment for a grid step dt: the largest power of two <= 65536
+// with S*dt <= 330,000 s (at least 512).  Over 330,000 s the orbital phase
+// moves by 0.066 rad and the degree-6 Chebyshev fit's truncation
+// ~ (Omega W/2)^7 / (2^6 7!) is ~1e-16 of the orbit radius (~1e-5 m, 1e-16 s
+// in the light times), below the FP64 evaluation of the exact geometry
+// itself; a longer segment only saves table work (7 exact FP64 evaluations
+// per segment).
 __host__ __device__ inline int seg_samples(double dt)
 {
     int S = kSegSamples;
-    while (S < 16384 && 2.0 * S * dt <= 100000.0) S *= 2;
+    while (S < 65536 && 2.0 * S * dt <= 330000.0) S *= 2;
     return S;
 }
 

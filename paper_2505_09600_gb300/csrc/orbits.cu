@@ -119,10 +119,12 @@ __device__ void sc_state(const OrbitDev& o, int sc, double t, double R[3], doubl
         const double M = W * t + o.kappa0 - b;
         double sM, cM;
         sincos(M, &sM, &cM);
+        // start at O(e^2) ~ 2.5e-5; Newton squares the error: three steps
+        // reach FP64 resolution
         double E = M + e * sM;
         double sE, cE;
 #pragma unroll 1
-        for (int it = 0; it < 4; ++it) {
+        for (int it = 0; it < 3; ++it) {
             sincos(E, &sE, &cE);
             E -= (E - e * sE - M) / (1.0 - e * cE);
         }
@@ -222,13 +224,14 @@ __device__ void geometry_exact(const OrbitDev& o, double t, double* q)
 }
 
 // Chebyshev fit of one quantity from its values at the 7 first-kind nodes,
-// stored as degree-6 monomial coefficients in x in [-1, 1].
-__device__ void cheb_fit_store(const double* v, double* dst)
+// stored as degree-6 monomial coefficients in x in [-1, 1]; cs[j][k] =
+// cos(pi j (k + 1/2) / 7).
+__device__ void cheb_fit_store(const double* v, const double (*cs)[kNodes], double* dst)
 {
     double c[kNodes];
     for (int j = 0; j < kNodes; ++j) {
         double acc = 0.0;
-        for (int k = 0; k < kNodes; ++k) acc += v[k] * cospi(j * (k + 0.5) / kNodes);
+        for (int k = 0; k < kNodes; ++k) acc = fma(v[k], cs[j][k], acc);
         c[j] = (2.0 / kNodes) * acc;
     }
     c[0] *= 0.5;
@@ -249,9 +252,23 @@ __device__ void seg_fit_block(const OrbitDev& o, double t0, double dt, int S, in
 {
     __shared__ double st[kNodes][3][9];       // R, V, A per node and spacecraft
     __shared__ double vals[kNQ][kNodes];
+    __shared__ double cb[8];                  // cos(pi m / 14), m = 0..7
+    __shared__ double cs[kNodes][kNodes];     // cos(pi j (2k + 1) / 14)
     const int t = threadIdx.x;
+    // The 49 cosines of the fit are +-cos(pi m / 14) for m = 0..7: eight FP64
+    // cosines per block (each FP64 instruction of a warp takes 16 cycles of
+    // the SM's FP64 pipe, so they are not recomputed per quantity).
+    if (t < 8) cb[t] = (t == 7) ? 0.0 : cospi(t / 14.0);
+    __syncthreads();
+    if (t < kNodes * kNodes) {
+        const int j = t / kNodes, k = t % kNodes;
+        int m = (j * (2 * k + 1)) % 28;
+        if (m > 14) m = 28 - m;
+        cs[j][k] = m <= 7 ? cb[m] : -cb[14 - m];
+    }
+    __syncthreads();
     auto node_time = [&](int node) {
-        const double xk = cospi((node + 0.5) / kNodes);
+        const double xk = cs[1][node];
         return t0 + ((double)(s * S) + 0.5 * S + xk * (0.5 * S)) * dt;
     };
     if (t < 3 * kNodes) {
@@ -276,7 +293,7 @@ __device__ void seg_fit_block(const OrbitDev& o, double t0, double dt, int S, in
         for (int c = 0; c < 3; ++c) vals[kQN + 3 * li + c][node] = n[c];
     }
     __syncthreads();
-    if (t < kNQ) cheb_fit_store(vals[t], coef + (int64_t)t * kNC);
+    if (t < kNQ) cheb_fit_store(vals[t], cs, coef + (int64_t)t * kNC);
     __syncthreads();
 }
 

@@ -340,11 +340,23 @@ __global__ void __launch_bounds__(kTile, 4) tdi_comb_kernel(TdiArgs a, int64_t t
 }
 
 // Launch over tiles [a.tile0, a.tile0 + tiles) (host side): groups of up to
-// 8 tiles, never wider than one orbit-table segment.
+// 8 tiles, never wider than one orbit-table segment, and narrower when that
+// leaves fewer than 4 CTAs per SM (the tiles of a group run one after the
+// other).
 int launch_tdi_comb(const TdiArgs& a, int64_t tiles, cudaStream_t st)
 {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
     int G = a.tab.S / kTile;
-    G = G > 8 ? 8 : (G < 2 ? 2 : G);
+    G = G > 8 ? 8 : G;
+    const int64_t fill = tiles / (4 * (int64_t)sms);
+    if (fill < G) G = (int)fill;
+    G = G < 2 ? 2 : G;
     const int64_t grid = (tiles + G - 1) / G;
     tdi_comb_kernel<<<(unsigned)grid, kTile, 0, st>>>(a, a.tile0 + tiles, G);
     return cuda_status(cudaGetLastError(), "tdi_comb_kernel launch");
