@@ -578,7 +578,7 @@ def run_ours(args):
     i_l = int(math.floor((tH + 0.5 * Tw - src.t0) / src.dt)) + 1
     achieved = flop * i_l / (lfa_avg_ms / 1e3) / 1e12
     achieved_w = flop_w * i_l / (lfa_avg_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": "lfa_kernel<mixed> (FP32 pipe)", "achieved": round(achieved, 3),
+    roof = {"bound": "alu", "kernel": "lfa_kernel_mixed (FP32 pipe)", "achieved": round(achieved, 3),
             "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
             "peak_note": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x clock, " + peak_note,
             "flop_per_sample": flop, "flop_note": "Lagrange taps (2 flop/tap) + stencils; weights not counted",

@@ -233,7 +233,10 @@ int lisa_plan_execute(lisa_plan* plan, void* stream);
 int lisa_plan_capture_graph(lisa_plan* plan, void* stream);
 int lisa_plan_replay(lisa_plan* plan, void* stream);
 /* Launch shape: CTAs per SM of the persistent kernel (clamped to what fits)
- * and output tiles per work item.  Drops a captured graph. */
+ * and output tiles (256 samples) per work item.  A source's tiles form fixed
+ * groups of up to 8 from its start; an item holds tiles_per_item / (group
+ * size) whole groups (at least one), so the results do not depend on the
+ * launch shape.  Drops a captured graph. */
 int lisa_plan_set_launch(lisa_plan* plan, int ctas_per_sm, int tiles_per_item);
 /* Time every (CTAs per SM in 1..4) x (tiles per item in 1,2,4,8) on this
  * plan's own data (synchronising), keep the fastest, report it. */

@@ -4,18 +4,20 @@
 // A plan owns, in device memory allocated once at creation:
 //   - one orbit polynomial table holding the segments of every source's grid
 //     (built by one batched kernel per execution),
-//   - a descriptor per source and the prefix of their tile counts,
-//   - a work counter.
-// The persistent kernel runs (SMs x CTAs per SM) blocks.  Each block takes the
-// next work item -- a run of `tiles_per_item` consecutive output tiles of one
-// source -- with one atomicAdd and, for every tile:
-//   - computes the LFA channels of its samples with t <= t_hyb + T/2
-//     (the same tile function as lisa_response_lfa),
-//   - computes the full-response channels of its samples with
-//     t >= t_hyb - T/2 by evaluating the six links over the window its TDI
-//     delays reach directly into shared memory, then the TDI from there,
-//   - blends them with the sigmoid weights of Eq. hybridized_xs and stores
-//     X, Y, Z or A, E, T.
+//   - a descriptor per source with the prefix of its work items,
+//   - a work counter and, per CTA of the persistent kernel, a link scratch.
+// A source's tiles form groups of up to 8 consecutive tiles from its start
+// (the grouping of lisa_response_lfa, fixed so that the results do not
+// depend on the launch shape); a work item is a run of groups of one source.
+// Each block takes the next item with one atomicAdd and runs the same code as
+// the single-source calls on each group:
+//   - the LFA channels of its samples with t <= t_hyb + T/2 (the grouped LFA
+//     of lisa_response_lfa: one FP64 prologue, sub-blocks of two tiles, bulk
+//     copies of the h windows), weighted by S(+1);
+//   - the six links over the samples the TDI delays of its full-response part
+//     reach (t >= t_hyb - T/2), into the block's scratch (L2-resident), then
+//     the TDI combination on per-link combined filters (as lisa_tdi), weighted
+//     by S(-1) and added where both parts contribute (Eq. hybridized_xs).
 // Blocks never wait on each other (no spin, no grid barrier), so uneven
 // sources are balanced by the queue alone.  The whole execution (counter
 // reset, tables, persistent kernel) can be captured in a CUDA graph.
@@ -28,7 +30,7 @@
 
 #include "lfa_tile.cuh"
 #include "links_tile.cuh"
-#include "tdi_tile.cuh"
+#include "tdi_comb.cuh"
 
 struct lisa_plan;
 
@@ -47,176 +49,173 @@ struct BatchSrc {
     float dtf, inv12dtf;  // FP32 copies of dt and 1/(12 dt)
     float c1f, c2f;       // 1/(12 dt), 1/(12 dt^2)
     int64_t iL, iF;      // LFA on samples <= iL, full response on samples >= iF
-    int64_t tile_begin;  // first work tile of this source
-    int64_t ntiles;
+    int64_t lo_links;    // first sample whose links the full part may read
+    int dm_links;        // samples the TDI delays reach back (plus margin)
+    int G;               // tiles per group (fixed: the results do not depend on the launch shape)
+    int gpi;             // groups per work item
+    int h_aligned;       // hp, hc on 16-byte boundaries (bulk copies)
+    int64_t ntiles, ngroups;
+    int64_t item_begin;  // first work item of this source
 };
 
 struct BatchKernelArgs {
     const BatchSrc* srcs;
     int nsrc;
-    int64_t total_tiles;
-    int tiles_per_item;
+    int64_t total_items;
     unsigned long long* counter;
+    float* scratch;      // per CTA: six link rows of scr_len samples
+    int scr_len;
     int gen, kind, channels;
     double Lc;
     float Lcf;
+    unsigned int* status;
 };
 
-struct BatchSmem {
-    LfaSmem<true> lfa;        // also provides the tile geometry of the full part
-    LinksTile<true> links;
-    TdiTile<true> tdi;
-    int64_t item;
-    int src;
-    float barg_c, barg_d;     // (t - t_hyb)/sigma at the tile centre, per sample
+// The three parts of an item use the block's shared memory one after the
+// other.
+union BatchShared {
+    Lfa2Smem lfa;
+    CombSmem tdi;
+    struct {
+        TileGeo g;
+        LinksTile<true> lk;
+    } ln;
 };
 
-__device__ __forceinline__ void batch_full_part(const BatchKernelArgs& ka, const BatchSrc& b, int64_t i0,
-                                                BatchSmem& sm, float (&Xf)[3])
+__global__ void __launch_bounds__(kTile, 4) batch_hybrid_kernel(BatchKernelArgs ka)
 {
-    const int64_t ic = i0 + kTile / 2;
-    const TileGeo& g = sm.lfa.g;
-    TdiArgs ta;
-    ta.tab = b.tab;
-    ta.ym = b.hm;            // links live on the output grid: identity map
-    ta.y = nullptr;
-    ta.ny = b.n;
-    ta.xyz = nullptr;
-    ta.nout = b.n;
-    ta.nterm = ka.gen == LISA_TDI20 ? 16 : 8;
-    ta.mode = LISA_FROZEN;
-    ta.channels = ka.channels;
-    ta.i_begin = 0;
-    ta.i_end = b.n;
-    ta.tile0 = 0;
-    ta.bl = BlendSpec{};
-    ta.t0_out = b.t0;
-    ta.dt_out = b.dt;
-    tdi_tile_prologue<true>(ta, g, ic, i0, sm.tdi);
-    LinksArgs la;
-    la.tab = b.tab;
-    la.sky = b.sky;
-    la.hm = b.hm;
-    la.hp = b.hp;
-    la.hc = b.hc;
-    la.y = nullptr;
-    la.ny = b.n;
-    la.i_begin = 0;
-    la.i_end = b.n;
-    la.tile0 = 0;
-    const int64_t ylo = sm.tdi.wlo;
-    const int ylen = sm.tdi.wlen;
-    links_tile_prologue<true>(la, g, ic, ylo, ylo + (ylen > 0 ? ylen - 1 : 0), sm.links);
-    for (int k = threadIdx.x; k < ylen; k += blockDim.x) {
-        const int64_t m = ylo + k;
-        if (m >= 0 && m < b.n) {
-            links_sample<true>(la, g, ic, m, sm.links, &sm.tdi.win[0][k], kWinY);
-        } else {
-#pragma unroll
-            for (int li = 0; li < 6; ++li) sm.tdi.win[li][k] = 0.f;
-        }
-    }
-    __syncthreads();
-    tdi_sample<true>(ta, g, ic, i0 + threadIdx.x, sm.tdi, Xf);
-}
-
-__global__ void __launch_bounds__(kTile) batch_hybrid_kernel(BatchKernelArgs ka)
-{
-    __shared__ BatchSmem sm;
+    __shared__ BatchShared u;
+    __shared__ int64_t s_item;
+    __shared__ int s_src;
     const int t = threadIdx.x;
+    float* scr = ka.scratch + (size_t)blockIdx.x * 6 * (size_t)ka.scr_len;
     for (;;) {
-        __syncthreads();   // the previous item is done with shared memory
+        __syncthreads();   // the previous item is done with shared memory and the scratch
         if (t == 0) {
-            sm.item = (int64_t)atomicAdd(ka.counter, 1ull);
-            const int64_t first = sm.item * ka.tiles_per_item;
+            const int64_t item = (int64_t)atomicAdd(ka.counter, 1ull);
             int lo = 0, hi = ka.nsrc - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (ka.srcs[mid].tile_begin <= first) lo = mid; else hi = mid - 1;
+                if (ka.srcs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
             }
-            sm.src = lo;
+            s_item = item;
+            s_src = lo;
         }
         __syncthreads();
-        const int64_t first = sm.item * ka.tiles_per_item;
-        if (first >= ka.total_tiles) break;
-        int src = sm.src;
-        for (int r = 0; r < ka.tiles_per_item; ++r) {
-            const int64_t gt = first + r;
-            if (gt >= ka.total_tiles) break;
-            // an item may run into the next source: advance (uniform in the block)
-            while (src + 1 < ka.nsrc && ka.srcs[src + 1].tile_begin <= gt) ++src;
-            const BatchSrc& b = ka.srcs[src];
-            const int64_t tile = gt - b.tile_begin;
-            const int64_t i0 = tile * kTile;
+        const int64_t item = s_item;
+        if (item >= ka.total_items) break;
+        const BatchSrc& b = ka.srcs[s_src];
+        const int64_t g0 = (item - b.item_begin) * b.gpi;
+        const int64_t g1 = g0 + b.gpi < b.ngroups ? g0 + b.gpi : b.ngroups;
+        for (int64_t grp = g0; grp < g1; ++grp) {
+        if (grp > g0) __syncthreads();   // the previous group is done with shared memory and the scratch
+        const int64_t t0 = grp * b.G;
+        const int nt = (int)(b.ntiles - t0 < b.G ? b.ntiles - t0 : b.G);
+        const int64_t i_lo = t0 * kTile, i_hi = (t0 + nt) * (int64_t)kTile;   // group samples [i_lo, i_hi)
+
+        // LFA part, weight S(+1), samples [i_lo, min(i_hi, iL + 1))
+        if (i_lo <= b.iL) {
+            LfaArgs a;
+            a.tab = b.tab;
+            a.sky = b.sky;
+            a.hm = b.hm;
+            a.Lc = ka.Lc;
+            a.gen = ka.gen;
+            a.kind = ka.kind;
+            a.channels = ka.channels;
+            a.hp = b.hp;
+            a.hc = b.hc;
+            a.z = nullptr;
+            a.xyz = b.out;
+            a.nout = b.n;
+            a.t0_out = b.t0;
+            a.dt_out = b.dt;
+            a.i_begin = 0;
+            a.i_end = b.iL + 1;
+            a.tile0 = 0;
+            a.bl = BlendSpec{1, b.t_hyb, b.sigma, +1.0, 0, 0};
+            a.Lcf = ka.Lcf;
+            a.dtf = b.dtf;
+            a.inv12dtf = b.inv12dtf;
+            a.c1f = b.c1f;
+            a.c2f = b.c2f;
+            a.h_aligned = b.h_aligned;
+            a.status = ka.status;
+            const int64_t last = b.iL / kTile;
+            const int nl = (int)(last - t0 + 1 < nt ? last - t0 + 1 : nt);
             if (t == 0) {
-                const double tc = b.t0 + (double)(i0 + kTile / 2) * b.dt;
-                sm.barg_c = (float)((tc - b.t_hyb) / b.sigma);
-                sm.barg_d = (float)(b.dt / b.sigma);
+                mbar_init(&u.lfa.bar[0], 1);
+                mbar_init(&u.lfa.bar[1], 1);
+                mbar_init_fence();
             }
-            const bool need_lfa = i0 <= b.iL;
-            const bool need_full = i0 + kTile - 1 >= b.iF;
-            float Xl[3] = {0.f, 0.f, 0.f}, Xf[3] = {0.f, 0.f, 0.f};
-            if (need_lfa) {
-                LfaArgs a;
-                a.tab = b.tab;
-                a.sky = b.sky;
-                a.hm = b.hm;
-                a.Lc = ka.Lc;
-                a.gen = ka.gen;
-                a.kind = ka.kind;
-                a.channels = ka.channels;
-                a.hp = b.hp;
-                a.hc = b.hc;
-                a.z = nullptr;
-                a.xyz = nullptr;
-                a.nout = b.n;
-                a.t0_out = b.t0;
-                a.dt_out = b.dt;
-                a.i_begin = 0;
-                a.i_end = b.n;
-                a.tile0 = 0;
-                a.bl = BlendSpec{};
-                a.Lcf = ka.Lcf;
-                a.dtf = b.dtf;
-                a.inv12dtf = b.inv12dtf;
-                a.c1f = b.c1f;
-                a.c2f = b.c2f;
-                a.h_aligned = 0;
-                a.status = nullptr;
-                lfa_tile_compute<true>(a, i0, sm.lfa, Xl);
-            } else {
-                tile_geo_load(sm.lfa.g, b.tab, i0 + kTile / 2, b.sky);
-            }
-            if (need_full) {
-                __syncthreads();
-                batch_full_part(ka, b, i0, sm, Xf);
-            }
-            const int64_t i = i0 + t;
-            if (i < b.n) {
-                // X = S(+1) X_LFA [i <= iL] + S(-1) X_Full [i >= iF]
-                const float arg = fmaf((float)(int)(i - (i0 + kTile / 2)), sm.barg_d, sm.barg_c);
-                float o[3];
-                const float wl = (i <= b.iL) ? 1.f / (1.f + expf(arg)) : 0.f;
-                const float wf = (i >= b.iF) ? 1.f / (1.f + expf(-arg)) : 0.f;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float v = 0.f;
-                    if (wl != 0.f) v += wl * Xl[c];
-                    if (wf != 0.f) v += wf * Xf[c];
-                    o[c] = v;
-                }
-                float* out = (float*)b.out;
-                if (ka.channels == LISA_AET) {
-                    out[i] = (o[2] - o[0]) * 0.70710678118654752440f;
-                    out[b.n + i] = (o[0] - 2.f * o[1] + o[2]) * 0.40824829046386301637f;
-                    out[2 * b.n + i] = (o[0] + o[1] + o[2]) * 0.57735026918962576451f;
-                } else {
-                    out[i] = o[0];
-                    out[b.n + i] = o[1];
-                    out[2 * b.n + i] = o[2];
-                }
-            }
+            uint32_t ph0 = 0u, ph1 = 0u;
+            const bool ok = lfa2_group(a, t0, nl, b.G, u.lfa, ph0, ph1);
+            // every copy has landed: the barriers are invalidated before the
+            // memory holds other data
             __syncthreads();
+            if (t == 0) {
+                mbar_inval(&u.lfa.bar[0]);
+                mbar_inval(&u.lfa.bar[1]);
+            }
+            if (!ok) return;   // a bounded wait timed out (status word flagged)
+        }
+        // samples covered by neither part are zero
+        if (b.iF > b.iL + 1) {
+            const int64_t z0 = b.iL + 1 > i_lo ? b.iL + 1 : i_lo, z1 = b.iF < i_hi ? b.iF : i_hi;
+            float* out = (float*)b.out;
+            for (int64_t i = z0 + t; i < z1; i += blockDim.x) {
+                out[i] = 0.f;
+                out[b.n + i] = 0.f;
+                out[2 * b.n + i] = 0.f;
+            }
+        }
+        // full part, weight S(-1), samples [max(i_lo, iF), i_hi)
+        const int64_t tf0 = b.iF / kTile > t0 ? b.iF / kTile : t0;
+        if (b.iF < b.n && tf0 < t0 + nt) {
+            const int nf = (int)(t0 + nt - tf0);
+            int64_t ys = tf0 * kTile - b.dm_links;
+            ys = ys > b.lo_links ? ys : b.lo_links;
+            int64_t ye = i_hi + 40;
+            ye = ye < b.n ? ye : b.n;
+            LinksArgs la;
+            la.tab = b.tab;
+            la.sky = b.sky;
+            la.hm = b.hm;
+            la.hp = b.hp;
+            la.hc = b.hc;
+            la.y = nullptr;
+            la.ny = ka.scr_len;
+            la.i_begin = ys;
+            la.i_end = ye;
+            la.tile0 = 0;
+            for (int64_t c0 = ys; c0 < ye; c0 += kTile) {
+                const int64_t c1 = c0 + kTile < ye ? c0 + kTile : ye;
+                const int64_t ic = c0 + kTile / 2;
+                __syncthreads();   // the previous chunk's readers of u.ln are done
+                tile_geo_load(u.ln.g, b.tab, ic, b.sky);
+                links_tile_prologue<true>(la, u.ln.g, ic, c0, c1 - 1, u.ln.lk);
+                const int64_t m = c0 + t;
+                if (m < c1) links_sample<true>(la, u.ln.g, ic, m, u.ln.lk, scr + (m - ys), ka.scr_len);
+            }
+            __syncthreads();   // the scratch links are visible to the block
+            TdiArgs ta;
+            ta.tab = b.tab;
+            ta.ym = GridMap{1.0, -ys, 0.0, b.dt, ye - ys, 1};
+            ta.y = scr;
+            ta.ny = ka.scr_len;
+            ta.xyz = b.out;
+            ta.nout = b.n;
+            ta.nterm = ka.gen == LISA_TDI20 ? 16 : 8;
+            ta.mode = LISA_FROZEN;
+            ta.channels = ka.channels;
+            ta.i_begin = b.iF;
+            ta.i_end = b.n;
+            ta.tile0 = 0;
+            ta.bl = BlendSpec{1, b.t_hyb, b.sigma, -1.0, b.iF, b.iL + 1};
+            ta.t0_out = b.t0;
+            ta.dt_out = b.dt;
+            comb_group(ta, tf0, nf, nf, u.tdi);
+        }
         }
     }
 }
@@ -232,15 +231,35 @@ struct lisa_plan {
     OrbitDev orb{};
     int gen = 20, kind = 0, channels = 1;
     int nsrc = 0;
+    std::vector<BatchSrc> hsrc;
     BatchSrc* d_srcs = nullptr;
     SegSource* d_segsrc = nullptr;
     double* d_coef = nullptr;
     unsigned long long* d_counter = nullptr;
-    int64_t total_segs = 0, total_tiles = 0, total_samples = 0;
-    int ctas_per_sm = 2, tiles_per_item = 1;
+    float* d_scratch = nullptr;
+    int scr_len = 0, max_ctas = 0;
+    int64_t total_segs = 0, total_tiles = 0, total_samples = 0, total_items = 0;
+    int ctas_per_sm = 2, tiles_per_item = 8;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
+
+// Work items of every source for the plan's tiles_per_item, uploaded to the
+// device descriptors.
+static int plan_items(lisa_plan* p)
+{
+    int64_t items = 0;
+    for (BatchSrc& b : p->hsrc) {
+        b.G = lfa_group(b.dt);
+        b.ngroups = (b.ntiles + b.G - 1) / b.G;
+        b.gpi = p->tiles_per_item / b.G > 1 ? p->tiles_per_item / b.G : 1;
+        b.item_begin = items;
+        items += (b.ngroups + b.gpi - 1) / b.gpi;
+    }
+    p->total_items = items;
+    return cuda_status(cudaMemcpy(p->d_srcs, p->hsrc.data(), sizeof(BatchSrc) * p->hsrc.size(), cudaMemcpyHostToDevice),
+                       "cudaMemcpy(sources)");
+}
 
 static int plan_enqueue(lisa_plan* p, cudaStream_t st)
 {
@@ -251,20 +270,22 @@ static int plan_enqueue(lisa_plan* p, cudaStream_t st)
     BatchKernelArgs ka;
     ka.srcs = p->d_srcs;
     ka.nsrc = p->nsrc;
-    ka.total_tiles = p->total_tiles;
-    ka.tiles_per_item = p->tiles_per_item;
+    ka.total_items = p->total_items;
     ka.counter = p->d_counter;
+    ka.scratch = p->d_scratch;
+    ka.scr_len = p->scr_len;
     ka.gen = p->gen;
     ka.kind = p->kind;
     ka.channels = p->channels;
     ka.Lc = p->orbit.L_m / kC;
     ka.Lcf = (float)ka.Lc;
+    ka.status = device_status_ptr();
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_hybrid_kernel, kTile, 0);
     const int cps = per_sm > 0 && p->ctas_per_sm > per_sm ? per_sm : p->ctas_per_sm;
-    const int64_t items = (p->total_tiles + p->tiles_per_item - 1) / p->tiles_per_item;
     int64_t grid = (int64_t)p->num_sms * (cps > 0 ? cps : 1);
-    if (grid > items) grid = items > 0 ? items : 1;
+    if (grid > p->max_ctas) grid = p->max_ctas;
+    if (grid > p->total_items) grid = p->total_items > 0 ? p->total_items : 1;
     prof_before("batch_hybrid_mixed", st);
     batch_hybrid_kernel<<<(unsigned)grid, kTile, 0, st>>>(ka);
     prof_after(st);
@@ -280,6 +301,7 @@ static void plan_free(lisa_plan* p)
     cudaFree(p->d_segsrc);
     cudaFree(p->d_coef);
     cudaFree(p->d_counter);
+    cudaFree(p->d_scratch);
     delete p;
 }
 
@@ -312,24 +334,12 @@ int lisa_plan_create(lisa_plan** out, const lisa_orbit* orbit, int precision, in
     std::vector<BatchSrc> hs(nsrc);
     std::vector<SegSource> ss(nsrc);
     int64_t segs = 0, tiles = 0, samples = 0;
+    int scr_len = 0;
     for (int k = 0; k < nsrc; ++k) {
         const lisa_source& s = sources[k];
         const lisa_grid& g = s.grid;
         if (!(g.dt >= 0.5) || !isfinite(g.t0) || g.n <= 0 || !s.hp || !s.hc || !s.out || !isfinite(s.t_hyb)) {
             set_error("source %d: need dt >= 0.5 s, n > 0, device pointers and a finite t_hyb", k);
-            delete p;
-            return LISA_EINVAL;
-        }
-        // the fused full-response tile keeps the links over its TDI window in
-        // shared memory: the largest TDI delay must fit that window
-        double Tmax = 1.6 * orbit->L_m / kC;
-        if (orbit->delay == LISA_DELAY_LINEAR) {
-            const double span = fmax(fabs(g.t0 - orbit->t_ref), fabs(g.t0 + g.n * g.dt - orbit->t_ref));
-            Tmax = 0.0;
-            for (int q = 0; q < 6; ++q) Tmax = fmax(Tmax, fabs(orbit->lin_T0[q]) + fabs(orbit->lin_Tdot[q]) * span);
-        }
-        if ((7.0 * Tmax + 1.0) / g.dt + 40.0 > (double)(kWinY - kTile)) {
-            set_error("source %d: dt=%g s is too small for the on-chip TDI window of batched plans", k, g.dt);
             delete p;
             return LISA_EINVAL;
         }
@@ -366,8 +376,15 @@ int lisa_plan_create(lisa_plan** out, const lisa_orbit* orbit, int precision, in
         while (iF < g.n && !(t_at(iF) >= lo_thr)) ++iF;
         b.iL = iL;
         b.iF = iF;
-        b.tile_begin = tiles;
+        // links from the earliest sample the TDI delays of [iF, n) can reach
+        // (as lisa_response_hybrid)
+        const double Dmax = 8.0 * max_light_time(orbit, g);
+        b.dm_links = (int)ceil(Dmax / g.dt) + 40;
+        b.lo_links = iF - b.dm_links > 0 ? iF - b.dm_links : 0;
+        b.h_aligned = ((uintptr_t)s.hp % 16 == 0) && ((uintptr_t)s.hc % 16 == 0);
         b.ntiles = (g.n + kTile - 1) / kTile;
+        const int need = 8 * kTile + 40 + b.dm_links;
+        scr_len = need > scr_len ? need : scr_len;
         segs += b.tab.nseg;
         tiles += b.ntiles;
         samples += g.n;
@@ -375,14 +392,20 @@ int lisa_plan_create(lisa_plan** out, const lisa_orbit* orbit, int precision, in
     p->total_segs = segs;
     p->total_tiles = tiles;
     p->total_samples = samples;
+    p->scr_len = (scr_len + 31) / 32 * 32;
+    p->max_ctas = 4 * (p->num_sms > 0 ? p->num_sms : 1);
     int rc = LISA_OK;
     rc = cuda_status(cudaMalloc(&p->d_coef, sizeof(double) * (size_t)segs * kNQ * kNC), "cudaMalloc(table)");
     if (!rc) rc = cuda_status(cudaMalloc(&p->d_srcs, sizeof(BatchSrc) * nsrc), "cudaMalloc(sources)");
     if (!rc) rc = cuda_status(cudaMalloc(&p->d_segsrc, sizeof(SegSource) * nsrc), "cudaMalloc(segments)");
     if (!rc) rc = cuda_status(cudaMalloc(&p->d_counter, sizeof(unsigned long long)), "cudaMalloc(counter)");
+    if (!rc)
+        rc = cuda_status(cudaMalloc(&p->d_scratch, sizeof(float) * 6 * (size_t)p->scr_len * (size_t)p->max_ctas),
+                         "cudaMalloc(link scratch)");
     if (rc) { plan_free(p); return rc; }
     for (int k = 0; k < nsrc; ++k) hs[k].tab.coef = p->d_coef + (size_t)ss[k].seg_begin * kNQ * kNC;
-    rc = cuda_status(cudaMemcpy(p->d_srcs, hs.data(), sizeof(BatchSrc) * nsrc, cudaMemcpyHostToDevice), "cudaMemcpy");
+    p->hsrc = hs;
+    rc = plan_items(p);
     if (!rc) rc = cuda_status(cudaMemcpy(p->d_segsrc, ss.data(), sizeof(SegSource) * nsrc, cudaMemcpyHostToDevice),
                               "cudaMemcpy");
     if (rc) { plan_free(p); return rc; }
@@ -436,7 +459,7 @@ int lisa_plan_set_launch(lisa_plan* plan, int ctas_per_sm, int tiles_per_item)
     plan->tiles_per_item = tiles_per_item;
     if (plan->exec) { cudaGraphExecDestroy(plan->exec); plan->exec = nullptr; }
     if (plan->graph) { cudaGraphDestroy(plan->graph); plan->graph = nullptr; }
-    return LISA_OK;
+    return plan_items(plan);
 }
 
 int lisa_plan_info(const lisa_plan* plan, int64_t* total_samples, int64_t* total_tiles, int* ctas_per_sm,
@@ -467,7 +490,8 @@ int lisa_plan_autotune(lisa_plan* plan, void* stream, lisa_tune_result* best)
         for (int tpi : tpi_opts) {
             plan->ctas_per_sm = cps;
             plan->tiles_per_item = tpi;
-            rc = plan_enqueue(plan, st);     // warm-up
+            rc = plan_items(plan);
+            if (!rc) rc = plan_enqueue(plan, st);     // warm-up
             if (rc) break;
             float tot = 0.f;
             for (int rep = 0; rep < 3 && !rc; ++rep) {

@@ -18,77 +18,41 @@
 
 namespace lisa {
 
-// Tiles per CTA (mixed form): the FP64 prologue (segment polynomials shifted
-// to the centre, the series' composed cubics) is shared by up to 8
-// consecutive tiles, as many as keep the block's half-span within 1.1e4 s:
-// the omitted quartic terms of the cubics (k.R/c: 500 s at the orbital
-// frequency) then stay below 4e-10 s, a phase error under 1e-10 rad at
-// 2e-2 Hz.
-inline int lfa_group(double dt)
-{
-    int G = (int)floor(80.0 / dt);
-    return G < 1 ? 1 : (G > 8 ? 8 : G);
-}
-
 #ifndef LISA_LFA_MINB
 #define LISA_LFA_MINB 4
 #endif
-// Mixed form: the block's tiles share one prologue; the h window of tile q+1
-// is fetched with bulk copies (two buffers) while tile q is computed.
-template <bool MIXED>
-__global__ void __launch_bounds__(kTile, MIXED ? LISA_LFA_MINB : 1) lfa_kernel(LfaArgs a, int64_t tile_end, int G)
+// FP64 form: one tile after another around the group's prologue.
+__global__ void __launch_bounds__(kTile, 1) lfa_kernel_f64(LfaArgs a, int64_t tile_end, int G)
 {
-    using Real = typename std::conditional<MIXED, float, double>::type;
-    constexpr int NB = MIXED ? 2 : 1;
-    __shared__ LfaSmem<MIXED, NB> sm;
+    __shared__ LfaSmem<false, 1> sm;
     const int64_t t0 = a.tile0 + (int64_t)blockIdx.x * G;
     const int64_t ic = t0 * kTile + (int64_t)G * kTile / 2;
     const int nt = (int)(tile_end - t0 < G ? tile_end - t0 : G);
-    if constexpr (MIXED) {
-        if (threadIdx.x == 0) {
-            mbar_init(&sm.bar[0], 1);
-            mbar_init(&sm.bar[1], 1);
-            mbar_init_fence();
-        }
+    lfa_tile_prologue<false>(a, ic, sm);   // ends with a block barrier
+    for (int q = 0; q < nt; ++q) {
+        const int64_t i0 = (t0 + q) * (int64_t)kTile;
+        double X[3];
+        lfa_tile_body<false, 1>(a, i0, ic, sm, X);
+        const int64_t i = i0 + threadIdx.x;
+        if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<double>(a, i, X);
     }
-    lfa_tile_prologue<MIXED, NB>(a, ic, sm);   // ends with a block barrier
-    if constexpr (!MIXED) {
-        for (int q = 0; q < nt; ++q) {
-            const int64_t i0 = (t0 + q) * (int64_t)kTile;
-            Real X[3];
-            lfa_tile_body<MIXED, NB>(a, i0, ic, sm, X);
-            const int64_t i = i0 + threadIdx.x;
-            if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<Real>(a, i, X);
-        }
-    } else {
-        uint32_t ph0 = 0u, ph1 = 0u;   // phase parities of the two buffers' barriers
-        lfa_window<MIXED, NB>(a, t0 * (int64_t)kTile, ic, sm, 0);
-        lfa_stage<MIXED, NB>(a, sm, 0);
-        for (int q = 0; q < nt; ++q) {
-            const int b = q & 1;
-            const int64_t i0 = (t0 + q) * (int64_t)kTile;
-            if (q + 1 < nt) {
-                lfa_window<MIXED, NB>(a, i0 + kTile, ic, sm, b ^ 1);
-                lfa_stage<MIXED, NB>(a, sm, b ^ 1);
-            }
-            if (!lfa_wait<MIXED, NB>(a, sm, b, b ? ph1 : ph0)) return;
-            if (sm.win[b].bulk) {
-                if (b) ph1 ^= 1u;
-                else ph0 ^= 1u;
-            }
-            // z of samples i0-2 .. i0+1 are the previous tile's last four values
-            if (q > 0 && threadIdx.x < 24) {
-                const int c = threadIdx.x >> 2, o = threadIdx.x & 3;
-                sm.zs[c][o] = sm.zs[c][kTile + o];
-            }
-            lfa_hdot<MIXED, NB>(a, sm, b);
-            lfa_zvalues<MIXED, NB>(a, i0, ic, sm, b, q > 0);
-            Real X[3];
-            lfa_channels<MIXED, NB>(a, i0, ic, sm, X);
-            const int64_t i = i0 + threadIdx.x;
-            if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<Real>(a, i, X, sm.barg_c, sm.barg_d, (int)(i - ic));
-        }
+}
+
+// Mixed form: the group's tiles share one prologue and run in sub-blocks of
+// two tiles; the h window of the next sub-block is fetched with bulk copies
+// (two buffers) while the current one is computed.
+__global__ void __launch_bounds__(kTile, LISA_LFA_MINB) lfa_kernel_mixed(LfaArgs a, int64_t tile_end, int G)
+{
+    __shared__ Lfa2Smem sm;
+    const int64_t t0 = a.tile0 + (int64_t)blockIdx.x * G;
+    const int nt = (int)(tile_end - t0 < G ? tile_end - t0 : G);
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        mbar_init_fence();
     }
+    uint32_t ph0 = 0u, ph1 = 0u;
+    lfa2_group(a, t0, nt, G, sm, ph0, ph1);
 }
 
 int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,
@@ -124,9 +88,9 @@ int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const l
                                    : (precision == LISA_MIXED ? "lfa_mixed" : "lfa_f64"), st);
     if (precision == LISA_MIXED) {
         const int G = lfa_group(og.dt);
-        lfa_kernel<true><<<(unsigned)((tiles + G - 1) / G), kTile, 0, st>>>(a, tile_end, G);
+        lfa_kernel_mixed<<<(unsigned)((tiles + G - 1) / G), kTile, 0, st>>>(a, tile_end, G);
     } else {
-        lfa_kernel<false><<<(unsigned)tiles, kTile, 0, st>>>(a, tile_end, 1);
+        lfa_kernel_f64<<<(unsigned)tiles, kTile, 0, st>>>(a, tile_end, 1);
     }
     prof_after(st);
     return cuda_status(cudaGetLastError(), "lfa_kernel launch");

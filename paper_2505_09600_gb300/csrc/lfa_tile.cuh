@@ -15,7 +15,7 @@ constexpr int kWinH = kTile + 384;
 constexpr int kZW = kTile + 4;
 constexpr int kWinP = kWinH + 8;   // planar h buffers: room for 16-byte alignment of the copy
 #ifndef LISA_LFA_UNROLL
-#define LISA_LFA_UNROLL 2
+#define LISA_LFA_UNROLL 6
 #endif
 constexpr int kLfaUnroll = LISA_LFA_UNROLL;   // series per unrolled step of the mixed z loop
 
@@ -182,8 +182,8 @@ struct LfaSmem {
 // of the segment polynomials) and, for the mixed form, the FP32 records of
 // the six z series.  Every thread of the block must call it (it
 // synchronises).
-template <bool MIXED, int NB>
-__device__ void lfa_tile_prologue(const LfaArgs& a, int64_t ic, LfaSmem<MIXED, NB>& sm)
+template <bool MIXED, class SM>
+__device__ void lfa_tile_prologue(const LfaArgs& a, int64_t ic, SM& sm)
 {
     TileGeo& g = sm.g;
     const int t = threadIdx.x;
@@ -470,8 +470,8 @@ __device__ __forceinline__ void lfa_sample_pos(const LfaArgs& a, float inv_half,
 // sample (|d delay/dt| << 1) and the window spans the indices at the tile's
 // two ends plus margins; the clamp only keeps shared-memory reads in bounds.
 // Without a window the stencils read global memory.
-template <int NB>
-__device__ __forceinline__ float lfa_z_mixed(const LfaArgs& a, const LfaSmem<true, NB>& sm, const LfaWin& W, int c,
+template <class SM>
+__device__ __forceinline__ float lfa_z_mixed(const LfaArgs& a, const SM& sm, const LfaWin& W, int c,
                                              float u, int jp, float fp, float c2, float s2, const float (&ku)[3],
                                              const float (&kv)[3])
 {
@@ -682,8 +682,217 @@ __device__ __forceinline__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, L
                                                  typename std::conditional<MIXED, float, double>::type (&X)[3])
 {
     const int64_t ic = i0 + kTile / 2;
-    lfa_tile_prologue<MIXED, NB>(a, ic, sm);
+    lfa_tile_prologue<MIXED>(a, ic, sm);
     lfa_tile_body<MIXED, NB>(a, i0, ic, sm, X);
+}
+
+// Tiles per CTA (mixed form): the FP64 prologue (segment polynomials shifted
+// to the centre, the series' composed cubics) is shared by up to 8
+// consecutive tiles, as many as keep the block's half-span within 1.1e4 s:
+// the omitted quartic terms of the cubics (k.R/c: 500 s at the orbital
+// frequency) then stay below 4e-10 s, a phase error under 1e-10 rad at
+// 2e-2 Hz.
+inline int lfa_group(double dt)
+{
+    int G = (int)floor(80.0 / dt);
+    return G < 1 ? 1 : (G > 8 ? 8 : G);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed form in sub-blocks of two tiles (the LFA kernel).
+//
+// A CTA's group of tiles shares one FP64 prologue; its tiles are processed two
+// at a time, each thread computing the samples i0 + t and i0 + kTile + t.  The
+// windows of every sub-block are located in the prologue, the h window of
+// sub-block q + 1 is fetched by bulk copies while q is computed, and a
+// sub-block costs three block barriers (copy landed, hdot formed, z formed)
+// for 512 samples.
+// ---------------------------------------------------------------------------
+constexpr int kSub2 = 2 * kTile;          // samples per sub-block
+constexpr int kWin2 = kSub2 + 384;        // hdot window of a sub-block
+constexpr int kWinP2 = kWin2 + 8;         // planar h buffers (16-byte alignment slack)
+constexpr int kZW2 = kSub2 + 4;           // z of a sub-block and its 2-sample halos
+constexpr int kMaxSub2 = 4;               // sub-blocks per group (groups of up to 8 tiles)
+
+struct Lfa2Smem {
+    TileGeo g;
+    alignas(16) float hb[2][2][kWinP2];   // h+ and hx windows, two buffers
+    float2 dw[kWin2];                     // hdot window (interleaved pairs)
+    float zs[6][kZW2];
+    LfaWin win[kMaxSub2];
+    uint64_t bar[2];                      // completion barriers of the bulk copies
+    int64_t jends[kMaxSub2][12];
+    SerF32 ser[6];
+    int64_t J[6];
+    double comp[6][6][4];
+    float c0[kRows];
+    Cubic cu[kRows];
+    float inv_half, inv_dt;
+    float barg_c, barg_d;
+};
+
+// Windows of the nsb sub-blocks starting at tile t0 (after the prologue at
+// the group centre ic).  Every thread must call it (it synchronises twice).
+static __device__ void lfa2_windows(const LfaArgs& a, int64_t t0, int nsb, int64_t ic, Lfa2Smem& sm)
+{
+    const int t = threadIdx.x;
+    if (t < 12 * nsb) {
+        const int sb = t / 12, k = t % 12, c = k % 6;
+        const int64_t i0 = (t0 + 2 * sb) * (int64_t)kTile;
+        const int64_t m = (k < 6) ? i0 - 2 : i0 + kSub2 + 1;
+        int jr;
+        float eps, u;
+        lfa_ser_locate(a, sm.ser[c], sm.inv_half, sm.inv_dt, (int)(m - ic), jr, eps, u);
+        sm.jends[sb][k] = sm.J[c] + jr;
+    }
+    __syncthreads();
+    if (t < nsb) {
+        int64_t lo = sm.jends[t][0], hi = sm.jends[t][0];
+        for (int k = 1; k < 12; ++k) {
+            lo = sm.jends[t][k] < lo ? sm.jends[t][k] : lo;
+            hi = sm.jends[t][k] > hi ? sm.jends[t][k] : hi;
+        }
+        LfaWin& w = sm.win[t];
+        w.wlo = lo - 15 - 3;
+        const int64_t len = (hi + 16 + 3) - w.wlo + 1;
+        w.wlen = (len + 4 <= kWin2) ? (int)len : 0;
+        const int64_t s0 = w.wlo - 2, s1 = w.wlo + w.wlen + 2;
+        const int64_t a0 = s0 - (((s0 % 4) + 4) % 4);
+        const int64_t a1 = s1 + (((4 - s1 % 4) % 4 + 4) % 4);
+        const bool bulk = a.h_aligned && w.wlen > 0 && a0 >= 0 && a1 <= a.hm.n_in && a1 - a0 <= kWinP2;
+        w.bulk = bulk ? 1 : 0;
+        w.a0 = bulk ? a0 : s0;
+        w.nh = bulk ? (int)(a1 - a0) : (w.wlen > 0 ? w.wlen + 4 : 0);
+        for (int c = 0; c < 6; ++c) w.jrel[c] = w.wlen ? (int)(sm.J[c] - w.wlo) - 15 : 0;
+    }
+    __syncthreads();
+}
+
+// Stage the h window of sub-block sb into buffer b: bulk copies issued by
+// thread 0 (completing on sm.bar[b]) or plain loads by every thread.
+static __device__ void lfa2_stage(const LfaArgs& a, Lfa2Smem& sm, int sb, int b)
+{
+    const LfaWin& w = sm.win[sb];
+    const float* __restrict__ hp = (const float*)a.hp;
+    const float* __restrict__ hc = (const float*)a.hc;
+    if (w.bulk) {
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = (uint32_t)w.nh * (uint32_t)sizeof(float);
+            mbar_arrive_expect_tx(&sm.bar[b], 2u * bytes);
+            bulk_copy_g2s(sm.hb[b][0], hp + w.a0, bytes, &sm.bar[b]);
+            bulk_copy_g2s(sm.hb[b][1], hc + w.a0, bytes, &sm.bar[b]);
+        }
+    } else {
+        for (int k = threadIdx.x; k < w.nh; k += blockDim.x) {
+            const int64_t idx = w.a0 + k;
+            const bool in = idx >= 0 && idx < a.hm.n_in;
+            sm.hb[b][0][k] = in ? hp[idx] : 0.f;
+            sm.hb[b][1][k] = in ? hc[idx] : 0.f;
+        }
+    }
+}
+
+// Wait for buffer b (bounded for bulk copies), then form hdot of sub-block
+// sb in sm.dw.  Synchronises twice.  False (for every thread) if a wait timed
+// out: the status word is flagged after a second bounded wait for the copy
+// to land, and the block must stop.
+static __device__ bool lfa2_wait_hdot(const LfaArgs& a, Lfa2Smem& sm, int sb, int b, uint32_t parity)
+{
+    const LfaWin& w = sm.win[sb];
+    bool ok = true;
+    if (w.bulk) ok = mbar_wait_bounded(&sm.bar[b], parity);
+    if (__syncthreads_or(ok ? 0 : 1)) {
+        if (threadIdx.x == 0) flag_timeout(a.status);
+        if (w.bulk) mbar_wait_bounded(&sm.bar[b], parity);
+        return false;
+    }
+    const int off = (int)(w.wlo - 2 - w.a0);
+    const float* P = sm.hb[b][0] + off;
+    const float* C = sm.hb[b][1] + off;
+    const float inv12dt = a.inv12dtf;
+    for (int k = threadIdx.x; k < w.wlen; k += blockDim.x) {
+        const int64_t idx = w.wlo + k;
+        const bool in = (idx >= 0 && idx < a.hm.n_in);
+        float2 d;
+        d.x = in ? ((P[k + 3] - P[k + 1]) * 8.f - (P[k + 4] - P[k])) * inv12dt : 0.f;
+        d.y = in ? ((C[k + 3] - C[k + 1]) * 8.f - (C[k + 4] - C[k])) * inv12dt : 0.f;
+        sm.dw[k] = d;
+    }
+    __syncthreads();
+    return true;
+}
+
+// z of sub-block sb starting at sample i0: the 2 x kTile new values per
+// series (offsets 4 + t and 4 + kTile + t), and on the group's first
+// sub-block also the leading halo (offsets 0..3); later sub-blocks take it
+// from the previous one (copied by the caller).  Synchronises at the end.
+static __device__ void lfa2_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lfa2Smem& sm, int sb, bool first)
+{
+    const LfaWin& W = sm.win[sb];
+    const int t = threadIdx.x;
+    const int dmt = (int)(i0 - ic);
+    const float c2 = a.sky.c2f, s2 = a.sky.s2f;
+    const float ku[3] = {a.sky.uf[0], a.sky.uf[1], a.sky.uf[2]};
+    const float kv[3] = {a.sky.vf[0], a.sky.vf[1], a.sky.vf[2]};
+    const bool interior = i0 - 2 >= 0 && i0 + kSub2 + 2 <= a.nout;
+    if (first && t < 24) {
+        const int c = t >> 2, o = t & 3;
+        const int64_t m = i0 - 2 + o;
+        float u, fp;
+        int jp;
+        lfa_sample_pos(a, sm.inv_half, dmt - 2 + o, u, jp, fp);
+        const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp, c2, s2, ku, kv);
+        sm.zs[c][o] = (interior || (m >= 0 && m < a.nout)) ? z : 0.f;
+    }
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+        const int o = 4 + r * kTile + t;
+        const int64_t m = i0 - 2 + o;
+        const bool valid = interior || (m >= 0 && m < a.nout);
+        float u, fp;
+        int jp;
+        lfa_sample_pos(a, sm.inv_half, dmt - 2 + o, u, jp, fp);
+#pragma unroll kLfaUnroll
+        for (int c = 0; c < 6; ++c) {
+            const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp, c2, s2, ku, kv);
+            sm.zs[c][o] = valid ? z : 0.f;
+        }
+    }
+    __syncthreads();
+}
+
+// Channels of sample i0 + r kTile + t from the z values of its sub-block.
+__device__ __forceinline__ void lfa2_channels(const LfaArgs& a, int64_t i0, int64_t ic, const Lfa2Smem& sm, int r,
+                                              float (&X)[3])
+{
+    const int t = threadIdx.x;
+    const bool equal = (a.kind == LISA_LFA_EQUAL);
+    const int o = r * kTile + t;               // zs[c][o .. o + 4] = z at i - 2 .. i + 2
+    const int64_t i = i0 + o;
+    if (a.z && i >= a.i_begin && i < a.i_end) {
+        float* zo = (float*)a.z;
+        for (int c = 0; c < 6; ++c) zo[(int64_t)c * a.nout + i] = sm.zs[c][o + 2];
+    }
+    const float k1 = a.c1f, k2 = a.c2f;
+    const float u = (float)(int)(i - ic) * sm.inv_half;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float Ta = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 0)] + sm.cu[kQT + lfa_arm(ch, 0)](u);
+        const float Tb = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 1)] + sm.cu[kQT + lfa_arm(ch, 1)](u);
+        const float* za = sm.zs[2 * ch] + o;
+        const float* zb = sm.zs[2 * ch + 1] + o;
+        if (a.gen == LISA_TDI20) {
+            auto d2 = [&](const float* z) {
+                const float e0 = z[1] - z[0], e1 = z[2] - z[1], e2 = z[3] - z[2], e3 = z[4] - z[3];
+                const float m1 = e1 - e0, c0 = e2 - e1, p1 = e3 - e2;
+                return (14.f * c0 - m1 - p1) * k2;
+            };
+            X[ch] = 8.f * (Ta + Tb) * (Ta * d2(za) - Tb * d2(zb));
+        } else {
+            auto d1 = [&](const float* z) { return ((z[3] - z[1]) * 8.f - (z[4] - z[0])) * k1; };
+            X[ch] = 4.f * (Ta * d1(za) - Tb * d1(zb));
+        }
+    }
 }
 
 // AET, sigmoid weight (LFA side: eps = +1) and store of one sample.
@@ -714,6 +923,45 @@ __device__ __forceinline__ void lfa_store(const LfaArgs& a, int64_t i, const Rea
     out[i] = o0;
     out[a.nout + i] = o1;
     out[2 * a.nout + i] = o2;
+}
+
+// One group of nt tiles from tile t0 (centre ic = t0 kTile + G kTile / 2)
+// in sub-blocks of two tiles, stored with the blend of the arguments.  The
+// caller initialised sm.bar[0..1]; ph0, ph1 carry their phase parities from
+// call to call.  Every thread must call it.  False if a bounded wait timed
+// out (the status word is flagged; the block must stop).
+static __device__ bool lfa2_group(const LfaArgs& a, int64_t t0, int nt, int G, Lfa2Smem& sm, uint32_t& ph0, uint32_t& ph1)
+{
+    const int64_t ic = t0 * kTile + (int64_t)G * kTile / 2;
+    const int nsb = (nt + 1) / 2;
+    lfa_tile_prologue<true>(a, ic, sm);   // ends with a block barrier
+    lfa2_windows(a, t0, nsb, ic, sm);
+    lfa2_stage(a, sm, 0, 0);
+    for (int sb = 0; sb < nsb; ++sb) {
+        const int b = sb & 1;
+        const int64_t i0 = (t0 + 2 * sb) * (int64_t)kTile;
+        if (sb + 1 < nsb) lfa2_stage(a, sm, sb + 1, b ^ 1);
+        if (!lfa2_wait_hdot(a, sm, sb, b, b ? ph1 : ph0)) return false;
+        if (sm.win[sb].bulk) {
+            if (b) ph1 ^= 1u;
+            else ph0 ^= 1u;
+        }
+        // z at samples i0-2 .. i0+1: the previous sub-block's last four values
+        // (the previous channels were read before the barriers just passed)
+        if (sb > 0 && threadIdx.x < 24) {
+            const int c = threadIdx.x >> 2, o = threadIdx.x & 3;
+            sm.zs[c][o] = sm.zs[c][kSub2 + o];
+        }
+        lfa2_zvalues(a, i0, ic, sm, sb, sb == 0);
+        for (int r = 0; r < 2; ++r) {
+            if (2 * sb + r >= nt) break;
+            float X[3];
+            lfa2_channels(a, i0, ic, sm, r, X);
+            const int64_t i = i0 + r * kTile + threadIdx.x;
+            if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<float>(a, i, X, sm.barg_c, sm.barg_d, (int)(i - ic));
+        }
+    }
+    return true;
 }
 
 }  // namespace lisa
