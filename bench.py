@@ -491,26 +491,27 @@ def run_ours(args):
     total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     value = whole_job_rate(world, n, args.steps, total_ms)
 
-    # end to end through the public call with host buffers (pinned), copies timed
+    # end to end through the public call on host buffers (page-locked): the
+    # host->device copies of h and the device->host copy of A, E, T are inside
+    # the timed region (the library overlaps them with its kernels in chunks)
     hp_h = torch.as_tensor(src.hp.astype(np.float32)).pin_memory()
     hc_h = torch.as_tensor(src.hc.astype(np.float32)).pin_memory()
     out_h = torch.empty((3, n), dtype=torch.float32).pin_memory()
-    hp_d = torch.empty_like(hp32)
-    hc_d = torch.empty_like(hc32)
     e2e_ms = []
     for k in range(args.warmup + args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        hp_d.copy_(hp_h, non_blocking=True)
-        hc_d.copy_(hc_h, non_blocking=True)
-        L.lisa_response_hybrid(orbit, sky, src.grid, hp_d, hc_d, L.MIXED, 20, L.LFA_UNEQUAL, L.AET, tH, Tw, sig,
-                               src.grid, out32)
-        out_h.copy_(out32, non_blocking=True)
+        L.lisa_response_hybrid_host(orbit, sky, src.grid, hp_h, hc_h, L.MIXED, 20, L.LFA_UNEQUAL, L.AET, tH, Tw, sig,
+                                    out_h, stream=stream.cuda_stream)
         b.record(stream)
         b.synchronize()
         if k >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
+    # the host-buffer call returns what the device call returns (the TDI blocks
+    # follow its chunks: FP32 rounding)
+    ref = out32.cpu()
+    e2e_diff = float((out_h - ref).abs().max() / ref.abs().max().clamp_min(1e-300))
     e2e_total = max_over_ranks(float(sum(e2e_ms)), world, dev)
     e2e_value = whole_job_rate(world, n, len(e2e_ms), e2e_total)
 
@@ -599,7 +600,9 @@ def run_ours(args):
                    "n_samples": n, "dt": src.dt, "sources_per_gpu": 1, "l2": "flushed between steps "
                    "(256 MiB write outside the timed events)", "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4, "d2h_bytes_per_step": 3 * n * 4},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4, "d2h_bytes_per_step": 3 * n * 4,
+                "call": "lisa_response_hybrid_host (page-locked host buffers, copies overlapped in chunks)",
+                "max_rel_diff_vs_device_call": e2e_diff},
         "gpu_launches": int(launches),
         "clocks": clk,
         "forms": forms,

@@ -195,6 +195,21 @@ int lisa_response_hybrid_static(const lisa_orbit* orbit, const lisa_sky* sky, li
                                 int channels, double t_hyb, double T_win, double sigma,
                                 lisa_grid out, void* xyz, void* stream);
 
+/* lisa_response_hybrid on series in host memory (the paper has no
+ * counterpart; an integration aid).  grid is both the h grid and the output
+ * grid.  hp, hc: host [grid.n]; xyz: host [3][grid.n] (float for LISA_MIXED,
+ * double for LISA_F64).  The grid is cut into up to 8 chunks on the LFA tile
+ * groups; the copy of chunk c+1 to the device and the copy of chunk c-1 back
+ * run on two internal streams while chunk c is computed on `stream`, so with
+ * page-locked host buffers the copies overlap the kernels.  Device buffers
+ * come from the stream-ordered allocator on `stream`.  The call returns after
+ * queuing; the results are in xyz once `stream` has completed the work
+ * queued up to the return.  The values equal lisa_response_hybrid's up to
+ * FP32 rounding in the TDI (its blocks follow the chunks). */
+int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid grid,
+                              const void* hp, const void* hc, int precision, int tdi_gen, int lfa_kind,
+                              int channels, double t_hyb, double T_win, double sigma, void* xyz, void* stream);
+
 /* Hybridisation time at leading PN order (Sec. IV, Eq. thyb):
  * t_hyb = tc - f^(-8/3) * 5/(8 pi)^(8/3) * (G Mc/c^3)^(-5/3); mc_s = G Mc/c^3 in s. */
 double lisa_t_hyb_from_f(double f_hyb, double mc_s, double tc);

@@ -55,6 +55,8 @@ __global__ void __launch_bounds__(kTile, LISA_LFA_MINB) lfa_kernel_mixed(LfaArgs
     lfa2_group(a, t0, nt, G, sm, ph0, ph1);
 }
 
+int lfa_group_host(double dt) { return lfa_group(dt); }
+
 int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,
                const void* hc, int precision, int gen, int kind, int channels, const lisa_grid& og, void* z,
                void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st)

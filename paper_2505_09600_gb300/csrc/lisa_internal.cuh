@@ -87,6 +87,8 @@ size_t real_size(int precision);
 int make_table(const lisa_orbit* orbit, const lisa_grid& g, Scratch& sc, SegTable& tab, cudaStream_t st);
 // Upper bound of any single light time (halo sizing).
 double max_light_time(const lisa_orbit* o, const lisa_grid& g);
+// Tiles per CTA group of the mixed LFA kernel for a grid step dt (host side).
+int lfa_group_host(double dt);
 // Hybrid regions on grid `out`: LFA samples [0, iL] (t <= t_hyb + Tw/2), full
 // samples [iF, n) (t >= t_hyb - Tw/2).
 void hybrid_split(const lisa_grid& out, double t_hyb, double Tw, int64_t& iL, int64_t& iF);

@@ -129,6 +129,8 @@ _SIGS = {
     "lisa_response_hybrid": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
                                        C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                        lisa_grid, _P, _P]),
+    "lisa_response_hybrid_host": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
+                                            C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _P, _P]),
     "lisa_corrector_num_params": (C.c_int64, []),
     "lisa_corrector_num_features": (C.c_int, []),
     "lisa_corrector_create": (C.c_int, [C.POINTER(C.c_void_p), _P, C.c_int64, C.c_uint64]),
@@ -212,6 +214,20 @@ def _ptr(t, dtype=None, numel=None, name="tensor"):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s (got %s)" % (name, dtype, t.dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements (got %d)" % (name, numel, t.numel()))
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t, dtype=None, numel=None, name="tensor"):
+    """Host memory: a contiguous CPU tensor (page-locked for overlapped copies)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a CPU tensor" % name)
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
     if dtype is not None and t.dtype != dtype:
@@ -320,6 +336,20 @@ def lisa_response_hybrid(orbit, sky, h_grid, hp, hc, precision, tdi_gen, lfa_kin
                                      precision, tdi_gen, lfa_kind, channels, float(t_hyb), float(T_win), float(sigma),
                                      og, _ptr(xyz, dt, 3 * og.n, "xyz"), _stream(stream))
     _check(rc, "lisa_response_hybrid")
+
+
+def lisa_response_hybrid_host(orbit, sky, grid, hp, hc, precision, tdi_gen, lfa_kind, channels, t_hyb, T_win, sigma,
+                              xyz, stream=None):
+    """Hybrid response of host series (CPU tensors, page-locked for overlap);
+    the results are in xyz once `stream` has completed."""
+    g = _grid(grid)
+    dt = _rdtype(precision)
+    o, s = _orb(orbit), _sky(sky)
+    rc = load().lisa_response_hybrid_host(C.byref(o), C.byref(s), g, _host_ptr(hp, dt, g.n, "hp"),
+                                          _host_ptr(hc, dt, g.n, "hc"), precision, tdi_gen, lfa_kind, channels,
+                                          float(t_hyb), float(T_win), float(sigma), _host_ptr(xyz, dt, 3 * g.n, "xyz"),
+                                          _stream(stream))
+    _check(rc, "lisa_response_hybrid_host")
 
 
 def lisa_profile_enable(enable=True):
