@@ -392,6 +392,55 @@ def bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, st
     return res
 
 
+def bench_loglike(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig):
+    """Log-likelihood evaluation as the paper times it (Sec. IV, steps ii-v
+    on given polarisations): hybrid response -> A, E, T -> real FFTs ->
+    noise-weighted inner products with fixed data d (here the response
+    itself), ln L = -(<d|d> + <h|h> - 2<d|h>)/2, read back to the host."""
+    n = src.n
+    nf = n // 2 + 1
+    f_min, f_max = 1e-4, 3e-2
+    w = torch.empty((2, nf), device=dev, dtype=torch.float64)
+    L.lisa_noise_weights_aet(src.grid, 20, ORBIT_KW.get("L_m", 2.5e9), 1.0, 1, f_min, f_max, w)
+    d = torch.empty((3, n), device=dev, dtype=torch.float32)
+    L.lisa_response_hybrid(orbit, sky, src.grid, hp32, hc32, L.MIXED, 20, L.LFA_UNEQUAL, L.AET, tH, Tw, sig,
+                           src.grid, d)
+    ip = torch.empty(9, device=dev, dtype=torch.float64)
+    ip_h = torch.empty(9, dtype=torch.float64).pin_memory()
+
+    def loglike():
+        L.lisa_response_hybrid(orbit, sky, src.grid, hp32, hc32, L.MIXED, 20, L.LFA_UNEQUAL, L.AET, tH, Tw, sig,
+                               src.grid, out32)
+        L.lisa_inner_aet(src.grid, d, out32, L.MIXED, w, ip)
+        ip_h.copy_(ip, non_blocking=True)
+
+    for _ in range(3):
+        loglike()
+    torch.cuda.synchronize()
+    L.lisa_profile_enable(False)
+    L.lisa_profile_enable(True)
+    ms = []
+    for _ in range(10):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        loglike()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    inner_ms, inner_n = L.lisa_profile_query("inner_aet")
+    L.lisa_profile_enable(False)
+    v = ip_h.numpy().reshape(3, 3)
+    lnl = [float(-0.5 * (v[c, 1] + v[c, 2] - 2.0 * v[c, 0])) for c in range(3)]
+    snr = [float(np.sqrt(max(v[c, 1], 0.0))) for c in range(3)]
+    best = float(np.median(ms))
+    return {"ms": round(best, 4), "evaluations_per_s": round(1e3 / best, 1),
+            "inner_ms": round(inner_ms / max(inner_n, 1), 4),
+            "steps": "hybrid response (A, E, T) + 2 x 3 real FFTs (cuFFT) + weighted inner products + 9-value read-back",
+            "band_hz": [f_min, f_max], "ln_L_per_channel": lnl, "snr_per_channel_of_d": snr,
+            "note": "d = the same response, so ln L = 0 up to FP32 rounding of the repeated evaluation"}
+
+
 def bench_batch(L, torch, dev, orbit, flush, stream, args):
     """Batched hybrid plan over the seeded config-3 population (Mc log-U
     [1e4, 1e7], q U[1, 10], 1 day to 3 months at 5 or 10 s): one persistent
@@ -562,6 +611,9 @@ def run_ours(args):
     corrector = None
     if not args.no_corrector and rank == 0:
         corrector = bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig)
+    loglike = None
+    if not args.no_loglike and rank == 0:
+        loglike = bench_loglike(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig)
     batched = None
     if not args.no_batch and rank == 0:
         batched = bench_batch(L, torch, dev, orbit, flush, stream, args)
@@ -612,6 +664,8 @@ def run_ours(args):
         line["corrector"] = corrector
     if batched is not None:
         line["batched"] = batched
+    if loglike is not None:
+        line["loglike"] = loglike
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = oracle_hybrid_rate(src, budget_s=args.cpu_budget, gpu_out=gpu_out)
     print(json.dumps(line), flush=True)
@@ -657,6 +711,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-corrector", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-loglike", action="store_true")
     ap.add_argument("--batch-sources", type=int, default=1024)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -210,6 +210,42 @@ int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky* sky, lisa
                               const void* hp, const void* hc, int precision, int tdi_gen, int lfa_kind,
                               int channels, double t_hyb, double T_win, double sigma, void* xyz, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Likelihood tail (Sec. IV steps iv-v; Sec. II C noise model): the Fourier
+ * transform of A, E, T and the noise-weighted inner product
+ *   <x|y> = 4 Re int_{f_min}^{f_max} df x~*(f) y~(f) / S_n(f)   (Eq. scalar_product),
+ * with x~(f) = int dt e^{-2 pi i f t} x(t) (App. A) taken as dt times the
+ * discrete transform on the bins f_k = k / (n dt), and the integral as the sum
+ * over the bins in [f_min, f_max] times df = 1/(n dt).  The overlap
+ * O = <x|y> / sqrt(<x|x><y|y>) and mismatch 1 - |O| (Eq. normalized_overlap)
+ * and ln L = -<d - h|d - h>/2 follow from the three products.
+ * ------------------------------------------------------------------------ */
+
+/* Noise PSDs of A/E and T (Eqs. SnAE, SnT) from the proof-mass, optical-path
+ * and galactic-foreground noises (Sec. II C, Eq. sgal; T_obs in years enters
+ * the foreground knees), Lambda = 4 sin^2(2x) for TDI 2.0 and 1 for 1.5,
+ * x = 2 pi f L / c.  psd: device double [2][nf] (S^{A,E}, then S^T) at
+ * f0 + k df, f0 > 0.  galaxy = 0 drops the foreground. */
+int lisa_psd_aet(double f0, double df, int64_t nf, int tdi_gen, double L_m, double t_obs_years, int galaxy,
+                 double* psd, void* stream);
+
+/* Weights of the inner product on the rfft bins of `grid` (nf = n/2 + 1):
+ * w[0][k] = 4 df / S^{A,E}(f_k), w[1][k] = 4 df / S^T(f_k) for f_k in
+ * [f_min, f_max] and k > 0, else 0.  w: device double [2][nf] for both
+ * precisions (S_n ~ 1e-44 puts 4 df / S_n beyond the FP32 range).  Compute
+ * once per grid and PSD. */
+int lisa_noise_weights_aet(lisa_grid grid, int tdi_gen, double L_m, double t_obs_years, int galaxy, double f_min,
+                           double f_max, double* w, void* stream);
+
+/* <x|y>, <x|x>, <y|y> for A, E and T: out (device double[9]) =
+ * {A: xy, xx, yy; E: ...; T: ...}.  x, y: device [3][grid.n] in the
+ * precision's type (y may equal x); w from lisa_noise_weights_aet.  Real
+ * FFTs by cuFFT (plans cached per device, length and precision), then one
+ * pass over the bins and a fixed-order reduction (run to run identical).
+ * Device scratch from the stream-ordered allocator on `stream`. */
+int lisa_inner_aet(lisa_grid grid, const void* x, const void* y, int precision, const double* w, double* out,
+                   void* stream);
+
 /* Hybridisation time at leading PN order (Sec. IV, Eq. thyb):
  * t_hyb = tc - f^(-8/3) * 5/(8 pi)^(8/3) * (G Mc/c^3)^(-5/3); mc_s = G Mc/c^3 in s. */
 double lisa_t_hyb_from_f(double f_hyb, double mc_s, double tc);
