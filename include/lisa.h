@@ -229,22 +229,31 @@ int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky* sky, lisa
 int lisa_psd_aet(double f0, double df, int64_t nf, int tdi_gen, double L_m, double t_obs_years, int galaxy,
                  double* psd, void* stream);
 
-/* Weights of the inner product on the rfft bins of `grid` (nf = n/2 + 1):
+/* Smallest 2^a 3^b 5^c 7^d >= n: a transform length that keeps cuFFT on its
+ * fast radices (one year at 5 s, 6,311,520 = 2^5 3^3 5 487 samples, pads to
+ * 6,322,176 = 2^11 3^2 7^3). */
+int64_t lisa_fft_length(int64_t n);
+
+/* Weights of the inner product on the rfft bins of `grid` zero-padded to
+ * nfft >= grid.n samples (0: grid.n), nf = nfft/2 + 1, f_k = k / (nfft dt):
  * w[0][k] = 4 df / S^{A,E}(f_k), w[1][k] = 4 df / S^T(f_k) for f_k in
  * [f_min, f_max] and k > 0, else 0.  w: device double [2][nf] for both
  * precisions (S_n ~ 1e-44 puts 4 df / S_n beyond the FP32 range).  Compute
  * once per grid and PSD. */
-int lisa_noise_weights_aet(lisa_grid grid, int tdi_gen, double L_m, double t_obs_years, int galaxy, double f_min,
-                           double f_max, double* w, void* stream);
+int lisa_noise_weights_aet(lisa_grid grid, int64_t nfft, int tdi_gen, double L_m, double t_obs_years, int galaxy,
+                           double f_min, double f_max, double* w, void* stream);
 
 /* <x|y>, <x|x>, <y|y> for A, E and T: out (device double[9]) =
  * {A: xy, xx, yy; E: ...; T: ...}.  x, y: device [3][grid.n] in the
- * precision's type (y may equal x); w from lisa_noise_weights_aet.  Real
- * FFTs by cuFFT (plans cached per device, length and precision), then one
- * pass over the bins and a fixed-order reduction (run to run identical).
- * Device scratch from the stream-ordered allocator on `stream`. */
-int lisa_inner_aet(lisa_grid grid, const void* x, const void* y, int precision, const double* w, double* out,
-                   void* stream);
+ * precision's type (y may equal x), zero-padded to nfft >= grid.n samples
+ * (0: none) in scratch; w from lisa_noise_weights_aet with the same nfft.
+ * Zero padding samples the same continuous transform more finely (on a flat
+ * PSD the products are unchanged, by Parseval).  Real FFTs by cuFFT (plans
+ * cached per device, length and precision), then one pass over the bins and a
+ * fixed-order reduction (run to run identical).  Device scratch from the
+ * stream-ordered allocator on `stream`. */
+int lisa_inner_aet(lisa_grid grid, int64_t nfft, const void* x, const void* y, int precision, const double* w,
+                   double* out, void* stream);
 
 /* Hybridisation time at leading PN order (Sec. IV, Eq. thyb):
  * t_hyb = tc - f^(-8/3) * 5/(8 pi)^(8/3) * (G Mc/c^3)^(-5/3); mc_s = G Mc/c^3 in s. */

@@ -76,22 +76,45 @@ def psd_aet(f, tdi_gen=20, L_m=2.5e9, t_obs_years=1.0, galaxy=True):
     return sae, st
 
 
-def spectrum(x, dt):
-    """x~(f_k) = dt * sum_n x_n e^{-2 pi i k n / N} on the rfft bins, per row."""
-    return dt * np.fft.rfft(np.asarray(x, dtype=np.float64), axis=-1)
+def fft_length(n):
+    """Smallest 2^a 3^b 5^c 7^d >= n (the transform length of a zero-padded row)."""
+    best = None
+    p2 = 1
+    while p2 < 2 * n:
+        p3 = p2
+        while p3 < 2 * n:
+            p5 = p3
+            while p5 < 2 * n:
+                p7 = p5
+                while p7 < 2 * n:
+                    if p7 >= n and (best is None or p7 < best):
+                        best = p7
+                    p7 *= 7
+                p5 *= 5
+            p3 *= 3
+        p2 *= 2
+    return best
 
 
-def inner_aet(x, y, dt, f_min, f_max, tdi_gen=20, L_m=2.5e9, t_obs_years=1.0, galaxy=True):
+def spectrum(x, dt, nfft=None):
+    """x~(f_k) = dt * sum_n x_n e^{-2 pi i k n / M} on the rfft bins of the row
+    zero-padded to M = nfft samples (M = N without padding)."""
+    return dt * np.fft.rfft(np.asarray(x, dtype=np.float64), n=nfft, axis=-1)
+
+
+def inner_aet(x, y, dt, f_min, f_max, tdi_gen=20, L_m=2.5e9, t_obs_years=1.0, galaxy=True, nfft=None):
     """<x|y>, <x|x>, <y|y> for each of A, E, T (rows of x, y: [3][N]), Eq.
-    scalar_product with the A/E PSD for A and E and the T PSD for T."""
+    scalar_product with the A/E PSD for A and E and the T PSD for T, on the
+    bins f_k = k / (M dt) of the rows zero-padded to M = nfft >= N samples
+    (zero padding samples the same continuous transform more finely)."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
-    n = x.shape[-1]
+    n = x.shape[-1] if nfft is None else int(nfft)
     f = np.arange(n // 2 + 1) / (n * dt)
     df = 1.0 / (n * dt)
     sel = (f >= f_min) & (f <= f_max) & (f > 0)
     sae, st = psd_aet(np.where(sel, f, 1.0), tdi_gen, L_m, t_obs_years, galaxy)
-    X, Y = spectrum(x, dt), spectrum(y, dt)
+    X, Y = spectrum(x, dt, n), spectrum(y, dt, n)
     out = np.zeros((3, 3))
     for c in range(3):
         s = sae if c < 2 else st

@@ -126,25 +126,26 @@ __device__ __forceinline__ void interp_hdot_global(const Real* __restrict__ hp, 
 // k.(R_s + R_r)/2c with the TDI shift sh, Sec. III) as FP32 cubics in the
 // block's coordinate u = (m - ic) * 2/S around the centre sample ic: the
 // total delay d(u) = D0 + d1 u + d2 u^2 + d3 u^3 (D0 split exactly into J, f
-// in FP64), the light time T_l and the link vector n_l at the retarded time.
+// in FP64), and the two projection factors of the link,
+//   F+(u) = -(T_l/2) (xi+ cos 2psi + xix sin 2psi),
+//   Fx(u) = -(T_l/2) (xix cos 2psi - xi+ sin 2psi),
+// so that z = F+ hdot+ + Fx hdotx (xi+ = (u.n)^2 - (v.n)^2, xix = 2 (u.n)(v.n),
+// geometry at the retarded coordinate).  The factors are products of the
+// composed T_l and n_l cubics, truncated at u^3 in FP64: over a group
+// (|u| < 0.04) the dropped terms are below 1e-12 of the factors.
 struct __align__(16) SerF32 {
     float f, d1, d2, d3;      // centre fraction, in-block delay variation (s)
-    float T[4];               // T_l(u) = T[0] + T[1] u + T[2] u^2 + T[3] u^3
-    float n[3][4];            // n_l components, same form
+    float Fp[4];              // F+(u) = Fp[0] + Fp[1] u + Fp[2] u^2 + Fp[3] u^3
+    float Fc[4];              // Fx(u), same form
 };
 
-// A record read as five 16-byte shared-memory loads.
-__device__ __forceinline__ SerF32 load_ser(const SerF32& r)
+// Truncated product of two cubics: (a b) mod u^4.
+__device__ __forceinline__ void cubic_mul(const double (&a)[4], const double (&b)[4], double (&c)[4])
 {
-    const float4* p = reinterpret_cast<const float4*>(&r);
-    const float4 a = p[0], b = p[1], c = p[2], d = p[3], e = p[4];
-    SerF32 o;
-    o.f = a.x; o.d1 = a.y; o.d2 = a.z; o.d3 = a.w;
-    o.T[0] = b.x; o.T[1] = b.y; o.T[2] = b.z; o.T[3] = b.w;
-    o.n[0][0] = c.x; o.n[0][1] = c.y; o.n[0][2] = c.z; o.n[0][3] = c.w;
-    o.n[1][0] = d.x; o.n[1][1] = d.y; o.n[1][2] = d.z; o.n[1][3] = d.w;
-    o.n[2][0] = e.x; o.n[2][1] = e.y; o.n[2][2] = e.z; o.n[2][3] = e.w;
-    return o;
+    c[0] = a[0] * b[0];
+    c[1] = a[0] * b[1] + a[1] * b[0];
+    c[2] = a[0] * b[2] + a[1] * b[1] + a[2] * b[0];
+    c[3] = a[0] * b[3] + a[1] * b[2] + a[2] * b[1] + a[3] * b[0];
 }
 
 // Staged window of one tile: hdot on samples [wlo, wlo + wlen) of the h grid
@@ -258,9 +259,29 @@ __device__ void lfa_tile_prologue(const LfaArgs& a, int64_t ic, SM& sm)
             R.d1 = (float)d[1];
             R.d2 = (float)d[2];
             R.d3 = (float)d[3];
-            for (int k = 0; k < 4; ++k) R.T[k] = (float)sm.comp[c][0][k];
-            for (int q = 0; q < 3; ++q)
-                for (int k = 0; k < 4; ++k) R.n[q][k] = (float)sm.comp[c][3 + q][k];
+            // projection factors: (u.n), (v.n) cubics, then xi+, xix, times -T_l/2
+            double un[4], vn[4], T[4];
+            for (int k = 0; k < 4; ++k) {
+                un[k] = a.sky.u[0] * sm.comp[c][3][k] + a.sky.u[1] * sm.comp[c][4][k] + a.sky.u[2] * sm.comp[c][5][k];
+                vn[k] = a.sky.v[0] * sm.comp[c][3][k] + a.sky.v[1] * sm.comp[c][4][k] + a.sky.v[2] * sm.comp[c][5][k];
+                T[k] = -0.5 * sm.comp[c][0][k];
+            }
+            double uu[4], vv[4], uv[4], xp[4], xc[4], gp[4], gc[4], Fp[4], Fc[4];
+            cubic_mul(un, un, uu);
+            cubic_mul(vn, vn, vv);
+            cubic_mul(un, vn, uv);
+            for (int k = 0; k < 4; ++k) {
+                xp[k] = uu[k] - vv[k];
+                xc[k] = 2.0 * uv[k];
+                gp[k] = xp[k] * a.sky.c2p + xc[k] * a.sky.s2p;
+                gc[k] = xc[k] * a.sky.c2p - xp[k] * a.sky.s2p;
+            }
+            cubic_mul(T, gp, Fp);
+            cubic_mul(T, gc, Fc);
+            for (int k = 0; k < 4; ++k) {
+                R.Fp[k] = (float)Fp[k];
+                R.Fc[k] = (float)Fc[k];
+            }
             sm.J[c] = j;
         }
     }
@@ -472,8 +493,7 @@ __device__ __forceinline__ void lfa_sample_pos(const LfaArgs& a, float inv_half,
 // Without a window the stencils read global memory.
 template <class SM>
 __device__ __forceinline__ float lfa_z_mixed(const LfaArgs& a, const SM& sm, const LfaWin& W, int c,
-                                             float u, int jp, float fp, float c2, float s2, const float (&ku)[3],
-                                             const float (&kv)[3])
+                                             float u, int jp, float fp)
 {
     const float4* rp = reinterpret_cast<const float4*>(&sm.ser[c]);
     const float4 r0 = rp[0];   // f, d1, d2, d3
@@ -492,15 +512,10 @@ __device__ __forceinline__ float lfa_z_mixed(const LfaArgs& a, const SM& sm, con
         dp = r2.x;
         dc = r2.y;
     }
-    const float4 rT = rp[1], rn0 = rp[2], rn1 = rp[3], rn2 = rp[4];
-    const float Tl = fmaf(u, fmaf(u, fmaf(u, rT.w, rT.z), rT.y), rT.x);
-    const float n0 = fmaf(u, fmaf(u, fmaf(u, rn0.w, rn0.z), rn0.y), rn0.x);
-    const float n1 = fmaf(u, fmaf(u, fmaf(u, rn1.w, rn1.z), rn1.y), rn1.x);
-    const float n2 = fmaf(u, fmaf(u, fmaf(u, rn2.w, rn2.z), rn2.y), rn2.x);
-    const float un = ku[0] * n0 + ku[1] * n1 + ku[2] * n2;
-    const float vn = kv[0] * n0 + kv[1] * n1 + kv[2] * n2;
-    const float xp = un * un - vn * vn, xc = 2.f * un * vn;
-    return -0.5f * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
+    const float4 rp1 = rp[1], rp2 = rp[2];
+    const float Fp = fmaf(u, fmaf(u, fmaf(u, rp1.w, rp1.z), rp1.y), rp1.x);
+    const float Fc = fmaf(u, fmaf(u, fmaf(u, rp2.w, rp2.z), rp2.y), rp2.x);
+    return fmaf(Fp, dp, Fc * dc);
 }
 
 // z values of the tile starting at i0 (window b staged, hdot in sm.dw): the
@@ -547,7 +562,7 @@ __device__ void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MI
             float u, fp;
             int jp;
             lfa_sample_pos(a, sm.inv_half, dmt - 2 + o, u, jp, fp);
-            const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp, c2, s2, ku, kv);
+            const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp);
             sm.zs[c][o] = (interior || (m >= 0 && m < a.nout)) ? z : 0.f;
         }
         {
@@ -559,7 +574,7 @@ __device__ void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MI
             lfa_sample_pos(a, sm.inv_half, dmt + 2 + t, u, jp, fp);
 #pragma unroll kLfaUnroll
             for (int c = 0; c < 6; ++c) {
-                const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp, c2, s2, ku, kv);
+                const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp);
                 sm.zs[c][o] = valid ? z : 0.f;
             }
         }
@@ -831,9 +846,6 @@ static __device__ void lfa2_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lf
     const LfaWin& W = sm.win[sb];
     const int t = threadIdx.x;
     const int dmt = (int)(i0 - ic);
-    const float c2 = a.sky.c2f, s2 = a.sky.s2f;
-    const float ku[3] = {a.sky.uf[0], a.sky.uf[1], a.sky.uf[2]};
-    const float kv[3] = {a.sky.vf[0], a.sky.vf[1], a.sky.vf[2]};
     const bool interior = i0 - 2 >= 0 && i0 + kSub2 + 2 <= a.nout;
     if (first && t < 24) {
         const int c = t >> 2, o = t & 3;
@@ -841,7 +853,7 @@ static __device__ void lfa2_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lf
         float u, fp;
         int jp;
         lfa_sample_pos(a, sm.inv_half, dmt - 2 + o, u, jp, fp);
-        const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp, c2, s2, ku, kv);
+        const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp);
         sm.zs[c][o] = (interior || (m >= 0 && m < a.nout)) ? z : 0.f;
     }
 #pragma unroll 1
@@ -854,7 +866,7 @@ static __device__ void lfa2_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lf
         lfa_sample_pos(a, sm.inv_half, dmt - 2 + o, u, jp, fp);
 #pragma unroll kLfaUnroll
         for (int c = 0; c < 6; ++c) {
-            const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp, c2, s2, ku, kv);
+            const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp);
             sm.zs[c][o] = valid ? z : 0.f;
         }
     }

@@ -78,11 +78,15 @@ __global__ void psd_kernel(NoiseSpec ns, double f0, double df, int64_t nf, doubl
 
 // Weights in FP64 for both forms: S_n is ~1e-44 (fractional frequency), so
 // 4 df / S_n is far above the FP32 range.
-__global__ void weights_kernel(NoiseSpec ns, double df, int64_t nf, double f_min, double f_max, double* __restrict__ w)
+// Bin frequency k / (M dt) by a division (the band test at f_min, f_max must
+// not depend on how f_k was rounded: next to a PSD zero one bin's weight can
+// dominate a product).
+__global__ void weights_kernel(NoiseSpec ns, double span, int64_t nf, double f_min, double f_max, double* __restrict__ w)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nf) return;
-    const double f = (double)k * df;
+    const double f = (double)k / span;
+    const double df = 1.0 / span;
     double wa = 0.0, wt = 0.0;
     if (k > 0 && f >= f_min && f <= f_max) {
         double sae, st;
@@ -215,10 +219,24 @@ int lisa_psd_aet(double f0, double df, int64_t nf, int tdi_gen, double L_m, doub
     return cuda_status(cudaGetLastError(), "psd_kernel launch");
 }
 
-int lisa_noise_weights_aet(lisa_grid grid, int tdi_gen, double L_m, double t_obs_years, int galaxy, double f_min,
-                           double f_max, double* w, void* stream)
+int64_t lisa_fft_length(int64_t n)
+{
+    if (n <= 1) return n < 1 ? 0 : 1;
+    int64_t best = -1;
+    for (int64_t p2 = 1; p2 < 2 * n; p2 *= 2)
+        for (int64_t p3 = p2; p3 < 2 * n; p3 *= 3)
+            for (int64_t p5 = p3; p5 < 2 * n; p5 *= 5)
+                for (int64_t p7 = p5; p7 < 2 * n; p7 *= 7)
+                    if (p7 >= n && (best < 0 || p7 < best)) best = p7;
+    return best;
+}
+
+int lisa_noise_weights_aet(lisa_grid grid, int64_t nfft, int tdi_gen, double L_m, double t_obs_years, int galaxy,
+                           double f_min, double f_max, double* w, void* stream)
 {
     LISA_TRY(check_grid(grid, "grid"));
+    if (nfft == 0) nfft = grid.n;
+    if (nfft < grid.n) { set_error("nfft = %lld is below the grid's %lld samples", (long long)nfft, (long long)grid.n); return LISA_EINVAL; }
     if (tdi_gen != LISA_TDI15 && tdi_gen != LISA_TDI20) { set_error("tdi_gen must be 15 or 20"); return LISA_EINVAL; }
     if (!(L_m > 0.0) || !(t_obs_years > 0.0) || !(f_max >= f_min)) {
         set_error("need L_m > 0, t_obs_years > 0, f_max >= f_min");
@@ -226,31 +244,51 @@ int lisa_noise_weights_aet(lisa_grid grid, int tdi_gen, double L_m, double t_obs
     }
     if (grid.n == 0) return LISA_OK;
     if (!w) { set_error("w is NULL"); return LISA_EINVAL; }
-    const int64_t nf = grid.n / 2 + 1;
-    const double df = 1.0 / ((double)grid.n * grid.dt);
+    const int64_t nf = nfft / 2 + 1;
+    const double span = (double)nfft * grid.dt;   // M dt: f_k = k / span, df = 1 / span
     cudaStream_t st = (cudaStream_t)stream;
     const NoiseSpec ns = make_spec(tdi_gen, L_m, t_obs_years, galaxy);
     const unsigned blocks = (unsigned)((nf + 255) / 256);
     prof_before("noise_weights", st);
-    weights_kernel<<<blocks, 256, 0, st>>>(ns, df, nf, f_min, f_max, w);
+    weights_kernel<<<blocks, 256, 0, st>>>(ns, span, nf, f_min, f_max, w);
     prof_after(st);
     return cuda_status(cudaGetLastError(), "weights_kernel launch");
 }
 
-int lisa_inner_aet(lisa_grid grid, const void* x, const void* y, int precision, const double* w, double* out,
-                   void* stream)
+int lisa_inner_aet(lisa_grid grid, int64_t nfft, const void* x, const void* y, int precision, const double* w,
+                   double* out, void* stream)
 {
     LISA_TRY(check_grid(grid, "grid"));
     if (precision != LISA_F64 && precision != LISA_MIXED) { set_error("precision unknown"); return LISA_EINVAL; }
     if (grid.n < 2) { set_error("need at least 2 samples"); return LISA_EINVAL; }
     if (!x || !y || !w || !out) { set_error("NULL pointer"); return LISA_EINVAL; }
-    const int64_t n = grid.n, nf = n / 2 + 1;
+    if (nfft == 0) nfft = grid.n;
+    if (nfft < grid.n) { set_error("nfft = %lld is below the grid's %lld samples", (long long)nfft, (long long)grid.n); return LISA_EINVAL; }
+    const int64_t n = grid.n, nf = nfft / 2 + 1;
     cudaStream_t st = (cudaStream_t)stream;
     cufftHandle plan;
     std::lock_guard<std::mutex> lock(g_plan_mutex);   // one plan object is bound to one stream at a time
-    LISA_TRY(get_plan(n, precision, plan));
+    LISA_TRY(get_plan(nfft, precision, plan));
     const size_t cs = precision == LISA_MIXED ? sizeof(cufftComplex) : sizeof(cufftDoubleComplex);
+    const size_t rs = real_size(precision);
     Scratch sc(st);
+    // rows zero-padded to nfft samples (a 7-smooth length keeps the transform fast)
+    auto padded = [&](const void* src) -> const void* {
+        if (nfft == n) return src;
+        char* p = (char*)sc.alloc(3 * (size_t)nfft * rs);
+        if (!p) return nullptr;
+        if (cudaMemcpy2DAsync(p, (size_t)nfft * rs, src, (size_t)n * rs, (size_t)n * rs, 3, cudaMemcpyDeviceToDevice,
+                              st) != cudaSuccess ||
+            cudaMemset2DAsync(p + (size_t)n * rs, (size_t)nfft * rs, 0, (size_t)(nfft - n) * rs, 3, st) != cudaSuccess)
+            return nullptr;
+        return p;
+    };
+    const void* xp = padded(x);
+    const void* yp = (y == x) ? xp : padded(y);
+    if (!xp || !yp) {
+        if (sc.status()) return sc.status();
+        return cuda_status(cudaGetLastError(), "zero padding");
+    }
     void* X = sc.alloc(3 * (size_t)nf * cs);
     void* Y = (x == y) ? X : sc.alloc(3 * (size_t)nf * cs);
     int nblocks = 0;
@@ -265,8 +303,8 @@ int lisa_inner_aet(lisa_grid grid, const void* x, const void* y, int precision, 
     double* partial = (double*)sc.alloc((size_t)nblocks * 9 * sizeof(double));
     if (!X || !Y || !partial) return sc.status();
     prof_before("inner_aet", st);
-    LISA_TRY(rfft3(plan, precision, x, X, st));
-    if (y != x) LISA_TRY(rfft3(plan, precision, y, Y, st));
+    LISA_TRY(rfft3(plan, precision, xp, X, st));
+    if (y != x) LISA_TRY(rfft3(plan, precision, yp, Y, st));
     if (precision == LISA_MIXED)
         inner_kernel<float2><<<nblocks, kRedThreads, 0, st>>>((const float2*)X, (const float2*)Y, w, nf, partial);
     else

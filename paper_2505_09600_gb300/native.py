@@ -133,9 +133,10 @@ _SIGS = {
                                             C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _P, _P]),
     "lisa_psd_aet": (C.c_int, [C.c_double, C.c_double, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int, _P,
                                _P]),
-    "lisa_noise_weights_aet": (C.c_int, [lisa_grid, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double,
-                                         _P, _P]),
-    "lisa_inner_aet": (C.c_int, [lisa_grid, _P, _P, C.c_int, _P, _P, _P]),
+    "lisa_fft_length": (C.c_int64, [C.c_int64]),
+    "lisa_noise_weights_aet": (C.c_int, [lisa_grid, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
+                                         C.c_double, _P, _P]),
+    "lisa_inner_aet": (C.c_int, [lisa_grid, C.c_int64, _P, _P, C.c_int, _P, _P, _P]),
     "lisa_corrector_num_params": (C.c_int64, []),
     "lisa_corrector_num_features": (C.c_int, []),
     "lisa_corrector_create": (C.c_int, [C.POINTER(C.c_void_p), _P, C.c_int64, C.c_uint64]),
@@ -365,23 +366,29 @@ def lisa_psd_aet(f0, df, nf, tdi_gen, L_m, t_obs_years, galaxy, psd, stream=None
     _check(rc, "lisa_psd_aet")
 
 
-def lisa_noise_weights_aet(grid, tdi_gen, L_m, t_obs_years, galaxy, f_min, f_max, w, stream=None):
-    """Inner-product weights 4 df / S on the rfft bins of grid into w (CUDA float64 [2][n/2+1])."""
+def lisa_fft_length(n):
+    return int(load().lisa_fft_length(int(n)))
+
+
+def lisa_noise_weights_aet(grid, nfft, tdi_gen, L_m, t_obs_years, galaxy, f_min, f_max, w, stream=None):
+    """Inner-product weights 4 df / S on the rfft bins of grid zero-padded to
+    nfft samples (0: none) into w (CUDA float64 [2][nfft/2+1])."""
     import torch
     g = _grid(grid)
-    rc = load().lisa_noise_weights_aet(g, tdi_gen, float(L_m), float(t_obs_years), int(galaxy), float(f_min),
-                                       float(f_max), _ptr(w, torch.float64, 2 * (g.n // 2 + 1), "w"),
-                                       _stream(stream))
+    m = int(nfft) or g.n
+    rc = load().lisa_noise_weights_aet(g, m, tdi_gen, float(L_m), float(t_obs_years), int(galaxy), float(f_min),
+                                       float(f_max), _ptr(w, torch.float64, 2 * (m // 2 + 1), "w"), _stream(stream))
     _check(rc, "lisa_noise_weights_aet")
 
 
-def lisa_inner_aet(grid, x, y, precision, w, out, stream=None):
+def lisa_inner_aet(grid, nfft, x, y, precision, w, out, stream=None):
     """<x|y>, <x|x>, <y|y> per channel into out (CUDA float64 [9] or [3][3])."""
     import torch
     g = _grid(grid)
+    m = int(nfft) or g.n
     dt = _rdtype(precision)
-    rc = load().lisa_inner_aet(g, _ptr(x, dt, 3 * g.n, "x"), _ptr(y, dt, 3 * g.n, "y"), precision,
-                               _ptr(w, torch.float64, 2 * (g.n // 2 + 1), "w"), _ptr(out, torch.float64, 9, "out"),
+    rc = load().lisa_inner_aet(g, m, _ptr(x, dt, 3 * g.n, "x"), _ptr(y, dt, 3 * g.n, "y"), precision,
+                               _ptr(w, torch.float64, 2 * (m // 2 + 1), "w"), _ptr(out, torch.float64, 9, "out"),
                                _stream(stream))
     _check(rc, "lisa_inner_aet")
 

@@ -41,7 +41,7 @@ def test_weights_match_oracle(L):
     f_min, f_max = 1e-4, 2.5e-2
     nf = grid[2] // 2 + 1
     w = torch.empty((2, nf), device="cuda", dtype=torch.float64)
-    L.lisa_noise_weights_aet(grid, 20, L_M, 1.0, 1, f_min, f_max, w)
+    L.lisa_noise_weights_aet(grid, 0, 20, L_M, 1.0, 1, f_min, f_max, w)
     f = np.arange(nf) / (grid[2] * grid[1])
     df = 1.0 / (grid[2] * grid[1])
     sel = (f >= f_min) & (f <= f_max) & (f > 0)
@@ -65,32 +65,41 @@ def _hybrid(L, s, precision):
     return out
 
 
+def test_fft_length(L):
+    for n in (1, 2, 17, 487, 30001, 6311520):
+        assert L.lisa_fft_length(n) == ON.fft_length(n)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
-def test_inner_products_match_oracle(L, precision):
-    s = synth.cfg2_small(n=30000)
+@pytest.mark.parametrize("pad", [False, True])
+def test_inner_products_match_oracle(L, precision, pad):
+    s = synth.cfg2_small(n=30001)
     x = _hybrid(L, s, precision)
     # y: the same signal with a small phase-like distortion (a shifted copy plus x)
     y = (0.8 * x + 0.2 * torch.roll(x, 3, dims=1)).contiguous()
-    f_min, f_max = 1e-4, 3e-2
-    nf = s.n // 2 + 1
+    # band below the TDI 2.0 PSD zero at c/(4L) = 0.02998 Hz, where 4 df / S blows up
+    f_min, f_max = 1e-4, 2.5e-2
+    m = ON.fft_length(s.n) if pad else s.n
+    nf = m // 2 + 1
     w = torch.empty((2, nf), device="cuda", dtype=torch.float64)
-    L.lisa_noise_weights_aet(s.grid, 20, L_M, 1.0, 1, f_min, f_max, w)
+    L.lisa_noise_weights_aet(s.grid, m, 20, L_M, 1.0, 1, f_min, f_max, w)
     out = torch.empty(9, device="cuda", dtype=torch.float64)
-    L.lisa_inner_aet(s.grid, x, y, precision, w, out)
+    L.lisa_inner_aet(s.grid, m, x, y, precision, w, out)
     got = out.cpu().numpy().reshape(3, 3)
-    want = ON.inner_aet(x.double().cpu().numpy(), y.double().cpu().numpy(), s.dt, f_min, f_max, 20, L_M, 1.0, True)
+    want = ON.inner_aet(x.double().cpu().numpy(), y.double().cpu().numpy(), s.dt, f_min, f_max, 20, L_M, 1.0, True,
+                        nfft=m)
     tol = 1e-11 if precision == 0 else 2e-5
     np.testing.assert_allclose(got, want, rtol=tol)
     np.testing.assert_allclose(ON.overlap(got), ON.overlap(want), rtol=tol, atol=tol)
     # <x|x> with y = x (one transform) equals the xx product of the pair call
     out2 = torch.empty(9, device="cuda", dtype=torch.float64)
-    L.lisa_inner_aet(s.grid, x, x, precision, w, out2)
+    L.lisa_inner_aet(s.grid, m, x, x, precision, w, out2)
     g2 = out2.cpu().numpy().reshape(3, 3)
     np.testing.assert_allclose(g2[:, 0], got[:, 1], rtol=1e-12)
     np.testing.assert_allclose(g2[:, 2], got[:, 1], rtol=1e-12)
     # run to run identical (fixed-order reduction)
     out3 = torch.empty(9, device="cuda", dtype=torch.float64)
-    L.lisa_inner_aet(s.grid, x, y, precision, w, out3)
+    L.lisa_inner_aet(s.grid, m, x, y, precision, w, out3)
     assert torch.equal(out, out3)
 
 
@@ -102,9 +111,9 @@ def test_mismatch_of_response_forms(L):
     x32 = _hybrid(L, s, 1).double()
     nf = s.n // 2 + 1
     w = torch.empty((2, nf), device="cuda", dtype=torch.float64)
-    L.lisa_noise_weights_aet(s.grid, 20, L_M, 1.0, 1, 1e-4, 3e-2, w)
+    L.lisa_noise_weights_aet(s.grid, 0, 20, L_M, 1.0, 1, 1e-4, 2.5e-2, w)
     out = torch.empty(9, device="cuda", dtype=torch.float64)
-    L.lisa_inner_aet(s.grid, x64, x32.contiguous(), 0, w, out)
+    L.lisa_inner_aet(s.grid, 0, x64, x32.contiguous(), 0, w, out)
     ip = out.cpu().numpy().reshape(3, 3)
     mm = ON.mismatch(ip)
     assert np.all(mm[:2] < 1e-8), mm

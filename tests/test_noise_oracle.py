@@ -16,7 +16,10 @@ and the mathematics fix, independently of its own formulas:
     flat PSD gives <x|x> = A^2 N dt / S (Parseval); sinusoids on different
     bins are orthogonal; <x|y> is symmetric and bilinear;
   * overlap(x, a x) = sign(a) and mismatch(x, x) = 0; an overall time shift
-    by a whole number of samples on a periodic signal leaves <x|x> unchanged.
+    by a whole number of samples on a periodic signal leaves <x|x> unchanged;
+  * zero padding: on a flat PSD covering every bin, <x|y> equals Parseval's
+    2 dt sum x y for any transform length, up to the DC and Nyquist bins;
+  * fft_length: the smallest 7-smooth number >= n.
 """
 import numpy as np
 import pytest
@@ -140,3 +143,45 @@ def test_overlap_and_mismatch():
     np.testing.assert_allclose(N.mismatch(ip), 0.0, atol=1e-12)
     ip2 = N.inner_aet(x, np.roll(x, 17, axis=-1), dt, 1e-4, 8e-2, 20, L)
     np.testing.assert_allclose(ip2[:, 2], ip[:, 1], rtol=1e-12)   # |x~| unchanged by a cyclic shift
+
+
+def test_fft_length():
+    assert N.fft_length(1) == 1
+    assert N.fft_length(6311520) == 6322176   # 2^11 3^2 7^3
+    for n in (17, 487, 1000, 4099, 6311520):
+        m = N.fft_length(n)
+        assert m >= n
+        r = m
+        for p in (2, 3, 5, 7):
+            while r % p == 0:
+                r //= p
+        assert r == 1
+        assert all(not _smooth(k) for k in range(n, m))
+
+
+def _smooth(k):
+    for p in (2, 3, 5, 7):
+        while k % p == 0:
+            k //= p
+    return k == 1
+
+
+def test_zero_padding_invariance_flat_psd(monkeypatch):
+    rng = np.random.default_rng(11)
+    n, dt = 1000, 5.0
+    x = rng.standard_normal((3, n))
+    y = rng.standard_normal((3, n))
+    # flat PSD S = 1 and a band covering every bin but DC
+    monkeypatch.setattr(N, "psd_aet", lambda f, *a, **k: (np.ones_like(f), np.ones_like(f)))
+    ref = None
+    for m in (n, 1024, 1536, 4000):
+        ip = N.inner_aet(x, y, dt, 1e-12, 1e9, nfft=m)
+        # 4 Re sum_{k>=1} X_k^* Y_k df = 2 dt sum x y - 2 X_0 Y_0 df (+ 2 X_{M/2} Y_{M/2} df if M is even:
+        # Parseval's two-sided sum holds the Nyquist bin once, the one-sided sum counts it once)
+        X = dt * np.fft.rfft(x, n=m)
+        Y = dt * np.fft.rfft(y, n=m)
+        df = 1.0 / (m * dt)
+        want = 2 * dt * np.sum(x * y, axis=1) - 2 * np.real(np.conj(X[:, 0]) * Y[:, 0]) * df
+        if m % 2 == 0:
+            want += 2 * np.real(np.conj(X[:, -1]) * Y[:, -1]) * df
+        np.testing.assert_allclose(ip[:, 0], want, rtol=1e-10)
