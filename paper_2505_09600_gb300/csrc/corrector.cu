@@ -96,6 +96,15 @@ __device__ __forceinline__ float gelu_f(float x)
     const float c = 0.7978845608028654f;
     return 0.5f * x * (1.f + tanh_fast(c * fmaf(0.044715f * x, x * x, x)));
 }
+// Twice the GELU, 2 GELU(x) = x (1 + tanh(x (c + c 0.044715 x^2))): five
+// operations.  The inference image carries the missing 1/2 in the next
+// layer's weights (a power-of-two scale, exact in BF16).
+__device__ __forceinline__ float gelu2_f(float x)
+{
+    const float c = 0.7978845608028654f;
+    const float p = fmaf(x * x, c * 0.044715f, c);
+    return fmaf(x, tanh_fast(x * p), x);
+}
 __device__ __forceinline__ float gelu_grad_f(float x)
 {
     const float c = 0.7978845608028654f;
@@ -577,14 +586,16 @@ __global__ void publish_tc_kernel(const float* __restrict__ p, unsigned char* __
         const int n = t / kInP, k = t % kInP;
         o[(kTcW1 + tc_off(n, k, 768)) / 2] = __float2bfloat16(k < kIn ? p[kOffW1 + n * kIn + k] : 0.f);
     }
+    // the layers after a GELU take half their weights: the kernel feeds them
+    // 2 GELU (see gelu2_f); BF16(w / 2) = BF16(w) / 2 exactly
     if (t < kWid * kWid) {           // W2, W3: 64 x 64
         const int n = t / kWid, k = t % kWid;
-        o[(kTcW2 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(p[kOffW2 + t]);
-        o[(kTcW3 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(p[kOffW3 + t]);
+        o[(kTcW2 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(0.5f * p[kOffW2 + t]);
+        o[(kTcW3 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(0.5f * p[kOffW3 + t]);
     }
     if (t < kOutP * kWid) {          // W4: 16 x 64
         const int n = t / kWid, k = t % kWid;
-        o[(kTcW4 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(n < kOut ? p[kOffW4 + n * kWid + k] : 0.f);
+        o[(kTcW4 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(n < kOut ? 0.5f * p[kOffW4 + n * kWid + k] : 0.f);
     }
 }
 
@@ -643,7 +654,14 @@ __device__ __forceinline__ bool tc_layer(TcSmem& sm, uint32_t wofs, uint32_t wsb
     return all_ok;
 }
 
-__global__ void __launch_bounds__(kTcRows, 1) corr_mlp_tc_kernel(TcArgs A)
+#ifndef LISA_CORR_CTAS
+#define LISA_CORR_CTAS 4
+#endif
+// CTAs per SM of the tensor-core kernel (shared memory allows 5; 4 keeps 128
+// registers per thread without spills)
+constexpr int kCorrCtas = LISA_CORR_CTAS;
+
+__global__ void __launch_bounds__(kTcRows, kCorrCtas) corr_mlp_tc_kernel(TcArgs A)
 {
     __shared__ TcSmem sm;
     const int t = threadIdx.x, warp = t >> 5;
@@ -722,7 +740,7 @@ __global__ void __launch_bounds__(kTcRows, 1) corr_mlp_tc_kernel(TcArgs A)
                 tmem_ld16(lane_base + cb * 16, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int k = 0; k < 16; ++k) v[k] = gelu_f(v[k] + sm.bias[l * kWid + cb * 16 + k]);
+                for (int k = 0; k < 16; ++k) v[k] = gelu2_f(v[k] + sm.bias[l * kWid + cb * 16 + k]);
                 store_row_bf16(sm.act, t, 2 * cb, v);
                 store_row_bf16(sm.act, t, 2 * cb + 1, v + 8);
             }
@@ -939,7 +957,7 @@ static int run_mlp_tc(const lisa_corrector* c, int64_t rows, const float* x, flo
     A.y = y;
     A.status = device_status_ptr();
     const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
-    const int64_t cap = (int64_t)sm_count() * 4;
+    const int64_t cap = (int64_t)sm_count() * kCorrCtas;
     const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
     prof_before(x ? "mlp_forward_tc" : "corr_fused_tc", st);
     corr_mlp_tc_kernel<<<grid, kTcRows, 0, st>>>(A);

@@ -491,7 +491,9 @@ __device__ __forceinline__ void lfa_sample_pos(const LfaArgs& a, float inv_half,
 // sample (|d delay/dt| << 1) and the window spans the indices at the tile's
 // two ends plus margins; the clamp only keeps shared-memory reads in bounds.
 // Without a window the stencils read global memory.
-template <class SM>
+// STAGED: 1 = the window is staged (stencils from shared memory), 0 = global
+// memory, -1 = decided here from W.wlen (a choice uniform over the block).
+template <int STAGED = -1, class SM>
 __device__ __forceinline__ float lfa_z_mixed(const LfaArgs& a, const SM& sm, const LfaWin& W, int c,
                                              float u, int jp, float fp)
 {
@@ -503,7 +505,7 @@ __device__ __forceinline__ float lfa_z_mixed(const LfaArgs& a, const SM& sm, con
     const int jr = jp + (int)fv;
     const float eps = v - fv;
     float dp, dc;
-    if (W.wlen > 0) {
+    if (STAGED == 1 || (STAGED < 0 && W.wlen > 0)) {
         const int base = min(max(W.jrel[c] + jr, 0), W.wlen - 32);
         lagrange32_dot2(eps, sm.dw + base, dp, dc);
     } else {
@@ -856,20 +858,26 @@ static __device__ void lfa2_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lf
         const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp);
         sm.zs[c][o] = (interior || (m >= 0 && m < a.nout)) ? z : 0.f;
     }
+    // the staged / global choice is uniform over the block: one loop each
+    auto run = [&](auto staged) {
+        constexpr int S = decltype(staged)::value;
 #pragma unroll 1
-    for (int r = 0; r < 2; ++r) {
-        const int o = 4 + r * kTile + t;
-        const int64_t m = i0 - 2 + o;
-        const bool valid = interior || (m >= 0 && m < a.nout);
-        float u, fp;
-        int jp;
-        lfa_sample_pos(a, sm.inv_half, dmt - 2 + o, u, jp, fp);
+        for (int r = 0; r < 2; ++r) {
+            const int o = 4 + r * kTile + t;
+            const int64_t m = i0 - 2 + o;
+            const bool valid = interior || (m >= 0 && m < a.nout);
+            float u, fp;
+            int jp;
+            lfa_sample_pos(a, sm.inv_half, dmt - 2 + o, u, jp, fp);
 #pragma unroll kLfaUnroll
-        for (int c = 0; c < 6; ++c) {
-            const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp);
-            sm.zs[c][o] = valid ? z : 0.f;
+            for (int c = 0; c < 6; ++c) {
+                const float z = lfa_z_mixed<S>(a, sm, W, c, u, jp, fp);
+                sm.zs[c][o] = valid ? z : 0.f;
+            }
         }
-    }
+    };
+    if (W.wlen > 0) run(std::integral_constant<int, 1>{});
+    else run(std::integral_constant<int, 0>{});
     __syncthreads();
 }
 
