@@ -24,7 +24,7 @@ namespace lisa {
 // FP64 form: one tile after another around the group's prologue.
 __global__ void __launch_bounds__(kTile, 1) lfa_kernel_f64(LfaArgs a, int64_t tile_end, int G)
 {
-    __shared__ LfaSmem<false, 1> sm;
+    __shared__ LfaSmem64 sm;
     const int64_t t0 = a.tile0 + (int64_t)blockIdx.x * G;
     const int64_t ic = t0 * kTile + (int64_t)G * kTile / 2;
     const int nt = (int)(tile_end - t0 < G ? tile_end - t0 : G);
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kTile, 1) lfa_kernel_f64(LfaArgs a, int64_t ti
     for (int q = 0; q < nt; ++q) {
         const int64_t i0 = (t0 + q) * (int64_t)kTile;
         double X[3];
-        lfa_tile_body<false, 1>(a, i0, ic, sm, X);
+        lfa_tile_body(a, i0, ic, sm, X);
         const int64_t i = i0 + threadIdx.x;
         if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<double>(a, i, X);
     }

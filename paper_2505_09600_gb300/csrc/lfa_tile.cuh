@@ -18,6 +18,9 @@ constexpr int kWinP = kWinH + 8;   // planar h buffers: room for 16-byte alignme
 #define LISA_LFA_UNROLL 6
 #endif
 constexpr int kLfaUnroll = LISA_LFA_UNROLL;   // series per unrolled step of the mixed z loop
+#ifndef LISA_LFA_PAIR
+#define LISA_LFA_PAIR 0   // staged z loop: 1 = a thread's two samples share packed weight instructions, 2 = adjacent samples also share the taps
+#endif
 
 template <typename Real>
 struct PairT;
@@ -158,25 +161,14 @@ struct LfaWin {
     int jrel[6];              // mixed form: J_c - wlo - 15
 };
 
-template <bool MIXED, int NB = 1>
-struct LfaSmem {
-    using Real = typename std::conditional<MIXED, float, double>::type;
-    using Real2 = typename PairT<Real>::T;
+// Shared memory of the FP64 form (one tile at a time).
+struct LfaSmem64 {
     TileGeo g;
-    alignas(16) Real hb[NB][2][kWinP];   // h+ and hx windows (NB buffers)
-    Real2 dw[kWinH];          // hdot window (interleaved pairs)
-    Real zs[6][kZW];
-    LfaWin win[NB];
-    uint64_t bar[NB];         // completion barriers of the bulk copies
+    double hb[2][kWinP];      // h+ and hx on the window
+    double2 dw[kWinH];        // hdot window (interleaved pairs)
+    double zs[6][kZW];
+    LfaWin win;
     int64_t jends[12];
-    // mixed: per-series records, arm rows (centre value, cubic) for the channels
-    SerF32 ser[6];
-    int64_t J[6];
-    double comp[6][6][4];         // prologue scratch: composed rows per series
-    float c0[kRows];
-    Cubic cu[kRows];
-    float inv_half, inv_dt;       // FP32 constants
-    float barg_c, barg_d;         // sigmoid argument at the centre and per sample
 };
 
 // FP64 set-up around the centre sample ic: the orbit geometry (Taylor shift
@@ -327,41 +319,33 @@ static __device__ __noinline__ float2 interp_hdot_global_ool(const float* __rest
     return make_float2(p, q);
 }
 
-// Window of the tile starting at i0 (prologue centre ic) into sm.win[b]: the
+// FP64 form: window of the tile starting at i0 (prologue centre ic): the
 // retarded samples of the six series at the tile's two ends (2-sample halo
 // included) bound the hdot window.  Every thread must call it (it
 // synchronises twice).
-template <bool MIXED, int NB>
-__device__ void lfa_window(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MIXED, NB>& sm, int b)
+__device__ inline void lfa_window(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem64& sm)
 {
     const int t = threadIdx.x;
     const bool equal = (a.kind == LISA_LFA_EQUAL);
     if (t < 12) {
         const int c = t % 6;
         const int64_t m = (t < 6) ? i0 - 2 : i0 + kTile + 1;
+        const TileGeo& g = sm.g;
+        const double half = 0.5 * a.tab.S;
+        const double u_per_s = 1.0 / (a.dt_out * half);
+        const double u = (double)(m - ic) / half;
+        const int ch = c >> 1, which = c & 1;
+        const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
+        const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
+        const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
+        const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
+        const double up = u - sh * u_per_s;
+        const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
+        const double d = sh + 0.5 * Tl
+                       + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
         int64_t j;
-        if constexpr (MIXED) {
-            int jr;
-            float eps, u;
-            lfa_ser_locate(a, sm.ser[c], sm.inv_half, sm.inv_dt, (int)(m - ic), jr, eps, u);
-            j = sm.J[c] + jr;
-        } else {
-            const TileGeo& g = sm.g;
-            const double half = 0.5 * a.tab.S;
-            const double u_per_s = 1.0 / (a.dt_out * half);
-            const double u = (double)(m - ic) / half;
-            const int ch = c >> 1, which = c & 1;
-            const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
-            const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
-            const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
-            const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
-            const double up = u - sh * u_per_s;
-            const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
-            const double d = sh + 0.5 * Tl
-                           + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
-            double eps;
-            split_f64(a.hm, m, d, j, eps);
-        }
+        double eps;
+        split_f64(a.hm, m, d, j, eps);
         sm.jends[t] = j;
     }
     __syncthreads();
@@ -371,99 +355,41 @@ __device__ void lfa_window(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MIX
             lo = sm.jends[k] < lo ? sm.jends[k] : lo;
             hi = sm.jends[k] > hi ? sm.jends[k] : hi;
         }
-        LfaWin& w = sm.win[b];
+        LfaWin& w = sm.win;
         w.wlo = lo - 15 - 3;
         const int64_t len = (hi + 16 + 3) - w.wlo + 1;
         w.wlen = (len + 4 <= kWinH) ? (int)len : 0;
-        // h needed on [wlo - 2, wlo + wlen + 2); a bulk copy moves whole
-        // 16-byte groups from a 16-byte boundary and must stay on the h array
-        const int64_t s0 = w.wlo - 2, s1 = w.wlo + w.wlen + 2;
-        const int64_t a0 = s0 - (((s0 % 4) + 4) % 4);
-        const int64_t a1 = s1 + (((4 - s1 % 4) % 4 + 4) % 4);
-        const bool bulk = MIXED && NB > 1 && a.h_aligned && w.wlen > 0 && a0 >= 0 && a1 <= a.hm.n_in &&
-                          a1 - a0 <= kWinP;
-        w.bulk = bulk ? 1 : 0;
-        w.a0 = bulk ? a0 : s0;
-        w.nh = bulk ? (int)(a1 - a0) : (w.wlen > 0 ? w.wlen + 4 : 0);
-        if constexpr (MIXED) {
-            // window-relative start of each series' stencils (32-bit: |J - wlo| <
-            // kWinH whenever the window is staged; otherwise unused)
-            for (int c = 0; c < 6; ++c) w.jrel[c] = w.wlen ? (int)(sm.J[c] - w.wlo) - 15 : 0;
-        }
+        // h needed on [wlo - 2, wlo + wlen + 2)
+        w.bulk = 0;
+        w.a0 = w.wlo - 2;
+        w.nh = w.wlen > 0 ? w.wlen + 4 : 0;
     }
     __syncthreads();
 }
 
-// Stage h of window b: one bulk copy per polarisation issued by thread 0
-// (completing on sm.bar[b]), or plain loads by every thread (complete at the
-// next block barrier).
-template <bool MIXED, int NB>
-__device__ void lfa_stage(const LfaArgs& a, LfaSmem<MIXED, NB>& sm, int b)
+// FP64 form: stage h on the window with plain loads (zero off the h grid),
+// then form hdot (5-point central stencil).  Synchronises the block twice.
+__device__ inline void lfa_stage_hdot(const LfaArgs& a, LfaSmem64& sm)
 {
-    using Real = typename std::conditional<MIXED, float, double>::type;
-    const LfaWin& w = sm.win[b];
-    const Real* __restrict__ hp = (const Real*)a.hp;
-    const Real* __restrict__ hc = (const Real*)a.hc;
-    if (w.bulk) {
-        if constexpr (MIXED && NB > 1) {
-            if (threadIdx.x == 0) {
-                const uint32_t bytes = (uint32_t)w.nh * (uint32_t)sizeof(float);
-                mbar_arrive_expect_tx(&sm.bar[b], 2u * bytes);
-                bulk_copy_g2s(sm.hb[b][0], hp + w.a0, bytes, &sm.bar[b]);
-                bulk_copy_g2s(sm.hb[b][1], hc + w.a0, bytes, &sm.bar[b]);
-            }
-        }
-    } else {
-        for (int k = threadIdx.x; k < w.nh; k += blockDim.x) {
-            const int64_t idx = w.a0 + k;
-            const bool in = idx >= 0 && idx < a.hm.n_in;
-            sm.hb[b][0][k] = in ? hp[idx] : Real(0);
-            sm.hb[b][1][k] = in ? hc[idx] : Real(0);
-        }
+    const LfaWin& w = sm.win;
+    const double* __restrict__ hp = (const double*)a.hp;
+    const double* __restrict__ hc = (const double*)a.hc;
+    for (int k = threadIdx.x; k < w.nh; k += blockDim.x) {
+        const int64_t idx = w.a0 + k;
+        const bool in = idx >= 0 && idx < a.hm.n_in;
+        sm.hb[0][k] = in ? hp[idx] : 0.0;
+        sm.hb[1][k] = in ? hc[idx] : 0.0;
     }
-}
-
-// Wait until window b is staged (bounded for bulk copies).  Synchronises the
-// block.  False (for every thread) if the wait timed out: the status word
-// is flagged after a second bounded wait for the copy to land, and the block
-// must stop.
-template <bool MIXED, int NB>
-__device__ bool lfa_wait(const LfaArgs& a, LfaSmem<MIXED, NB>& sm, int b, uint32_t parity)
-{
-    bool ok = true;
-    if constexpr (MIXED && NB > 1) {
-        if (sm.win[b].bulk) ok = mbar_wait_bounded(&sm.bar[b], parity);
-    }
-    if (__syncthreads_or(ok ? 0 : 1)) {
-        if constexpr (MIXED && NB > 1) {
-            if (threadIdx.x == 0) flag_timeout(a.status);
-            if (sm.win[b].bulk) mbar_wait_bounded(&sm.bar[b], parity);
-        }
-        return false;
-    }
-    return true;
-}
-
-// hdot of window b (5-point central stencil on the staged h, zero outside the
-// h grid).  Synchronises the block at the end.
-template <bool MIXED, int NB>
-__device__ void lfa_hdot(const LfaArgs& a, LfaSmem<MIXED, NB>& sm, int b)
-{
-    using Real = typename std::conditional<MIXED, float, double>::type;
-    using Real2 = typename PairT<Real>::T;
-    const LfaWin& w = sm.win[b];
-    Real inv12dt;
-    if constexpr (MIXED) inv12dt = a.inv12dtf;
-    else inv12dt = 1.0 / (12.0 * a.hm.dt_in);
-    const int off = (int)(w.wlo - 2 - w.a0);
-    const Real* P = sm.hb[b][0] + off;
-    const Real* C = sm.hb[b][1] + off;
+    __syncthreads();
+    const double inv12dt = 1.0 / (12.0 * a.hm.dt_in);
+    const double* P = sm.hb[0];
+    const double* C = sm.hb[1];
     for (int k = threadIdx.x; k < w.wlen; k += blockDim.x) {
         const int64_t idx = w.wlo + k;
         const bool in = (idx >= 0 && idx < a.hm.n_in);
-        Real2 d;
-        d.x = in ? ((P[k + 3] - P[k + 1]) * Real(8) - (P[k + 4] - P[k])) * inv12dt : Real(0);
-        d.y = in ? ((C[k + 3] - C[k + 1]) * Real(8) - (C[k + 4] - C[k])) * inv12dt : Real(0);
+        double2 d;
+        d.x = in ? ((P[k + 3] - P[k + 1]) * 8.0 - (P[k + 4] - P[k])) * inv12dt : 0.0;
+        d.y = in ? ((C[k + 3] - C[k + 1]) * 8.0 - (C[k + 4] - C[k])) * inv12dt : 0.0;
         sm.dw[k] = d;
     }
     __syncthreads();
@@ -520,187 +446,139 @@ __device__ __forceinline__ float lfa_z_mixed(const LfaArgs& a, const SM& sm, con
     return fmaf(Fp, dp, Fc * dc);
 }
 
-// z values of the tile starting at i0 (window b staged, hdot in sm.dw): the
-// tile and its 2-sample halo, or with reuse_halo only the kTile new values
-// per series (the previous tile's last four values are this tile's leading
-// halo, copied by the caller).  Synchronises the block at the end.
-template <bool MIXED, int NB>
-__device__ void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MIXED, NB>& sm, int b, bool reuse_halo)
+// Mixed form, window staged: z of series c at two samples of the sub-block
+// (block coordinates u.x, u.y; own positions jp + fp), the Lagrange weights of
+// both formed together (lagrange32_dot2_pair).  Same arithmetic per sample as
+// lfa_z_mixed<1>.  ADJ: the samples are adjacent, and where every lane's
+// two stencils start one node apart (the common case on a unit-ratio grid)
+// the warp reads the 33 values once for both.  Every lane of the warp must
+// call it.
+template <bool ADJ, class SM>
+__device__ __forceinline__ float2 lfa_z_mixed_pair(const SM& sm, const LfaWin& W, int c, float2 u, int2 jp,
+                                                   float2 fp)
 {
-    using Real = typename std::conditional<MIXED, float, double>::type;
-    const Real* __restrict__ hp = (const Real*)a.hp;
-    const Real* __restrict__ hc = (const Real*)a.hc;
+    const float4* rp = reinterpret_cast<const float4*>(&sm.ser[c]);
+    const float4 r0 = rp[0];   // f, d1, d2, d3
+    const float Da = u.x * fmaf(u.x, fmaf(u.x, r0.w, r0.z), r0.y);
+    const float Db = u.y * fmaf(u.y, fmaf(u.y, r0.w, r0.z), r0.y);
+    const float va = fmaf(-Da, sm.inv_dt, fp.x + r0.x);
+    const float vb = fmaf(-Db, sm.inv_dt, fp.y + r0.x);
+    const float fa = floorf(va), fb = floorf(vb);
+    const int ba = min(max(W.jrel[c] + jp.x + (int)fa, 0), W.wlen - 32);
+    const int bb = min(max(W.jrel[c] + jp.y + (int)fb, 0), W.wlen - 32);
+    float2 ha, hb;
+    if (ADJ && __all_sync(0xffffffffu, bb == ba + 1))
+        lagrange32_dot2_adjacent(make_float2(va - fa, vb - fb), sm.dw + ba, ha, hb);
+    else
+        lagrange32_dot2_pair(make_float2(va - fa, vb - fb), sm.dw + ba, sm.dw + bb, ha, hb);
+    const float4 rp1 = rp[1], rp2 = rp[2];
+    const float Fpa = fmaf(u.x, fmaf(u.x, fmaf(u.x, rp1.w, rp1.z), rp1.y), rp1.x);
+    const float Fca = fmaf(u.x, fmaf(u.x, fmaf(u.x, rp2.w, rp2.z), rp2.y), rp2.x);
+    const float Fpb = fmaf(u.y, fmaf(u.y, fmaf(u.y, rp1.w, rp1.z), rp1.y), rp1.x);
+    const float Fcb = fmaf(u.y, fmaf(u.y, fmaf(u.y, rp2.w, rp2.z), rp2.y), rp2.x);
+    return make_float2(fmaf(Fpa, ha.x, Fca * ha.y), fmaf(Fpb, hb.x, Fcb * hb.y));
+}
+
+// FP64 form: z values of the tile starting at i0 and its 2-sample halo (hdot
+// in sm.dw).  Synchronises the block at the end.
+__device__ inline void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem64& sm)
+{
+    const double* __restrict__ hp = (const double*)a.hp;
+    const double* __restrict__ hc = (const double*)a.hc;
     const TileGeo& g = sm.g;
-    const LfaWin& W = sm.win[b];
-    const int64_t wlo = W.wlo;
-    const int wlen = W.wlen;
+    const int64_t wlo = sm.win.wlo;
+    const int wlen = sm.win.wlen;
     const double half = 0.5 * a.tab.S;
     const double u_per_s = 1.0 / (a.dt_out * half);
-    const int t = threadIdx.x;
     const bool equal = (a.kind == LISA_LFA_EQUAL);
-    const int dmt = (int)(i0 - ic);   // block offset of the tile's first sample
-    Real inv12dt;
-    if constexpr (MIXED) inv12dt = a.inv12dtf;
-    else inv12dt = 1.0 / (12.0 * a.hm.dt_in);
-    Real c2, s2, ku[3], kv[3];
-    if constexpr (MIXED) {
-        c2 = a.sky.c2f; s2 = a.sky.s2f;
-        for (int q = 0; q < 3; ++q) { ku[q] = a.sky.uf[q]; kv[q] = a.sky.vf[q]; }
-    } else {
-        c2 = a.sky.c2p; s2 = a.sky.s2p;
-        for (int q = 0; q < 3; ++q) { ku[q] = a.sky.u[q]; kv[q] = a.sky.v[q]; }
-    }
-    // After a reused halo every series has exactly kTile new values (iteration
-    // c covers series c for the whole block).  On interior tiles no sample of
-    // the tile or its halo is off the grid.
+    const double inv12dt = 1.0 / (12.0 * a.hm.dt_in);
+    const double c2 = a.sky.c2p, s2 = a.sky.s2p;
+    const double* ku = a.sky.u;
+    const double* kv = a.sky.v;
+    // On interior tiles no sample of the tile or its halo is off the grid.
     const bool interior = i0 - 2 >= 0 && i0 + kTile + 2 <= a.nout;
-    if constexpr (MIXED) {
-        // One thread per sample (blockDim.x == kTile): the sample's position
-        // is shared by the six series, which are unrolled.  Off-grid samples
-        // (edge tiles only) are computed on clamped indices and masked.
-        if (!reuse_halo && t < 24) {   // leading halo, samples i0-2 .. i0+1
-            const int c = t >> 2, o = t & 3;
-            const int64_t m = i0 - 2 + o;
-            float u, fp;
-            int jp;
-            lfa_sample_pos(a, sm.inv_half, dmt - 2 + o, u, jp, fp);
-            const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp);
-            sm.zs[c][o] = (interior || (m >= 0 && m < a.nout)) ? z : 0.f;
-        }
-        {
-            const int o = 4 + t;
-            const int64_t m = i0 + 2 + t;
-            const bool valid = interior || (m >= 0 && m < a.nout);
-            float u, fp;
-            int jp;
-            lfa_sample_pos(a, sm.inv_half, dmt + 2 + t, u, jp, fp);
-#pragma unroll kLfaUnroll
-            for (int c = 0; c < 6; ++c) {
-                const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp);
-                sm.zs[c][o] = valid ? z : 0.f;
-            }
-        }
-    } else {
-    const int per = reuse_halo ? kTile : kZW;
-    for (int w = t; w < 6 * per; w += blockDim.x) {
-        // constant divisors: kTile values per series after a reused halo, else kZW
-        const int c = reuse_halo ? w / kTile : w / kZW;
-        const int o = reuse_halo ? 4 + w % kTile : w % kZW;
+    for (int w = threadIdx.x; w < 6 * kZW; w += blockDim.x) {
+        const int c = w / kZW, o = w % kZW;
         const int64_t m = i0 - 2 + o;
-        Real zval = Real(0);
+        double zval = 0.0;
         if (interior || (m >= 0 && m < a.nout)) {
-            {
-                const int ch = c >> 1, which = c & 1;
-                const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
-                const double u = (double)(m - ic) / half;
-                const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
-                const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
-                const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
-                const double up = u - sh * u_per_s;
-                const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
-                const double dtau = sh + 0.5 * Tl
-                                  + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
-                double n3[3];
-                for (int q = 0; q < 3; ++q) n3[q] = tg_eval(g, kQN + 3 * l + q, up);
-                int64_t j;
-                double eps;
-                split_f64(a.hm, m, dtau, j, eps);
-                const double un = ku[0] * n3[0] + ku[1] * n3[1] + ku[2] * n3[2];
-                const double vn = kv[0] * n3[0] + kv[1] * n3[1] + kv[2] * n3[2];
-                const double xp = un * un - vn * vn, xc = 2.0 * un * vn;
-                double dp, dc;
-                bool ok;
-                dp = interp_pair_w<double>(sm.dw, wlo, wlen, nullptr, j, eps, dc, ok);
-                if (!ok) interp_hdot_global<double>(hp, hc, a.hm.n_in, j, eps, inv12dt, dp, dc);
-                zval = -0.5 * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
-            }
+            const int ch = c >> 1, which = c & 1;
+            const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
+            const double u = (double)(m - ic) / half;
+            const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
+            const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
+            const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
+            const double up = u - sh * u_per_s;
+            const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
+            const double dtau = sh + 0.5 * Tl
+                              + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
+            double n3[3];
+            for (int q = 0; q < 3; ++q) n3[q] = tg_eval(g, kQN + 3 * l + q, up);
+            int64_t j;
+            double eps;
+            split_f64(a.hm, m, dtau, j, eps);
+            const double un = ku[0] * n3[0] + ku[1] * n3[1] + ku[2] * n3[2];
+            const double vn = kv[0] * n3[0] + kv[1] * n3[1] + kv[2] * n3[2];
+            const double xp = un * un - vn * vn, xc = 2.0 * un * vn;
+            double dp, dc;
+            bool ok;
+            dp = interp_pair_w<double>(sm.dw, wlo, wlen, nullptr, j, eps, dc, ok);
+            if (!ok) interp_hdot_global<double>(hp, hc, a.hm.n_in, j, eps, inv12dt, dp, dc);
+            zval = -0.5 * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
         }
         sm.zs[c][o] = zval;
     }
-    }
     __syncthreads();
 }
 
-// Channels of sample i0 + t from the z values in shared memory (and z stored
-// if requested).
-template <bool MIXED, int NB>
-__device__ void lfa_channels(const LfaArgs& a, int64_t i0, int64_t ic, const LfaSmem<MIXED, NB>& sm,
-                             typename std::conditional<MIXED, float, double>::type (&X)[3])
+// FP64 form: channels of sample i0 + t from the z values in shared memory (and
+// z stored if requested).
+__device__ inline void lfa_channels(const LfaArgs& a, int64_t i0, int64_t ic, const LfaSmem64& sm, double (&X)[3])
 {
-    using Real = typename std::conditional<MIXED, float, double>::type;
     const TileGeo& g = sm.g;
     const int t = threadIdx.x;
     const bool equal = (a.kind == LISA_LFA_EQUAL);
     const double half = 0.5 * a.tab.S;
-    const int dmt = (int)(i0 - ic);
     const int64_t i = i0 + t;
     if (a.z && i >= a.i_begin && i < a.i_end) {
-        Real* zo = (Real*)a.z;
+        double* zo = (double*)a.z;
         for (int c = 0; c < 6; ++c) zo[(int64_t)c * a.nout + i] = sm.zs[c][t + 2];
     }
-    Real k1, k2;   // 1/(12 dt), 1/(12 dt^2)
-    if constexpr (MIXED) {
-        k1 = a.c1f;
-        k2 = a.c2f;
-    } else {
-        k1 = 1.0 / (12.0 * a.dt_out);
-        k2 = k1 / a.dt_out;
-    }
+    const double k1 = 1.0 / (12.0 * a.dt_out);   // 1/(12 dt)
+    const double k2 = k1 / a.dt_out;             // 1/(12 dt^2)
+    const double u = (double)(i - ic) / half;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-        Real Ta, Tb;
-        if constexpr (!MIXED) {
-            const double u = (double)(i - ic) / half;
-            Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
-            Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
-        } else {
-            const float u = (float)(dmt + t) * sm.inv_half;
-            Ta = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 0)] + sm.cu[kQT + lfa_arm(ch, 0)](u);
-            Tb = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 1)] + sm.cu[kQT + lfa_arm(ch, 1)](u);
-        }
-        const Real* za = sm.zs[2 * ch] + t;       // za[0..4] = z at i-2..i+2
-        const Real* zb = sm.zs[2 * ch + 1] + t;
+        const double Ta = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 0), u);
+        const double Tb = equal ? a.Lc : tg_eval(g, kQT + lfa_arm(ch, 1), u);
+        const double* za = sm.zs[2 * ch] + t;       // za[0..4] = z at i-2..i+2
+        const double* zb = sm.zs[2 * ch + 1] + t;
         if (a.gen == LISA_TDI20) {
             // 5-point second derivative as (14 d2_0 - d2_-1 - d2_1)/12, d2 from first differences
-            auto d2 = [&](const Real* z) {
-                const Real e0 = z[1] - z[0], e1 = z[2] - z[1], e2 = z[3] - z[2], e3 = z[4] - z[3];
-                const Real m1 = e1 - e0, c0 = e2 - e1, p1 = e3 - e2;
-                return (Real(14) * c0 - m1 - p1) * k2;
+            auto d2 = [&](const double* z) {
+                const double e0 = z[1] - z[0], e1 = z[2] - z[1], e2 = z[3] - z[2], e3 = z[4] - z[3];
+                const double m1 = e1 - e0, c0 = e2 - e1, p1 = e3 - e2;
+                return (14.0 * c0 - m1 - p1) * k2;
             };
-            X[ch] = Real(8) * (Ta + Tb) * (Ta * d2(za) - Tb * d2(zb));
+            X[ch] = 8.0 * (Ta + Tb) * (Ta * d2(za) - Tb * d2(zb));
         } else {
-            auto d1 = [&](const Real* z) { return ((z[3] - z[1]) * Real(8) - (z[4] - z[0])) * k1; };
-            X[ch] = Real(4) * (Ta * d1(za) - Tb * d1(zb));
+            auto d1 = [&](const double* z) { return ((z[3] - z[1]) * 8.0 - (z[4] - z[0])) * k1; };
+            X[ch] = 4.0 * (Ta * d1(za) - Tb * d1(zb));
         }
     }
 }
 
-// One tile [i0, i0 + kTile) after lfa_tile_prologue at the centre ic, staged
-// with plain loads (one buffer): on return thread t holds X, Y, Z of sample
-// i0 + t (before AET, blend and store) and z has been written if requested.
-// Every thread of the block must call it; it does not return early, so it
-// can run inside a persistent loop.
-template <bool MIXED, int NB>
-__device__ void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem<MIXED, NB>& sm,
-                              typename std::conditional<MIXED, float, double>::type (&X)[3])
+// FP64 form: one tile [i0, i0 + kTile) after lfa_tile_prologue at the centre
+// ic: on return thread t holds X, Y, Z of sample i0 + t (before AET, blend
+// and store) and z has been written if requested.  Every thread of the
+// block must call it.
+__device__ inline void lfa_tile_body(const LfaArgs& a, int64_t i0, int64_t ic, LfaSmem64& sm, double (&X)[3])
 {
     __syncthreads();   // the previous tile's readers of the shared buffers are done
-    lfa_window<MIXED, NB>(a, i0, ic, sm, 0);
-    lfa_stage<MIXED, NB>(a, sm, 0);
-    __syncthreads();
-    lfa_hdot<MIXED, NB>(a, sm, 0);
-    lfa_zvalues<MIXED, NB>(a, i0, ic, sm, 0, false);
-    lfa_channels<MIXED, NB>(a, i0, ic, sm, X);
-}
-
-// Prologue and body of one tile around its own centre.
-template <bool MIXED, int NB>
-__device__ __forceinline__ void lfa_tile_compute(const LfaArgs& a, int64_t i0, LfaSmem<MIXED, NB>& sm,
-                                                 typename std::conditional<MIXED, float, double>::type (&X)[3])
-{
-    const int64_t ic = i0 + kTile / 2;
-    lfa_tile_prologue<MIXED>(a, ic, sm);
-    lfa_tile_body<MIXED, NB>(a, i0, ic, sm, X);
+    lfa_window(a, i0, ic, sm);
+    lfa_stage_hdot(a, sm);
+    lfa_zvalues(a, i0, ic, sm);
+    lfa_channels(a, i0, ic, sm, X);
 }
 
 // Tiles per CTA (mixed form): the FP64 prologue (segment polynomials shifted
@@ -858,6 +736,28 @@ static __device__ void lfa2_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lf
         const float z = lfa_z_mixed(a, sm, W, c, u, jp, fp);
         sm.zs[c][o] = (interior || (m >= 0 && m < a.nout)) ? z : 0.f;
     }
+#if LISA_LFA_PAIR
+    if (W.wlen > 0) {
+        // window staged: the thread's two samples together
+        // LISA_LFA_PAIR 2: adjacent samples 2t, 2t + 1; 1: samples t, kTile + t
+        const int o0 = LISA_LFA_PAIR == 2 ? 4 + 2 * t : 4 + t;
+        const int o1 = LISA_LFA_PAIR == 2 ? o0 + 1 : 4 + kTile + t;
+        const bool v0 = interior || (i0 - 2 + o0 >= 0 && i0 - 2 + o0 < a.nout);
+        const bool v1 = interior || (i0 - 2 + o1 >= 0 && i0 - 2 + o1 < a.nout);
+        float2 u, fp;
+        int2 jp;
+        lfa_sample_pos(a, sm.inv_half, dmt - 2 + o0, u.x, jp.x, fp.x);
+        lfa_sample_pos(a, sm.inv_half, dmt - 2 + o1, u.y, jp.y, fp.y);
+#pragma unroll kLfaUnroll
+        for (int c = 0; c < 6; ++c) {
+            const float2 z = lfa_z_mixed_pair<LISA_LFA_PAIR == 2>(sm, W, c, u, jp, fp);
+            sm.zs[c][o0] = v0 ? z.x : 0.f;
+            sm.zs[c][o1] = v1 ? z.y : 0.f;
+        }
+        __syncthreads();
+        return;
+    }
+#endif
     // the staged / global choice is uniform over the block: one loop each
     auto run = [&](auto staged) {
         constexpr int S = decltype(staged)::value;

@@ -56,10 +56,13 @@ __host__ __device__ inline int seg_samples(double dt)
 // y_231, y_1-32); 0-based spacecraft of sender and receiver.
 __host__ __device__ constexpr int link_sender(int li) { return li == 0 ? 2 : li == 1 ? 1 : li == 2 ? 0 : li == 3 ? 2 : li == 4 ? 1 : 0; }
 __host__ __device__ constexpr int link_receiver(int li) { return li == 0 ? 1 : li == 1 ? 2 : li == 2 ? 2 : li == 3 ? 0 : li == 4 ? 0 : 1; }
-// Cyclic relabelling |l| -> |l| mod 3 + 1 applied `times` times (Y, Z from X).
+// Cyclic relabelling |l| -> |l| mod 3 + 1 applied `times` (>= 0) times (Y, Z
+// from X): the arm index li >> 1 advances by `times` modulo 3, the direction
+// bit li & 1 is kept.  Closed form, so that it inlines (a recursive form is
+// compiled as an out-of-line call).
 __host__ __device__ constexpr int link_cycle(int li, int times)
 {
-    return times == 0 ? li : link_cycle((((li >> 1) + 1) % 3) * 2 + (li & 1), times - 1);
+    return (((li >> 1) + times) % 3) * 2 + (li & 1);
 }
 
 // Orbit parameters as the kernels use them (derived constants included).
@@ -199,6 +202,101 @@ __device__ __forceinline__ void lagrange32_dot2(float eps, const float2* __restr
     });
     ox = ax;
     oy = ay;
+}
+
+// Two samples at once: the weights of eps.x and eps.y are formed as in
+// lagrange32_paired_f32 with packed FP32 pair instructions (one instruction
+// for both samples, each lane rounded as the scalar operation), and each
+// sample's weights are applied to its own interleaved pair series (va for
+// eps.x, vb for eps.y).  The mirrored factor -s - k - 1/2 enters as
+// -(s + k + 1/2), its sign taken by the tap's fused multiply-add.
+__device__ __forceinline__ void lagrange32_dot2_pair(float2 eps, const float2* __restrict__ va,
+                                                     const float2* __restrict__ vb, float2& oa, float2& ob)
+{
+    const float2 s = __fadd2_rn(eps, make_float2(-0.5f, -0.5f));
+    const float2 sig = __fmul2_rn(s, s);
+    float2 e[16];
+    e[0] = __fmul2_rn(eps, __fadd2_rn(eps, make_float2(-1.f, -1.f)));
+#pragma unroll
+    for (int k = 1; k < 16; ++k) {
+        const float c2 = float((k + 0.5) * (k + 0.5));
+        e[k] = __fadd2_rn(sig, make_float2(-c2, -c2));
+    }
+    float2 S[16];   // S[k] = prod_{j>k} e_j
+    S[15] = make_float2(1.f, 1.f);
+#pragma unroll
+    for (int k = 14; k >= 0; --k) S[k] = __fmul2_rn(S[k + 1], e[k + 1]);
+    float2 P = make_float2(1.f, 1.f);   // prod_{j<k} e_j
+    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float K = float(lagrange32_k(15 - k));
+        const float c = float(k + 0.5);
+        const float2 Q = __fmul2_rn(__fmul2_rn(P, S[k]), make_float2(K, K));
+        const float2 wl = __fmul2_rn(__fadd2_rn(s, make_float2(-c, -c)), Q);   // w_{15-k}
+        const float2 wr = __fmul2_rn(__fadd2_rn(s, make_float2(c, c)), Q);     // -w_{16+k}
+        const float2 al = va[15 - k], ar = va[16 + k];
+        const float2 bl = vb[15 - k], br = vb[16 + k];
+        ax = fmaf(wl.x, al.x, ax);
+        ay = fmaf(wl.x, al.y, ay);
+        ax = fmaf(-wr.x, ar.x, ax);
+        ay = fmaf(-wr.x, ar.y, ay);
+        bx = fmaf(wl.y, bl.x, bx);
+        by = fmaf(wl.y, bl.y, by);
+        bx = fmaf(-wr.y, br.x, bx);
+        by = fmaf(-wr.y, br.y, by);
+        if (k < 15) P = __fmul2_rn(P, e[k]);
+    }
+    oa = make_float2(ax, ay);
+    ob = make_float2(bx, by);
+}
+
+// Two adjacent samples whose stencils start one node apart (sample b's node p
+// is sample a's node p + 1): weights as in lagrange32_dot2_pair, and the 33
+// distinct values of v[0..32] are read once, each feeding both sums.
+__device__ __forceinline__ void lagrange32_dot2_adjacent(float2 eps, const float2* __restrict__ v, float2& oa,
+                                                         float2& ob)
+{
+    const float2 s = __fadd2_rn(eps, make_float2(-0.5f, -0.5f));
+    const float2 sig = __fmul2_rn(s, s);
+    float2 e[16];
+    e[0] = __fmul2_rn(eps, __fadd2_rn(eps, make_float2(-1.f, -1.f)));
+#pragma unroll
+    for (int k = 1; k < 16; ++k) {
+        const float c2 = float((k + 0.5) * (k + 0.5));
+        e[k] = __fadd2_rn(sig, make_float2(-c2, -c2));
+    }
+    float2 S[16];
+    S[15] = make_float2(1.f, 1.f);
+#pragma unroll
+    for (int k = 14; k >= 0; --k) S[k] = __fmul2_rn(S[k + 1], e[k + 1]);
+    float2 P = make_float2(1.f, 1.f);
+    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+    float2 pl = v[16], pr = pl;   // v[16 - k] and v[16 + k] of the step before
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float K = float(lagrange32_k(15 - k));
+        const float c = float(k + 0.5);
+        const float2 Q = __fmul2_rn(__fmul2_rn(P, S[k]), make_float2(K, K));
+        const float2 wl = __fmul2_rn(__fadd2_rn(s, make_float2(-c, -c)), Q);   // w_{15-k}
+        const float2 wr = __fmul2_rn(__fadd2_rn(s, make_float2(c, c)), Q);     // -w_{16+k}
+        const float2 l = v[15 - k], r = v[17 + k];
+        // sample a: nodes 15 - k, 16 + k = v[15 - k], v[16 + k]
+        ax = fmaf(wl.x, l.x, ax);
+        ay = fmaf(wl.x, l.y, ay);
+        ax = fmaf(-wr.x, pr.x, ax);
+        ay = fmaf(-wr.x, pr.y, ay);
+        // sample b: nodes 15 - k, 16 + k = v[16 - k], v[17 + k]
+        bx = fmaf(wl.y, pl.x, bx);
+        by = fmaf(wl.y, pl.y, by);
+        bx = fmaf(-wr.y, r.x, bx);
+        by = fmaf(-wr.y, r.y, by);
+        pl = l;
+        pr = r;
+        if (k < 15) P = __fmul2_rn(P, e[k]);
+    }
+    oa = make_float2(ax, ay);
+    ob = make_float2(bx, by);
 }
 
 // Monomial -> re-expansion around xc: b_m = sum_{p>=m} C(p,m) a_p xc^(p-m).
