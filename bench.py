@@ -591,6 +591,7 @@ def run_ours(args):
             keep = args.forms.split(",")
             cases = {k: v for k, v in cases.items() if k in keep}
         for name, fn in cases.items():
+            torch.cuda.nvtx.range_push("form_" + name)   # range for targeted profiler captures
             fn()
             torch.cuda.synchronize()
             reps = 3
@@ -603,6 +604,7 @@ def run_ours(args):
                 b.record(stream)
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
+            torch.cuda.nvtx.range_pop()
             best = float(np.median(ms))
             forms[name] = {"ms": round(best, 4), "samples_per_s": n / (best / 1e3)}
         del hp64, hc64, out64

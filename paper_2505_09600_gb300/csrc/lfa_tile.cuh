@@ -15,11 +15,11 @@ constexpr int kWinH = kTile + 384;
 constexpr int kZW = kTile + 4;
 constexpr int kWinP = kWinH + 8;   // planar h buffers: room for 16-byte alignment of the copy
 #ifndef LISA_LFA_UNROLL
-#define LISA_LFA_UNROLL 6
+#define LISA_LFA_UNROLL 2
 #endif
 constexpr int kLfaUnroll = LISA_LFA_UNROLL;   // series per unrolled step of the mixed z loop
 #ifndef LISA_LFA_PAIR
-#define LISA_LFA_PAIR 0   // staged z loop: 1 = a thread's two samples share packed weight instructions, 2 = adjacent samples also share the taps
+#define LISA_LFA_PAIR 1   // staged z loop: 1 = a thread's two samples share packed weight instructions, 2 = adjacent samples also share the taps
 #endif
 
 template <typename Real>
