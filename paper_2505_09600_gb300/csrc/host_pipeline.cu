@@ -18,10 +18,100 @@
 // after the last read-back.
 #include <math.h>
 
+#include <mutex>
+#include <vector>
+
 #include "lisa_common.cuh"
 #include "lisa_internal.cuh"
 
 using namespace lisa;
+
+#ifndef LISA_HOST_CHUNKS
+#define LISA_HOST_CHUNKS 8
+#endif
+#ifndef LISA_HOST_EDGE
+#define LISA_HOST_EDGE 1
+#endif
+
+namespace {
+
+constexpr int kMaxChunks = 16;
+constexpr int kChunks = LISA_HOST_CHUNKS;
+static_assert(kChunks >= 1 && kChunks <= kMaxChunks, "LISA_HOST_CHUNKS out of range");
+
+// Streams and events of one pipeline.  They live for the process and are
+// reused by later calls on the same device (creating three streams and 2K+2
+// events per call cost tens of microseconds of host time before the first
+// copy could be queued).  A set is held by one call at a time; work a
+// previous call left queued on its streams runs before the next call's.
+struct PipeRes {
+    int device = -1;
+    bool busy = false;
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_cmp2 = nullptr;
+    cudaEvent_t e_ready = nullptr, e_tab = nullptr, e_done = nullptr;
+    cudaEvent_t e_in[kMaxChunks] = {}, e_cmp[kMaxChunks] = {};
+};
+
+std::mutex g_pipe_mu;
+std::vector<PipeRes*> g_pipes;
+
+void pipe_destroy(PipeRes* p)
+{
+    for (int c = 0; c < kMaxChunks; ++c) {
+        if (p->e_in[c]) cudaEventDestroy(p->e_in[c]);
+        if (p->e_cmp[c]) cudaEventDestroy(p->e_cmp[c]);
+    }
+    if (p->e_ready) cudaEventDestroy(p->e_ready);
+    if (p->e_tab) cudaEventDestroy(p->e_tab);
+    if (p->e_done) cudaEventDestroy(p->e_done);
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
+    if (p->s_cmp2) cudaStreamDestroy(p->s_cmp2);
+    delete p;
+}
+
+PipeRes* pipe_acquire(int& rc)
+{
+    int dev = 0;
+    rc = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pipe_mu);
+        for (PipeRes* p : g_pipes)
+            if (!p->busy && p->device == dev) {
+                p->busy = true;
+                return p;
+            }
+    }
+    PipeRes* p = new PipeRes;
+    p->device = dev;
+    rc = cuda_status(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!rc) rc = cuda_status(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!rc) rc = cuda_status(cudaStreamCreateWithFlags(&p->s_cmp2, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&p->e_ready, cudaEventDisableTiming), "cudaEventCreate");
+    if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&p->e_tab, cudaEventDisableTiming), "cudaEventCreate");
+    if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&p->e_done, cudaEventDisableTiming), "cudaEventCreate");
+    for (int c = 0; c < kMaxChunks && !rc; ++c) {
+        rc = cuda_status(cudaEventCreateWithFlags(&p->e_in[c], cudaEventDisableTiming), "cudaEventCreate");
+        if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&p->e_cmp[c], cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (rc) {
+        pipe_destroy(p);
+        return nullptr;
+    }
+    p->busy = true;
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    g_pipes.push_back(p);
+    return p;
+}
+
+void pipe_release(PipeRes* p)
+{
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    p->busy = false;
+}
+
+}  // namespace
 
 extern "C" int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid grid,
                                          const void* hp_host, const void* hc_host, int precision, int tdi_gen,
@@ -45,9 +135,6 @@ extern "C" int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky
 
     cudaStream_t st = (cudaStream_t)stream;
     Scratch sc(st);
-    SegTable tab;
-    LISA_TRY(make_table(orbit, grid, sc, tab, st));
-    const SkyDev skyd = make_sky_dev(*sky);
     char* hp = (char*)sc.alloc((size_t)n * rs);
     char* hc = (char*)sc.alloc((size_t)n * rs);
     char* xyz = (char*)sc.alloc(3 * (size_t)n * rs);
@@ -56,11 +143,26 @@ extern "C" int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky
     for (int q = 0; q < 2 && iF < n; ++q) ybuf[q] = (char*)sc.alloc(6 * (size_t)n * rs);
     if (!hp || !hc || !xyz || (iF < n && (!ybuf[0] || !ybuf[1]))) return sc.status();
 
-    // chunks: whole LFA tile groups, at most 8
+    // chunks: whole LFA tile groups, at most kChunks.  With LISA_HOST_EDGE
+    // the first and last chunks are half as long as the others: the first
+    // copy-in and the last read-back are the parts of the pipeline that
+    // nothing overlaps.
     const int64_t gt = (int64_t)lfa_group_host(grid.dt) * kTile;
     const int64_t groups = (n + gt - 1) / gt;
-    const int K = (int)(groups < 8 ? groups : 8);
-    const int64_t C = (groups + K - 1) / K * gt;
+    const int K = (int)(groups < kChunks ? groups : kChunks);
+    int64_t cb[kMaxChunks + 1];   // chunk c = samples [cb[c], cb[c + 1])
+    {
+        const int edge = (LISA_HOST_EDGE && K >= 3) ? 1 : 2;
+        const int64_t wsum = 2 * (int64_t)K - 2 * (2 - edge);
+        int64_t acc = 0;
+        cb[0] = 0;
+        for (int c = 0; c < K; ++c) {
+            acc += (c == 0 || c == K - 1) ? edge : 2;
+            const int64_t g = groups * acc / wsum;
+            cb[c + 1] = g * gt < n ? g * gt : n;
+        }
+        cb[K] = n;
+    }
     // samples the retarded times reach ahead of (and behind) an output sample:
     // |k.R/c| <= 1.01 AU/c, the light times, the stencils and window margins
     const double Tmax = max_light_time(orbit, grid);
@@ -71,28 +173,30 @@ extern "C" int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky
     // chunks alternate between two compute streams (the caller's and an
     // internal one), so that one chunk's kernels fill the SMs left idle by
     // the other's tail
-    cudaStream_t s_in = nullptr, s_out = nullptr, s_cmp2 = nullptr;
-    cudaEvent_t e_ready = nullptr, e_in[8] = {}, e_cmp[8] = {};
-    int rc = cuda_status(cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking), "cudaStreamCreate");
-    if (!rc) rc = cuda_status(cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking), "cudaStreamCreate");
-    if (!rc) rc = cuda_status(cudaStreamCreateWithFlags(&s_cmp2, cudaStreamNonBlocking), "cudaStreamCreate");
-    if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&e_ready, cudaEventDisableTiming), "cudaEventCreate");
-    for (int c = 0; c < K && !rc; ++c) {
-        rc = cuda_status(cudaEventCreateWithFlags(&e_in[c], cudaEventDisableTiming), "cudaEventCreate");
-        if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&e_cmp[c], cudaEventDisableTiming), "cudaEventCreate");
-    }
-    // the copy streams start after the allocations on the caller's stream
-    if (!rc) rc = cuda_status(cudaEventRecord(e_ready, st), "cudaEventRecord");
+    int rc = 0;
+    PipeRes* R = pipe_acquire(rc);
+    if (!R) return rc;
+    cudaStream_t s_in = R->s_in, s_out = R->s_out, s_cmp2 = R->s_cmp2;
+    cudaEvent_t e_ready = R->e_ready;
+    cudaEvent_t* e_in = R->e_in;
+    cudaEvent_t* e_cmp = R->e_cmp;
+    // the copy streams start after the allocations on the caller's stream;
+    // the first input copy overlaps the orbit table, which the second compute
+    // stream waits for
+    rc = cuda_status(cudaEventRecord(e_ready, st), "cudaEventRecord");
     if (!rc) rc = cuda_status(cudaStreamWaitEvent(s_in, e_ready, 0), "cudaStreamWaitEvent");
     if (!rc) rc = cuda_status(cudaStreamWaitEvent(s_out, e_ready, 0), "cudaStreamWaitEvent");
-    if (!rc) rc = cuda_status(cudaStreamWaitEvent(s_cmp2, e_ready, 0), "cudaStreamWaitEvent");
+    SegTable tab;
+    if (!rc) rc = make_table(orbit, grid, sc, tab, st);
+    const SkyDev skyd = make_sky_dev(*sky);
+    if (!rc) rc = cuda_status(cudaEventRecord(R->e_tab, st), "cudaEventRecord");
+    if (!rc) rc = cuda_status(cudaStreamWaitEvent(s_cmp2, R->e_tab, 0), "cudaStreamWaitEvent");
     const cudaStream_t cs[2] = {st, s_cmp2};
 
     int64_t h_done = 0;
     for (int c = 0; c < K && !rc; ++c) {
-        const int64_t a = (int64_t)c * C;
-        const int64_t b = a + C < n ? a + C : n;
-        if (a >= b) break;
+        const int64_t a = cb[c], b = cb[c + 1];
+        if (a >= b) continue;
         // copy-in: h up to b + halo
         int64_t h_to = b + halo < n ? b + halo : n;
         if (c == K - 1) h_to = n;
@@ -142,8 +246,8 @@ extern "C" int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky
                              "cudaMemcpy2DAsync(xyz)");
     }
     // the caller's stream (and the scratch release on it) waits for the last read-back
-    if (!rc) rc = cuda_status(cudaEventRecord(e_ready, s_out), "cudaEventRecord");
-    if (!rc) rc = cuda_status(cudaStreamWaitEvent(st, e_ready, 0), "cudaStreamWaitEvent");
+    if (!rc) rc = cuda_status(cudaEventRecord(R->e_done, s_out), "cudaEventRecord");
+    if (!rc) rc = cuda_status(cudaStreamWaitEvent(st, R->e_done, 0), "cudaStreamWaitEvent");
     if (rc) {
         // an error after work was queued: let the queued work finish before
         // the scratch goes back to the pool
@@ -152,13 +256,6 @@ extern "C" int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky
         cudaStreamSynchronize(s_out);
         cudaStreamSynchronize(st);
     }
-    for (int c = 0; c < K; ++c) {
-        if (e_in[c]) cudaEventDestroy(e_in[c]);
-        if (e_cmp[c]) cudaEventDestroy(e_cmp[c]);
-    }
-    if (e_ready) cudaEventDestroy(e_ready);
-    if (s_in) cudaStreamDestroy(s_in);
-    if (s_out) cudaStreamDestroy(s_out);
-    if (s_cmp2) cudaStreamDestroy(s_cmp2);
+    pipe_release(R);
     return rc;
 }
