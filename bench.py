@@ -607,6 +607,28 @@ def run_ours(args):
             torch.cuda.nvtx.range_pop()
             best = float(np.median(ms))
             forms[name] = {"ms": round(best, 4), "samples_per_s": n / (best / 1e3)}
+        if "full20_f64" in cases:
+            # expansion point of the LFA link (App. B): the central point against
+            # the non-central backward / forward variants, mixed A/E/T, error
+            # against the FP64 full response on the LFA side of the switch (t <= t_H)
+            ref_aet = out64   # the full20_f64 case ran last: FP64 full response, A/E/T
+            i_h = int(math.floor((tH - src.t0) / src.dt)) + 1
+            # the first samples see the step of h at the grid start through delays of up to
+            # |k.R|/c: excluded, as in the corrector's error measure
+            m0 = int(math.ceil((1.01 * 499.0048 + 100.0 + 20.0 * src.dt) / src.dt)) + 4
+            ref_aet = ref_aet[:, m0:]
+            i_h -= m0
+            scale = ref_aet[:, :i_h].abs().max().item()
+            points = {}
+            for pname, kind in (("central", L.LFA_UNEQUAL), ("backward", L.LFA_BACKWARD), ("forward", L.LFA_FORWARD)):
+                fn = lambda: L.lisa_response_lfa(orbit, sky, src.grid, hp32, hc32, L.MIXED, 20, kind, L.AET, src.grid,
+                                                 out32)
+                best = _timed(torch, stream, flush, fn)
+                err = ((out32[:, m0:m0 + i_h].double() - ref_aet[:, :i_h]).abs().amax(dim=1) / scale).tolist()
+                points[pname] = {"ms": round(best, 4), "err_aet_vs_full_f64": err}
+            forms["lfa20_mixed_expansion_point"] = {
+                "points": points, "range": "t <= t_H (LFA side), grid start excluded (%d samples); errors / max |A,E,T| of the FP64 full response there" % m0,
+                "note": "central: Eq. tau_t_dependence; backward / forward: App. B non-central variants"}
         del hp64, hc64, out64
 
     # the headline step's output, for the oracle comparison below

@@ -85,7 +85,15 @@ enum { LISA_F64 = 0, LISA_MIXED = 1 };
 enum { LISA_TDI15 = 15, LISA_TDI20 = 20 };
 enum { LISA_XYZ = 0, LISA_AET = 1 };
 enum { LISA_FROZEN = 0, LISA_NESTED = 1 };
-enum { LISA_LFA_UNEQUAL = 0, LISA_LFA_EQUAL = 1 };
+/* LFA kind.  UNEQUAL and EQUAL expand the link around the central point
+ * tau = t - T_l/2 - k.(R_s + R_r)/(2c) (Sec. III, Eq. tau_t_dependence; EQUAL
+ * with every T_l = L/c).  BACKWARD and FORWARD are the non-central variants of
+ * App. B ("Other finite differences", Eqs. yslr_backward, yslr_forward), with
+ * unequal arms: the link's leading term -(T_l/2) Hdot is evaluated at the
+ * sender end tau_0 = t - T_l - k.R_s/c (backward, epsilon = 0) or at the
+ * receiver end tau_1 = t - k.R_r/c (forward, epsilon = 1); their truncation
+ * error is one order lower than the central point's. */
+enum { LISA_LFA_UNEQUAL = 0, LISA_LFA_EQUAL = 1, LISA_LFA_BACKWARD = 2, LISA_LFA_FORWARD = 3 };
 
 /* Version of this ABI (major*10000 + minor*100 + patch). */
 int lisa_version(void);

@@ -28,7 +28,7 @@ _lib = None
 KEPLER1, KEPLER2, STATIC = 0, 1, 2
 DELAY_LIGHTTIME, DELAY_ANALYTIC, DELAY_EQUAL, DELAY_LINEAR = 0, 1, 2, 3
 FROZEN, NESTED = 0, 1
-LFA_UNEQUAL, LFA_EQUAL = 0, 1
+LFA_UNEQUAL, LFA_EQUAL, LFA_BACKWARD, LFA_FORWARD = 0, 1, 2, 3   # central (2 kinds); App. B non-central
 C_LIGHT = 299792458.0
 AU = 1.495978707e11
 YEAR = 31557600.0

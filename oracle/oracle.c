@@ -516,7 +516,11 @@ static double og_arm(const og_orbit* o, int li, double t, int kind)
     return (kind == OG_LFA_EQUAL) ? o->L_m / OG_C : og_light_time(o, li, t);
 }
 
-/* y^LFA_l at time t' = t_i - a (S holds hdot as its series). */
+/* y^LFA_l at time t' = t_i - a (S holds hdot as its series): the leading
+ * term -(T_l/2) [xi+ hdot+ + xix hdotx] (Eq. yslr_strain_derivatives) at the
+ * expansion point tau_eps = t' - delta_s + eps (delta_s - delta_r), with
+ * delta_s = T_l + k.R_s/c and delta_r = k.R_r/c (App. B): eps = 1/2 for the
+ * central kinds (Eq. tau_t_dependence), 0 for backward, 1 for forward. */
 static double og_link_lfa_at(const og_src* S, og_grid gout, int64_t i, double a, int li, int kind)
 {
     const double tp = (gout.t0 + (double)i * gout.dt) - a;
@@ -528,7 +532,11 @@ static double og_link_lfa_at(const og_src* S, og_grid gout, int64_t i, double a,
     const double T = og_arm(S->orb, li, tp, kind);
     double xp, xc;
     og_antenna(S->u, S->v, n, &xp, &xc);
-    const double d_tau = a + 0.5 * T + 0.5 * (og_dot(S->k, Rs) + og_dot(S->k, Rr)) / OG_C;
+    const double delta_s = T + og_dot(S->k, Rs) / OG_C, delta_r = og_dot(S->k, Rr) / OG_C;
+    double d_tau;
+    if (kind == OG_LFA_BACKWARD) d_tau = a + delta_s;
+    else if (kind == OG_LFA_FORWARD) d_tau = a + delta_r;
+    else d_tau = a + 0.5 * T + 0.5 * (og_dot(S->k, Rs) + og_dot(S->k, Rr)) / OG_C;
     const double dp = og_interp_at(S->hp, S->gh, gout, i, d_tau);
     const double dc = og_interp_at(S->hc, S->gh, gout, i, d_tau);
     return -0.5 * T * (xp * (dp * S->c2p - dc * S->s2p) + xc * (dp * S->s2p + dc * S->c2p));

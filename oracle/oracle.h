@@ -15,7 +15,10 @@ typedef struct { double t0, dt; int64_t n; } og_grid;
 enum { OG_KEPLER1 = 0, OG_KEPLER2 = 1, OG_STATIC = 2 };
 enum { OG_DELAY_LIGHTTIME = 0, OG_DELAY_ANALYTIC = 1, OG_DELAY_EQUAL = 2, OG_DELAY_LINEAR = 3 };
 enum { OG_FROZEN = 0, OG_NESTED = 1 };
-enum { OG_LFA_UNEQUAL = 0, OG_LFA_EQUAL = 1 };
+/* LFA kinds: central expansion point (unequal or equal arms), and the
+ * non-central variants of App. B ("Other finite differences"): backward
+ * (epsilon = 0, tau_0 = t - delta_s) and forward (epsilon = 1, tau_1 = t - delta_r). */
+enum { OG_LFA_UNEQUAL = 0, OG_LFA_EQUAL = 1, OG_LFA_BACKWARD = 2, OG_LFA_FORWARD = 3 };
 
 typedef struct {
     int32_t kind, delay;

@@ -121,7 +121,7 @@ extern "C" int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky
     LISA_TRY(check_orbit(orbit));
     LISA_TRY(check_grid(grid, "grid"));
     LISA_TRY(check_common(precision, tdi_gen, channels));
-    if (lfa_kind != LISA_LFA_UNEQUAL && lfa_kind != LISA_LFA_EQUAL) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
+    if (!lfa_kind_ok(lfa_kind)) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
     if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
     if (!isfinite(t_hyb)) { set_error("t_hyb must be finite"); return LISA_EINVAL; }
     if (grid.n == 0) return LISA_OK;

@@ -64,6 +64,17 @@ inline void lfa_args_f32(LfaArgs& a)
 __device__ __forceinline__ int lfa_link(int ch, int which) { return link_cycle(which ? 4 : 2, ch); }
 __device__ __forceinline__ int lfa_arm(int ch, int which) { return link_cycle(which ? 2 : 4, ch); }
 
+// Delay of the LFA link's expansion point after the TDI shift sh, from T_l,
+// k.R_s/c and k.R_r/c: the central point T_l/2 + k.(R_s + R_r)/(2c)
+// (Eq. tau_t_dependence), or, for the non-central variants of App. B, the
+// sender end T_l + k.R_s/c (backward) or the receiver end k.R_r/c (forward).
+__device__ __forceinline__ double lfa_point_delay(int kind, double sh, double Tl, double ks, double kr)
+{
+    if (kind == LISA_LFA_BACKWARD) return sh + Tl + ks;
+    if (kind == LISA_LFA_FORWARD) return sh + kr;
+    return sh + 0.5 * Tl + 0.5 * (ks + kr);
+}
+
 __device__ __forceinline__ double lfa_shift(int gen, double Ta, double Tb)
 {
     return gen == LISA_TDI20 ? 2.0 * Ta + 1.5 * Tb : gen == LISA_TDI15 ? Ta + 0.5 * Tb : 0.0;
@@ -240,9 +251,12 @@ __device__ void lfa_tile_prologue(const LfaArgs& a, int64_t ic, SM& sm)
                 for (int k = 0; k < 4; ++k)
                     sh[k] = equal ? (k == 0 ? (al + be) * a.Lc : 0.0) : al * g.b[ra][k] + be * g.b[rb][k];
             }
+            // delay of the expansion point: central, or the sender / receiver end
             double d[4];
             for (int k = 0; k < 4; ++k)
-                d[k] = sh[k] + 0.5 * (sm.comp[c][0][k] + sm.comp[c][1][k] + sm.comp[c][2][k]);
+                d[k] = a.kind == LISA_LFA_BACKWARD ? sh[k] + sm.comp[c][0][k] + sm.comp[c][1][k]
+                     : a.kind == LISA_LFA_FORWARD ? sh[k] + sm.comp[c][2][k]
+                     : sh[k] + 0.5 * (sm.comp[c][0][k] + sm.comp[c][1][k] + sm.comp[c][2][k]);
             int64_t j;
             double eps;
             split_f64(a.hm, ic, d[0], j, eps);
@@ -341,8 +355,8 @@ __device__ inline void lfa_window(const LfaArgs& a, int64_t i0, int64_t ic, LfaS
         const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
         const double up = u - sh * u_per_s;
         const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
-        const double d = sh + 0.5 * Tl
-                       + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
+        const double d = lfa_point_delay(a.kind, sh, Tl, tg_eval(g, kRowKR + link_sender(l), up),
+                                         tg_eval(g, kRowKR + link_receiver(l), up));
         int64_t j;
         double eps;
         split_f64(a.hm, m, d, j, eps);
@@ -510,8 +524,8 @@ __device__ inline void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lfa
             const double sh = which ? lfa_shift(a.gen, Tb, Ta) : lfa_shift(a.gen, Ta, Tb);
             const double up = u - sh * u_per_s;
             const double Tl = equal ? a.Lc : tg_eval(g, kQT + l, up);
-            const double dtau = sh + 0.5 * Tl
-                              + 0.5 * (tg_eval(g, kRowKR + link_sender(l), up) + tg_eval(g, kRowKR + link_receiver(l), up));
+            const double dtau = lfa_point_delay(a.kind, sh, Tl, tg_eval(g, kRowKR + link_sender(l), up),
+                                                tg_eval(g, kRowKR + link_receiver(l), up));
             double n3[3];
             for (int q = 0; q < 3; ++q) n3[q] = tg_eval(g, kQN + 3 * l + q, up);
             int64_t j;

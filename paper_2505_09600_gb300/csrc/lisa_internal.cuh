@@ -34,6 +34,12 @@ private:
 // Tile size (output samples per CTA) of the response kernels.
 constexpr int kTile = 256;
 
+// Known LFA kinds (central unequal / equal arms, non-central backward / forward).
+inline bool lfa_kind_ok(int k)
+{
+    return k == LISA_LFA_UNEQUAL || k == LISA_LFA_EQUAL || k == LISA_LFA_BACKWARD || k == LISA_LFA_FORWARD;
+}
+
 // Segment tables of many grids in one launch (batched plans).
 struct SegSource {
     double t0, dt;

@@ -77,7 +77,7 @@ extern "C" int lisa_response_hybrid_static(const lisa_orbit* orbit, const lisa_s
     }
     if (precision != LISA_F64 && precision != LISA_MIXED) { set_error("precision unknown"); return LISA_EINVAL; }
     if (tdi_gen != LISA_TDI15 && tdi_gen != LISA_TDI20) { set_error("tdi_gen must be 15 or 20"); return LISA_EINVAL; }
-    if (lfa_kind != LISA_LFA_UNEQUAL && lfa_kind != LISA_LFA_EQUAL) { set_error("lfa_kind unknown"); return LISA_EINVAL; }
+    if (!lfa_kind_ok(lfa_kind)) { set_error("lfa_kind unknown"); return LISA_EINVAL; }
     if (channels != LISA_XYZ && channels != LISA_AET) { set_error("channels unknown"); return LISA_EINVAL; }
     if (!isfinite(t_hyb)) { set_error("t_hyb must be finite"); return LISA_EINVAL; }
     if (out.n == 0) return LISA_OK;

@@ -56,16 +56,16 @@ def _small_source(n=900, f0=3e-3, ratio=1.5, dt=5.0, seed=1):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_links_lfa_own(L, oracle_mod, precision):
+@pytest.mark.parametrize("kind", [0, 2, 3])   # central, backward, forward expansion point
+def test_links_lfa_own(L, oracle_mod, precision, kind):
     s = _small_source(n=1300)
     oo, lo = orbit_pair("kepler2_flex")
     sky = (s.beta, s.lam, s.psi)
     hp = s.hp.astype(np.float32).astype(np.float64) if precision == 1 else s.hp
     hc = s.hc.astype(np.float32).astype(np.float64) if precision == 1 else s.hc
     z = torch.full((6, s.n), float("nan"), device="cuda", dtype=torch.float64 if precision == 0 else torch.float32)
-    L.lisa_links_lfa_own(lo, sky, s.grid, to_dev(hp, precision), to_dev(hc, precision), precision, L.LFA_UNEQUAL,
-                         s.grid, z)
-    want = oracle_mod.links_lfa_own(oo, sky, s.grid, hp, hc, oracle_mod.LFA_UNEQUAL, s.grid)
+    L.lisa_links_lfa_own(lo, sky, s.grid, to_dev(hp, precision), to_dev(hc, precision), precision, kind, s.grid, z)
+    want = oracle_mod.links_lfa_own(oo, sky, s.grid, hp, hc, kind, s.grid)
     got = z.cpu().numpy().astype(np.float64)
     tol = np.full(6, F64_TOL) if precision == 0 else np.array(MIXED_TOL["z"])
     assert np.all(rel_err(got, want) <= tol), rel_err(got, want)

@@ -369,6 +369,74 @@ def test_lfa_converges_as_f_squared(oracle_mod, gen):
     assert 1.8 < slope < 2.2, (slope, errs)
 
 
+def _link_lfa_err(oracle_mod, o, f, kind, n=3000, dt=5.0, t0=3.0e7):
+    sky = (0.41, 2.3, 0.77)
+    hp, hc = synth.monochromatic(t0, dt, n, f, 1.0, 0.8, 0.2)
+    g = (t0, dt, n)
+    yf = oracle_mod.links_full(o, sky, g, hp, hc, g)
+    yl = oracle_mod.links_lfa_own(o, sky, g, hp, hc, kind, g)
+    sl = slice(400, n - 400)
+    return yl[:, sl] - yf[:, sl], np.abs(yf[:, sl]).max()
+
+
+def test_lfa_expansion_point_orders(oracle_mod):
+    # App. B, "Other finite differences": expanding the link around
+    # tau_eps = t - delta_s + eps (delta_s - delta_r), the m = 2 term of the
+    # series has the coefficient (1 - 2 eps)/2, zero only at the central
+    # point.  So on a rigid static constellation the leading-term link error
+    # falls as f^2 (relative) at eps = 1/2 and as f at eps = 0 (backward) and
+    # eps = 1 (forward), and the backward and forward errors are opposite at
+    # leading order: their mean falls as f^2 again.
+    o = oracle_mod.Orbit(kind=oracle_mod.STATIC, t_static=2.2e7)
+    fs = np.array([2e-4, 5e-4, 1e-3, 2e-3])
+    slope = lambda e: np.polyfit(np.log(fs), np.log(e), 1)[0]
+    ec, eb, ef, em = [], [], [], []
+    for f in fs:
+        dc, sc = _link_lfa_err(oracle_mod, o, f, oracle_mod.LFA_UNEQUAL)
+        db, _ = _link_lfa_err(oracle_mod, o, f, oracle_mod.LFA_BACKWARD)
+        df, _ = _link_lfa_err(oracle_mod, o, f, oracle_mod.LFA_FORWARD)
+        ec.append(np.abs(dc).max() / sc)
+        eb.append(np.abs(db).max() / sc)
+        ef.append(np.abs(df).max() / sc)
+        em.append(np.abs(0.5 * (db + df)).max() / sc)
+    assert 1.9 < slope(ec) < 2.1, ec
+    assert 0.9 < slope(eb) < 1.1, eb
+    assert 0.9 < slope(ef) < 1.1, ef
+    assert 1.8 < slope(em) < 2.2, em
+    # at 1 mHz the non-central errors are ~100x the central one
+    assert eb[2] > 50 * ec[2] and ef[2] > 50 * ec[2]
+    # the backward point is the sender end: at f -> 0 all three agree with the full link
+    assert max(eb[0], ef[0]) < 1e-2
+
+
+def test_lfa_noncentral_leading_error_term(oracle_mod):
+    # Which end is which: on a static constellation the full link is
+    # y = -[H(t - delta_s) - H(t - delta_r)] / (2 (1 - k.n)); expanding about the
+    # sender end (backward) leaves y_back - y = -(Delta/2) dy/dt and about the
+    # receiver end (forward) +(Delta/2) dy/dt at leading order, with
+    # Delta = delta_s - delta_r = T_l (1 - k.n_l) from the constellation's
+    # positions (y_slr: sender s, receiver r; links +1,-1,+2,-2,+3,-3).
+    sender, receiver = (2, 1, 0, 2, 1, 0), (1, 2, 2, 0, 0, 1)
+    t_st = 2.2e7
+    o = oracle_mod.Orbit(kind=oracle_mod.STATIC, t_static=t_st)
+    sky = (0.41, 2.3, 0.77)
+    k, _, _ = oracle_mod.sky_basis(sky[0], sky[1])
+    t0, dt, n, f = 3.0e7, 5.0, 3000, 5e-4
+    g = (t0, dt, n)
+    hp, hc = synth.monochromatic(t0, dt, n, f, 1.0, 0.8, 0.2)
+    yf = oracle_mod.links_full(o, sky, g, hp, hc, g)
+    sl = slice(400, n - 400)
+    for kind, sign in ((oracle_mod.LFA_BACKWARD, -1.0), (oracle_mod.LFA_FORWARD, +1.0)):
+        e = oracle_mod.links_lfa_own(o, sky, g, hp, hc, kind, g) - yf
+        for li in range(6):
+            Rs = oracle_mod.position(o, sender[li], t_st)
+            Rr = oracle_mod.position(o, receiver[li], t_st)
+            delta = (np.linalg.norm(Rr - Rs) + k @ (Rs - Rr)) / C
+            yd = oracle_mod.hdot(g, yf[li])[sl]
+            coef = (e[li, sl] @ yd) / (yd @ yd)
+            assert abs(coef - sign * 0.5 * delta) < 0.05 * 0.5 * delta, (kind, li, coef, delta)
+
+
 def test_lfa_error_floors_moving_orbits(oracle_mod):
     # Sec. III / App. B: with moving arms the unequal-delay LFA is limited at
     # O(R Omega / c) ~ 1e-4 and the equal-delay one at O(e) ~ 1e-3.

@@ -95,7 +95,7 @@ def test_response_full_f64_config1(L, oracle_mod, cfg1):
 
 
 @pytest.mark.parametrize("gen", [15, 20])
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])   # central unequal / equal, backward, forward
 def test_lfa_f64(L, oracle_mod, cfg2s, gen, kind):
     oo, lo = orbit_pair("kepler2_flex")
     s = cfg2s

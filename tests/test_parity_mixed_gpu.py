@@ -59,7 +59,7 @@ def test_full_mixed(L, oracle_mod, case, gen, channels):
 
 
 @pytest.mark.parametrize("gen", [15, 20])
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])   # central unequal / equal, backward, forward
 def test_lfa_mixed(L, oracle_mod, case, gen, kind):
     s, hp, hc = case
     oo, lo = orbit_pair("kepler2_flex")
