@@ -8,7 +8,10 @@ contraction); this module only builds it and marshals numpy arrays.
 
 Functions and the paper passages they follow are documented in oracle.c.
 Parity pins that check this oracle against what the paper and mathematics fix
-live in tests/test_oracle_pins.py.
+live in tests/test_oracle_pins.py.  Submodules in plain numpy: ``noise`` (the
+likelihood tail), ``mlp`` and ``corrector`` (the learned corrector),
+``waveform`` (the synthetic source family generated on the device; pins in
+tests/test_waveform_oracle.py).
 """
 from __future__ import annotations
 
