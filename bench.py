@@ -475,6 +475,79 @@ def bench_batch(L, torch, dev, orbit, flush, stream, args):
             "workload": "hybrid TDI2.0 AET, f_hyb=1e-3 Hz, mixed precision, one persistent launch (graph replay)"}
 
 
+def bench_pe_draws(L, torch, dev, orbit, stream, args):
+    """Config 5: PE draws around Mc = 5e5 Msun, q = 2 (eccentric), one year at
+    10 s each, generated on the device (lisa_chirp_ringdown) and put through the
+    hybrid response, a chunk of draws at a time (generation into one buffer,
+    then one batched persistent plan per chunk).  Plans are built before the
+    timed region; the timed region covers generation and response of every
+    draw."""
+    import synth
+    ndraw, chunk = args.pe_draws, min(args.pe_chunk, args.pe_draws)
+    n, dt, t0 = 3155760, 10.0, 2.0e7
+    tc = t0 + n * dt - 1.0e4
+    ps = synth.pe_params(ndraw=ndraw)
+    draws = [dict(mc_s=p["mc"] * synth.T_SUN, q=p["q"], dist_m=10.0 * synth.GPC, iota=0.5, phi_c=p["phi_c"], tc=tc,
+                  e0=p["e0"], f_cut=0.8 * 0.5 / dt) for p in ps]
+    hp = torch.empty((chunk, n), device=dev)
+    hc = torch.empty((chunk, n), device=dev)
+    out = torch.empty((chunk, 3, n), device=dev)
+    t_setup = time.perf_counter()
+    plans = []
+    for c0 in range(0, ndraw, chunk):
+        descs = []
+        for k, d in enumerate(draws[c0:c0 + chunk]):
+            p = ps[c0 + k]
+            descs.append(dict(grid=(t0, dt, n), hp=hp[k], hc=hc[k], sky=(p["beta"], p["lam"], p["psi"]),
+                              t_hyb=L.lisa_t_hyb_from_f(F_HYB, d["mc_s"], tc), out=out[k]))
+        plans.append((c0, L.LisaPlan(orbit, descs)))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+
+    def run_all():
+        for c0, plan in plans:
+            part = draws[c0:c0 + chunk]
+            L.lisa_chirp_ringdown(part, (t0, dt, n), L.MIXED, hp[:len(part)], hc[:len(part)],
+                                  stream=stream.cuda_stream)
+            plan.execute(stream=stream.cuda_stream)
+
+    def gen_only():
+        for c0, _ in plans:
+            part = draws[c0:c0 + chunk]
+            L.lisa_chirp_ringdown(part, (t0, dt, n), L.MIXED, hp[:len(part)], hc[:len(part)],
+                                  stream=stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        run_all()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run_all()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        gen_only()
+        b.record(stream)
+        b.synchronize()
+        gen_ms = a.elapsed_time(b)
+    best = float(np.median(ms))
+    finite = bool(torch.isfinite(out).all().item())
+    for _, plan in plans:
+        plan.close()
+    del hp, hc, out
+    total = ndraw * n
+    return {"draws": ndraw, "samples_per_draw": n, "samples": total, "ms": round(best, 2),
+            "draws_per_s": ndraw / (best / 1e3), "samples_per_s": total / (best / 1e3),
+            "generation_ms": round(gen_ms, 2), "generation_share": round(gen_ms / best, 4),
+            "chunk": chunk, "plan_setup_s": round(t_setup, 2), "outputs_finite": finite,
+            "workload": "config 5: eccentric chirp + ringdown draws (Mc 5e5 Msun, q 2, e0 U[0, 0.3]), 1 yr at 10 s, "
+                        "generated on the device (mixed) + hybrid TDI2.0 AET (f_hyb = 1e-3 Hz), batched plans"}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -645,6 +718,9 @@ def run_ours(args):
     batched = None
     if not args.no_batch and rank == 0:
         batched = bench_batch(L, torch, dev, orbit, flush, stream, args)
+    pe_draws = None
+    if not args.no_pe and rank == 0:
+        pe_draws = bench_pe_draws(L, torch, dev, orbit, stream, args)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -692,6 +768,8 @@ def run_ours(args):
         line["corrector"] = corrector
     if batched is not None:
         line["batched"] = batched
+    if pe_draws is not None:
+        line["pe_draws"] = pe_draws
     if loglike is not None:
         line["loglike"] = loglike
     if not args.no_cpu and world == 1:
@@ -741,6 +819,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-loglike", action="store_true")
     ap.add_argument("--batch-sources", type=int, default=1024)
+    ap.add_argument("--no-pe", action="store_true")
+    ap.add_argument("--pe-draws", type=int, default=4096)
+    ap.add_argument("--pe-chunk", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -95,6 +95,31 @@ enum { LISA_FROZEN = 0, LISA_NESTED = 1 };
  * error is one order lower than the central point's. */
 enum { LISA_LFA_UNEQUAL = 0, LISA_LFA_EQUAL = 1, LISA_LFA_BACKWARD = 2, LISA_LFA_FORWARD = 3 };
 
+/* Synthetic source family generated on the device, ahead of the response (the
+ * paper's IMRPhenomTHM/TEHM waveforms are not available; this family has their
+ * time-domain structure).  A Newtonian (0PN) chirp, masses in seconds
+ * (G M / c^3), tau = tc - t:
+ *   f = (1/pi)(5/256)^(3/8) Mc^(-5/8) tau^(-3/8),  phi = phi_c - 2 (tau/(5 Mc))^(5/8),
+ *   A = 4 c Mc^(5/3) (pi f)^(2/3) / D,  Phi = phi + 4 e_t sin(phi/2),
+ *   e_t = e0 (f/f0)^(-19/18) with f0 the frequency at the grid's first sample,
+ *   h+ = A (1 + cos^2 iota)/2 cos Phi,  hx = A cos iota sin Phi,
+ * up to t_join = tc - tau(f_join), f_join = min(f_ISCO, f_cut) with
+ * f_ISCO = 1/(6^(3/2) pi M), M = Mc eta^(-3/5); after it a (2,2,0) damped
+ * sinusoid of the remnant (m_final_frac M, spin a_final; Berti-Cardoso-Will
+ * fits, frequency capped at f_cut) continuing amplitude and phase. */
+typedef struct {
+    double mc_s;          /* chirp mass G Mc / c^3 (s), > 0 */
+    double q;             /* mass ratio m1 / m2 >= 1 */
+    double dist_m;        /* luminosity distance (m), > 0 */
+    double iota;          /* inclination (rad) */
+    double phi_c;         /* coalescence phase (rad) */
+    double tc;            /* coalescence time (s) */
+    double e0;            /* eccentricity at the grid's first sample, in [0, 1) (0: circular) */
+    double f_cut;         /* cap on the join and ringdown frequencies (Hz); <= 0: none */
+    double m_final_frac;  /* remnant mass / total mass, in (0, 1] */
+    double a_final;       /* remnant dimensionless spin, in [0, 1) */
+} lisa_chirp;
+
 /* Version of this ABI (major*10000 + minor*100 + patch). */
 int lisa_version(void);
 /* Static message for a status code. */
@@ -160,6 +185,14 @@ int lisa_links_lfa_own(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h
  * 5-point central differences on z_grid, arms at the output time. */
 int lisa_tdi_lfa(const lisa_orbit* orbit, lisa_grid z_grid, const void* z, int precision,
                  int tdi_gen, int lfa_kind, int channels, void* xyz, void* stream);
+
+/* h+, hx of nsrc draws (host array src[nsrc], nsrc <= 65535) on one grid,
+ * into device hp, hc laid out [nsrc][grid.n] (double for LISA_F64, float for
+ * LISA_MIXED: FP32 output continuing an FP64 phase anchor per 32 samples).
+ * One launch; asynchronous on stream (the parameters are staged before the
+ * call returns). */
+int lisa_chirp_ringdown(const lisa_chirp* src, int nsrc, lisa_grid grid, int precision, void* hp, void* hc,
+                        void* stream);
 
 /* a8-a10 in one call (z kept on chip). */
 int lisa_response_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,

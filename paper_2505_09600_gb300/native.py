@@ -53,6 +53,12 @@ class lisa_source(C.Structure):
                 ("t_hyb", C.c_double), ("T_win", C.c_double), ("sigma", C.c_double), ("out", C.c_void_p)]
 
 
+class lisa_chirp(C.Structure):
+    _fields_ = [("mc_s", C.c_double), ("q", C.c_double), ("dist_m", C.c_double), ("iota", C.c_double),
+                ("phi_c", C.c_double), ("tc", C.c_double), ("e0", C.c_double), ("f_cut", C.c_double),
+                ("m_final_frac", C.c_double), ("a_final", C.c_double)]
+
+
 class lisa_tune_result(C.Structure):
     _fields_ = [("ctas_per_sm", C.c_int), ("tiles_per_item", C.c_int), ("ms", C.c_float)]
 
@@ -134,6 +140,7 @@ _SIGS = {
     "lisa_psd_aet": (C.c_int, [C.c_double, C.c_double, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int, _P,
                                _P]),
     "lisa_fft_length": (C.c_int64, [C.c_int64]),
+    "lisa_chirp_ringdown": (C.c_int, [C.POINTER(lisa_chirp), C.c_int, lisa_grid, C.c_int, _P, _P, _P]),
     "lisa_noise_weights_aet": (C.c_int, [lisa_grid, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
                                          C.c_double, _P, _P]),
     "lisa_inner_aet": (C.c_int, [lisa_grid, C.c_int64, _P, _P, C.c_int, _P, _P, _P]),
@@ -364,6 +371,23 @@ def lisa_psd_aet(f0, df, nf, tdi_gen, L_m, t_obs_years, galaxy, psd, stream=None
     rc = load().lisa_psd_aet(float(f0), float(df), int(nf), tdi_gen, float(L_m), float(t_obs_years), int(galaxy),
                              _ptr(psd, torch.float64, 2 * int(nf), "psd"), _stream(stream))
     _check(rc, "lisa_psd_aet")
+
+
+def lisa_chirp_ringdown(draws, grid, precision, hp, hc, stream=None):
+    """Synthetic chirp + ringdown of each draw (dicts with keys mc_s, q, dist_m,
+    iota, phi_c, tc and optionally e0, f_cut, m_final_frac, a_final) on grid,
+    into CUDA tensors hp, hc of shape [len(draws)][n] (float64 for F64, float32
+    for MIXED)."""
+    arr = (lisa_chirp * max(len(draws), 1))()
+    for k, d in enumerate(draws):
+        arr[k] = lisa_chirp(float(d["mc_s"]), float(d["q"]), float(d["dist_m"]), float(d["iota"]),
+                            float(d["phi_c"]), float(d["tc"]), float(d.get("e0", 0.0)), float(d.get("f_cut", 0.0)),
+                            float(d.get("m_final_frac", 0.95)), float(d.get("a_final", 0.7)))
+    g = _grid(grid)
+    dt = _rdtype(precision)
+    rc = load().lisa_chirp_ringdown(arr, len(draws), g, precision, _ptr(hp, dt, len(draws) * g.n, "hp"),
+                                    _ptr(hc, dt, len(draws) * g.n, "hc"), _stream(stream))
+    _check(rc, "lisa_chirp_ringdown")
 
 
 def lisa_fft_length(n):
