@@ -434,6 +434,11 @@ int lisa_corrector_report(lisa_corrector* c, int64_t* spot_tiles, int64_t* spot_
  * synchronises the device, returns the word in *status (may be NULL), clears
  * it if reset != 0, and returns LISA_ETIMEOUT if bit 0 was set. */
 int lisa_device_status(unsigned int* status, int reset);
+/* Test of the bounded-wait path: one CTA waits on an mbarrier that nothing
+ * arrives on; the wait gives up after its bound (about a second), sets the
+ * status word and the kernel returns, leaving the context usable.  A later
+ * lisa_device_status returns LISA_ETIMEOUT. */
+int lisa_selftest_wait_timeout(void* stream);
 
 /* Instrumentation (no counterpart in the paper).
  * lisa_profile_enable(1) clears the record and makes every kernel launch of

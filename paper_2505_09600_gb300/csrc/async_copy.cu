@@ -24,9 +24,34 @@ unsigned int* device_status_ptr()
     return addr[dev];
 }
 
+// Test of the bounded-wait path: thread 0 of one CTA waits on an mbarrier
+// that expects one arrival and gets none; the wait gives up after its bound
+// (kAsyncSpinLimit polls, about a second), flags the status word and the
+// kernel returns.
+__global__ void wait_timeout_selftest_kernel(unsigned int* status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        if (!mbar_wait_bounded(&bar, 0)) flag_timeout(status);
+    }
+}
+
 }  // namespace lisa
 
 using namespace lisa;
+
+extern "C" int lisa_selftest_wait_timeout(void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* status = device_status_ptr();
+    if (!status) { set_error("device status word unavailable"); return LISA_ECUDA; }
+    prof_before("wait_timeout_selftest", st);
+    wait_timeout_selftest_kernel<<<1, 32, 0, st>>>(status);
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "wait_timeout_selftest_kernel");
+}
 
 extern "C" int lisa_device_status(unsigned int* status, int reset)
 {

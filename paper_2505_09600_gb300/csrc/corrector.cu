@@ -105,6 +105,15 @@ __device__ __forceinline__ float gelu2_f(float x)
     const float p = fmaf(x * x, c * 0.044715f, c);
     return fmaf(x, tanh_fast(x * p), x);
 }
+// gelu2_f of a pair, the polynomial in packed FP32 pair instructions (one
+// issue slot for both values, each lane rounded as the scalar operation).
+__device__ __forceinline__ float2 gelu2_f2(float2 x)
+{
+    const float c = 0.7978845608028654f;
+    const float2 p = __ffma2_rn(__fmul2_rn(x, x), make_float2(c * 0.044715f, c * 0.044715f), make_float2(c, c));
+    const float2 xp = __fmul2_rn(x, p);
+    return __ffma2_rn(x, make_float2(tanh_fast(xp.x), tanh_fast(xp.y)), x);
+}
 __device__ __forceinline__ float gelu_grad_f(float x)
 {
     const float c = 0.7978845608028654f;
@@ -741,7 +750,12 @@ __global__ void __launch_bounds__(kTcRows, kCorrCtas) corr_mlp_tc_kernel(TcArgs 
                 tmem_ld16(lane_base + cb * 16, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int k = 0; k < 16; ++k) v[k] = gelu2_f(v[k] + sm.bias[l * kWid + cb * 16 + k]);
+                for (int k = 0; k < 16; k += 2) {
+                    const float2 b = *reinterpret_cast<const float2*>(&sm.bias[l * kWid + cb * 16 + k]);
+                    const float2 g = gelu2_f2(__fadd2_rn(make_float2(v[k], v[k + 1]), b));
+                    v[k] = g.x;
+                    v[k + 1] = g.y;
+                }
                 store_row_bf16(sm.act, t, 2 * cb, v);
                 store_row_bf16(sm.act, t, 2 * cb + 1, v + 8);
             }

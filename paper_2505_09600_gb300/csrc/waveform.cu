@@ -47,6 +47,9 @@ struct ChirpDev {
     double kp, kc;    // (1 + cos^2 i)/2, cos i
     double tau_join, t_join, a_join, ph_join, f_rd, tau_rd;
     int64_t i_join;   // last grid sample with t <= t_join (-1: none)
+    // FP32 copies for the mixed form (a double -> float conversion in device
+    // code runs on the FP64 pipe)
+    float kpf, kcf, kff, kaf, f0f, e0f;
 };
 
 // Chirp phase (with the eccentric modulation) and amplitude at tau > 0, FP64.
@@ -110,7 +113,7 @@ constexpr int kSub = 32;
 constexpr int kWarpSpan = 32 * kSub;
 
 __global__ void __launch_bounds__(kWaveThreads) chirp_kernel_f32(const ChirpDev* __restrict__ P, double t0, double dt,
-                                                                 int64_t n, float* __restrict__ hp,
+                                                                 float dtf, int64_t n, float* __restrict__ hp,
                                                                  float* __restrict__ hc)
 {
     const ChirpDev& p = P[blockIdx.y];
@@ -133,11 +136,11 @@ __global__ void __launch_bounds__(kWaveThreads) chirp_kernel_f32(const ChirpDev*
         a_inv = 1.f / taf;
         a_A = (float)Aa;
         a_off = (float)(tau_s - tau_a);   // tau = tau_a + a_off - (i - ia) dt
-        const float fa = (float)p.kf * powf(taf, -0.375f);
-        a_amp = (float)p.ka * powf(fa, 2.f / 3.f);
-        a_e = p.e0 != 0.0 ? (float)p.e0 * powf(fa / (float)p.f0, -19.f / 18.f) : 0.f;
+        const float fa = p.kff * powf(taf, -0.375f);
+        a_amp = p.kaf * powf(fa, 2.f / 3.f);
+        a_e = p.e0f != 0.f ? p.e0f * powf(fa / p.f0f, -19.f / 18.f) : 0.f;
     }
-    const float kp = (float)p.kp, kc = (float)p.kc, dtf = (float)dt;
+    const float kp = p.kpf, kc = p.kcf;
     const int64_t o0 = (int64_t)blockIdx.y * n;
     for (int k = 0; k < 32; ++k) {
         const int64_t b0 = wbase + (int64_t)k * kSub;
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kWaveThreads) chirp_kernel_f32(const ChirpDev*
         if (i >= n) continue;
         float vp, vc;
         if (i <= p.i_join) {
-            const float dtau = off - (float)(lane - kSub / 2) * dtf;
+            const float dtau = off - (float)(lane - kSub / 2) * dtf;   // dtf: dt in FP32
             const float l = log1pf(dtau * inv);
             const float dph = -A * expm1f(0.625f * l);
             float sd, cd;
@@ -236,6 +239,12 @@ int make_chirp(const lisa_chirp& c, const lisa_grid& g, ChirpDev& p)
     while (ij + 1 <= g.n - 1 && g.t0 + (double)(ij + 1) * g.dt <= p.t_join) ++ij;
     while (ij >= 0 && !(g.t0 + (double)ij * g.dt <= p.t_join)) --ij;
     p.i_join = ij;
+    p.kpf = (float)p.kp;
+    p.kcf = (float)p.kc;
+    p.kff = (float)p.kf;
+    p.kaf = (float)p.ka;
+    p.f0f = (float)p.f0;
+    p.e0f = (float)p.e0;
     return LISA_OK;
 }
 
@@ -281,7 +290,8 @@ extern "C" int lisa_chirp_ringdown(const lisa_chirp* src, int nsrc, lisa_grid gr
         const int64_t per_block = (int64_t)(kWaveThreads / 32) * kWarpSpan;
         const dim3 blocks((unsigned)((grid.n + per_block - 1) / per_block), (unsigned)nsrc);
         prof_before("chirp_mixed", st);
-        chirp_kernel_f32<<<blocks, kWaveThreads, 0, st>>>(dev, grid.t0, grid.dt, grid.n, (float*)hp, (float*)hc);
+        chirp_kernel_f32<<<blocks, kWaveThreads, 0, st>>>(dev, grid.t0, grid.dt, (float)grid.dt, grid.n, (float*)hp,
+                                                          (float*)hc);
     }
     prof_after(st);
     return cuda_status(cudaGetLastError(), "chirp_kernel");

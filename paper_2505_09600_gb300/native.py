@@ -132,6 +132,7 @@ _SIGS = {
     "lisa_profile_query": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "lisa_launch_count": (C.c_int64, []),
     "lisa_device_status": (C.c_int, [C.POINTER(C.c_uint), C.c_int]),
+    "lisa_selftest_wait_timeout": (C.c_int, [_P]),
     "lisa_response_hybrid": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
                                        C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                        lisa_grid, _P, _P]),
@@ -439,6 +440,12 @@ def lisa_device_status(reset=True):
     st = C.c_uint()
     _check(load().lisa_device_status(C.byref(st), 1 if reset else 0), "lisa_device_status")
     return st.value
+
+
+def lisa_selftest_wait_timeout(stream=None):
+    """Launch the bounded-wait self-test (a wait that times out after about a
+    second and flags the device status word)."""
+    _check(load().lisa_selftest_wait_timeout(_stream(stream)), "lisa_selftest_wait_timeout")
 
 
 def lisa_response_hybrid_static(orbit, sky, h_grid, hp, hc, precision, tdi_gen, lfa_kind, channels, t_hyb, T_win,

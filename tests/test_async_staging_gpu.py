@@ -51,3 +51,23 @@ def test_bulk_and_plain_staging_agree(L, n, dt):
         assert torch.equal(out_a, out_u)
         assert torch.equal(z_a, z_u)
     assert L.lisa_device_status() == 0
+
+
+def test_bounded_wait_times_out_and_context_survives(L):
+    # a wait on an mbarrier that nothing arrives on gives up after its bound,
+    # flags the status word and returns; the host reads LISA_ETIMEOUT once,
+    # the word is cleared, and the context keeps working
+    assert L.lisa_device_status() == 0
+    L.lisa_selftest_wait_timeout()
+    with pytest.raises(L.LisaError) as e:
+        L.lisa_device_status()
+    assert e.value.status == -4          # LISA_ETIMEOUT
+    assert L.lisa_device_status() == 0   # cleared by the read
+    s = synth.cfg2_small(n=3000)
+    _, lo = orbit_pair("kepler2_flex")
+    out = torch.full((3, s.n), float("nan"), device="cuda")
+    L.lisa_response_lfa(lo, sky_of(s), s.grid, torch.as_tensor(s.hp.astype(np.float32), device="cuda"),
+                        torch.as_tensor(s.hc.astype(np.float32), device="cuda"), L.MIXED, L.TDI20, L.LFA_UNEQUAL,
+                        L.AET, s.grid, out)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
