@@ -54,16 +54,29 @@ struct CombSmem {
     int64_t Jt[48];           // stencil centre of each term at the sub-block centre
     float ft[48], at[48];     // fraction there and its drift per sample
     int toff[6][8];
-    int base0[6], L[6];
+    int base0[6], L[6], wsh[6];   // wsh: link window shifted back by 0 or 1 so that base0 is even
     int64_t wlo;
     int wlen;
     float2 wt[48][32];
     float4 coef[6][kCombMax];
-    float win[6][kWinC];
+    alignas(8) float win[6][kWinC + 2];
     float inv_half, inv_dt, barg_c, barg_d;
 };
 
 __device__ __forceinline__ int comb_link_cha(int ls) { return ls < 2 ? 1 : 0; }
+
+#ifndef LISA_COMB_CPASYNC
+#define LISA_COMB_CPASYNC 1   // link windows filled by asynchronous 4-byte copies
+#endif
+
+// 4-byte asynchronous global -> shared copy; n (0 or 4) bytes are read and the
+// rest of the word is zero-filled.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int n)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Per-sample weights (blocks outside the combined filters' bounds): the
 // delays from the group-centre split and cubic, stencils from the window or
@@ -84,7 +97,8 @@ static __device__ __noinline__ void comb_exact_sample(const TdiArgs& a, const Co
             const float eps = v - fv;
             const TdiTerm& tm = c_terms[q];
             const int ls = c_cyc[ch][tm.link];
-            const float val = interp_one<float>(s.win[ls], s.wlo, s.wlen, yg + (int64_t)ls * a.ny, a.ym.n_in, j, eps);
+            const float val = interp_one<float>(s.win[ls], s.wlo - s.wsh[ls], s.wlen + s.wsh[ls],
+                                                yg + (int64_t)ls * a.ny, a.ym.n_in, j, eps);
             acc[ch] += tm.sign > 0 ? val : -val;
         }
     }
@@ -203,11 +217,6 @@ static __device__ void comb_group(const TdiArgs& a, int64_t t0, int nt, int G, C
         __syncthreads();
         const int64_t wlo = s.wlo;
         const int wlen = s.wlen;
-        for (int li = 0; li < 6; ++li)
-            for (int o = t; o < wlen; o += blockDim.x) {
-                const int64_t idx = wlo + o;
-                s.win[li][o] = (idx >= 0 && idx < a.ym.n_in) ? yg[(int64_t)li * a.ny + idx] : 0.f;
-            }
         // (5) link filters: offsets and lengths
         if (t < 6) {
             const int ls = t;
@@ -222,9 +231,30 @@ static __device__ void comb_group(const TdiArgs& a, int64_t t0, int nt, int G, C
             // samples di in [-kTile, kTile) read [b0 + di, b0 + di + L)
             if (wlen == 0 || L > kCombMax || b0 - kTile < 0 || b0 + kTile - 1 + L > wlen) good = false;
             s.L[ls] = (int)(L < kCombMax ? L : kCombMax);
-            s.base0[ls] = (int)b0;
+            // the link's window starts one sample earlier when b0 is odd, so
+            // that a thread's tap pairs (two adjacent samples) are 8-byte aligned
+            const int sh = (int)(b0 & 1);
+            s.wsh[ls] = sh;
+            s.base0[ls] = (int)b0 + sh;
         }
         good = __syncthreads_and(good);
+        // link windows: y on [wlo - wsh, wlo - wsh + wlen + 2) (the last two
+        // entries only feed the unused half of a thread's last tap pair)
+        // (asynchronous copies complete before the barrier ahead of the filters,
+        // overlapping the weights and coefficients below)
+        for (int li = 0; li < 6; ++li) {
+            const int64_t org = wlo - s.wsh[li];
+            const float* __restrict__ yl = yg + (int64_t)li * a.ny;
+            for (int o = t; o < wlen + 2; o += blockDim.x) {
+                const int64_t idx = org + o;
+                const bool in = idx >= 0 && idx < a.ym.n_in;
+#if LISA_COMB_CPASYNC
+                cp_async4(&s.win[li][o], in ? yl + idx : yl, in ? 4 : 0);
+#else
+                s.win[li][o] = in ? yl[idx] : 0.f;
+#endif
+            }
+        }
         // (6) weights and eps-derivatives: one warp per term, lane p
         if (good) {
             for (int w = warp; w < nw; w += kTile / 32) {
@@ -277,33 +307,50 @@ static __device__ void comb_group(const TdiArgs& a, int64_t t0, int nt, int G, C
                 s.coef[ls][q] = v;
             }
         }
+#if LISA_COMB_CPASYNC
+        cp_async_wait_all();
+#endif
         __syncthreads();
-        // (8) samples i0 + t and i0 + kTile + t (block offsets di = t - kTile, t)
+        // (8) samples i0 + 2t and i0 + 2t + 1 (block offsets di = 2t - kTile and
+        // one more): the second sample's stencil is the first's shifted by one,
+        // so the window is read as aligned pairs, each feeding both samples
         float X0[3], X1[3];
         if (good) {
             float a0[3] = {0.f, 0.f, 0.f}, a1[3] = {0.f, 0.f, 0.f};
-            const float d0 = (float)(t - kTile), d1 = (float)t;
+            const float d0 = (float)(2 * t - kTile), d1 = d0 + 1.f;
 #pragma unroll 1
             for (int ls = 0; ls < 6; ++ls) {
-                const float* __restrict__ y0 = s.win[ls] + s.base0[ls] + (t - kTile);
-                const float* __restrict__ y1 = y0 + kTile;
+                const float2* __restrict__ yp =
+                    reinterpret_cast<const float2*>(s.win[ls] + s.base0[ls] + (2 * t - kTile));
                 const float4* __restrict__ cf = s.coef[ls];
                 const int L = s.L[ls];
                 float pa0 = 0.f, pa1 = 0.f, pb0 = 0.f, pb1 = 0.f;   // sample 0: channel a value/drift, b
                 float qa0 = 0.f, qa1 = 0.f, qb0 = 0.f, qb1 = 0.f;   // sample 1
+                float2 P = yp[0];
                 for (int q = 0; q < L; q += 4) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float4 cc = cf[q + k];
-                        const float ya = y0[q + k], yb = y1[q + k];
-                        pa0 = fmaf(cc.x, ya, pa0);
-                        pa1 = fmaf(cc.y, ya, pa1);
-                        pb0 = fmaf(cc.z, ya, pb0);
-                        pb1 = fmaf(cc.w, ya, pb1);
-                        qa0 = fmaf(cc.x, yb, qa0);
-                        qa1 = fmaf(cc.y, yb, qa1);
-                        qb0 = fmaf(cc.z, yb, qb0);
-                        qb1 = fmaf(cc.w, yb, qb1);
+                    for (int k = 0; k < 4; k += 2) {
+                        const float2 Pn = yp[(q + k) / 2 + 1];
+                        const float4 c0 = cf[q + k], c1 = cf[q + k + 1];
+                        // tap q + k: sample 0 reads P.x, sample 1 P.y
+                        pa0 = fmaf(c0.x, P.x, pa0);
+                        pa1 = fmaf(c0.y, P.x, pa1);
+                        pb0 = fmaf(c0.z, P.x, pb0);
+                        pb1 = fmaf(c0.w, P.x, pb1);
+                        qa0 = fmaf(c0.x, P.y, qa0);
+                        qa1 = fmaf(c0.y, P.y, qa1);
+                        qb0 = fmaf(c0.z, P.y, qb0);
+                        qb1 = fmaf(c0.w, P.y, qb1);
+                        // tap q + k + 1: sample 0 reads P.y, sample 1 Pn.x
+                        pa0 = fmaf(c1.x, P.y, pa0);
+                        pa1 = fmaf(c1.y, P.y, pa1);
+                        pb0 = fmaf(c1.z, P.y, pb0);
+                        pb1 = fmaf(c1.w, P.y, pb1);
+                        qa0 = fmaf(c1.x, Pn.x, qa0);
+                        qa1 = fmaf(c1.y, Pn.x, qa1);
+                        qb0 = fmaf(c1.z, Pn.x, qb0);
+                        qb1 = fmaf(c1.w, Pn.x, qb1);
+                        P = Pn;
                     }
                 }
                 const float va0 = fmaf(d0, pa1, pa0), vb0 = fmaf(d0, pb1, pb0);
@@ -321,18 +368,20 @@ static __device__ void comb_group(const TdiArgs& a, int64_t t0, int nt, int G, C
                 X1[c] = a1[c];
             }
         }
-        for (int r = 0; r < 2; ++r) {
-            if (r == 1 && sb + 1 >= nt) break;
-            const int64_t i = i0 + r * kTile + t;
-            if (i < a.i_begin || i >= a.i_end) continue;
-            float X[3];
-            if (good) {
-                for (int c = 0; c < 3; ++c) X[c] = r ? X1[c] : X0[c];
-            } else {
-                comb_exact_sample(a, s, ic, i, X);
+        // a sub-block of one tile (the group's last) has samples on t < kTile / 2 only
+        if (sb + 1 < nt || 2 * t < kTile) {
+            for (int r = 0; r < 2; ++r) {
+                const int64_t i = i0 + 2 * t + r;
+                if (i < a.i_begin || i >= a.i_end) continue;
+                float X[3];
+                if (good) {
+                    for (int c = 0; c < 3; ++c) X[c] = r ? X1[c] : X0[c];
+                } else {
+                    comb_exact_sample(a, s, ic, i, X);
+                }
+                store_channels_f32(X[0], X[1], X[2], a.channels, a.bl, s.barg_c, s.barg_d, (int)(i - ic), i,
+                                   (float*)a.xyz, a.nout);
             }
-            store_channels_f32(X[0], X[1], X[2], a.channels, a.bl, s.barg_c, s.barg_d, (int)(i - ic), i,
-                               (float*)a.xyz, a.nout);
         }
         __syncthreads();   // the sub-block's shared data are reused by the next one
     }
