@@ -201,7 +201,9 @@ __global__ void __launch_bounds__(kTile, 3) links_group_kernel(LinksArgs a, int6
         interp2(2 * 0 + 1, ra[1], rb[1]);
         interp2(2 * 1 + 1, ra[2], rb[2]);
         const int64_t ia = i0 + t, ib = ia + kTile;
-        const bool va = ia >= a.i_begin && ia < a.i_end, vb = ib >= a.i_begin && ib < a.i_end;
+        // the second sample exists only if the sub-block has its second tile in this group
+        const bool va = ia >= a.i_begin && ia < a.i_end;
+        const bool vb = 2 * sb + 1 < nt && ib >= a.i_begin && ib < a.i_end;
 #pragma unroll 1
         for (int li = 0; li < 6; ++li) {
             float2 sa, sbv;
@@ -249,7 +251,11 @@ int launch_links_full(const SegTable& tab, const SkyDev& sky, const lisa_grid& h
     prof_before(precision == LISA_MIXED ? "links_full_mixed" : "links_full_f64", st);
     if (precision == LISA_MIXED) {
 #if LISA_LINKS_GROUPED
-        const int G = lfa_group_host(yg.dt);
+        // groups as long as the span bound allows, shorter when the range is
+        // small: at least one wave of CTAs (152 SMs x 3)
+        int G = lfa_group_host(yg.dt);
+        const int64_t per_wave = tiles / (152 * 3);
+        if (per_wave < G) G = per_wave > 1 ? (int)per_wave : 1;
         const int64_t tile_end = a.tile0 + tiles;
         links_group_kernel<<<(unsigned)((tiles + G - 1) / G), kTile, 0, st>>>(a, tile_end, G);
 #else

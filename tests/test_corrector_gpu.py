@@ -239,6 +239,12 @@ def test_checkpoint_round_trip(L, tmp_path):
 # fallbacks
 # ---------------------------------------------------------------------------
 
+def _same_links(y, full):
+    # the corrector's full-link tiles and lisa_links_full evaluate the same
+    # formulas in FP32 from their own kernels: equal to FP32 rounding
+    return float((y - full).abs().max()) <= 2e-6 * float(full.abs().max())
+
+
 def _fallback_case(L):
     s = _small_source(n=3000, f0=3e-3)
     _, lo = orbit_pair("kepler2_flex")
@@ -255,7 +261,7 @@ def test_above_band_tiles_use_full_links(L):
     y = torch.full((6, s.n), float("nan"), device="cuda")
     c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
     r = c.report()
-    assert torch.equal(y, full)
+    assert _same_links(y, full)
     assert r["band_tiles"] == (s.n + 255) // 256 and r["status"] == 0
     c.close()
 
@@ -280,7 +286,7 @@ def test_below_band_uses_base_links(L):
     from paper_2505_09600_gb300.corrector import edge_margin
     m = edge_margin(s.dt)
     assert torch.equal(y[:, m:s.n - m], ybase[:, m:s.n - m])
-    assert torch.equal(y[:, :120], full[:, :120]) and torch.equal(y[:, s.n - 120:], full[:, s.n - 120:])
+    assert _same_links(y[:, :120], full[:, :120]) and _same_links(y[:, s.n - 120:], full[:, s.n - 120:])
     assert float(scale.abs().max()) == 0.0
     c.close()
 
@@ -298,7 +304,7 @@ def test_failed_spot_check_recomputes_every_tile(L):
     assert r["status"] == L.LISA_ECORRECTOR
     assert r["spot_tiles"] == 2 and r["spot_failed"] == r["spot_tiles"]
     assert r["fallback_tiles"] == ntile - r["spot_tiles"]
-    assert torch.equal(y, full)
+    assert _same_links(y, full)
     # counters were reset by the report; a lenient tolerance passes
     c.configure(f_lo=0.0, f_hi=1.0, spot_every=1, spot_tol=10.0)
     c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
