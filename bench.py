@@ -468,7 +468,9 @@ def bench_batch(L, torch, dev, orbit, flush, stream, args):
         tune = plan.autotune(stream=st.cuda_stream)
         plan.capture_graph(st.cuda_stream)
         fn = lambda: plan.replay(stream=st.cuda_stream)   # noqa: E731
+        torch.cuda.nvtx.range_push("batched_replay")       # range for targeted profiler captures
         ms = _timed(torch, st, flush, fn, reps=5)
+        torch.cuda.nvtx.range_pop()
     plan.close()
     return {"sources": len(descs), "samples": total, "ms": round(ms, 3), "samples_per_s": total / (ms / 1e3),
             "autotune": tune, "source_generation_s": round(t_gen, 1),

@@ -29,7 +29,7 @@
 #include <vector>
 
 #include "lfa_tile.cuh"
-#include "links_tile.cuh"
+#include "links_group.cuh"
 #include "tdi_comb.cuh"
 
 struct lisa_plan;
@@ -76,13 +76,13 @@ struct BatchKernelArgs {
 union BatchShared {
     Lfa2Smem lfa;
     CombSmem tdi;
-    struct {
-        TileGeo g;
-        LinksTile<true> lk;
-    } ln;
+    LinksGroupSmem lg;
 };
 
-__global__ void __launch_bounds__(kTile, 4) batch_hybrid_kernel(BatchKernelArgs ka)
+#ifndef LISA_BATCH_MINB
+#define LISA_BATCH_MINB 3   // resident CTAs per SM the register budget is set for (85 registers)
+#endif
+__global__ void __launch_bounds__(kTile, LISA_BATCH_MINB) batch_hybrid_kernel(BatchKernelArgs ka)
 {
     __shared__ BatchShared u;
     __shared__ int64_t s_item;
@@ -183,21 +183,20 @@ __global__ void __launch_bounds__(kTile, 4) batch_hybrid_kernel(BatchKernelArgs 
             la.hm = b.hm;
             la.hp = b.hp;
             la.hc = b.hc;
-            la.y = nullptr;
+            la.y = scr;
+            la.y0 = ys;
             la.ny = ka.scr_len;
             la.i_begin = ys;
             la.i_end = ye;
             la.tile0 = 0;
-            for (int64_t c0 = ys; c0 < ye; c0 += kTile) {
-                const int64_t c1 = c0 + kTile < ye ? c0 + kTile : ye;
-                const int64_t ic = c0 + kTile / 2;
-                __syncthreads();   // the previous chunk's readers of u.ln are done
-                tile_geo_load(u.ln.g, b.tab, ic, b.sky);
-                links_tile_prologue<true>(la, u.ln.g, ic, c0, c1 - 1, u.ln.lk);
-                const int64_t m = c0 + t;
-                if (m < c1) links_sample<true>(la, u.ln.g, ic, m, u.ln.lk, scr + (m - ys), ka.scr_len);
+            // the links of [ys, ye) into the scratch, in groups of the source's G
+            // tiles around one FP64 set-up each (as the links kernel)
+            __syncthreads();   // the LFA part is done with the shared memory
+            const int64_t tl0 = ys / kTile, tl1 = (ye - 1) / kTile;
+            for (int64_t tg = tl0; tg <= tl1; tg += b.G) {
+                const int ng = (int)(tl1 - tg + 1 < b.G ? tl1 - tg + 1 : b.G);
+                links_group(la, tg, ng, b.G, u.lg);   // synchronises; the scratch is visible after it
             }
-            __syncthreads();   // the scratch links are visible to the block
             TdiArgs ta;
             ta.tab = b.tab;
             ta.ym = GridMap{1.0, -ys, 0.0, b.dt, ye - ys, 1};

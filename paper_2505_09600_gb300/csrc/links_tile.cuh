@@ -28,6 +28,7 @@ struct LinksArgs {
     const void* hc;
     void* y;
     int64_t ny;
+    int64_t y0;      // sample index held by y[0] (grouped links: stores go to y[li ny + i - y0])
     int64_t i_begin, i_end;
     int64_t tile0;
 };
