@@ -847,12 +847,22 @@ __device__ __forceinline__ void lfa_store(const LfaArgs& a, int64_t i, const Rea
             const double ti = a.t0_out + (double)i * a.dt_out;
             arg = a.bl.eps * (ti - a.bl.t_hyb) / a.bl.sigma;
         }
-        Real wgt;
-        if constexpr (sizeof(Real) == 4) wgt = 1.f / (1.f + expf(fmaf((float)di, barg_d, barg_c)));
-        else wgt = 1.0 / (1.0 + exp(arg));
-        o0 *= wgt;
-        o1 *= wgt;
-        o2 *= wgt;
+        if constexpr (sizeof(Real) == 4) {
+            // below -17.5 the weight 1 / (1 + e^arg) rounds to 1 in FP32 (e^arg < 2^-24):
+            // skipped, bit for bit the same
+            const float ar = fmaf((float)di, barg_d, barg_c);
+            if (ar > -17.5f) {
+                const float wgt = 1.f / (1.f + expf(ar));
+                o0 *= wgt;
+                o1 *= wgt;
+                o2 *= wgt;
+            }
+        } else {
+            const Real wgt = 1.0 / (1.0 + exp(arg));
+            o0 *= wgt;
+            o1 *= wgt;
+            o2 *= wgt;
+        }
     }
     out[i] = o0;
     out[a.nout + i] = o1;
