@@ -89,3 +89,24 @@ def test_hybrid_mixed(L, oracle_mod, case, gen, channels):
     L.lisa_response_hybrid(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, gen, 0, channels,
                            tH, Tw, sig, s.grid, out)
     _check(out.cpu().numpy(), want, MIXED_TOL["hybrid%d" % gen]["aet" if channels else "xyz"], aet=channels == 1)
+
+
+@pytest.mark.parametrize("shift,ratio", [(0.0, 1), (2.5, 1), (0.0, 2), (1.7, 3)])
+def test_mixed_input_grid_differs_from_output(L, oracle_mod, shift, ratio):
+    """Mixed forms with h on one grid and the outputs on another (offset start,
+    other step): the grouped links and the LFA take the non-unit-ratio path
+    of the sample position (FP64 split of the offset times the ratio)."""
+    oo, lo = orbit_pair("kepler2_flex")
+    s = synth.cfg2_small(n=12000)
+    hp, hc = host_inputs(s, 1)
+    # the window holds the merger (h peaks at sample ~9,600): errors are scaled by each
+    # link's largest value, as in the other parity tests
+    og = (s.t0 + shift + 600.0, s.dt * ratio, int(10400 / ratio))
+    y_want = oracle_mod.links_full(oo, sky_of(s), s.grid, hp, hc, og)
+    y = empty((6, og[2]), 1)
+    L.lisa_links_full(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, og, y)
+    _check(y.cpu().numpy(), y_want, MIXED_TOL["links"])
+    x_want = oracle_mod.response_lfa(oo, sky_of(s), s.grid, hp, hc, 20, 0, "xyz", og)
+    x = empty((3, og[2]), 1)
+    L.lisa_response_lfa(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, 20, 0, L.XYZ, og, x)
+    _check(x.cpu().numpy(), x_want, MIXED_TOL["lfa20"]["xyz"])
