@@ -239,7 +239,10 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None):
     if gpu_out is not None:
         # agreement of the timed GPU step with the oracle on the sampled outputs
         idxf = np.arange(i_full, s.n)
-        blend_idx = np.concatenate([idx[:: max(1, chunk // 200)], idxf[::10]])
+        # plus points spread over the whole series, log-spaced in time before the end,
+        # so that every frequency decade of the chirp holds some
+        spread = (s.n - 1 - np.unique(np.geomspace(1, s.n - 1, 400).astype(np.int64))).astype(np.int64)
+        blend_idx = np.unique(np.concatenate([idx[:: max(1, chunk // 200)], idxf[::10], spread]))
         lf = oracle.tdi_lfa_direct(oo, sky, s.grid, hp, hc, 20, 0, s.grid, blend_idx, hd=hd)
         fu = np.zeros_like(lf)
         need = s.t0 + blend_idx * s.dt >= tH - 0.5 * Tw
@@ -250,6 +253,24 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None):
         scale = np.abs(gpu_out).max()
         out["gpu_max_rel_err_sampled"] = (np.abs(gpu_out[:, blend_idx] - want).max(axis=1) / scale).tolist()
         out["gpu_err_tolerance"] = "A,E,T <= 3e-5 of the largest channel (tests/tolerances.py, hybrid20)"
+        # local diagnostic: per decade of the source's instantaneous frequency (0PN chirp
+        # before the ringdown join, the ringdown frequency after), the error scaled by
+        # the largest sampled |A, E, T| in that decade
+        tt = s.t0 + blend_idx * s.dt
+        t_join = s.meta.get("t_join", s.tc)
+        f_inst = np.where(tt <= t_join, synth.chirp_frequency(np.maximum(s.tc - tt, 1e-9), s.mc_s),
+                          s.meta.get("f_rd", 1e-2))
+        local = {}
+        for k in range(-6, -1):
+            sel = (f_inst >= 10.0 ** k) & (f_inst < 10.0 ** (k + 1))
+            if sel.sum() < 3:
+                continue
+            sc_d = np.abs(want[:, sel]).max()
+            if sc_d > 0:
+                local["1e%d-1e%d Hz" % (k, k + 1)] = {
+                    "points": int(sel.sum()),
+                    "err": (np.abs(gpu_out[:, blend_idx[sel]] - want[:, sel]).max(axis=1) / sc_d).tolist()}
+        out["gpu_local_rel_err_sampled"] = local
     return out
 
 
