@@ -22,6 +22,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -111,8 +112,10 @@ class ClockSampler:
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % self.index)
+            # the raw samples go to LISA_BENCH_OUT (default: the system temporary directory)
+            out_dir = os.environ.get("LISA_BENCH_OUT") or tempfile.gettempdir()
+            os.makedirs(out_dir, exist_ok=True)
+            self.path = os.path.join(out_dir, "clocks_rank%d.csv" % self.index)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "200"],
@@ -249,7 +252,7 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None):
         if need.any():
             fu[:, need] = oracle.tdi_full_direct(oo, sky, s.grid, hp, hc, s.grid, 20, 0, s.grid, blend_idx[need])
         want = oracle.aet(oracle.hybrid_blend(s.grid, tH, Tw, sig, lf, fu, blend_idx))
-        # A, E, T errors relative to the largest channel maximum (as the tests judge them)
+        # A, E, T errors relative to the largest channel maximum (as the tests measure them)
         scale = np.abs(gpu_out).max()
         out["gpu_max_rel_err_sampled"] = (np.abs(gpu_out[:, blend_idx] - want).max(axis=1) / scale).tolist()
         out["gpu_err_tolerance"] = "A,E,T <= 3e-5 of the largest channel (tests/tolerances.py, hybrid20)"
