@@ -110,3 +110,24 @@ def test_mixed_input_grid_differs_from_output(L, oracle_mod, shift, ratio):
     x = empty((3, og[2]), 1)
     L.lisa_response_lfa(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, 20, 0, L.XYZ, og, x)
     _check(x.cpu().numpy(), x_want, MIXED_TOL["lfa20"]["xyz"])
+
+
+def test_links_mixed_grouped_large(L, oracle_mod):
+    """Links over a range long enough for groups of 8 tiles (one FP64 set-up per
+    2,048 samples) and a last group of 3 tiles, on sampled outputs: the group
+    boundaries, the last group, and points spread over the series."""
+    oo, lo = orbit_pair("kepler2_flex")
+    s = synth.cfg2_source(n=1000000, dt=5.0)
+    hp, hc = host_inputs(s, 1)
+    y = empty((6, s.n), 1)
+    L.lisa_links_full(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, s.grid, y)
+    got = y.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(21)
+    g = 8 * 256
+    edges = np.arange(g, s.n, g)
+    idx = np.unique(np.concatenate([rng.integers(0, s.n, 1200), edges[::20] - 1, edges[::20],
+                                    np.arange(s.n - 3 * 256 - 300, s.n)]))
+    want = oracle_mod.links_full(oo, sky_of(s), s.grid, hp, hc, s.grid, idx=idx)
+    scale = np.abs(got).max(axis=1)
+    err = np.abs(got[:, idx] - want).max(axis=1) / scale
+    assert np.all(err <= np.asarray(MIXED_TOL["links"])), err
