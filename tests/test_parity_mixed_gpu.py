@@ -131,3 +131,19 @@ def test_links_mixed_grouped_large(L, oracle_mod):
     scale = np.abs(got).max(axis=1)
     err = np.abs(got[:, idx] - want).max(axis=1) / scale
     assert np.all(err <= np.asarray(MIXED_TOL["links"])), err
+
+
+def test_full_mixed_large_sampled(L, oracle_mod):
+    """Full TDI 2.0 A/E/T over one million samples (grouped links, combined
+    filters in large groups) against the oracle on sampled outputs."""
+    oo, lo = orbit_pair("kepler2_flex")
+    s = synth.cfg2_source(n=1000000, dt=5.0)
+    hp, hc = host_inputs(s, 1)
+    out = empty((3, s.n), 1)
+    L.lisa_response_full(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, 20, L.AET, s.grid, out)
+    got = out.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(22)
+    idx = np.unique(np.concatenate([rng.integers(200, s.n, 300), np.arange(s.n - 4000, s.n, 8)]))
+    want = oracle_mod.aet(oracle_mod.tdi_full_direct(oo, sky_of(s), s.grid, hp, hc, s.grid, 20, 0, s.grid, idx))
+    err = np.abs(got[:, idx] - want).max(axis=1) / np.abs(got).max()
+    assert np.all(err <= np.asarray(MIXED_TOL["full20"]["aet"])), err
