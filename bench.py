@@ -181,7 +181,7 @@ def make_source(rank):
 # CPU baseline: the oracle as it stands, on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 
-def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None):
+def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None, one_core=False):
     """Oracle samples/s for the hybrid workload on the host cores.
 
     The oracle computes the LFA on every sample and the full response on the
@@ -239,6 +239,16 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None):
         out["cores"] = int(os.environ.get("OMP_NUM_THREADS", 0)) or _s.host_cores()
     except Exception:
         out["cores"] = os.cpu_count()
+    # the same legs on one core (a fresh process with OMP_NUM_THREADS=1), to set beside
+    # single-core CPU figures; its LFA chunk is 20,000 samples
+    if one_core:
+        try:
+            env = dict(os.environ, OMP_NUM_THREADS="1")
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-one-core"], env=env,
+                               capture_output=True, text=True, timeout=300)
+            out["one_core"] = json.loads(r.stdout.strip().splitlines()[-1])
+        except Exception as e:   # reported, not fatal: the main figure stands
+            out["one_core"] = {"unavailable": str(e)[:200]}
     if gpu_out is not None:
         # agreement of the timed GPU step with the oracle on the sampled outputs
         idxf = np.arange(i_full, s.n)
@@ -799,7 +809,7 @@ def run_ours(args):
     if loglike is not None:
         line["loglike"] = loglike
     if not args.no_cpu and world == 1:
-        line["cpu_baseline"] = oracle_hybrid_rate(src, budget_s=args.cpu_budget, gpu_out=gpu_out)
+        line["cpu_baseline"] = oracle_hybrid_rate(src, budget_s=args.cpu_budget, gpu_out=gpu_out, one_core=True)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -857,5 +867,19 @@ def main():
         run_ours(args)
 
 
+def oracle_one_core():
+    """The oracle legs of oracle_hybrid_rate on one core: the LFA on a
+    20,000-sample chunk, extrapolated, plus the full response on its whole
+    region.  Must run in a process started with OMP_NUM_THREADS=1."""
+    if os.environ.get("OMP_NUM_THREADS") != "1":
+        raise SystemExit("--oracle-one-core needs OMP_NUM_THREADS=1 in the environment")
+    src = make_source(0)
+    r = oracle_hybrid_rate(src, budget_s=0.0)
+    print(json.dumps({"value": r["value"], "unit": r["unit"], "cores": 1, "sample": r["sample"]}))
+
+
 if __name__ == "__main__":
+    if "--oracle-one-core" in sys.argv:
+        oracle_one_core()
+        sys.exit(0)
     main()
