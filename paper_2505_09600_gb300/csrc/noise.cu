@@ -99,15 +99,15 @@ __global__ void weights_kernel(NoiseSpec ns, double span, int64_t nf, double f_m
 }
 
 constexpr int kRedThreads = 256;
+constexpr float kSc32 = 18446744073709551616.f;   // 2^64
+constexpr float kLo32 = 2.0194839173657902e-28f;    // 2^-92
 
-// Per block: the nine sums (channel c: sum w Re(X* Y), sum w |X|^2, sum w |Y|^2)
-// over a grid-stride range of bins, FP64 in the block tree.
+// The nine sums of one thread's grid-stride range of bins in FP64 (channel c:
+// sum w Re(X* Y), sum w |X|^2, sum w |Y|^2).
 template <typename Cplx>
-__global__ void __launch_bounds__(kRedThreads) inner_kernel(const Cplx* __restrict__ X, const Cplx* __restrict__ Y,
-                                                            const double* __restrict__ w, int64_t nf,
-                                                            double* __restrict__ partial)
+__device__ __forceinline__ void inner_bins_f64(const Cplx* __restrict__ X, const Cplx* __restrict__ Y,
+                                               const double* __restrict__ w, int64_t nf, double* acc)
 {
-    double acc[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) acc[q] = 0.0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += (int64_t)gridDim.x * blockDim.x) {
@@ -122,6 +122,92 @@ __global__ void __launch_bounds__(kRedThreads) inner_kernel(const Cplx* __restri
             acc[3 * c + 2] = fma(ww, bx * bx + by * by, acc[3 * c + 2]);
         }
     }
+}
+
+// FP32 spectra: on this part the FP64 pipe (which also converts between FP32 and
+// FP64) runs far below the FP32 rate, so a bin's products, weighting and sums are
+// formed in FP32 where the values allow, and the FP32 sums are added to FP64 ones
+// every kFlush bins of a thread.
+//  - Operands are scaled by 2^64: for max|component| in [2^-92, 2^-1) the scaled
+//    squares and their sums are normal FP32 numbers. The weight carries the
+//    scale 2^-128 and is used in FP32 when it is zero or in [2^-60, 2^61)
+//    after scaling (converted with integer operations, off the FP64 pipe).
+//  - A product with an operand or weight outside those ranges is formed in FP64.
+//    Each square is decided by its own operand, so <X|X> does not depend on Y.
+//  - A thread whose FP32 sums of squares reach 2^120 or overflow (the cross sums
+//    are bounded by them) recomputes its bins in FP64.
+constexpr int kFlush = 16;
+
+// w * 2^-128 as an FP32 number, formed from the bits of w with integer
+// operations (round to nearest, ties away), for w == 0 or w * 2^-128 in
+// [2^-60, 2^61); false for anything else (negative, NaN or out of range).
+__device__ __forceinline__ bool weight_f32(double w, float& f)
+{
+    const long long bits = __double_as_longlong(w);
+    const long long e = bits >> 52;                            // biased exponent (sign 0)
+    const bool ok = bits == 0 || (e >= 1023 + 128 - 60 && e <= 1023 + 128 + 60);
+    const long long r = ((bits + (1LL << 28)) >> 29) - (1024LL << 23);
+    f = bits == 0 ? 0.f : __int_as_float((int)r);
+    return ok;
+}
+
+__device__ __forceinline__ void inner_bins_f32(const float2* __restrict__ X, const float2* __restrict__ Y,
+                                               const double* __restrict__ w, int64_t nf, double* acc)
+{
+    float s[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) { acc[q] = 0.0; s[q] = 0.f; }
+    bool bad = false;
+    int cnt = 0;
+    auto flush = [&]() {
+        bool fine = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) fine = fine && s[3 * c + 1] < 1.329228e36f && s[3 * c + 2] < 1.329228e36f;
+        bad = bad || !fine;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { acc[q] += (double)s[q]; s[q] = 0.f; }
+    };
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += (int64_t)gridDim.x * blockDim.x) {
+        const double wa = w[k], wt = w[nf + k];
+        float fa, ft;
+        const bool oka = weight_f32(wa, fa), okt = weight_f32(wt, ft);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 a = X[(int64_t)c * nf + k], b = Y[(int64_t)c * nf + k];
+            const bool okw = c < 2 ? oka : okt;
+            const float wf = c < 2 ? fa : ft;
+            const float mA = fmaxf(fabsf(a.x), fabsf(a.y)), mB = fmaxf(fabsf(b.x), fabsf(b.y));
+            const bool okA = okw && mA >= kLo32 && mA < 0.5f, okB = okw && mB >= kLo32 && mB < 0.5f;
+            const float ax = a.x * kSc32, ay = a.y * kSc32, bx = b.x * kSc32, by = b.y * kSc32;
+            if (okA && okB) {
+                s[3 * c + 0] = fmaf(wf, fmaf(ax, bx, ay * by), s[3 * c + 0]);
+                s[3 * c + 1] = fmaf(wf, fmaf(ax, ax, ay * ay), s[3 * c + 1]);
+                s[3 * c + 2] = fmaf(wf, fmaf(bx, bx, by * by), s[3 * c + 2]);
+            } else {
+                const double ww = c < 2 ? wa : wt;
+                const double dax = a.x, day = a.y, dbx = b.x, dby = b.y;
+                acc[3 * c + 0] = fma(ww, dax * dbx + day * dby, acc[3 * c + 0]);
+                if (okA) s[3 * c + 1] = fmaf(wf, fmaf(ax, ax, ay * ay), s[3 * c + 1]);
+                else acc[3 * c + 1] = fma(ww, dax * dax + day * day, acc[3 * c + 1]);
+                if (okB) s[3 * c + 2] = fmaf(wf, fmaf(bx, bx, by * by), s[3 * c + 2]);
+                else acc[3 * c + 2] = fma(ww, dbx * dbx + dby * dby, acc[3 * c + 2]);
+            }
+        }
+        if (++cnt == kFlush) { flush(); cnt = 0; }
+    }
+    flush();
+    if (bad) inner_bins_f64(X, Y, w, nf, acc);
+}
+
+// Per block: the nine sums over the block's threads, FP64 in a fixed-order tree.
+template <typename Cplx>
+__global__ void __launch_bounds__(kRedThreads) inner_kernel(const Cplx* __restrict__ X, const Cplx* __restrict__ Y,
+                                                            const double* __restrict__ w, int64_t nf,
+                                                            double* __restrict__ partial)
+{
+    double acc[9];
+    if constexpr (sizeof(X->x) == 4) inner_bins_f32(X, Y, w, nf, acc);
+    else inner_bins_f64(X, Y, w, nf, acc);
     __shared__ double red[9][kRedThreads];
 #pragma unroll
     for (int q = 0; q < 9; ++q) red[q][threadIdx.x] = acc[q];
@@ -134,14 +220,17 @@ __global__ void __launch_bounds__(kRedThreads) inner_kernel(const Cplx* __restri
     if (threadIdx.x < 9) partial[(int64_t)blockIdx.x * 9 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// Sum of the block partials in block order, times dt^2.
+// Sum of the block partials, times dt^2: warp q sums value q, lane l the blocks
+// l, l + 32, ... in order, then a fixed butterfly (run-to-run identical).
 __global__ void inner_finish_kernel(const double* __restrict__ partial, int nblocks, double dt2, double* __restrict__ out)
 {
-    const int q = threadIdx.x;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (q >= 9) return;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * 9 + q];
-    out[q] = s * dt2;
+    for (int b = lane; b < nblocks; b += 32) s += partial[(int64_t)b * 9 + q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[q] = s * dt2;
 }
 
 // cuFFT plans (three real rows of n samples, batched), one per (device, n,
@@ -296,7 +385,13 @@ int lisa_inner_aet(lisa_grid grid, int64_t nfft, const void* x, const void* y, i
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        nblocks = 4 * (sms > 0 ? sms : 1);
+        // one wave of resident blocks (a second, partial wave would idle most SMs)
+        int per_sm = 0;
+        if (precision == LISA_MIXED)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inner_kernel<float2>, kRedThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inner_kernel<double2>, kRedThreads, 0);
+        nblocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
         const int64_t need = (nf + kRedThreads - 1) / kRedThreads;
         if (need < nblocks) nblocks = (int)(need > 0 ? need : 1);
     }
@@ -309,7 +404,7 @@ int lisa_inner_aet(lisa_grid grid, int64_t nfft, const void* x, const void* y, i
         inner_kernel<float2><<<nblocks, kRedThreads, 0, st>>>((const float2*)X, (const float2*)Y, w, nf, partial);
     else
         inner_kernel<double2><<<nblocks, kRedThreads, 0, st>>>((const double2*)X, (const double2*)Y, w, nf, partial);
-    inner_finish_kernel<<<1, 32, 0, st>>>(partial, nblocks, grid.dt * grid.dt, out);
+    inner_finish_kernel<<<1, 9 * 32, 0, st>>>(partial, nblocks, grid.dt * grid.dt, out);
     prof_after(st);
     return cuda_status(cudaGetLastError(), "inner_kernel launch");
 }

@@ -103,6 +103,40 @@ def test_inner_products_match_oracle(L, precision, pad):
     assert torch.equal(out, out3)
 
 
+@pytest.mark.parametrize("peak_exp", [4, -80, -96])
+def test_inner_products_extreme_scales(L, peak_exp):
+    """FP32 spectra far from the usual fractional-frequency scale: the response
+    scaled so that its loudest bin sits at 2^peak_exp. At 2^4 the loud bins
+    exceed the mixed kernel's scaled FP32 window [2^-92, 2^-1), at 2^-80 the
+    quiet bins fall below it, at 2^-96 every bin does; those bins' products are
+    formed in FP64. (All three rows take one scale: a batched FP32 transform
+    of rows of very different size lets the rounding of the large row leak
+    into the small ones, which no inner-product kernel can undo.)"""
+    s = synth.cfg2_small(n=30001)
+    x = _hybrid(L, s, 1)
+    peak = torch.fft.rfft(x.double(), dim=1).abs().max().item()
+    x = (x * float(2.0 ** peak_exp / peak)).contiguous()
+    y = (0.8 * x + 0.2 * torch.roll(x, 3, dims=1)).contiguous()
+    xs = torch.fft.rfft(x.double(), dim=1)
+    comp = torch.maximum(xs.real.abs(), xs.imag.abs())
+    if peak_exp == 4:
+        assert comp.max().item() >= 0.5 and (comp < 0.5).any().item()
+    elif peak_exp == -80:
+        assert (comp >= 2.0 ** -92).any().item() and (comp[:, 1:] < 2.0 ** -92).any().item()
+    else:
+        assert comp.max().item() < 2.0 ** -92
+    f_min, f_max = 1e-4, 2.5e-2
+    nf = s.n // 2 + 1
+    w = torch.empty((2, nf), device="cuda", dtype=torch.float64)
+    L.lisa_noise_weights_aet(s.grid, 0, 20, L_M, 1.0, 1, f_min, f_max, w)
+    out = torch.empty(9, device="cuda", dtype=torch.float64)
+    L.lisa_inner_aet(s.grid, 0, x, y, 1, w, out)
+    got = out.cpu().numpy().reshape(3, 3)
+    want = ON.inner_aet(x.double().cpu().numpy(), y.double().cpu().numpy(), s.dt, f_min, f_max, 20, L_M, 1.0, True)
+    assert np.isfinite(got).all()
+    np.testing.assert_allclose(got, want, rtol=2e-5)
+
+
 def test_mismatch_of_response_forms(L):
     """Mismatch between the mixed and FP64 hybrid responses: small, as the
     per-sample errors (~1e-6 of the peak) predict."""
