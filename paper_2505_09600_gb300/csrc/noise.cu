@@ -167,13 +167,33 @@ __device__ __forceinline__ void inner_bins_f32(const float2* __restrict__ X, con
 #pragma unroll
         for (int q = 0; q < 9; ++q) { acc[q] += (double)s[q]; s[q] = 0.f; }
     };
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += (int64_t)gridDim.x * blockDim.x) {
-        const double wa = w[k], wt = w[nf + k];
+    // the next bin's loads are issued before the current bin is formed (two bins in
+    // flight per thread: the pass is bound by memory latency)
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float2 ca[3], cb[3];
+    double wa = 0.0, wt = 0.0;
+    if (k < nf) {
+        wa = w[k];
+        wt = w[nf + k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { ca[c] = X[(int64_t)c * nf + k]; cb[c] = Y[(int64_t)c * nf + k]; }
+    }
+    for (; k < nf; k += step) {
+        const int64_t kn = k + step;
+        float2 na[3] = {}, nb[3] = {};
+        double nwa = 0.0, nwt = 0.0;
+        if (kn < nf) {
+            nwa = w[kn];
+            nwt = w[nf + kn];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { na[c] = X[(int64_t)c * nf + kn]; nb[c] = Y[(int64_t)c * nf + kn]; }
+        }
         float fa, ft;
         const bool oka = weight_f32(wa, fa), okt = weight_f32(wt, ft);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float2 a = X[(int64_t)c * nf + k], b = Y[(int64_t)c * nf + k];
+            const float2 a = ca[c], b = cb[c];
             const bool okw = c < 2 ? oka : okt;
             const float wf = c < 2 ? fa : ft;
             const float mA = fmaxf(fabsf(a.x), fabsf(a.y)), mB = fmaxf(fabsf(b.x), fabsf(b.y));
@@ -193,6 +213,10 @@ __device__ __forceinline__ void inner_bins_f32(const float2* __restrict__ X, con
                 else acc[3 * c + 2] = fma(ww, dbx * dbx + dby * dby, acc[3 * c + 2]);
             }
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { ca[c] = na[c]; cb[c] = nb[c]; }
+        wa = nwa;
+        wt = nwt;
         if (++cnt == kFlush) { flush(); cnt = 0; }
     }
     flush();
@@ -201,7 +225,7 @@ __device__ __forceinline__ void inner_bins_f32(const float2* __restrict__ X, con
 
 // Per block: the nine sums over the block's threads, FP64 in a fixed-order tree.
 template <typename Cplx>
-__global__ void __launch_bounds__(kRedThreads) inner_kernel(const Cplx* __restrict__ X, const Cplx* __restrict__ Y,
+__global__ void __launch_bounds__(kRedThreads, 3) inner_kernel(const Cplx* __restrict__ X, const Cplx* __restrict__ Y,
                                                             const double* __restrict__ w, int64_t nf,
                                                             double* __restrict__ partial)
 {
