@@ -291,8 +291,13 @@ int lisa_noise_weights_aet(lisa_grid grid, int64_t nfft, int tdi_gen, double L_m
  * Zero padding samples the same continuous transform more finely (on a flat
  * PSD the products are unchanged, by Parseval).  Real FFTs by cuFFT (plans
  * cached per device, length and precision), then one pass over the bins and a
- * fixed-order reduction (run to run identical).  Device scratch from the
- * stream-ordered allocator on `stream`. */
+ * fixed-order reduction (run to run identical).  LISA_F64: products and sums
+ * in FP64.  LISA_MIXED: a bin's products and weighting in FP32 (spectra
+ * scaled by 2^64, weights by 2^-128, both exact), FP32 running sums added to
+ * FP64 ones every 16 bins; a bin whose spectrum components leave
+ * [2^-92, 2^-1) or whose scaled weight leaves [2^-60, 2^61) is formed in FP64,
+ * so any finite input is accepted.  Device scratch from the stream-ordered
+ * allocator on `stream`. */
 int lisa_inner_aet(lisa_grid grid, int64_t nfft, const void* x, const void* y, int precision, const double* w,
                    double* out, void* stream);
 
