@@ -219,10 +219,14 @@ int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid
  * lisa_response_hybrid computes, with the same arguments, but takes its
  * scratch (orbit tables and link series) from one fixed device array of
  * LISA_STATIC_SCRATCH_BYTES inside the library and calls no cudaMalloc,
- * cudaFree or allocating routine.
+ * cudaFree or allocating routine.  It builds the same orbit table and the
+ * same link range as lisa_response_hybrid and launches the same kernels, so
+ * the two give identical outputs.
  *  - The array is resident on every GPU that loads the library until exit.
  *  - A call whose scratch does not fit returns LISA_EINVAL and says how many
- *    bytes it needed (a one-year series at 5 s needs under 4 MB).
+ *    bytes it needed (the orbit table, 2.1 KB per segment of up to 65,536
+ *    samples, and 6 links over the full part and its TDI reach: a one-year
+ *    series at 5 s switched in its last hours needs under 0.5 MB).
  *  - The first call on a device looks up the array's device address (once
  *    per device, with that device current); make that first call before any
  *    stream capture on the device.
@@ -456,6 +460,19 @@ int lisa_selftest_wait_timeout(void* stream);
 int lisa_profile_enable(int enable);
 int lisa_profile_query(const char* name, double* total_ms, int64_t* launches);
 int64_t lisa_launch_count(void);
+
+/* Arithmetic peak microbenchmark (no counterpart in the paper; it gives the
+ * rooflines a measured denominator).  One launch of blocks_per_sm CTAs of 256
+ * threads on every SM; each thread runs 8 independent fused multiply-add
+ * recurrences for `iters` steps.  kind 0: FP64 (sink: device double
+ * [blocks x 256]); 1: FP32; 2: FP32 as packed pairs (__ffma2_rn) (sink:
+ * device float [blocks x 256]).  *flop receives the launch's flop count (2 per
+ * multiply-add); the caller times the launch on `stream`.
+ * lisa_peak_fma_blocks gives the CTA count (SMs x blocks_per_sm) to size the
+ * sink.  LISA_EINVAL on a bad kind, iters < 1, blocks_per_sm outside 1..64
+ * or a NULL pointer. */
+int lisa_peak_fma_blocks(int blocks_per_sm, int64_t* blocks);
+int lisa_peak_fma(int kind, int64_t iters, int blocks_per_sm, void* sink, double* flop, void* stream);
 
 #ifdef __cplusplus
 }

@@ -117,6 +117,15 @@ double max_light_time(const lisa_orbit* o, const lisa_grid& g)
     return 1.5 * flex * o->L_m / kC;
 }
 
+// First sample of the full links a hybrid needs: the earliest sample that the
+// TDI delays of the full part [iF, n) can reach (8 light times and a margin).
+int64_t hybrid_links_begin(const lisa_orbit* orbit, const lisa_grid& out, int64_t iF)
+{
+    const double Dmax = 8.0 * max_light_time(orbit, out);
+    const int64_t lo = iF - (int64_t)ceil(Dmax / out.dt) - 40;
+    return lo < 0 ? 0 : lo;
+}
+
 // LFA samples: t_i <= t_hyb + Tw/2 -> [0, iL]; full samples: t_i >= t_hyb - Tw/2
 // -> [iF, n) (the same FP64 comparisons as the definition).
 void hybrid_split(const lisa_grid& out, double t_hyb, double Tw, int64_t& iL_out, int64_t& iF_out)
@@ -343,15 +352,13 @@ int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid
                             xyz, 0, iL + 1, bl, st));
     }
     if (iF < n) {
-        // links from the earliest sample the TDI delays of [iF, n) can reach
-        const double Dmax = 8.0 * max_light_time(orbit, out);
-        int64_t lo = iF - (int64_t)ceil(Dmax / out.dt) - 40;
-        lo = lo < 0 ? 0 : lo;
-        void* y = sc.alloc(6 * (size_t)n * rs);
+        const int64_t lo = hybrid_links_begin(orbit, out, iF);
+        // the links are held for samples [lo, n) only
+        void* y = sc.alloc(6 * (size_t)(n - lo) * rs);
         if (!y) return sc.status();
-        LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, precision, out, y, lo, n, st));
+        LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, precision, out, y, lo, n, st, lo));
         BlendSpec bl{1, t_hyb, sg, -1.0, iF, iL + 1};
-        LISA_TRY(launch_tdi(tab, out, y, precision, tdi_gen, LISA_FROZEN, channels, out, xyz, iF, n, bl, st));
+        LISA_TRY(launch_tdi(tab, out, y, precision, tdi_gen, LISA_FROZEN, channels, out, xyz, iF, n, bl, st, lo));
     }
     return LISA_OK;
 }

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kTile) links_full_kernel(LinksArgs a)
     links_tile_prologue<MIXED>(a, g, ic, i0, i0 + kTile - 1, s);
     const int64_t i = i0 + threadIdx.x;
     if (i < a.i_begin || i >= a.i_end) return;
-    links_sample<MIXED>(a, g, ic, i, s, (Real*)a.y + i, a.ny);
+    links_sample<MIXED>(a, g, ic, i, s, (Real*)a.y + (i - a.y0), a.ny);
 }
 
 __global__ void __launch_bounds__(kTile, 3) links_group_kernel(LinksArgs a, int64_t tile_end, int G)
@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(kTile, 3) links_group_kernel(LinksArgs a, int6
 }
 
 int launch_links_full(const SegTable& tab, const SkyDev& sky, const lisa_grid& hg, const void* hp, const void* hc,
-                      int precision, const lisa_grid& yg, void* y, int64_t i_begin, int64_t i_end, cudaStream_t st)
+                      int precision, const lisa_grid& yg, void* y, int64_t i_begin, int64_t i_end, cudaStream_t st,
+                      int64_t y0)
 {
     if (i_end <= i_begin) return LISA_OK;
     LinksArgs a;
@@ -57,8 +58,8 @@ int launch_links_full(const SegTable& tab, const SkyDev& sky, const lisa_grid& h
     a.hp = hp;
     a.hc = hc;
     a.y = y;
-    a.y0 = 0;
-    a.ny = yg.n;
+    a.y0 = y0;
+    a.ny = yg.n - y0;
     a.i_begin = i_begin;
     a.i_end = i_end;
     a.tile0 = i_begin / kTile;

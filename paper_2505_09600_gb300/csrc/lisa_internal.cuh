@@ -52,9 +52,11 @@ int build_seg_tables_batched(const OrbitDev& orb, const SegSource* srcs_dev, int
 int run_orbits(const lisa_orbit* orbit, lisa_grid g, double* R, double* T, double* nh, cudaStream_t st);
 
 // Full links on y-grid samples [i_begin, i_end) using a segment table built
-// on the y grid.
+// on the y grid.  y holds the samples [y0, yg.n) of the grid: link li, sample
+// i at y[li (yg.n - y0) + i - y0] (y0 = 0: the whole grid).
 int launch_links_full(const SegTable& tab, const SkyDev& sky, const lisa_grid& hg, const void* hp, const void* hc,
-                      int precision, const lisa_grid& yg, void* y, int64_t i_begin, int64_t i_end, cudaStream_t st);
+                      int precision, const lisa_grid& yg, void* y, int64_t i_begin, int64_t i_end, cudaStream_t st,
+                      int64_t y0 = 0);
 
 // TDI on out-grid samples [i_begin, i_end).  Hybrid support: each output is
 // multiplied by the sigmoid weight S(t; t_hyb, sigma, -1) if `blend` is set,
@@ -64,8 +66,11 @@ struct BlendSpec {
     double t_hyb, sigma, eps;   // weight S(t; t_hyb, sigma, eps)
     int64_t acc_begin, acc_end; // samples where the existing output is added
 };
+// y holds the samples [y0, yg.n) of the link grid yg, laid out as in
+// launch_links_full; samples below y0 read as zero.
 int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int precision, int gen, int mode, int channels,
-               const lisa_grid& og, void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st);
+               const lisa_grid& og, void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st,
+               int64_t y0 = 0);
 
 // LFA: z series (optional) and channels (optional) on out-grid samples
 // [i_begin, i_end), z recomputed with its 2-sample halo inside each tile.
@@ -98,5 +103,7 @@ int lfa_group_host(double dt);
 // Hybrid regions on grid `out`: LFA samples [0, iL] (t <= t_hyb + Tw/2), full
 // samples [iF, n) (t >= t_hyb - Tw/2).
 void hybrid_split(const lisa_grid& out, double t_hyb, double Tw, int64_t& iL, int64_t& iF);
+// First sample of the full links a hybrid needs for its full samples [iF, n).
+int64_t hybrid_links_begin(const lisa_orbit* orbit, const lisa_grid& out, int64_t iF);
 
 }  // namespace lisa

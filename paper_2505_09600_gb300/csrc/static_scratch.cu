@@ -14,6 +14,9 @@
 // the GPU (different streams, or different host threads) race on it and must
 // be serialised by the caller.  Nothing in it needs to start at zero: each
 // call writes every table coefficient and link sample before it reads them.
+// The scratch holds what lisa_response_hybrid allocates (the orbit table on
+// the output grid and the full links of the samples the TDI part reaches), in
+// the same layout, so the two calls give the same bits.
 #include <math.h>
 #include <string.h>
 
@@ -86,40 +89,19 @@ extern "C" int lisa_response_hybrid_static(const lisa_orbit* orbit, const lisa_s
     const double Tw = T_win > 0.0 ? T_win : 800.0 * out.dt;
     const double sg = sigma > 0.0 ? sigma : Tw / 40.0;
     const int64_t n = out.n;
-    volatile double hi_thr = t_hyb + 0.5 * Tw, lo_thr = t_hyb - 0.5 * Tw;
-    auto t_at = [&](int64_t i) { volatile double p = (double)i * out.dt; return out.t0 + p; };
-    int64_t iL = (int64_t)floor((hi_thr - out.t0) / out.dt);
-    iL = iL < -1 ? -1 : (iL > n - 1 ? n - 1 : iL);
-    while (iL + 1 <= n - 1 && t_at(iL + 1) <= hi_thr) ++iL;
-    while (iL >= 0 && !(t_at(iL) <= hi_thr)) --iL;
-    int64_t iF = (int64_t)ceil((lo_thr - out.t0) / out.dt);
-    iF = iF < 0 ? 0 : (iF > n ? n : iF);
-    while (iF - 1 >= 0 && t_at(iF - 1) >= lo_thr) --iF;
-    while (iF < n && !(t_at(iF) >= lo_thr)) ++iF;
+    int64_t iL, iF;
+    hybrid_split(out, t_hyb, Tw, iL, iF);
 
-    // scratch layout: [orbit table on `out`] [orbit table on the link grid] [links]
+    // scratch layout: [orbit table on `out`] [links of samples [lo, n)], the
+    // same table and link range as lisa_response_hybrid, so the two calls
+    // launch the same kernels on the same values
     const size_t rs = precision == LISA_MIXED ? sizeof(float) : sizeof(double);
     const int S = seg_samples(out.dt);
     const int64_t nseg = seg_count(n, S);
-    int64_t lo = n;
-    if (iF < n) {
-        double Tmax = 1.6 * orbit->L_m / kC;
-        if (orbit->delay == LISA_DELAY_LINEAR) {
-            const double span = fmax(fabs(out.t0 - orbit->t_ref), fabs(out.t0 + n * out.dt - orbit->t_ref)) + 1e3;
-            Tmax = 0.0;
-            for (int q = 0; q < 6; ++q) Tmax = fmax(Tmax, fabs(orbit->lin_T0[q]) + fabs(orbit->lin_Tdot[q]) * span);
-        } else if (orbit->kind == LISA_ORB_KEPLER2) {
-            Tmax *= 1.0 + 60.0 * fabs(orbit->kepler_tilt - 1.0);
-        }
-        lo = iF - (int64_t)ceil(8.0 * Tmax / out.dt) - 40;
-        lo = lo < 0 ? 0 : lo;
-    }
-    const lisa_grid yg{out.t0 + (double)lo * out.dt, out.dt, n - lo};
-    const int64_t nseg_y = yg.n > 0 ? seg_count(yg.n, S) : 0;
+    const int64_t lo = iF < n ? hybrid_links_begin(orbit, out, iF) : n;
     const size_t b_tab = align256(sizeof(double) * (size_t)nseg * kNQ * kNC);
-    const size_t b_taby = align256(sizeof(double) * (size_t)nseg_y * kNQ * kNC);
-    const size_t b_y = align256(6 * (size_t)yg.n * rs);
-    const size_t need = b_tab + b_taby + b_y;
+    const size_t b_y = align256(6 * (size_t)(n - lo) * rs);
+    const size_t need = b_tab + b_y;
     if (need > (size_t)LISA_STATIC_SCRATCH_BYTES) {
         set_error("lisa_response_hybrid_static needs %zu bytes of scratch for this call; the static scratch holds "
                   "%zu bytes (LISA_STATIC_SCRATCH_BYTES): use lisa_response_hybrid or a shorter grid",
@@ -130,12 +112,10 @@ extern "C" int lisa_response_hybrid_static(const lisa_orbit* orbit, const lisa_s
     int rc = static_scratch_address(&base);
     if (rc) return rc;
     double* coef = (double*)base;
-    double* coef_y = (double*)((char*)base + b_tab);
-    void* y = (char*)base + b_tab + b_taby;
+    void* y = (char*)base + b_tab;
 
     cudaStream_t st = (cudaStream_t)stream;
-    const OrbitDev od = make_orbit_dev(*orbit);
-    rc = build_seg_table(od, out, S, coef, nseg, st);
+    rc = build_seg_table(make_orbit_dev(*orbit), out, S, coef, nseg, st);
     if (rc) return rc;
     const SegTable tab{coef, nseg, S, out.t0, out.dt};
     const SkyDev skyd = make_sky_dev(*sky);
@@ -153,13 +133,10 @@ extern "C" int lisa_response_hybrid_static(const lisa_orbit* orbit, const lisa_s
         if (rc) return rc;
     }
     if (iF < n) {
-        rc = build_seg_table(od, yg, S, coef_y, nseg_y, st);
-        if (rc) return rc;
-        const SegTable taby{coef_y, nseg_y, S, yg.t0, yg.dt};
-        rc = launch_links_full(taby, skyd, h_grid, hp, hc, precision, yg, y, 0, yg.n, st);
+        rc = launch_links_full(tab, skyd, h_grid, hp, hc, precision, out, y, lo, n, st, lo);
         if (rc) return rc;
         BlendSpec bl{1, t_hyb, sg, -1.0, iF, iL + 1};
-        rc = launch_tdi(tab, yg, y, precision, tdi_gen, LISA_FROZEN, channels, out, xyz, iF, n, bl, st);
+        rc = launch_tdi(tab, out, y, precision, tdi_gen, LISA_FROZEN, channels, out, xyz, iF, n, bl, st, lo);
         if (rc) return rc;
     }
     return LISA_OK;

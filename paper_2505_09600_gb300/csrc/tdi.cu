@@ -42,14 +42,19 @@ __global__ void __launch_bounds__(kTile) tdi_kernel(TdiArgs a)
 }
 
 int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int precision, int gen, int mode, int channels,
-               const lisa_grid& og, void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st)
+               const lisa_grid& og, void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st,
+               int64_t y0)
 {
     if (i_end <= i_begin) return LISA_OK;
     TdiArgs a;
     a.tab = tab;
+    // y holds the link grid's samples [y0, yg.n): the map to it is the map to
+    // the whole grid shifted by the integer y0 (exact)
     a.ym = make_grid_map(og, yg);
+    a.ym.jb -= y0;
+    a.ym.n_in = yg.n - y0;
     a.y = y;
-    a.ny = yg.n;
+    a.ny = yg.n - y0;
     a.xyz = xyz;
     a.nout = og.n;
     a.nterm = (gen == LISA_TDI20) ? 16 : 8;

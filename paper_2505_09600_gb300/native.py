@@ -131,6 +131,8 @@ _SIGS = {
     "lisa_profile_enable": (C.c_int, [C.c_int]),
     "lisa_profile_query": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "lisa_launch_count": (C.c_int64, []),
+    "lisa_peak_fma_blocks": (C.c_int, [C.c_int, C.POINTER(C.c_int64)]),
+    "lisa_peak_fma": (C.c_int, [C.c_int, C.c_int64, C.c_int, _P, C.POINTER(C.c_double), _P]),
     "lisa_device_status": (C.c_int, [C.POINTER(C.c_uint), C.c_int]),
     "lisa_selftest_wait_timeout": (C.c_int, [_P]),
     "lisa_response_hybrid": (C.c_int, [C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid, _P, _P, C.c_int,
@@ -432,6 +434,30 @@ def lisa_profile_query(name=None):
 
 def lisa_launch_count():
     return load().lisa_launch_count()
+
+
+def lisa_peak_fma(kind, iters, blocks_per_sm=8, stream=None, reps=5):
+    """Measured fused multiply-add throughput (TFLOP/s) of the FP64 (kind 0),
+    FP32 (kind 1) or packed-pair FP32 (kind 2) pipe: the best of `reps`
+    launches after one warm-up, each timed with CUDA events on `stream`."""
+    import torch
+    nb = C.c_int64()
+    _check(load().lisa_peak_fma_blocks(int(blocks_per_sm), C.byref(nb)), "lisa_peak_fma_blocks")
+    sink = torch.empty(nb.value * 256, device="cuda", dtype=torch.float64 if kind == 0 else torch.float32)
+    st = torch.cuda.current_stream() if stream is None else stream
+    flop = C.c_double()
+    best = None
+    for r in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        _check(load().lisa_peak_fma(int(kind), int(iters), int(blocks_per_sm), C.c_void_p(sink.data_ptr()),
+                                    C.byref(flop), C.c_void_p(st.cuda_stream)), "lisa_peak_fma")
+        b.record(st)
+        b.synchronize()
+        if r > 0:
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+    return flop.value / (best / 1e3) / 1e12, best
 
 
 def lisa_device_status(reset=True):
