@@ -32,6 +32,8 @@ KEPLER1, KEPLER2, STATIC = 0, 1, 2
 DELAY_LIGHTTIME, DELAY_ANALYTIC, DELAY_EQUAL, DELAY_LINEAR = 0, 1, 2, 3
 FROZEN, NESTED = 0, 1
 LFA_UNEQUAL, LFA_EQUAL, LFA_BACKWARD, LFA_FORWARD = 0, 1, 2, 3   # central (2 kinds); App. B non-central
+LFA_NLO = 4       # central, next-to-leading order (App. B series and Michelson expansions)
+LFA_STRAIN = 5    # strain-derivative form with the constellation centre (Sec. III)
 C_LIGHT = 299792458.0
 AU = 1.495978707e11
 YEAR = 31557600.0
@@ -125,6 +127,11 @@ def _load():
                 "og_tdi_full_direct": (None, [po, ps, Grid, pd, pd, Grid, i32, i32, Grid, pd, pi64, i64]),
                 "og_aet": (None, [pd, pd, i64]),
                 "og_hdot": (None, [Grid, pd, pd]),
+                "og_d2": (None, [Grid, pd, pd]),
+                "og_z_lfa_nlo": (None, [po, ps, Grid, pd, pd, pd, pd, i32, Grid, pd, pi64, i64]),
+                "og_tdi_lfa_direct_nlo": (None, [po, ps, Grid, pd, pd, pd, pd, i32, Grid, pd, pi64, i64]),
+                "og_tdi_strain": (None, [po, ps, Grid, pd, pd, i32, Grid, pd, pi64, i64]),
+                "og_links_lfa_own_nlo": (None, [po, ps, Grid, pd, pd, pd, pd, Grid, pd, pi64, i64]),
                 "og_z_lfa": (None, [po, ps, Grid, pd, pd, i32, i32, Grid, pd, pi64, i64]),
                 "og_tdi_lfa_from_z": (None, [po, Grid, pd, i32, i32, pd, pi64, i64]),
                 "og_tdi_lfa_direct": (None, [po, ps, Grid, pd, pd, i32, i32, Grid, pd, pi64, i64]),
@@ -290,16 +297,53 @@ def hdot(grid, h):
     return out
 
 
+def d2(grid, x):
+    """5-point second derivative on the grid, zero outside (og_d2)."""
+    x = _arr(x)
+    out = np.zeros_like(x)
+    _load().og_d2(_g(grid), _pd(x), _pd(out))
+    return out
+
+
 def z_lfa(orbit, sky, hgrid, hp, hc, gen, kind, outgrid, idx=None, hd=None):
-    """TDI-shifted LFA link series z[6, m] (X_a, X_b, Y_a, Y_b, Z_a, Z_b)."""
+    """TDI-shifted LFA link series z[6, m] (X_a, X_b, Y_a, Y_b, Z_a, Z_b).
+    kind LFA_NLO adds the next-to-leading link term (third derivative of h
+    = og_d2 of hdot); LFA_STRAIN has no z series."""
+    if kind == LFA_STRAIN:
+        raise ValueError("the strain-derivative form has no z series")
     hdp, hdc = (hdot(hgrid, hp), hdot(hgrid, hc)) if hd is None else hd
     go = _g(outgrid)
     ix, pix, nix = _idx(idx)
     m = nix if ix is not None else go.n
     z = np.zeros((6, m))
+    if kind == LFA_NLO:
+        h3p, h3c = d2(hgrid, hdp), d2(hgrid, hdc)
+        _load().og_z_lfa_nlo(C.byref(orbit.c()), C.byref(_sky(*sky)), _g(hgrid), _pd(hdp), _pd(hdc), _pd(h3p),
+                             _pd(h3c), gen, go, _pd(z), pix, nix)
+        return z
     _load().og_z_lfa(C.byref(orbit.c()), C.byref(_sky(*sky)), _g(hgrid), _pd(hdp), _pd(hdc),
                      gen, kind, go, _pd(z), pix, nix)
     return z
+
+
+def strain_series(hgrid, h, gen, hd=None):
+    """The strain derivative the strain-derivative form interpolates:
+    d2h/dt2 = hdot of hdot (TDI 1.5), d3h/dt3 = og_d2 of hdot (TDI 2.0)."""
+    hd = hdot(hgrid, h) if hd is None else hd
+    return hdot(hgrid, hd) if gen == 15 else d2(hgrid, hd)
+
+
+def tdi_strain(orbit, sky, hgrid, hp, hc, gen, outgrid, idx=None, hd=None):
+    """X, Y, Z of the strain-derivative form (og_tdi_strain)."""
+    hdp, hdc = (None, None) if hd is None else hd
+    sp, sc = strain_series(hgrid, hp, gen, hdp), strain_series(hgrid, hc, gen, hdc)
+    go = _g(outgrid)
+    ix, pix, nix = _idx(idx)
+    m = nix if ix is not None else go.n
+    xyz = np.zeros((3, m))
+    _load().og_tdi_strain(C.byref(orbit.c()), C.byref(_sky(*sky)), _g(hgrid), _pd(sp), _pd(sc), gen, go,
+                          _pd(xyz), pix, nix)
+    return xyz
 
 
 def tdi_lfa_from_z(orbit, zgrid, z, gen, kind, idx=None):
@@ -317,8 +361,15 @@ def tdi_lfa_direct(orbit, sky, hgrid, hp, hc, gen, kind, outgrid, idx, hd=None):
         hdp, hdc = hdot(hgrid, hp), hdot(hgrid, hc)
     else:
         hdp, hdc = hd
+    if kind == LFA_STRAIN:
+        return tdi_strain(orbit, sky, hgrid, hp, hc, gen, outgrid, idx, hd=(hdp, hdc))
     ix, pix, nix = _idx(idx)
     xyz = np.zeros((3, nix))
+    if kind == LFA_NLO:
+        h3p, h3c = d2(hgrid, hdp), d2(hgrid, hdc)
+        _load().og_tdi_lfa_direct_nlo(C.byref(orbit.c()), C.byref(_sky(*sky)), _g(hgrid), _pd(hdp), _pd(hdc),
+                                      _pd(h3p), _pd(h3c), gen, _g(outgrid), _pd(xyz), pix, nix)
+        return xyz
     _load().og_tdi_lfa_direct(C.byref(orbit.c()), C.byref(_sky(*sky)), _g(hgrid), _pd(hdp), _pd(hdc),
                               gen, kind, _g(outgrid), _pd(xyz), pix, nix)
     return xyz
@@ -326,17 +377,27 @@ def tdi_lfa_direct(orbit, sky, hgrid, hp, hc, gen, kind, outgrid, idx, hd=None):
 
 def response_lfa(orbit, sky, hgrid, hp, hc, gen=20, kind=LFA_UNEQUAL, channels="xyz", outgrid=None):
     go = _g(outgrid) if outgrid is not None else _g(hgrid)
+    if kind == LFA_STRAIN:
+        xyz = tdi_strain(orbit, sky, hgrid, hp, hc, gen, go)
+        return aet(xyz) if channels == "aet" else xyz
     z = z_lfa(orbit, sky, hgrid, hp, hc, gen, kind, go)
     xyz = tdi_lfa_from_z(orbit, go, z, gen, kind)
     return aet(xyz) if channels == "aet" else xyz
 
 
 def links_lfa_own(orbit, sky, hgrid, hp, hc, kind, ygrid, idx=None):
+    if kind == LFA_STRAIN:
+        raise ValueError("the strain-derivative form has no link series")
     hdp, hdc = hdot(hgrid, hp), hdot(hgrid, hc)
     g = _g(ygrid)
     ix, pix, nix = _idx(idx)
     m = nix if ix is not None else g.n
     y = np.zeros((6, m))
+    if kind == LFA_NLO:
+        h3p, h3c = d2(hgrid, hdp), d2(hgrid, hdc)
+        _load().og_links_lfa_own_nlo(C.byref(orbit.c()), C.byref(_sky(*sky)), _g(hgrid), _pd(hdp), _pd(hdc),
+                                     _pd(h3p), _pd(h3c), g, _pd(y), pix, nix)
+        return y
     _load().og_links_lfa_own(C.byref(orbit.c()), C.byref(_sky(*sky)), _g(hgrid), _pd(hdp), _pd(hdc),
                              kind, g, _pd(y), pix, nix)
     return y

@@ -291,6 +291,7 @@ typedef struct {
     double k[3], u[3], v[3], c2p, s2p;
     og_grid gh;
     const double *hp, *hc;
+    const double *h3p, *h3c;   /* LFA next-to-leading order: third derivatives of h on gh */
 } og_src;
 
 static void og_src_init(og_src* S, const og_orbit* o, const og_sky* sky, og_grid gh, const double* hp, const double* hc)
@@ -302,6 +303,8 @@ static void og_src_init(og_src* S, const og_orbit* o, const og_sky* sky, og_grid
     S->gh = gh;
     S->hp = hp;
     S->hc = hc;
+    S->h3p = NULL;
+    S->h3c = NULL;
 }
 
 static double og_link_full_at(const og_src* S, og_grid gy, int64_t i, int li)
@@ -511,6 +514,19 @@ void og_hdot(og_grid g, const double* h, double* hd)
     }
 }
 
+/* 5-point central second derivative on the grid (the stencil of the TDI 2.0
+ * channels), zero outside the grid:
+ *   x''_i = (-x_{i-2} + 16 x_{i-1} - 30 x_i + 16 x_{i+1} - x_{i+2}) / (12 dt^2).
+ * Applied to hdot it gives the third derivative of h that the next-to-leading
+ * terms need; hdot once more gives the second derivative. */
+void og_d2(og_grid g, const double* x, double* out)
+{
+    for (int64_t i = 0; i < g.n; ++i) {
+        out[i] = (-og_at(x, g.n, i - 2) + 16.0 * og_at(x, g.n, i - 1) - 30.0 * og_at(x, g.n, i)
+                  + 16.0 * og_at(x, g.n, i + 1) - og_at(x, g.n, i + 2)) / (12.0 * g.dt * g.dt);
+    }
+}
+
 static double og_arm(const og_orbit* o, int li, double t, int kind)
 {
     return (kind == OG_LFA_EQUAL) ? o->L_m / OG_C : og_light_time(o, li, t);
@@ -521,7 +537,7 @@ static double og_arm(const og_orbit* o, int li, double t, int kind)
  * expansion point tau_eps = t' - delta_s + eps (delta_s - delta_r), with
  * delta_s = T_l + k.R_s/c and delta_r = k.R_r/c (App. B): eps = 1/2 for the
  * central kinds (Eq. tau_t_dependence), 0 for backward, 1 for forward. */
-static double og_link_lfa_at(const og_src* S, og_grid gout, int64_t i, double a, int li, int kind)
+static double og_link_lfa_at(const og_src* S, og_grid gout, int64_t i, double a, int li, int kind, int pair_mean)
 {
     const double tp = (gout.t0 + (double)i * gout.dt) - a;
     double Rs[3], Rr[3], n[3];
@@ -537,8 +553,24 @@ static double og_link_lfa_at(const og_src* S, og_grid gout, int64_t i, double a,
     if (kind == OG_LFA_BACKWARD) d_tau = a + delta_s;
     else if (kind == OG_LFA_FORWARD) d_tau = a + delta_r;
     else d_tau = a + 0.5 * T + 0.5 * (og_dot(S->k, Rs) + og_dot(S->k, Rr)) / OG_C;
-    const double dp = og_interp_at(S->hp, S->gh, gout, i, d_tau);
-    const double dc = og_interp_at(S->hc, S->gh, gout, i, d_tau);
+    double dp = og_interp_at(S->hp, S->gh, gout, i, d_tau);
+    double dc = og_interp_at(S->hc, S->gh, gout, i, d_tau);
+    if (kind == OG_LFA_NLO) {
+        /* m = 1 term of the central series (App. B, Eq. yslr_with_tau_derivatives):
+         * -(T/2) (1/3!) [(T/2)(1 - k.n)]^2 d3H/dtau3, with xi at t' as in the
+         * leading term and d/dtau read as d/dt.  In the TDI-shifted series the
+         * link stands for itself and its reverse (y_123 for y_123 and y_3-21:
+         * the channels of Eqs. X15_nonequal and X20_nonequal rest on link
+         * reversal), whose leading terms coincide but whose m = 1 terms carry
+         * (1 - k.n) and (1 + k.n): the channels take their mean,
+         * (T/2)^2 (1 + (k.n)^2) / 6 (pair_mean).  A link at its own time
+         * (og_links_lfa_own) keeps its own (1 - k.n). */
+        const double kn = og_dot(S->k, n);
+        const double kap = pair_mean ? 0.25 * T * T * (1.0 + kn * kn) / 6.0
+                                     : 0.25 * T * T * (1.0 - kn) * (1.0 - kn) / 6.0;
+        dp += kap * og_interp_at(S->h3p, S->gh, gout, i, d_tau);
+        dc += kap * og_interp_at(S->h3c, S->gh, gout, i, d_tau);
+    }
     return -0.5 * T * (xp * (dp * S->c2p - dc * S->s2p) + xc * (dp * S->s2p + dc * S->c2p));
 }
 
@@ -561,8 +593,8 @@ static void og_z_sample(const og_src* S, int gen, int kind, og_grid gout, int64_
         double sa, sb;
         if (gen == 20) { sa = 2.0 * Ta + 1.5 * Tb; sb = 2.0 * Tb + 1.5 * Ta; }
         else { sa = Ta + 0.5 * Tb; sb = Tb + 0.5 * Ta; }
-        z6[2 * ch] = og_link_lfa_at(S, gout, i, sa, la, kind);
-        z6[2 * ch + 1] = og_link_lfa_at(S, gout, i, sb, lb, kind);
+        z6[2 * ch] = og_link_lfa_at(S, gout, i, sa, la, kind, 1);
+        z6[2 * ch + 1] = og_link_lfa_at(S, gout, i, sb, lb, kind, 1);
     }
 }
 
@@ -595,10 +627,30 @@ static void og_tdi_lfa_sample(const og_orbit* o, const double* zwin /*[6][5], i-
             const double d2a = (-za[0] + 16.0 * za[1] - 30.0 * za[2] + 16.0 * za[3] - za[4]) / (12.0 * dt * dt);
             const double d2b = (-zb[0] + 16.0 * zb[1] - 30.0 * zb[2] + 16.0 * zb[3] - zb[4]) / (12.0 * dt * dt);
             xyz[ch] = 8.0 * (Ta + Tb) * (Ta * d2a - Tb * d2b);
+            if (kind == OG_LFA_NLO) {
+                /* next term of the TDI 2.0 expansion: the l = +-2 terms of X are
+                 * (1 + D_Tb)(1 - D_2Ta)(1 - D_2(Ta+Tb)) y, i.e. around their centre
+                 * 2cosh(s Tb/2) 2sinh(s Ta) 2sinh(s (Ta+Tb)) in the derivative s:
+                 * 8 Ta (Ta+Tb) [s^2 + s^4 (Tb^2/8 + Ta^2/6 + (Ta+Tb)^2/6)]; l = +-3
+                 * alike with Ta <-> Tb.  Fourth derivative: 5-point stencil. */
+                const double d4a = (za[0] - 4.0 * za[1] + 6.0 * za[2] - 4.0 * za[3] + za[4]) / (dt * dt * dt * dt);
+                const double d4b = (zb[0] - 4.0 * zb[1] + 6.0 * zb[2] - 4.0 * zb[3] + zb[4]) / (dt * dt * dt * dt);
+                const double ka = Tb * Tb / 8.0 + Ta * Ta / 6.0 + (Ta + Tb) * (Ta + Tb) / 6.0;
+                const double kb = Ta * Ta / 8.0 + Tb * Tb / 6.0 + (Ta + Tb) * (Ta + Tb) / 6.0;
+                xyz[ch] += 8.0 * (Ta + Tb) * (Ta * ka * d4a - Tb * kb * d4b);
+            }
         } else {
             const double d1a = (za[0] - 8.0 * za[1] + 8.0 * za[3] - za[4]) / (12.0 * dt);
             const double d1b = (zb[0] - 8.0 * zb[1] + 8.0 * zb[3] - zb[4]) / (12.0 * dt);
             xyz[ch] = 4.0 * (Ta * d1a - Tb * d1b);
+            if (kind == OG_LFA_NLO) {
+                /* TDI 1.5: (1 + D_Tb)(1 - D_2Ta) y around its centre is
+                 * 2cosh(s Tb/2) 2sinh(s Ta) = 4 Ta [s + s^3 (Ta^2/6 + Tb^2/8)];
+                 * third derivative: 5-point stencil */
+                const double d3a = (-za[0] + 2.0 * za[1] - 2.0 * za[3] + za[4]) / (2.0 * dt * dt * dt);
+                const double d3b = (-zb[0] + 2.0 * zb[1] - 2.0 * zb[3] + zb[4]) / (2.0 * dt * dt * dt);
+                xyz[ch] += 4.0 * (Ta * (Ta * Ta / 6.0 + Tb * Tb / 8.0) * d3a - Tb * (Tb * Tb / 6.0 + Ta * Ta / 8.0) * d3b);
+            }
         }
     }
 }
@@ -640,6 +692,115 @@ void og_tdi_lfa_direct(const og_orbit* o, const og_sky* sky, og_grid gh, const d
     }
 }
 
+/* Next-to-leading order (kind OG_LFA_NLO): the z series with the m = 1 link
+ * term (h3: third derivative of h on the h grid, og_d2 of hdot), and sampled
+ * channels straight from hdot and h3.  The channel NLO terms are applied by
+ * og_tdi_lfa_from_z / og_tdi_lfa_sample for this kind. */
+void og_z_lfa_nlo(const og_orbit* o, const og_sky* sky, og_grid gh, const double* hdp, const double* hdc,
+                  const double* h3p, const double* h3c, int gen, og_grid gout, double* z, const int64_t* idx,
+                  int64_t nidx)
+{
+    og_src S;
+    og_src_init(&S, o, sky, gh, hdp, hdc);
+    S.h3p = h3p;
+    S.h3c = h3c;
+    const int64_t m = idx ? nidx : gout.n;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < m; ++q) {
+        double z6[6];
+        og_z_sample(&S, gen, OG_LFA_NLO, gout, idx ? idx[q] : q, z6);
+        for (int c = 0; c < 6; ++c) z[c * m + q] = z6[c];
+    }
+}
+
+void og_tdi_lfa_direct_nlo(const og_orbit* o, const og_sky* sky, og_grid gh, const double* hdp, const double* hdc,
+                           const double* h3p, const double* h3c, int gen, og_grid gout, double* xyz,
+                           const int64_t* idx, int64_t nidx)
+{
+    og_src S;
+    og_src_init(&S, o, sky, gh, hdp, hdc);
+    S.h3p = h3p;
+    S.h3c = h3c;
+    const int64_t m = idx ? nidx : gout.n;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = idx ? idx[q] : q;
+        double zw[30], z6[6], v[3];
+        for (int s5 = 0; s5 < 5; ++s5) {
+            const int64_t ii = i - 2 + s5;
+            if (ii < 0 || ii >= gout.n) { for (int c = 0; c < 6; ++c) zw[c * 5 + s5] = 0.0; continue; }
+            og_z_sample(&S, gen, OG_LFA_NLO, gout, ii, z6);
+            for (int c = 0; c < 6; ++c) zw[c * 5 + s5] = z6[c];
+        }
+        og_tdi_lfa_sample(o, zw, gen, OG_LFA_NLO, gout, i, v);
+        for (int ch = 0; ch < 3; ++ch) xyz[ch * m + q] = v[ch];
+    }
+}
+
+/* Links at their own time with the next-to-leading term (kind OG_LFA_NLO),
+ * each with its own (1 - k.n_l). */
+void og_links_lfa_own_nlo(const og_orbit* o, const og_sky* sky, og_grid gh, const double* hdp, const double* hdc,
+                          const double* h3p, const double* h3c, og_grid gy, double* y, const int64_t* idx,
+                          int64_t nidx)
+{
+    og_src S;
+    og_src_init(&S, o, sky, gh, hdp, hdc);
+    S.h3p = h3p;
+    S.h3c = h3c;
+    const int64_t m = idx ? nidx : gy.n;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = idx ? idx[q] : q;
+        for (int li = 0; li < 6; ++li) y[li * m + q] = og_link_lfa_at(&S, gy, i, 0.0, li, OG_LFA_NLO, 0);
+    }
+}
+
+/* Strain-derivative form with the constellation centre (Sec. III, Eqs.
+ * X15_with_strain_derivatives, X20_with_strain_derivatives): equal constant
+ * arms T = L/c, k.(R_s + R_r)/2c replaced by k.R0/c with R0 the centre of the
+ * constellation (the mean of the three spacecraft positions), antenna
+ * patterns at t:
+ *   X1.5(t) = 2 T^2 [(xi+_3 - xi+_2) d2h+SSB/dt2 + (xix_3 - xix_2) d2hxSSB/dt2](t - 2T - k.R0/c)
+ *   X2.0(t) = 8 T^3 [(xi+_3 - xi+_2) d3h+SSB/dt3 + (xix_3 - xix_2) d3hxSSB/dt3](t - 4T - k.R0/c)
+ * xi_2, xi_3 of the links +2 (y_123) and +3 (y_231); Y, Z cyclic.  sp, sc
+ * hold the derivative of h on the h grid (the 5-point first derivative
+ * applied twice for TDI 1.5; the second-derivative stencil applied to hdot
+ * for TDI 2.0), interpolated with the 32-point Lagrange weights. */
+void og_tdi_strain(const og_orbit* o, const og_sky* sky, og_grid gh, const double* sp, const double* sc, int gen,
+                   og_grid gout, double* xyz, const int64_t* idx, int64_t nidx)
+{
+    og_src S;
+    og_src_init(&S, o, sky, gh, sp, sc);
+    const double T = o->L_m / OG_C;
+    const int64_t m = idx ? nidx : gout.n;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = idx ? idx[q] : q;
+        const double t = gout.t0 + (double)i * gout.dt;
+        double R0[3] = {0.0, 0.0, 0.0};
+        for (int sc3 = 0; sc3 < 3; ++sc3) {
+            double R[3];
+            og_position(o, sc3, t, R);
+            for (int d = 0; d < 3; ++d) R0[d] += R[d] / 3.0;
+        }
+        const double shift = (gen == 20 ? 4.0 : 2.0) * T + og_dot(S.k, R0) / OG_C;
+        const double dp = og_interp_at(sp, gh, gout, i, shift);
+        const double dc = og_interp_at(sc, gh, gout, i, shift);
+        const double Hp = dp * S.c2p - dc * S.s2p, Hc = dp * S.s2p + dc * S.c2p;   /* SSB frame */
+        double xp[6], xc[6];
+        for (int li = 0; li < 6; li += 2) {
+            double n[3];
+            og_link_vector(o, li, t, og_light_time(o, li, t), n);
+            og_antenna(S.u, S.v, n, &xp[li], &xc[li]);
+        }
+        const double pref = gen == 20 ? 8.0 * T * T * T : 2.0 * T * T;
+        for (int ch = 0; ch < 3; ++ch) {
+            const int l3 = og_perm(4, ch), l2 = og_perm(2, ch);
+            xyz[ch * m + q] = pref * ((xp[l3] - xp[l2]) * Hp + (xc[l3] - xc[l2]) * Hc);
+        }
+    }
+}
+
 /* LFA links at their own time t (no TDI shift) from the LFA link formula
  * (Sec. III, Eq. yslr_strain_derivatives) applied to each of the six links
  * with its own T_l, n_l and end positions.  (The paper's LFA channels only
@@ -654,7 +815,7 @@ void og_links_lfa_own(const og_orbit* o, const og_sky* sky, og_grid gh, const do
     for (int64_t q = 0; q < m; ++q) {
         const int64_t i = idx ? idx[q] : q;
         for (int li = 0; li < 6; ++li)
-            y[li * m + q] = og_link_lfa_at(&S, gy, i, 0.0, li, kind);
+            y[li * m + q] = og_link_lfa_at(&S, gy, i, 0.0, li, kind, 0);
     }
 }
 

@@ -18,7 +18,12 @@ enum { OG_FROZEN = 0, OG_NESTED = 1 };
 /* LFA kinds: central expansion point (unequal or equal arms), and the
  * non-central variants of App. B ("Other finite differences"): backward
  * (epsilon = 0, tau_0 = t - delta_s) and forward (epsilon = 1, tau_1 = t - delta_r). */
-enum { OG_LFA_UNEQUAL = 0, OG_LFA_EQUAL = 1, OG_LFA_BACKWARD = 2, OG_LFA_FORWARD = 3 };
+enum { OG_LFA_UNEQUAL = 0, OG_LFA_EQUAL = 1, OG_LFA_BACKWARD = 2, OG_LFA_FORWARD = 3,
+       /* App. B next-to-leading order of the central expansion (link and channel terms) */
+       OG_LFA_NLO = 4,
+       /* Sec. III strain-derivative form with the constellation centre R0 (Eqs.
+        * X15_with_strain_derivatives, X20_with_strain_derivatives) */
+       OG_LFA_STRAIN = 5 };
 
 typedef struct {
     int32_t kind, delay;
@@ -53,6 +58,18 @@ void og_tdi_full_direct(const og_orbit* o, const og_sky* sky, og_grid gh, const 
                         og_grid gy, int gen, int mode, og_grid gout, double* xyz, const int64_t* idx, int64_t nidx);
 void og_aet(const double* xyz, double* aet, int64_t n);
 void og_hdot(og_grid g, const double* h, double* hd);
+void og_d2(og_grid g, const double* x, double* out);
+void og_z_lfa_nlo(const og_orbit* o, const og_sky* sky, og_grid gh, const double* hdp, const double* hdc,
+                  const double* h3p, const double* h3c, int gen, og_grid gout, double* z, const int64_t* idx,
+                  int64_t nidx);
+void og_tdi_lfa_direct_nlo(const og_orbit* o, const og_sky* sky, og_grid gh, const double* hdp, const double* hdc,
+                           const double* h3p, const double* h3c, int gen, og_grid gout, double* xyz,
+                           const int64_t* idx, int64_t nidx);
+void og_links_lfa_own_nlo(const og_orbit* o, const og_sky* sky, og_grid gh, const double* hdp, const double* hdc,
+                          const double* h3p, const double* h3c, og_grid gy, double* y, const int64_t* idx,
+                          int64_t nidx);
+void og_tdi_strain(const og_orbit* o, const og_sky* sky, og_grid gh, const double* sp, const double* sc, int gen,
+                   og_grid gout, double* xyz, const int64_t* idx, int64_t nidx);
 void og_z_lfa(const og_orbit* o, const og_sky* sky, og_grid gh, const double* hdp, const double* hdc,
               int gen, int kind, og_grid gout, double* z, const int64_t* idx, int64_t nidx);
 void og_tdi_lfa_from_z(const og_orbit* o, og_grid gz, const double* z, int gen, int kind,

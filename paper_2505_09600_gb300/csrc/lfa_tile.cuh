@@ -18,6 +18,10 @@ constexpr int kWinP = kWinH + 8;   // planar h buffers: room for 16-byte alignme
 #define LISA_LFA_UNROLL 2
 #endif
 constexpr int kLfaUnroll = LISA_LFA_UNROLL;   // series per unrolled step of the mixed z loop
+#ifndef LISA_LFA_DUNROLL
+#define LISA_LFA_DUNROLL 1
+#endif
+constexpr int kLfaDUnroll = LISA_LFA_DUNROLL;   // series per unrolled step of the differenced channel loop
 #ifndef LISA_LFA_PAIR
 #define LISA_LFA_PAIR 1   // staged z loop: 1 = a thread's two samples share packed weight instructions, 2 = adjacent samples also share the taps
 #endif
@@ -169,6 +173,7 @@ struct LfaWin {
     int64_t wlo, a0;
     int wlen, nh;
     int bulk;                 // filled by an asynchronous bulk copy
+    int diff;                 // mixed form: the differenced window may be formed (interior, unit ratio)
     int jrel[6];              // mixed form: J_c - wlo - 15
 };
 
@@ -619,15 +624,20 @@ inline int lfa_group(double dt)
 // ---------------------------------------------------------------------------
 constexpr int kSub2 = 2 * kTile;          // samples per sub-block
 constexpr int kWin2 = kSub2 + 384;        // hdot window of a sub-block
-constexpr int kWinP2 = kWin2 + 8;         // planar h buffers (16-byte alignment slack)
+constexpr int kWinP2 = kWin2 + 16;        // planar h buffers: 4-sample margins and 16-byte alignment slack
 constexpr int kZW2 = kSub2 + 4;           // z of a sub-block and its 2-sample halos
 constexpr int kMaxSub2 = 4;               // sub-blocks per group (groups of up to 8 tiles)
 
 struct Lfa2Smem {
     TileGeo g;
     alignas(16) float hb[2][2][kWinP2];   // h+ and hx windows, two buffers
-    float2 dw[kWin2];                     // hdot window (interleaved pairs)
-    float zs[6][kZW2];
+    float2 dw[kWin2];                     // hdot window, or the differenced window S (interleaved pairs)
+    float2 qw[kWin2];                     // differenced form: the B-term differences Q (interleaved pairs)
+    union {
+        float zs[6][kZW2];                // z values of a sub-block (z-series form)
+        float4 d2[kWin2 + 8];             // second differences of h as (hi, lo) pairs (differenced form)
+        float xacc[6][kTile];             // differenced form: channel sums of a thread's two samples
+    };
     LfaWin win[kMaxSub2];
     uint64_t bar[2];                      // completion barriers of the bulk copies
     int64_t jends[kMaxSub2][12];
@@ -638,6 +648,7 @@ struct Lfa2Smem {
     Cubic cu[kRows];
     float inv_half, inv_dt;
     float barg_c, barg_d;
+    unsigned int smooth[3];               // differenced form: window maxima of |D3 h|, |D7 h|, |h| (float bits)
 };
 
 // Windows of the nsb sub-blocks starting at tile t0 (after the prologue at
@@ -665,13 +676,18 @@ static __device__ void lfa2_windows(const LfaArgs& a, int64_t t0, int nsb, int64
         w.wlo = lo - 15 - 3;
         const int64_t len = (hi + 16 + 3) - w.wlo + 1;
         w.wlen = (len + 4 <= kWin2) ? (int)len : 0;
-        const int64_t s0 = w.wlo - 2, s1 = w.wlo + w.wlen + 2;
+        // h on [wlo - 4, wlo + wlen + 4): the 5-point hdot needs 2 samples each
+        // side, the differenced window (9-point composite stencils) 4
+        const int64_t s0 = w.wlo - 4, s1 = w.wlo + w.wlen + 4;
         const int64_t a0 = s0 - (((s0 % 4) + 4) % 4);
         const int64_t a1 = s1 + (((4 - s1 % 4) % 4 + 4) % 4);
         const bool bulk = a.h_aligned && w.wlen > 0 && a0 >= 0 && a1 <= a.hm.n_in && a1 - a0 <= kWinP2;
         w.bulk = bulk ? 1 : 0;
         w.a0 = bulk ? a0 : s0;
-        w.nh = bulk ? (int)(a1 - a0) : (w.wlen > 0 ? w.wlen + 4 : 0);
+        w.nh = bulk ? (int)(a1 - a0) : (w.wlen > 0 ? w.wlen + 8 : 0);
+        // differenced form: the composite stencils and B-term differences of
+        // every staged element stay inside the h grid (no zero padding)
+        w.diff = a.hm.unit_rho && a.gen != kLfaOwnTime && !a.z && w.wlen > 0 && s0 >= 0 && s1 <= a.hm.n_in;
         for (int c = 0; c < 6; ++c) w.jrel[c] = w.wlen ? (int)(sm.J[c] - w.wlo) - 15 : 0;
     }
     __syncthreads();
@@ -701,11 +717,178 @@ static __device__ void lfa2_stage(const LfaArgs& a, Lfa2Smem& sm, int sb, int b)
     }
 }
 
-// Wait for buffer b (bounded for bulk copies), then form hdot of sub-block
-// sb in sm.dw.  Synchronises twice.  False (for every thread) if a wait timed
-// out: the status word is flagged after a second bounded wait for the copy
-// to land, and the block must stop.
-static __device__ bool lfa2_wait_hdot(const LfaArgs& a, Lfa2Smem& sm, int sb, int b, uint32_t parity)
+// ---------------------------------------------------------------------------
+// Differenced form of the mixed LFA channels (unit grid ratio, interior
+// sub-blocks).
+//
+// The TDI 2.0 channel takes the 5-point second difference of each z series
+// on the output grid, sum_k c_k z(t_{i+k}) with c = (-1, 16, -30, 16, -1)
+// (TDI 1.5: the first difference, d = (1, -8, 0, 8, -1)), and that difference
+// cancels to O((omega dt)^2) of z.  Formed from FP32-rounded z values, FP32
+// rounding is amplified by 1/(omega dt)^2.  Here the cancellation happens on
+// the exact FP32 inputs instead.  With z_i = F(t_i) I(x_i), I the 32-point
+// interpolant of hdot and x_i the retarded position of sample i on the h grid
+// (x_{i+k} = x_i + k (1 + a1) + a2 k^2 + O(k^3), a1, a2 from the series'
+// delay cubic), Taylor expansion in the small drift a1 ~ v/c and in the
+// orbital variation of F gives, for TDI 2.0,
+//   sum_k c_k z_{i+k} = (1 + a1)^2 F_i sum_p w_p(eps_i) S[J_i + p]
+//                       + 24 (F1 + F a2) I'(x_i) + R,
+//   S[m] = sum_k c_k hdot[m + k]   (a fixed 9-point stencil of h),
+// with F1 = dF/di and I' = dI/dx.  The dropped terms R are O(a1 (omega dt)^4)
+// ~ 1e-8, O(F'' ) ~ 1e-12 and O(a2 / (omega dt)) ~ 3e-8 of the first term
+// (the second is itself below 1e-3 of it).  For TDI 1.5:
+//   sum_k d_k z_{i+k} = (1 + a1) F_i sum_p w_p S1[J_i + p] + 12 F1 I(x_i) + R.
+// S is formed on the staged window from third (TDI 1.5: second) differences
+// of h with their rounding errors carried (two-sum): it is then exact to
+// FP32 rounding of itself, so the interpolated sum keeps FP32 relative
+// accuracy however small S is next to h.  The B-term (24 (F1 + F a2) I') needs
+// ~1e-3 relative accuracy only (it is at most ~1e-3 of the first term for f
+// >= 1e-4 Hz): I' is taken from the centred second difference Q of h at the
+// two nodes around x (I' ~ Q / dt; TDI 1.5: I ~ Q1 / dt with Q1 the half
+// central difference), interpolated linearly.
+// ---------------------------------------------------------------------------
+
+// |Seventh difference of h| from six consecutive second differences v[0..5]
+// (their fifth difference), the larger of the two polarisations (value parts
+// .x, .z).
+__device__ __forceinline__ float lfa_d7_first(const float4 (&v)[7])
+{
+    const float p = (v[5].x - v[0].x) - 5.f * (v[4].x - v[1].x) + 10.f * (v[3].x - v[2].x);
+    const float c = (v[5].z - v[0].z) - 5.f * (v[4].z - v[1].z) + 10.f * (v[3].z - v[2].z);
+    return fmaxf(fabsf(p), fabsf(c));
+}
+
+// a - b split into its rounded value and exact error (two-sum).
+__device__ __forceinline__ float2 two_diff(float a, float b)
+{
+    const float s = __fsub_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(-b, bb));
+    return make_float2(s, e);
+}
+
+// Second difference h[n+2] - 2 h[n+1] + h[n] as (value, error) pairs whose
+// sum is exact but for the final addition of the error parts.
+__device__ __forceinline__ float2 second_diff_pair(const float* P, int n)
+{
+    const float2 d0 = two_diff(P[n + 1], P[n]);
+    const float2 d1 = two_diff(P[n + 2], P[n + 1]);
+    const float2 dd = two_diff(d1.x, d0.x);
+    return make_float2(dd.x, __fadd_rn(dd.y, __fsub_rn(d1.y, d0.y)));
+}
+
+// Differenced window of a sub-block: S (TDI 2.0: sum_k c_k hdot[m+k]; TDI
+// 1.5: sum_k d_k hdot[m+k]) as interleaved pairs in sm.dw and the B-term
+// differences Q in sm.qw, for the window samples m = wlo .. wlo + wlen - 1
+// (P, C: h+, hx with P[q] at sample wlo - 4 + q).  With hdot = D1 h / (12 dt),
+// S = C(z) D(z) h / (12 dt): the composite polynomial is
+//   z^-4 (z - 1)^3 G(z),   G = (z + 1)(z^2 - 14 z + 1)(z^2 - 8 z + 1)
+//                            = 1 - 21 z + 92 z^2 + 92 z^3 - 21 z^4 + z^5
+// for TDI 2.0, and z^-4 (z - 1)^2 G1(z), G1 = (z + 1)^2 (z^2 - 8 z + 1)^2 =
+// 1 - 14 z + 35 z^2 + 100 z^3 + 35 z^4 - 14 z^5 + z^6 for TDI 1.5.
+// Synchronises twice.
+static __device__ bool lfa2_diff_window(const LfaArgs& a, Lfa2Smem& sm, const LfaWin& w, const float* P,
+                                        const float* C)
+{
+    const int wlen = w.wlen;
+    if (threadIdx.x < 3) sm.smooth[threadIdx.x] = 0u;
+    // pass 1: second differences with their errors, d2[n] for the samples
+    // wlo - 4 + n .. wlo - 2 + n, n = 0 .. wlen + 5
+    for (int n = threadIdx.x; n < wlen + 6; n += blockDim.x) {
+        const float2 p = second_diff_pair(P, n), c = second_diff_pair(C, n);
+        sm.d2[n] = make_float4(p.x, p.y, c.x, c.y);
+    }
+    __syncthreads();
+    float m3 = 0.f, m7 = 0.f, mh = 0.f;   // smoothness indicator of the window (below)
+    const float inv12dt = a.inv12dtf;
+    const bool tdi20 = a.gen == LISA_TDI20;
+    for (int k = threadIdx.x; k < wlen; k += blockDim.x) {
+        float4 v[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) v[j] = sm.d2[k + j];
+        float2 S;
+        if (tdi20) {
+            // third differences (of the value and the error parts separately:
+            // adjacent second differences are within a factor two of each other
+            // away from their zeros, so the value difference is exact there)
+            constexpr float g[6] = {1.f, -21.f, 92.f, 92.f, -21.f, 1.f};
+            float sp = 0.f, ep = 0.f, sc = 0.f, ec = 0.f;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                sp = fmaf(g[j], __fsub_rn(v[j + 1].x, v[j].x), sp);
+                ep = fmaf(g[j], __fsub_rn(v[j + 1].y, v[j].y), ep);
+                sc = fmaf(g[j], __fsub_rn(v[j + 1].z, v[j].z), sc);
+                ec = fmaf(g[j], __fsub_rn(v[j + 1].w, v[j].w), ec);
+            }
+            S = make_float2((sp + ep) * inv12dt, (sc + ec) * inv12dt);
+            // Q: centred second difference at m = d2[k + 3]
+            sm.qw[k] = make_float2(v[3].x + v[3].y, v[3].z + v[3].w);
+            // third and seventh differences of h starting at the element's first
+            // second difference (value parts): over the window's elements they
+            // cover every start once
+            m3 = fmaxf(m3, fmaxf(fabsf(v[1].x - v[0].x), fabsf(v[1].z - v[0].z)));
+            m7 = fmaxf(m7, lfa_d7_first(v));
+            mh = fmaxf(mh, fmaxf(fabsf(P[k + 4]), fabsf(C[k + 4])));
+        } else {
+            constexpr float g1[7] = {1.f, -14.f, 35.f, 100.f, 35.f, -14.f, 1.f};
+            float sp = 0.f, ep = 0.f, sc = 0.f, ec = 0.f;
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                sp = fmaf(g1[j], v[j].x, sp);
+                ep = fmaf(g1[j], v[j].y, ep);
+                sc = fmaf(g1[j], v[j].z, sc);
+                ec = fmaf(g1[j], v[j].w, ec);
+            }
+            S = make_float2((sp + ep) * inv12dt, (sc + ec) * inv12dt);
+            // Q1: half central difference at m
+            sm.qw[k] = make_float2(0.5f * (P[k + 5] - P[k + 3]), 0.5f * (C[k + 5] - C[k + 3]));
+            m3 = fmaxf(m3, fmaxf(fabsf(v[1].x - v[0].x), fabsf(v[1].z - v[0].z)));
+            m7 = fmaxf(m7, lfa_d7_first(v));
+            mh = fmaxf(mh, fmaxf(fabsf(P[k + 4]), fabsf(C[k + 4])));
+        }
+        sm.dw[k] = S;
+    }
+    // Smoothness test.  The drift terms of the expansion are exact for h
+    // smooth on the stencil scale; their error is ~ a1 times a functional
+    // of the interpolant that vanishes on quintics, which the seventh
+    // difference of h bounds.  Measured on chirps, ringdowns and an h with a
+    // jump in its derivative (FP64 emulation): error / output ~ 1e-10 at
+    // D7/D3 ~ 1e-6 (inspiral), 1e-8 at 2e-3 (ringdown at 0.2 rad per
+    // sample), 4e-5 at 9 (the derivative jump).  The form is kept where
+    // |a1| D7 <= 2.5e-6 D3 (D7/D3 <= 0.025 at a1 = 1e-4), plus the FP32
+    // rounding of h itself, which the seventh difference amplifies
+    // ~60-fold (allowance 300 ulp of the window's largest |h|: the drift
+    // terms carry it at a1 times the noise, as the exact form does).
+    // Otherwise the sub-block falls back to the z-series form.
+    const unsigned int lane = threadIdx.x & 31u;
+    const unsigned int b3 = __reduce_max_sync(0xffffffffu, __float_as_uint(m3));
+    const unsigned int b7 = __reduce_max_sync(0xffffffffu, __float_as_uint(m7));
+    const unsigned int bh = __reduce_max_sync(0xffffffffu, __float_as_uint(mh));
+    if (lane == 0) {
+        atomicMax(&sm.smooth[0], b3);
+        atomicMax(&sm.smooth[1], b7);
+        atomicMax(&sm.smooth[2], bh);
+    }
+    __syncthreads();
+    float a1max = 0.f;
+    for (int c = 0; c < 6; ++c) {
+        const SerF32& R = sm.ser[c];
+        a1max = fmaxf(a1max, fabsf(R.d1) + 2.f * fabsf(R.d2) + 3.f * fabsf(R.d3));
+    }
+    a1max *= sm.inv_half * sm.inv_dt;   // |u| <= 1 over a group
+    const float M3 = __uint_as_float(sm.smooth[0]), M7 = __uint_as_float(sm.smooth[1]);
+    const float H = __uint_as_float(sm.smooth[2]);
+    return a1max * M7 <= 2.5e-6f * M3 + a1max * 300.f * 5.9604645e-8f * H;
+}
+
+// Wait for buffer b (bounded for bulk copies), then form the window of
+// sub-block sb: with dpath, the differenced window (lfa2_diff_window), kept
+// if the window passes its smoothness test (returns 1); otherwise hdot in
+// sm.dw for the z-series form (returns 0).  Synchronises two to four times.
+// Returns -1 (for every thread) if a wait timed out: the status word is
+// flagged after a second bounded wait for the copy to land, and the block
+// must stop.
+static __device__ int lfa2_wait_hdot(const LfaArgs& a, Lfa2Smem& sm, int sb, int b, uint32_t parity, bool dpath)
 {
     const LfaWin& w = sm.win[sb];
     bool ok = true;
@@ -713,22 +896,23 @@ static __device__ bool lfa2_wait_hdot(const LfaArgs& a, Lfa2Smem& sm, int sb, in
     if (__syncthreads_or(ok ? 0 : 1)) {
         if (threadIdx.x == 0) flag_timeout(a.status);
         if (w.bulk) mbar_wait_bounded(&sm.bar[b], parity);
-        return false;
+        return -1;
     }
-    const int off = (int)(w.wlo - 2 - w.a0);
-    const float* P = sm.hb[b][0] + off;
+    const int off = (int)(w.wlo - 4 - w.a0);
+    const float* P = sm.hb[b][0] + off;   // P[q] = h+ at sample wlo - 4 + q
     const float* C = sm.hb[b][1] + off;
     const float inv12dt = a.inv12dtf;
+    if (dpath && lfa2_diff_window(a, sm, w, P, C)) return 1;   // (the decision is uniform over the block)
     for (int k = threadIdx.x; k < w.wlen; k += blockDim.x) {
         const int64_t idx = w.wlo + k;
         const bool in = (idx >= 0 && idx < a.hm.n_in);
         float2 d;
-        d.x = in ? ((P[k + 3] - P[k + 1]) * 8.f - (P[k + 4] - P[k])) * inv12dt : 0.f;
-        d.y = in ? ((C[k + 3] - C[k + 1]) * 8.f - (C[k + 4] - C[k])) * inv12dt : 0.f;
+        d.x = in ? ((P[k + 5] - P[k + 3]) * 8.f - (P[k + 6] - P[k + 2])) * inv12dt : 0.f;
+        d.y = in ? ((C[k + 5] - C[k + 3]) * 8.f - (C[k + 6] - C[k + 2])) * inv12dt : 0.f;
         sm.dw[k] = d;
     }
     __syncthreads();
-    return true;
+    return 0;
 }
 
 // z of sub-block sb starting at sample i0: the 2 x kTile new values per
@@ -869,6 +1053,93 @@ __device__ __forceinline__ void lfa_store(const LfaArgs& a, int64_t i, const Rea
     out[2 * a.nout + i] = o2;
 }
 
+// Differenced form: channels of the samples i0 + t and i0 + kTile + t of
+// sub-block sb (after lfa2_diff_window), stored with the blend.  Per series,
+// the first term interpolates S with the 32-point weights of the sample's own
+// retarded position (both samples' weights formed together in packed pair
+// instructions, as in lfa_z_mixed_pair); the B-term uses the two Q values
+// around it.  Each series adds its link's term straight into its channel:
+// X = 8 (T_a + T_b) [T_a R_a - T_b R_b] / (12 dt^2) (TDI 2.0) or
+// X = 4 [T_a R_a - T_b R_b] / (12 dt) (TDI 1.5), R the stencil sums above.
+static __device__ void lfa2_dvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lfa2Smem& sm, int sb, int nr)
+{
+    const LfaWin& W = sm.win[sb];
+    const int t = threadIdx.x;
+    const int dm0 = (int)(i0 - ic) + t;
+    const bool tdi20 = a.gen == LISA_TDI20;
+    const bool equal = a.kind == LISA_LFA_EQUAL;
+    // channel sums of the thread's two samples live in shared memory (the
+    // pair weights need the registers); sm.xacc[2 ch + r][t]
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sm.xacc[q][t] = 0.f;
+#pragma unroll kLfaDUnroll
+    for (int c = 0; c < 6; ++c) {
+        const float ih = sm.inv_half, idt = sm.inv_dt;
+        const float2 u = make_float2((float)dm0 * ih, (float)(dm0 + kTile) * ih);
+        const float4* rp = reinterpret_cast<const float4*>(&sm.ser[c]);
+        float2 e;
+        int ba, bb;
+        {
+            const float4 r0 = rp[0];   // f, d1, d2, d3
+            const float Da = u.x * fmaf(u.x, fmaf(u.x, r0.w, r0.z), r0.y);
+            const float Db = u.y * fmaf(u.y, fmaf(u.y, r0.w, r0.z), r0.y);
+            const float va = fmaf(-Da, idt, r0.x);
+            const float vb = fmaf(-Db, idt, r0.x);
+            const float fa = floorf(va), fb = floorf(vb);
+            e = make_float2(va - fa, vb - fb);
+            ba = min(max(W.jrel[c] + dm0 + (int)fa, 0), W.wlen - 32);
+            bb = min(max(W.jrel[c] + dm0 + kTile + (int)fb, 0), W.wlen - 32);
+        }
+        float2 sv[2];
+        lagrange32_dot2_pair(e, sm.dw + ba, sm.dw + bb, sv[0], sv[1]);
+        const int ch = c >> 1, arm = lfa_arm(ch, c & 1);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float uu = r ? u.y : u.x;
+            const float ee = r ? e.y : e.x;
+            const int base = r ? bb : ba;
+            const float4 r0 = rp[0], rp1 = rp[1], rp2 = rp[2];
+            const float Fp = fmaf(uu, fmaf(uu, fmaf(uu, rp1.w, rp1.z), rp1.y), rp1.x);
+            const float Fc = fmaf(uu, fmaf(uu, fmaf(uu, rp2.w, rp2.z), rp2.y), rp2.x);
+            // dF/di, and a1 = dx/di - 1 = -D'(u) ih / dt
+            const float Fp1 = fmaf(uu, fmaf(uu, 3.f * rp1.w, 2.f * rp1.z), rp1.y) * ih;
+            const float Fc1 = fmaf(uu, fmaf(uu, 3.f * rp2.w, 2.f * rp2.z), rp2.y) * ih;
+            const float a1 = -fmaf(uu, fmaf(uu, 3.f * r0.w, 2.f * r0.z), r0.y) * ih * idt;
+            const float2 q0 = sm.qw[base + 15], q1 = sm.qw[base + 16];
+            const float qp = fmaf(ee, q1.x - q0.x, q0.x), qc = fmaf(ee, q1.y - q0.y, q0.y);
+            const float m = fmaf(Fp, sv[r].x, Fc * sv[r].y);
+            float R;
+            if (tdi20) {
+                // a2 = x''/2 = -(d2 + 3 d3 u) ih^2 / dt; B-term 24 (F1 + F a2) I', I' ~ Q / dt
+                const float a2 = -fmaf(uu, 3.f * r0.w, r0.z) * ih * ih * idt;
+                const float g = (1.f + a1) * (1.f + a1);
+                R = fmaf(g, m, (24.f * idt) * fmaf(fmaf(Fp, a2, Fp1), qp, fmaf(Fc, a2, Fc1) * qc));
+            } else {
+                // B-term 12 F1 I, I ~ Q1 / dt
+                R = fmaf(1.f + a1, m, (12.f * idt) * fmaf(Fp1, qp, Fc1 * qc));
+            }
+            // this series' arm factor: +T_a for link a, -T_b for link b
+            const float T = equal ? a.Lcf : sm.c0[kQT + arm] + sm.cu[kQT + arm](uu);
+            sm.xacc[2 * ch + r][t] = fmaf((c & 1) ? -T : T, R, sm.xacc[2 * ch + r][t]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (r >= nr) break;
+        const float uu = (float)(dm0 + r * kTile) * sm.inv_half;
+        float X[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float Ta = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 0)] + sm.cu[kQT + lfa_arm(ch, 0)](uu);
+            const float Tb = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 1)] + sm.cu[kQT + lfa_arm(ch, 1)](uu);
+            const float pref = tdi20 ? 8.f * (Ta + Tb) * a.c2f : 4.f * a.c1f;
+            X[ch] = pref * sm.xacc[2 * ch + r][t];
+        }
+        const int64_t i = i0 + r * kTile + t;
+        if (a.xyz && i >= a.i_begin && i < a.i_end) lfa_store<float>(a, i, X, sm.barg_c, sm.barg_d, (int)(i - ic));
+    }
+}
+
 // One group of nt tiles from tile t0 (centre ic = t0 kTile + G kTile / 2)
 // in sub-blocks of two tiles, stored with the blend of the arguments.  The
 // caller initialised sm.bar[0..1]; ph0, ph1 carry their phase parities from
@@ -881,22 +1152,37 @@ static __device__ bool lfa2_group(const LfaArgs& a, int64_t t0, int nt, int G, L
     lfa_tile_prologue<true>(a, ic, sm);   // ends with a block barrier
     lfa2_windows(a, t0, nsb, ic, sm);
     lfa2_stage(a, sm, 0, 0);
+    bool prev_z = false;   // the previous sub-block left its z values in sm.zs
     for (int sb = 0; sb < nsb; ++sb) {
         const int b = sb & 1;
         const int64_t i0 = (t0 + 2 * sb) * (int64_t)kTile;
+        // differenced form where the sub-block and its 2-sample z halos are
+        // inside the output grid and its window inside the h grid (a choice
+        // uniform over the block); the z-series form elsewhere
+        const bool dwant = sm.win[sb].diff && i0 - 2 >= 0 && i0 + kSub2 + 2 <= a.nout;
         if (sb + 1 < nsb) lfa2_stage(a, sm, sb + 1, b ^ 1);
-        if (!lfa2_wait_hdot(a, sm, sb, b, b ? ph1 : ph0)) return false;
+        const int wr = lfa2_wait_hdot(a, sm, sb, b, b ? ph1 : ph0, dwant);
+        if (wr < 0) return false;
         if (sm.win[sb].bulk) {
             if (b) ph1 ^= 1u;
             else ph0 ^= 1u;
         }
+        if (wr == 1) {
+            lfa2_dvalues(a, i0, ic, sm, sb, nt - 2 * sb < 2 ? nt - 2 * sb : 2);
+            prev_z = false;
+            continue;
+        }
         // z at samples i0-2 .. i0+1: the previous sub-block's last four values
-        // (the previous channels were read before the barriers just passed)
-        if (sb > 0 && threadIdx.x < 24) {
+        // (the previous channels were read before the barriers just passed),
+        // unless they were overwritten by an attempted differenced window
+        // (which shares the memory): then they are computed again
+        const bool keep_halo = prev_z && !dwant;
+        if (keep_halo && threadIdx.x < 24) {
             const int c = threadIdx.x >> 2, o = threadIdx.x & 3;
             sm.zs[c][o] = sm.zs[c][kSub2 + o];
         }
-        lfa2_zvalues(a, i0, ic, sm, sb, sb == 0);
+        lfa2_zvalues(a, i0, ic, sm, sb, !keep_halo);
+        prev_z = true;
         for (int r = 0; r < 2; ++r) {
             if (2 * sb + r >= nt) break;
             float X[3];

@@ -215,17 +215,17 @@ __device__ __forceinline__ void lagrange32_dot2_pair(float2 eps, const float2* _
 {
     const float2 s = __fadd2_rn(eps, make_float2(-0.5f, -0.5f));
     const float2 sig = __fmul2_rn(s, s);
-    float2 e[16];
-    e[0] = __fmul2_rn(eps, __fadd2_rn(eps, make_float2(-1.f, -1.f)));
-#pragma unroll
-    for (int k = 1; k < 16; ++k) {
+    // e_k = s^2 - (k + 1/2)^2 (k >= 1) is one addition: it is formed again in
+    // the prefix pass instead of being held in registers between the passes
+    auto ek = [&](int k) {
         const float c2 = float((k + 0.5) * (k + 0.5));
-        e[k] = __fadd2_rn(sig, make_float2(-c2, -c2));
-    }
+        return __fadd2_rn(sig, make_float2(-c2, -c2));
+    };
+    const float2 e0 = __fmul2_rn(eps, __fadd2_rn(eps, make_float2(-1.f, -1.f)));
     float2 S[16];   // S[k] = prod_{j>k} e_j
     S[15] = make_float2(1.f, 1.f);
 #pragma unroll
-    for (int k = 14; k >= 0; --k) S[k] = __fmul2_rn(S[k + 1], e[k + 1]);
+    for (int k = 14; k >= 0; --k) S[k] = __fmul2_rn(S[k + 1], ek(k + 1));
     float2 P = make_float2(1.f, 1.f);   // prod_{j<k} e_j
     float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
 #pragma unroll
@@ -245,7 +245,7 @@ __device__ __forceinline__ void lagrange32_dot2_pair(float2 eps, const float2* _
         by = fmaf(wl.y, bl.y, by);
         bx = fmaf(-wr.y, br.x, bx);
         by = fmaf(-wr.y, br.y, by);
-        if (k < 15) P = __fmul2_rn(P, e[k]);
+        if (k < 15) P = __fmul2_rn(P, k == 0 ? e0 : ek(k));
     }
     oa = make_float2(ax, ay);
     ob = make_float2(bx, by);

@@ -48,6 +48,28 @@ def rel_err(got, want, signal=False):
     return np.abs(got - want).max(axis=-1) / scale
 
 
+def rel_err_own(got, want):
+    """Per channel on its own scale (the error measure per channel):
+    max |got - want| / max |want| of that channel."""
+    return rel_err(got, want, signal=False)
+
+
+def check_aet(got, want, tol_big, tol_T_own, equal_arms=False):
+    """A, E, T against the oracle: every channel within tol_big of the
+    largest channel maximum, A and E within tol_big of their own maxima, and
+    T within tol_T_own of its own maximum (for equal-arm LFA outputs, where T
+    vanishes identically, T is judged on the largest channel only).  Returns
+    (largest-channel errors, own-scale errors)."""
+    big = rel_err(got, want, signal=True)
+    own = rel_err_own(got, want)
+    tb = np.broadcast_to(np.asarray(tol_big, dtype=np.float64), (3,))
+    assert np.all(big <= tb), ("largest-channel scale", big, tb)
+    assert np.all(own[:2] <= tb[:2]), ("own scale A, E", own, tb)
+    if not equal_arms:
+        assert own[2] <= tol_T_own, ("own scale T", own, tol_T_own)
+    return big, own
+
+
 def to_dev(a, precision):
     import torch
     dt = torch.float32 if precision == 1 else torch.float64

@@ -524,3 +524,148 @@ def test_generators_phase_derivative_is_frequency():
     dphi = (synth.chirp_phase(tau - h, mc_s, 0.3) - synth.chirp_phase(tau + h, mc_s, 0.3)) / (2 * h)
     f = synth.chirp_frequency(tau, mc_s)
     assert np.allclose(dphi, 2 * math.pi * f, rtol=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# Higher-order LFA (App. B): next-to-leading order of the central series and
+# of the Michelson expansions; the strain-derivative form with the
+# constellation centre (Sec. III)
+# ---------------------------------------------------------------------------
+
+def _normal_sky(oracle_mod, t_st, psi=0.77):
+    """Sky position whose propagation direction is the normal of the static
+    constellation's plane (k.n_l = 0 for every link)."""
+    o = oracle_mod.Orbit(kind=oracle_mod.STATIC, t_static=t_st)
+    R = [oracle_mod.position(o, s, t_st) for s in range(3)]
+    nrm = np.cross(R[1] - R[0], R[2] - R[0])
+    nrm /= np.linalg.norm(nrm)
+    e_r = -nrm   # k = -e_r
+    sky = (math.asin(e_r[2]), math.atan2(e_r[1], e_r[0]), psi)
+    k, _, _ = oracle_mod.sky_basis(sky[0], sky[1])
+    assert abs(k @ nrm - 1.0) < 1e-12
+    return o, sky
+
+
+def _lfa_err(oracle_mod, o, sky, f, gen, kind, n=3000, dt=5.0, t0=3.0e7):
+    hp, hc = synth.monochromatic(t0, dt, n, f, 1.0, 0.8, 0.2)
+    g = (t0, dt, n)
+    full = oracle_mod.response_full(o, sky, g, hp, hc, gen)
+    lfa = oracle_mod.response_lfa(o, sky, g, hp, hc, gen, kind)
+    sl = slice(400, n - 400)
+    return np.abs(lfa[:, sl] - full[:, sl]).max() / np.abs(full[:, sl]).max()
+
+
+@pytest.mark.parametrize("gen", [15, 20])
+def test_lfa_nlo_error_order_normal_incidence(oracle_mod, gen):
+    # With the source on the normal of a rigid constellation every link has
+    # k.n = 0, so a link and its reverse carry the same m = 1 term: the
+    # next-to-leading link term of Eq. yslr_with_tau_derivatives and the next
+    # term of the Michelson expansion leave an error of relative order
+    # (omega L)^4, against (omega L)^2 at leading order.
+    o, sky = _normal_sky(oracle_mod, 2.2e7)
+    fs = np.array([5e-4, 1e-3, 2e-3, 5e-3])
+    lo = np.array([_lfa_err(oracle_mod, o, sky, f, gen, oracle_mod.LFA_UNEQUAL) for f in fs])
+    nlo = np.array([_lfa_err(oracle_mod, o, sky, f, gen, oracle_mod.LFA_NLO) for f in fs])
+    slope = lambda e: np.polyfit(np.log(fs), np.log(e), 1)[0]
+    assert 1.9 < slope(lo) < 2.1, lo
+    assert 3.7 < slope(nlo) < 4.3, nlo
+    assert np.all(nlo < 3e-2 * lo), (nlo, lo)
+    assert nlo[1] < 1e-3 * lo[1], (nlo, lo)      # at 1 mHz
+
+
+@pytest.mark.parametrize("gen", [15, 20])
+def test_lfa_nlo_error_order_general_direction(oracle_mod, gen):
+    # For a general direction a link and its reverse carry m = 1 terms with
+    # (1 - k.n) and (1 + k.n); the channels take their mean, which leaves the
+    # difference: an error of relative order (omega L)^3, still one order
+    # below the leading-order error (omega L)^2.
+    o = oracle_mod.Orbit(kind=oracle_mod.STATIC, t_static=2.2e7)
+    sky = (0.41, 2.3, 0.77)
+    fs = np.array([5e-4, 1e-3, 2e-3, 5e-3])
+    lo = np.array([_lfa_err(oracle_mod, o, sky, f, gen, oracle_mod.LFA_UNEQUAL) for f in fs])
+    nlo = np.array([_lfa_err(oracle_mod, o, sky, f, gen, oracle_mod.LFA_NLO) for f in fs])
+    slope = lambda e: np.polyfit(np.log(fs), np.log(e), 1)[0]
+    assert 1.9 < slope(lo) < 2.1, lo
+    assert 2.7 < slope(nlo) < 3.6, nlo
+    assert np.all(nlo < 2.5e-2 * lo), (nlo, lo)
+
+
+def test_lfa_nlo_link_error_order(oracle_mod):
+    # The link alone (at its own time, its own (1 - k.n)): the central series
+    # has odd powers only, so after the m = 1 term the error is O(f^4).
+    o = oracle_mod.Orbit(kind=oracle_mod.STATIC, t_static=2.2e7)
+    fs = np.array([2e-4, 5e-4, 1e-3, 2e-3, 5e-3])
+    e_lo, e_nlo = [], []
+    for f in fs:
+        d, sc = _link_lfa_err(oracle_mod, o, f, oracle_mod.LFA_UNEQUAL)
+        d2, _ = _link_lfa_err(oracle_mod, o, f, oracle_mod.LFA_NLO)
+        e_lo.append(np.abs(d).max() / sc)
+        e_nlo.append(np.abs(d2).max() / sc)
+    slope = lambda e: np.polyfit(np.log(fs), np.log(e), 1)[0]
+    assert 1.9 < slope(e_lo) < 2.1, e_lo
+    assert 3.8 < slope(e_nlo) < 4.2, e_nlo
+
+
+@pytest.mark.parametrize("gen", [15, 20])
+def test_strain_form_equals_equal_arm_lfa_at_normal_incidence(oracle_mod, gen):
+    # Eqs. X15_with_strain_derivatives, X20_with_strain_derivatives replace
+    # k.(R_s + R_r)/2c by k.R0/c in the equal-arm LFA (Eqs. X15_equal,
+    # X20_equal).  With k normal to the constellation's plane the two are the
+    # same number for every link, and for a rigid constellation the strain
+    # form is then the equal-arm LFA itself: the derivative stencil applied
+    # on the h grid before interpolation equals the one applied to the
+    # interpolated z series on the output grid (unit ratio).
+    t0, dt, n, f = 3.0e7, 5.0, 3000, 1e-3
+    o, sky = _normal_sky(oracle_mod, 2.2e7)
+    hp, hc = synth.monochromatic(t0, dt, n, f, 1.0, 0.8, 0.2)
+    g = (t0, dt, n)
+    eq = oracle_mod.response_lfa(o, sky, g, hp, hc, gen, oracle_mod.LFA_EQUAL)
+    st = oracle_mod.response_lfa(o, sky, g, hp, hc, gen, oracle_mod.LFA_STRAIN)
+    sl = slice(400, n - 400)
+    assert np.abs(st[:, sl] - eq[:, sl]).max() <= 1e-11 * np.abs(eq[:, sl]).max()
+
+
+def test_strain_form_leading_difference_and_T(oracle_mod):
+    # General direction, rigid constellation: the equal-arm LFA's link y_l is
+    # the strain form's shifted by delta_l = k.((R_s + R_r)/2 - R0)/c, so at
+    # leading order X_equal - X_strain = -2 T^2 [G_3 delta_3 - G_2 delta_2]
+    # d3h/dt3 (TDI 1.5), G_l the link's projection of h^SSB (xi from Eqs.
+    # xi_plus, xi_cross).  And X + Y + Z = 0 identically in the strain form
+    # (the xi differences are cyclic), so T vanishes.
+    t_st, t0, dt, n, f = 2.2e7, 3.0e7, 5.0, 3000, 1e-3
+    o = oracle_mod.Orbit(kind=oracle_mod.STATIC, t_static=t_st)
+    beta, lam, psi = 0.41, 2.3, 0.77
+    k, u, v = oracle_mod.sky_basis(beta, lam)
+    A, B, ph0 = 1.0, 0.8, 0.2
+    hp, hc = synth.monochromatic(t0, dt, n, f, A, B, ph0)
+    g = (t0, dt, n)
+    eq = oracle_mod.response_lfa(o, (beta, lam, psi), g, hp, hc, 15, oracle_mod.LFA_EQUAL)
+    st = oracle_mod.response_lfa(o, (beta, lam, psi), g, hp, hc, 15, oracle_mod.LFA_STRAIN)
+    T = 2.5e9 / C
+    R = [oracle_mod.position(o, s, t_st) for s in range(3)]
+    R0 = (R[0] + R[1] + R[2]) / 3.0
+    t = t0 + np.arange(n) * dt
+    tau0 = t - 2 * T - (k @ R0) / C
+    w = 2 * math.pi * f
+    # third derivatives of h+ = A cos(w (t - t0) + ph0), hx = B sin(...), rotated by psi
+    d3p = A * w ** 3 * np.sin(w * (tau0 - t0) + ph0)
+    d3c = -B * w ** 3 * np.cos(w * (tau0 - t0) + ph0)
+    c2, s2 = math.cos(2 * psi), math.sin(2 * psi)
+    Hp, Hc = d3p * c2 - d3c * s2, d3p * s2 + d3c * c2
+
+    def proj(sender, receiver):
+        nl = R[receiver] - R[sender]
+        nl = nl / np.linalg.norm(nl)
+        xp, xc = oracle_mod.antenna(u, v, nl)
+        delta = (k @ (0.5 * (R[sender] + R[receiver]) - R0)) / C
+        return xp * Hp + xc * Hc, delta
+
+    G2, d2 = proj(0, 2)    # link +2: y_123 (1 -> 3)
+    G3, d3 = proj(1, 0)    # link +3: y_231 (2 -> 1)
+    pred = -2 * T * T * (G3 * d3 - G2 * d2)
+    sl = slice(400, n - 400)
+    got = (eq - st)[0, sl]
+    assert abs(d2) > 0.3 and abs(d3) > 0.3      # the shifts are not small here
+    assert np.abs(got - pred[sl]).max() <= 0.02 * np.abs(pred[sl]).max()
+    aet = oracle_mod.aet(st)
+    assert np.abs(aet[2]).max() <= 1e-14 * np.abs(aet[:2]).max()

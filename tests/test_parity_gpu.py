@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import F64_TOL, empty, host_inputs, orbit_pair, rel_err, sky_of, to_dev
+from gpu_util import F64_TOL, check_aet, empty, host_inputs, orbit_pair, rel_err, sky_of, to_dev
+from tolerances import T_OWN_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -79,8 +80,11 @@ def test_tdi_f64_from_links(L, oracle_mod, gen, mode, channels):
         want = oracle_mod.aet(want)
     out = empty((3, 1500), 0)
     L.lisa_tdi(lo, g, to_dev(y, 0), L.F64, gen, mode, channels, g, out)
-    err = rel_err(out.cpu().numpy(), want, signal=channels == 1)
-    assert err.max() <= F64_TOL, err
+    if channels == 1:
+        check_aet(out.cpu().numpy(), want, F64_TOL, T_OWN_TOL["f64"])
+    else:
+        err = rel_err(out.cpu().numpy(), want)
+        assert err.max() <= F64_TOL, err
 
 
 def test_response_full_f64_config1(L, oracle_mod, cfg1):
@@ -111,7 +115,11 @@ def test_lfa_f64(L, oracle_mod, cfg2s, gen, kind):
     # channels from caller-held z
     x2 = empty((3, s.n), 0)
     L.lisa_tdi_lfa(lo, s.grid, z, L.F64, gen, kind, L.AET, x2)
-    assert rel_err(x2.cpu().numpy(), oracle_mod.aet(x_want), signal=True).max() <= F64_TOL
+    check_aet(x2.cpu().numpy(), oracle_mod.aet(x_want), F64_TOL, T_OWN_TOL["f64"], equal_arms=kind == 1)
+    # the same channels from the fused call
+    x3 = empty((3, s.n), 0)
+    L.lisa_response_lfa(lo, sky_of(s), s.grid, hp, hc, L.F64, gen, kind, L.AET, s.grid, x3)
+    check_aet(x3.cpu().numpy(), oracle_mod.aet(x_want), F64_TOL, T_OWN_TOL["f64"], equal_arms=kind == 1)
 
 
 @pytest.mark.parametrize("where", ["middle", "before_start", "after_end", "near_end"])
@@ -126,8 +134,7 @@ def test_hybrid_f64(L, oracle_mod, cfg2s, where):
     out = empty((3, s.n), 0)
     L.lisa_response_hybrid(lo, sky_of(s), s.grid, to_dev(s.hp, 0), to_dev(s.hc, 0), L.F64, 20, 0, L.AET,
                            tH, Tw, sig, s.grid, out)
-    err = rel_err(out.cpu().numpy(), want, signal=True)
-    assert err.max() <= F64_TOL, err
+    check_aet(out.cpu().numpy(), want, F64_TOL, T_OWN_TOL["f64"])
 
 
 @pytest.mark.parametrize("n", [1, 7, 255, 257, 513, 1031])

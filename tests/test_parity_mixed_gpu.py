@@ -7,8 +7,8 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import empty, host_inputs, orbit_pair, rel_err, sky_of, to_dev
-from tolerances import MIXED_TOL
+from gpu_util import check_aet, empty, host_inputs, orbit_pair, rel_err, sky_of, to_dev
+from tolerances import MIXED_TOL, T_OWN_TOL
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -32,8 +32,12 @@ def case():
     return s, hp, hc
 
 
-def _check(got, want, tol, aet=False):
-    err = rel_err(got, want, signal=aet)
+def _check(got, want, tol, aet=False, form=None, equal_arms=False):
+    if aet:
+        # every channel on the largest channel's scale and on its own (T at its
+        # own frozen tolerance)
+        return check_aet(got, want, tol, T_OWN_TOL["mixed"][form], equal_arms=equal_arms)[1]
+    err = rel_err(got, want)
     assert np.all(err <= np.asarray(tol)), (err, tol)
     return err
 
@@ -55,7 +59,8 @@ def test_full_mixed(L, oracle_mod, case, gen, channels):
     want = oracle_mod.response_full(oo, sky_of(s), s.grid, hp, hc, gen, 0, "aet" if channels else "xyz")
     out = empty((3, s.n), 1)
     L.lisa_response_full(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, gen, channels, s.grid, out)
-    _check(out.cpu().numpy(), want, MIXED_TOL["full%d" % gen]["aet" if channels else "xyz"], aet=channels == 1)
+    _check(out.cpu().numpy(), want, MIXED_TOL["full%d" % gen]["aet" if channels else "xyz"], aet=channels == 1,
+           form="full")
 
 
 @pytest.mark.parametrize("gen", [15, 20])
@@ -73,7 +78,8 @@ def test_lfa_mixed(L, oracle_mod, case, gen, kind):
         out = empty((3, s.n), 1)
         L.lisa_response_lfa(lo, sky_of(s), s.grid, hpd, hcd, L.MIXED, gen, kind, channels, s.grid, out)
         want = oracle_mod.aet(x_want) if channels else x_want
-        _check(out.cpu().numpy(), want, MIXED_TOL["lfa%d" % gen]["aet" if channels else "xyz"], aet=channels == 1)
+        _check(out.cpu().numpy(), want, MIXED_TOL["lfa%d" % gen]["aet" if channels else "xyz"], aet=channels == 1,
+               form="lfa", equal_arms=kind == 1)
 
 
 @pytest.mark.parametrize("gen", [15, 20])
@@ -88,7 +94,8 @@ def test_hybrid_mixed(L, oracle_mod, case, gen, channels):
     out = empty((3, s.n), 1)
     L.lisa_response_hybrid(lo, sky_of(s), s.grid, to_dev(hp, 1), to_dev(hc, 1), L.MIXED, gen, 0, channels,
                            tH, Tw, sig, s.grid, out)
-    _check(out.cpu().numpy(), want, MIXED_TOL["hybrid%d" % gen]["aet" if channels else "xyz"], aet=channels == 1)
+    _check(out.cpu().numpy(), want, MIXED_TOL["hybrid%d" % gen]["aet" if channels else "xyz"], aet=channels == 1,
+           form="hybrid")
 
 
 @pytest.mark.parametrize("shift,ratio", [(0.0, 1), (2.5, 1), (0.0, 2), (1.7, 3)])
