@@ -5,12 +5,14 @@ Workload (one step): the hybrid TDI 2.0 A/E/T response of one synthetic
 source -- one year at 5 s (6,311,520 samples), Newtonian chirp (Mc=1e6 Msun,
 q=3) to f_isco joined to a ringdown, exact Keplerian orbits with 1% arm
 flexing, 32-point Lagrange interpolation, LFA with 5-point central differences,
-switch at f_Hyb = 1e-3 Hz (T = 800 dt, sigma = T/40) -- computed in the mixed
-precision form (FP32 arithmetic, FP64 times).  One step runs every stage:
+switch at f_Hyb = 1e-3 Hz (T = 800 dt, sigma = T/40) -- computed in the
+FP64-accurate line-of-record form (REC_PRECISION: FP64 inputs and outputs,
+results within the FP64 tolerance of the oracle).  One step runs every stage:
 orbit table, LFA z-series and channels, full links, TDI, A/E/T, sigmoid blend.
 
 Metric: TDI samples/s (one sample = one output time, all three channels).
-Other forms (full, LFA, FP64) are timed and reported under "forms".
+Other forms (mixed FP32 arithmetic, full, LFA, higher-order LFA kinds) are
+timed and reported under "forms", with their errors and rooflines.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -59,6 +61,24 @@ FLOP_PER_SAMPLE = {
 }
 
 
+# Precision of the line of record: 0 = FP64 (the paper's arithmetic).
+REC_PRECISION = 0
+REC_DTYPE = {0: "f64"}
+REC_KERNEL = {0: "lfa_f64"}
+
+
+def measured_fma_peaks(L):
+    """FMA throughput of the FP64 and FP32 pipes on this GPU, measured in this
+    run by the project's microbenchmark (lisa_peak_fma: 8 independent
+    multiply-add chains per thread, 8 CTAs of 256 threads per SM; best of 5
+    launches).  TFLOP/s, 2 flop per multiply-add."""
+    f64, _ = L.lisa_peak_fma(0, 20000)
+    f32a, _ = L.lisa_peak_fma(1, 200000)
+    f32b, _ = L.lisa_peak_fma(2, 100000)
+    return {"fp64_tflops": f64, "fp32_tflops": max(f32a, f32b), "fp32_scalar_tflops": f32a, "fp32_pair_tflops": f32b,
+            "how": "lisa_peak_fma in this run: 8 independent FMA chains per thread, SMs x 8 CTAs of 256 threads, best of 5"}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     d = {}
@@ -70,13 +90,6 @@ def peaks():
     return d
 
 
-def fp32_peak_tflops(pk):
-    """FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x max SM clock."""
-    mhz = float(pk.get("sm_max_mhz", 2070.0))
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12, ("of measured max clock %.0f MHz" % mhz if "sm_max_mhz" in pk
-                                                else "of fallback 2070 MHz")
-
-
 def kernel_src_hash():
     h = hashlib.sha256()
     for f in ("lfa.cu", "lfa_tile.cuh", "async_copy.cuh", "lisa_common.cuh", "tile_geo.cuh"):
@@ -84,9 +97,9 @@ def kernel_src_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic():
+def committed_traffic(kernel):
     """DRAM bytes per launch of the dominant kernel from a committed ncu
-    capture, if it was taken on the current kernel source."""
+    capture, if it was taken on this kernel and its current source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -94,7 +107,7 @@ def committed_traffic():
         d = json.load(open(p))
     except Exception:
         return None
-    if d.get("src_hash") != kernel_src_hash():
+    if d.get("src_hash") != kernel_src_hash() or d.get("kernel", "lfa_mixed") != kernel:
         return None
     return d.get("bytes_per_launch")
 
@@ -181,7 +194,7 @@ def make_source(rank):
 # CPU baseline: the oracle as it stands, on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 
-def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None, one_core=False, tol_big=3e-5, tol_t_own=5e-4):
+def oracle_hybrid_rate(src, budget_s=12.0, one_core=False, fp32_inputs=False):
     """Oracle samples/s for the hybrid workload on the host cores.
 
     The oracle computes the LFA on every sample and the full response on the
@@ -195,10 +208,9 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None, one_core=False, tol_big
     s = src
     oo = oracle.Orbit(**ORBIT_KW)
     sky = (s.beta, s.lam, s.psi)
-    hp = s.hp.astype(np.float32).astype(np.float64)
-    hc = s.hc.astype(np.float32).astype(np.float64)
+    hp, hc = _oracle_inputs(s, fp32_inputs)
     tH = oracle.t_hyb(F_HYB, s.mc_s, s.tc)
-    Tw, sig = 800 * s.dt, 20 * s.dt
+    Tw = 800 * s.dt
     i_full = max(0, int(math.ceil((tH - 0.5 * Tw - s.t0) / s.dt)))
     n_full = s.n - i_full
     t0 = time.perf_counter()
@@ -212,12 +224,11 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None, one_core=False, tol_big
         zg = (s.t0 + (i0 - 2) * s.dt, s.dt, chunk + 4)
         t0 = time.perf_counter()
         z = oracle.z_lfa(oo, sky, s.grid, hp, hc, 20, 0, zg, hd=hd)
-        lfa = oracle.tdi_lfa_from_z(oo, zg, z, 20, 0, idx=np.arange(2, chunk + 2))
+        oracle.tdi_lfa_from_z(oo, zg, z, 20, 0, idx=np.arange(2, chunk + 2))
         t_lfa = time.perf_counter() - t0
         if t_lfa > 0.4 * budget_s or chunk >= s.n // 4:
             break
         chunk = int(chunk * min(8.0, 0.5 * budget_s / max(t_lfa, 1e-3)))
-    idx = np.arange(i0, i0 + chunk)
     # full response on its whole region: links on the grid from 60 s before
     # the first full sample (the TDI delays never exceed that), then TDI
     marg = int(math.ceil(60.0 / s.dt)) + 20
@@ -226,14 +237,14 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None, one_core=False, tol_big
     ogrid = (s.t0 + i_full * s.dt, s.dt, n_full)
     t0 = time.perf_counter()
     y = oracle.links_full(oo, sky, s.grid, hp, hc, ygrid)
-    full = oracle.tdi_from_y(oo, ygrid, y, 20, oracle.FROZEN, ogrid)
+    oracle.tdi_from_y(oo, ygrid, y, 20, oracle.FROZEN, ogrid)
     t_full = time.perf_counter() - t0
     total = t_hdot + t_lfa * s.n / chunk + t_full
     out = {"value": s.n / total, "unit": UNIT, "kind": "oracle",
            "sample": ("LFA (z series then channels) on %d contiguous samples, extrapolated to all %d; "
                       "full response (links then TDI) on its whole region of %d samples"
                       % (chunk, s.n, n_full)),
-           "seconds": round(t_hdot + t_lfa + t_full, 3)}
+           "seconds": round(t_hdot + t_lfa + t_full, 3), "chunk": [int(i0), int(chunk)]}
     try:
         import synth as _s
         out["cores"] = int(os.environ.get("OMP_NUM_THREADS", 0)) or _s.host_cores()
@@ -249,49 +260,70 @@ def oracle_hybrid_rate(src, budget_s=12.0, gpu_out=None, one_core=False, tol_big
             out["one_core"] = json.loads(r.stdout.strip().splitlines()[-1])
         except Exception as e:   # reported, not fatal: the main figure stands
             out["one_core"] = {"unavailable": str(e)[:200]}
-    if gpu_out is not None:
-        # agreement of the timed GPU step with the oracle on the sampled outputs
-        idxf = np.arange(i_full, s.n)
-        # plus points spread over the whole series, log-spaced in time before the end,
-        # so that every frequency decade of the chirp holds some
-        spread = (s.n - 1 - np.unique(np.geomspace(1, s.n - 1, 400).astype(np.int64))).astype(np.int64)
-        blend_idx = np.unique(np.concatenate([idx[:: max(1, chunk // 200)], idxf[::10], spread]))
-        lf = oracle.tdi_lfa_direct(oo, sky, s.grid, hp, hc, 20, 0, s.grid, blend_idx, hd=hd)
-        fu = np.zeros_like(lf)
-        need = s.t0 + blend_idx * s.dt >= tH - 0.5 * Tw
-        if need.any():
-            fu[:, need] = oracle.tdi_full_direct(oo, sky, s.grid, hp, hc, s.grid, 20, 0, s.grid, blend_idx[need])
-        want = oracle.aet(oracle.hybrid_blend(s.grid, tH, Tw, sig, lf, fu, blend_idx))
-        # A, E, T errors relative to the largest channel maximum (as the tests measure them)
-        scale = np.abs(gpu_out).max()
-        out["gpu_max_rel_err_sampled"] = (np.abs(gpu_out[:, blend_idx] - want).max(axis=1) / scale).tolist()
-        # each channel on its own scale (max |want| of that channel over the sampled set)
-        own = np.abs(want).max(axis=1)
-        out["gpu_max_rel_err_sampled_own"] = (np.abs(gpu_out[:, blend_idx] - want).max(axis=1)
-                                              / np.where(own > 0, own, 1.0)).tolist()
-        out["gpu_err_tolerance"] = ("A,E,T <= %s of the largest channel; A,E on their own scale the same, T on its "
-                                    "own scale <= %s (tests/tolerances.py)" % (tol_big, tol_t_own))
-        # local diagnostic: per decade of the source's instantaneous frequency (0PN chirp
-        # before the ringdown join, the ringdown frequency after), the error scaled by
-        # the largest sampled |A, E, T| in that decade
-        tt = s.t0 + blend_idx * s.dt
-        t_join = s.meta.get("t_join", s.tc)
-        f_inst = np.where(tt <= t_join, synth.chirp_frequency(np.maximum(s.tc - tt, 1e-9), s.mc_s),
-                          s.meta.get("f_rd", 1e-2))
-        local = {}
-        for k in range(-6, -1):
-            sel = (f_inst >= 10.0 ** k) & (f_inst < 10.0 ** (k + 1))
-            if sel.sum() < 3:
-                continue
-            sc_d = np.abs(want[:, sel]).max()
-            if sc_d > 0:
-                d = np.abs(gpu_out[:, blend_idx[sel]] - want[:, sel]).max(axis=1)
-                own_d = np.abs(want[:, sel]).max(axis=1)
-                local["1e%d-1e%d Hz" % (k, k + 1)] = {
-                    "points": int(sel.sum()), "err": (d / sc_d).tolist(),
-                    "err_own": (d / np.where(own_d > 0, own_d, 1.0)).tolist()}
-        out["gpu_local_rel_err_sampled"] = local
     return out
+
+
+def _oracle_inputs(s, fp32_inputs):
+    """h as the GPU form reads it, as FP64 for the oracle."""
+    if fp32_inputs:
+        return s.hp.astype(np.float32).astype(np.float64), s.hc.astype(np.float32).astype(np.float64)
+    return s.hp, s.hc
+
+
+def sampled_errors(src, gpu_out, fp32_inputs, chunk=None):
+    """The timed GPU output against the oracle on sampled outputs (the oracle
+    evaluates them one by one): an inspiral chunk, the full-response region and
+    400 points log-spaced in time before the end.  Returns the global measure
+    (largest channel maximum), the own-scale measure (each channel on its own
+    maximum) and the local diagnostic per frequency decade."""
+    import oracle
+    import synth
+    oracle.build()
+    s = src
+    oo = oracle.Orbit(**ORBIT_KW)
+    sky = (s.beta, s.lam, s.psi)
+    hp, hc = _oracle_inputs(s, fp32_inputs)
+    hd = (oracle.hdot(s.grid, hp), oracle.hdot(s.grid, hc))
+    tH = oracle.t_hyb(F_HYB, s.mc_s, s.tc)
+    Tw, sig = 800 * s.dt, 20 * s.dt
+    i_full = max(0, int(math.ceil((tH - 0.5 * Tw - s.t0) / s.dt)))
+    i0, ch = chunk if chunk else (s.n // 3, 20000)
+    idx = np.arange(i0, i0 + ch)
+    idxf = np.arange(i_full, s.n)
+    spread = (s.n - 1 - np.unique(np.geomspace(1, s.n - 1, 400).astype(np.int64))).astype(np.int64)
+    blend_idx = np.unique(np.concatenate([idx[:: max(1, ch // 200)], idxf[::10], spread]))
+    lf = oracle.tdi_lfa_direct(oo, sky, s.grid, hp, hc, 20, 0, s.grid, blend_idx, hd=hd)
+    fu = np.zeros_like(lf)
+    need = s.t0 + blend_idx * s.dt >= tH - 0.5 * Tw
+    if need.any():
+        fu[:, need] = oracle.tdi_full_direct(oo, sky, s.grid, hp, hc, s.grid, 20, 0, s.grid, blend_idx[need])
+    want = oracle.aet(oracle.hybrid_blend(s.grid, tH, Tw, sig, lf, fu, blend_idx))
+    d = np.abs(gpu_out[:, blend_idx] - want).max(axis=1)
+    own = np.abs(want).max(axis=1)
+    res = {"points": int(blend_idx.size),
+           "max_rel_err": (d / np.abs(gpu_out).max()).tolist(),
+           "max_rel_err_own": (d / np.where(own > 0, own, 1.0)).tolist()}
+    # local diagnostic: per decade of the source's instantaneous frequency (0PN chirp
+    # before the ringdown join, the ringdown frequency after), the error scaled by
+    # the largest sampled |A, E, T| in that decade (and each channel by its own)
+    tt = s.t0 + blend_idx * s.dt
+    t_join = s.meta.get("t_join", s.tc)
+    f_inst = np.where(tt <= t_join, synth.chirp_frequency(np.maximum(s.tc - tt, 1e-9), s.mc_s),
+                      s.meta.get("f_rd", 1e-2))
+    local = {}
+    for k in range(-6, -1):
+        sel = (f_inst >= 10.0 ** k) & (f_inst < 10.0 ** (k + 1))
+        if sel.sum() < 3:
+            continue
+        sc_d = np.abs(want[:, sel]).max()
+        if sc_d > 0:
+            dd = np.abs(gpu_out[:, blend_idx[sel]] - want[:, sel]).max(axis=1)
+            own_d = np.abs(want[:, sel]).max(axis=1)
+            local["1e%d-1e%d Hz" % (k, k + 1)] = {
+                "points": int(sel.sum()), "err": (dd / sc_d).tolist(),
+                "err_own": (dd / np.where(own_d > 0, own_d, 1.0)).tolist()}
+    res["local_per_decade"] = local
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -624,10 +656,20 @@ def run_ours(args):
     hp32 = torch.as_tensor(src.hp.astype(np.float32), device=dev)
     hc32 = torch.as_tensor(src.hc.astype(np.float32), device=dev)
     out32 = torch.empty((3, n), device=dev, dtype=torch.float32)
+    hp64 = torch.as_tensor(src.hp, device=dev)
+    hc64 = torch.as_tensor(src.hc, device=dev)
+    out64 = torch.empty((3, n), device=dev, dtype=torch.float64)
     flush = torch.empty(2 * L2_BYTES // 4, device=dev, dtype=torch.float32)
     stream = torch.cuda.current_stream()
+    fma_peaks = measured_fma_peaks(L)
+    prec = REC_PRECISION
 
     def step():
+        # the line of record: FP64 inputs and outputs, FP64-accurate arithmetic
+        L.lisa_response_hybrid(orbit, sky, src.grid, hp64, hc64, prec, 20, L.LFA_UNEQUAL, L.AET, tH, Tw, sig,
+                               src.grid, out64)
+
+    def step_mixed():
         L.lisa_response_hybrid(orbit, sky, src.grid, hp32, hc32, L.MIXED, 20, L.LFA_UNEQUAL, L.AET, tH, Tw, sig,
                                src.grid, out32)
 
@@ -654,7 +696,7 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    lfa_ms, lfa_launches = L.lisa_profile_query("lfa_mixed")
+    lfa_ms, lfa_launches = L.lisa_profile_query(REC_KERNEL[prec])
     all_ms, _ = L.lisa_profile_query(None)
     L.lisa_profile_enable(False)
     total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
@@ -663,15 +705,15 @@ def run_ours(args):
     # end to end through the public call on host buffers (page-locked): the
     # host->device copies of h and the device->host copy of A, E, T are inside
     # the timed region (the library overlaps them with its kernels in chunks)
-    hp_h = torch.as_tensor(src.hp.astype(np.float32)).pin_memory()
-    hc_h = torch.as_tensor(src.hc.astype(np.float32)).pin_memory()
-    out_h = torch.empty((3, n), dtype=torch.float32).pin_memory()
+    hp_h = torch.as_tensor(src.hp).pin_memory()
+    hc_h = torch.as_tensor(src.hc).pin_memory()
+    out_h = torch.empty((3, n), dtype=torch.float64).pin_memory()
     e2e_ms = []
     for k in range(args.warmup + args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        L.lisa_response_hybrid_host(orbit, sky, src.grid, hp_h, hc_h, L.MIXED, 20, L.LFA_UNEQUAL, L.AET, tH, Tw, sig,
+        L.lisa_response_hybrid_host(orbit, sky, src.grid, hp_h, hc_h, prec, 20, L.LFA_UNEQUAL, L.AET, tH, Tw, sig,
                                     out_h, stream=stream.cuda_stream)
         b.record(stream)
         b.synchronize()
@@ -679,7 +721,7 @@ def run_ours(args):
             e2e_ms.append(a.elapsed_time(b))
     # the host-buffer call returns what the device call returns (the TDI blocks
     # follow its chunks: FP32 rounding)
-    ref = out32.cpu()
+    ref = out64.cpu()
     e2e_diff = float((out_h - ref).abs().max() / ref.abs().max().clamp_min(1e-300))
     e2e_total = max_over_ranks(float(sum(e2e_ms)), world, dev)
     e2e_value = whole_job_rate(world, n, len(e2e_ms), e2e_total)
@@ -687,11 +729,8 @@ def run_ours(args):
     # other forms (same source), fewer steps
     forms = {}
     if not args.no_forms:
-        hp64 = torch.as_tensor(src.hp, device=dev)
-        hc64 = torch.as_tensor(src.hc, device=dev)
-        out64 = torch.empty((3, n), device=dev, dtype=torch.float64)
         cases = {
-            "hybrid20_mixed": lambda: step(),
+            "hybrid20_mixed": lambda: step_mixed(),
             "lfa20_mixed": lambda: L.lisa_response_lfa(orbit, sky, src.grid, hp32, hc32, L.MIXED, 20, 0, L.AET,
                                                        src.grid, out32),
             "full20_mixed": lambda: L.lisa_response_full(orbit, sky, src.grid, hp32, hc32, L.MIXED, 20, L.AET,
@@ -706,12 +745,19 @@ def run_ours(args):
         if args.forms:
             keep = args.forms.split(",")
             cases = {k: v for k, v in cases.items() if k in keep}
+        # per-kernel rooflines of the forms: algorithmic flop per sample (Lagrange
+        # taps, 2 flop each, and stencils; weights not counted) against the
+        # measured FMA peak of the pipe the kernel runs on
+        kern_flop = {"lfa_mixed": LFA_TAPS_FLOP, "lfa_f64": LFA_TAPS_FLOP,
+                     "links_full_mixed": 12 * 2 * TAP, "links_full_f64": 12 * 2 * TAP,
+                     "tdi_mixed": 48 * TAP, "tdi_f64": 48 * TAP}
         for name, fn in cases.items():
             torch.cuda.nvtx.range_push("form_" + name)   # range for targeted profiler captures
             fn()
             torch.cuda.synchronize()
             reps = 3
             ms = []
+            L.lisa_profile_enable(True)
             for _ in range(reps):
                 flush.zero_()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -723,6 +769,24 @@ def run_ours(args):
             torch.cuda.nvtx.range_pop()
             best = float(np.median(ms))
             forms[name] = {"ms": round(best, 4), "samples_per_s": n / (best / 1e3)}
+            roofs = {}
+            for kn, fl in kern_flop.items():
+                kms, kcnt = L.lisa_profile_query(kn)
+                if not kcnt:
+                    continue
+                avg = kms / kcnt
+                pk64 = kn.endswith("_f64")
+                units = n if name.startswith(("lfa", "full")) else (
+                    int(math.floor((tH + 0.5 * Tw - src.t0) / src.dt)) + 1 if kn.startswith("lfa") else n)
+                ach = fl * units / (avg / 1e3) / 1e12
+                pk = fma_peaks["fp64_tflops"] if pk64 else fma_peaks["fp32_tflops"]
+                roofs[kn] = {"avg_launch_ms": round(avg, 5), "achieved_tflops": round(ach, 4),
+                             "peak_tflops": round(pk, 3), "frac": round(ach / pk, 4),
+                             "peak": ("FP64" if pk64 else "FP32") + " FMA, measured (lisa_peak_fma)",
+                             "flop_per_sample": fl, "samples_per_launch": units}
+            L.lisa_profile_enable(False)
+            if roofs:
+                forms[name]["roofline"] = roofs
         if "full20_f64" in cases:
             # expansion point of the LFA link (App. B): the central point against
             # the non-central backward / forward variants, mixed A/E/T, error
@@ -736,21 +800,33 @@ def run_ours(args):
             i_h -= m0
             scale = ref_aet[:, :i_h].abs().max().item()
             points = {}
-            for pname, kind in (("central", L.LFA_UNEQUAL), ("backward", L.LFA_BACKWARD), ("forward", L.LFA_FORWARD)):
-                fn = lambda: L.lisa_response_lfa(orbit, sky, src.grid, hp32, hc32, L.MIXED, 20, kind, L.AET, src.grid,
-                                                 out32)
+            out64b = torch.empty_like(out64)
+            kinds = (("central", L.LFA_UNEQUAL, L.MIXED), ("backward", L.LFA_BACKWARD, L.MIXED),
+                     ("forward", L.LFA_FORWARD, L.MIXED), ("strain_R0", L.LFA_STRAIN, L.MIXED),
+                     ("central_f64", L.LFA_UNEQUAL, L.F64), ("nlo_f64", L.LFA_NLO, L.F64),
+                     ("strain_R0_f64", L.LFA_STRAIN, L.F64))
+            for pname, kind, pr in kinds:
+                o_ = out32 if pr == L.MIXED else out64b
+                h_ = (hp32, hc32) if pr == L.MIXED else (hp64, hc64)
+                fn = lambda: L.lisa_response_lfa(orbit, sky, src.grid, h_[0], h_[1], pr, 20, kind, L.AET, src.grid, o_)
                 best = _timed(torch, stream, flush, fn)
-                err = ((out32[:, m0:m0 + i_h].double() - ref_aet[:, :i_h]).abs().amax(dim=1) / scale).tolist()
-                points[pname] = {"ms": round(best, 4), "err_aet_vs_full_f64": err}
-            forms["lfa20_mixed_expansion_point"] = {
-                "points": points, "range": "t <= t_H (LFA side), grid start excluded (%d samples); errors / max |A,E,T| of the FP64 full response there" % m0,
-                "note": "central: Eq. tau_t_dependence; backward / forward: App. B non-central variants"}
-        del hp64, hc64, out64
+                d = (o_[:, m0:m0 + i_h].double() - ref_aet[:, :i_h]).abs().amax(dim=1)
+                own = ref_aet[:, :i_h].abs().amax(dim=1).clamp_min(1e-300)
+                points[pname] = {"ms": round(best, 4), "samples_per_s": n / (best / 1e3),
+                                 "err_aet_vs_full_f64": (d / scale).tolist(), "err_aet_vs_full_f64_own": (d / own).tolist()}
+            del out64b
+            forms["lfa20_kinds_vs_full"] = {
+                "points": points, "range": "t <= t_H (LFA side), grid start excluded (%d samples); errors / max |A,E,T| of the FP64 full response there (own: each channel on its own maximum)" % m0,
+                "note": "central: Eq. tau_t_dependence; backward / forward: App. B non-central variants; nlo: App. B next-to-leading order (link m = 1 term and next Michelson term); strain_R0: Sec. III strain-derivative form with the constellation centre (Eqs. X15/X20_with_strain_derivatives)"}
 
-    # the headline step's output, for the oracle comparison below
+    # the headline step's output, for the oracle comparison below, and the mixed form's
     step()
     torch.cuda.synchronize()
-    gpu_out = out32.float().cpu().numpy().astype(np.float64) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    keep_out = rank == 0 and world == 1 and not args.no_cpu
+    gpu_out = out64.cpu().numpy() if keep_out else None
+    step_mixed()
+    torch.cuda.synchronize()
+    gpu_out_mixed = out32.float().cpu().numpy().astype(np.float64) if keep_out else None
 
     corrector = None
     if not args.no_corrector and rank == 0:
@@ -770,41 +846,43 @@ def run_ours(args):
         return
 
     pk = peaks()
-    peak, peak_note = fp32_peak_tflops(pk)
     flop = LFA_TAPS_FLOP
-    flop_w = FLOP_PER_SAMPLE["lfa20"]
     lfa_avg_ms = lfa_ms / max(lfa_launches, 1)
     # samples the LFA kernel covers per launch: t <= t_hyb + T/2
     i_l = int(math.floor((tH + 0.5 * Tw - src.t0) / src.dt)) + 1
     achieved = flop * i_l / (lfa_avg_ms / 1e3) / 1e12
-    achieved_w = flop_w * i_l / (lfa_avg_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": "lfa_kernel_mixed (FP32 pipe)", "achieved": round(achieved, 3),
-            "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-            "peak_note": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x clock, " + peak_note,
+    f64_pipe = prec == 0
+    peak = fma_peaks["fp64_tflops"] if f64_pipe else fma_peaks["fp32_tflops"]
+    roof = {"bound": "alu", "kernel": "%s (%s pipe)" % (REC_KERNEL[prec], "FP64" if f64_pipe else "FP32"),
+            "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_note": ("%s FMA throughput measured in this run by lisa_peak_fma (project microbenchmark); "
+                          "of measured" % ("FP64" if f64_pipe else "FP32")),
             "flop_per_sample": flop, "flop_note": "Lagrange taps (2 flop/tap) + stencils; weights not counted",
-            "flop_per_sample_incl_weights": flop_w, "frac_incl_weights": round(achieved_w / peak, 4),
             "samples_per_launch": i_l, "avg_launch_ms": round(lfa_avg_ms, 5),
             "share_of_step": round(lfa_ms / max(all_ms, 1e-9), 4),
-            "hbm_gbs": round(20 * i_l / (lfa_avg_ms / 1e3) / 1e9, 1),
-            "hbm_frac_of_measured": round(20 * i_l / (lfa_avg_ms / 1e3) / 1e9 / float(pk.get("hbm_gbs", 6800.0)), 4)}
-    tr = committed_traffic()
+            "hbm_gbs": round(40 * i_l / (lfa_avg_ms / 1e3) / 1e9, 1),
+            "hbm_frac_of_measured": round(40 * i_l / (lfa_avg_ms / 1e3) / 1e9 / float(pk.get("hbm_gbs", 6800.0)), 4)}
+    tr = committed_traffic(REC_KERNEL[prec])
     if tr is not None:
         roof["traffic"] = tr
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": REC_DTYPE[prec], "data": "synthetic",
         "config": {"workload": "hybrid TDI2.0 AET, chirp+ringdown Mc=1e6 q=3, 1 yr @ 5 s (6311520 samples), "
-                               "Kepler ellipses 1% flex, f_hyb=1e-3 Hz, mixed precision (FP32 math, FP64 times)",
+                               "Kepler ellipses 1% flex, f_hyb=1e-3 Hz, FP64 inputs and outputs, FP64 arithmetic",
+                   "precision_of_record": REC_DTYPE[prec],
                    "n_samples": n, "dt": src.dt, "sources_per_gpu": 1, "l2": "flushed between steps "
                    "(256 MiB write outside the timed events)", "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4, "d2h_bytes_per_step": 3 * n * 4,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": 3 * n * 8,
                 "call": "lisa_response_hybrid_host (page-locked host buffers, copies overlapped in chunks)",
                 "max_rel_diff_vs_device_call": e2e_diff},
         "gpu_launches": int(launches),
         "clocks": clk,
         "forms": forms,
+        "fma_peaks_measured": fma_peaks,
         "gpu_name": torch.cuda.get_device_name(dev),
     }
     if corrector is not None:
@@ -816,7 +894,15 @@ def run_ours(args):
     if loglike is not None:
         line["loglike"] = loglike
     if not args.no_cpu and world == 1:
-        line["cpu_baseline"] = oracle_hybrid_rate(src, budget_s=args.cpu_budget, gpu_out=gpu_out, one_core=True)
+        cb = oracle_hybrid_rate(src, budget_s=args.cpu_budget, one_core=True)
+        er = sampled_errors(src, gpu_out, fp32_inputs=False, chunk=cb.get("chunk"))
+        er["tolerance"] = "A,E,T <= 5e-12 of the largest channel and A,E on their own scale; T on its own <= 1e-10"
+        cb["gpu_err_sampled"] = er
+        line["cpu_baseline"] = cb
+        em = sampled_errors(src, gpu_out_mixed, fp32_inputs=True, chunk=cb.get("chunk"))
+        em["tolerance"] = ("A,E,T <= 3e-5 of the largest channel and A,E on their own scale; T on its own <= 5e-4 "
+                           "(tests/tolerances.py, hybrid20)")
+        forms.setdefault("hybrid20_mixed", {})["err_sampled"] = em
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -93,7 +93,36 @@ enum { LISA_FROZEN = 0, LISA_NESTED = 1 };
  * sender end tau_0 = t - T_l - k.R_s/c (backward, epsilon = 0) or at the
  * receiver end tau_1 = t - k.R_r/c (forward, epsilon = 1); their truncation
  * error is one order lower than the central point's. */
-enum { LISA_LFA_UNEQUAL = 0, LISA_LFA_EQUAL = 1, LISA_LFA_BACKWARD = 2, LISA_LFA_FORWARD = 3 };
+/* NLO (unequal arms, central point) adds the next-to-leading order of both
+ * expansions of App. B: the m = 1 term of the central series of the link
+ * (Eq. yslr_with_tau_derivatives),
+ *   y_l = -(T_l/2) [Hdot + kappa_l d3H/dt3](tau),
+ * kappa_l = [T_l (1 - k.n_l)/2]^2 / 6 for a link at its own time and, in the
+ * TDI-shifted series, the mean over the link and its reverse,
+ * (T_l/2)^2 (1 + (k.n_l)^2) / 6 (the channels rest on link reversal), and the
+ * next term of the Michelson expansions:
+ *   1.5: X += 4 [T_a (T_a^2/6 + T_b^2/8) d3z_a/dt3 - T_b (T_b^2/6 + T_a^2/8) d3z_b/dt3],
+ *   2.0: X += 8 (T_a + T_b) [T_a k_a d4z_a/dt4 - T_b k_b d4z_b/dt4],
+ *        k_a = T_b^2/8 + T_a^2/6 + (T_a + T_b)^2/6 (k_b: a <-> b),
+ * from expanding the channels' delay operators about their centre.  d3h/dt3
+ * is the 5-point second-derivative stencil applied to hdot; d3z/dt3 and
+ * d4z/dt4 are 5-point stencils on the output grid.  NLO is an FP64 form:
+ * LISA_MIXED returns LISA_EINVAL (the higher stencils amplify FP32 rounding of
+ * z beyond the terms they add at low frequency).
+ * STRAIN is the strain-derivative form with the constellation centre
+ * (Sec. III, Eqs. X15_with_strain_derivatives, X20_with_strain_derivatives):
+ * equal constant arms T = L/c and k.(R_s + R_r)/2c replaced by k.R0/c, R0 the
+ * mean of the three spacecraft positions:
+ *   X1.5 = 2 T^2 [(xi_3 - xi_2) . d2h/dt2](t - 2T - k.R0/c),
+ *   X2.0 = 8 T^3 [(xi_3 - xi_2) . d3h/dt3](t - 4T - k.R0/c),
+ * (xi_2, xi_3: the links +2, +3 at t; "." the sum over + and x of the SSB
+ * polarisations), Y and Z cyclic: one interpolation per sample serves all
+ * three channels.  d2h/dt2 is the 5-point first-derivative stencil applied to
+ * hdot, d3h/dt3 the second-derivative stencil applied to hdot.  STRAIN has no
+ * link series: lisa_links_lfa, lisa_links_lfa_own and lisa_tdi_lfa reject it
+ * with LISA_EINVAL. */
+enum { LISA_LFA_UNEQUAL = 0, LISA_LFA_EQUAL = 1, LISA_LFA_BACKWARD = 2, LISA_LFA_FORWARD = 3,
+       LISA_LFA_NLO = 4, LISA_LFA_STRAIN = 5 };
 
 /* Synthetic source family generated on the device, ahead of the response (the
  * paper's IMRPhenomTHM/TEHM waveforms are not available; this family has their

@@ -245,7 +245,7 @@ int lisa_links_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_gri
     LISA_TRY(check_grid(h_grid, "h_grid"));
     LISA_TRY(check_grid(out, "out"));
     LISA_TRY(check_common(precision, tdi_gen, LISA_XYZ));
-    if (!lfa_kind_ok(lfa_kind)) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
+    if (!lfa_kind_series_ok(lfa_kind)) { set_error("lfa_kind %d unknown or without link series", lfa_kind); return LISA_EINVAL; }
     if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
     if (out.n == 0) return LISA_OK;
     if (!z || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
@@ -265,7 +265,7 @@ int lisa_links_lfa_own(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h
     LISA_TRY(check_grid(h_grid, "h_grid"));
     LISA_TRY(check_grid(out, "out"));
     LISA_TRY(check_common(precision, LISA_TDI15, LISA_XYZ));
-    if (!lfa_kind_ok(lfa_kind)) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
+    if (!lfa_kind_series_ok(lfa_kind)) { set_error("lfa_kind %d unknown or without link series", lfa_kind); return LISA_EINVAL; }
     if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
     if (out.n == 0) return LISA_OK;
     if (!y || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
@@ -284,7 +284,7 @@ int lisa_tdi_lfa(const lisa_orbit* orbit, lisa_grid z_grid, const void* z, int p
     LISA_TRY(check_orbit(orbit));
     LISA_TRY(check_grid(z_grid, "z_grid"));
     LISA_TRY(check_common(precision, tdi_gen, channels));
-    if (!lfa_kind_ok(lfa_kind)) { set_error("lfa_kind %d unknown", lfa_kind); return LISA_EINVAL; }
+    if (!lfa_kind_series_ok(lfa_kind)) { set_error("lfa_kind %d unknown or without link series", lfa_kind); return LISA_EINVAL; }
     if (z_grid.n == 0) return LISA_OK;
     if (!z || !xyz) { set_error("NULL series pointer"); return LISA_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;

@@ -314,7 +314,7 @@ int lisa_plan_create(lisa_plan** out, const lisa_orbit* orbit, int precision, in
     if (!orbit || !sources || nsrc <= 0) { set_error("need an orbit and at least one source"); return LISA_EINVAL; }
     if (precision != LISA_MIXED) { set_error("batched plans run the mixed-precision form (precision=LISA_MIXED)"); return LISA_EINVAL; }
     if (tdi_gen != LISA_TDI15 && tdi_gen != LISA_TDI20) { set_error("tdi_gen must be 15 or 20"); return LISA_EINVAL; }
-    if (!lfa_kind_ok(lfa_kind)) { set_error("lfa_kind unknown"); return LISA_EINVAL; }
+    if (!lfa_kind_lo(lfa_kind)) { set_error("lfa_kind unknown (batched plans take the leading-order kinds)"); return LISA_EINVAL; }
     if (channels != LISA_XYZ && channels != LISA_AET) { set_error("channels unknown"); return LISA_EINVAL; }
     if (orbit->kind < 0 || orbit->kind > 2 || orbit->delay < 0 || orbit->delay > 3 || !(orbit->L_m > 0.0)) {
         set_error("invalid orbit");

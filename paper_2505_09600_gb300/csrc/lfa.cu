@@ -57,10 +57,17 @@ __global__ void __launch_bounds__(kTile, LISA_LFA_MINB) lfa_kernel_mixed(LfaArgs
 
 int lfa_group_host(double dt) { return lfa_group(dt); }
 
+int launch_lfa_strain(const LfaArgs& a, double L_nominal, int precision, cudaStream_t st);
+
 int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,
                const void* hc, int precision, int gen, int kind, int channels, const lisa_grid& og, void* z,
                void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st)
 {
+    if (kind == LISA_LFA_NLO && precision == LISA_MIXED) {
+        set_error("the next-to-leading-order LFA is an FP64 form: its third- and fourth-derivative stencils "
+                  "amplify FP32 rounding beyond the terms they add at low frequency");
+        return LISA_EINVAL;
+    }
     if (i_end <= i_begin) return LISA_OK;
     LfaArgs a;
     a.tab = tab;
@@ -84,6 +91,16 @@ int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const l
     lfa_args_f32(a);
     a.h_aligned = ((uintptr_t)hp % 16 == 0) && ((uintptr_t)hc % 16 == 0);
     a.status = device_status_ptr();
+    if (kind == LISA_LFA_STRAIN) {
+        if (z || gen == kLfaOwnTime) {
+            set_error("the strain-derivative form has no link series");
+            return LISA_EINVAL;
+        }
+        prof_before(precision == LISA_MIXED ? "lfa_strain_mixed" : "lfa_strain_f64", st);
+        const int rc = launch_lfa_strain(a, L_nominal, precision, st);
+        prof_after(st);
+        return rc;
+    }
     const int64_t tiles = (i_end - 1) / kTile - a.tile0 + 1;
     const int64_t tile_end = a.tile0 + tiles;
     prof_before(gen == kLfaOwnTime ? (precision == LISA_MIXED ? "lfa_own_mixed" : "lfa_own_f64")
@@ -140,9 +157,11 @@ __global__ void __launch_bounds__(kTile) tdi_lfa_kernel(TdiLfaArgs a)
                 return (Real(14) * (e2 - e1) - (e1 - e0) - (e3 - e2)) / (Real(12) * dt * dt);
             };
             X[ch] = Real(8) * (Ta + Tb) * (Ta * d2(za) - Tb * d2(zb));
+            if (a.kind == LISA_LFA_NLO) X[ch] += lfa_nlo_channel20<Real>(Ta, Tb, za, zb, a.dt);
         } else {
             auto d1 = [&](const Real* zz) { return ((zz[3] - zz[1]) * Real(8) - (zz[4] - zz[0])) / (Real(12) * dt); };
             X[ch] = Real(4) * (Ta * d1(za) - Tb * d1(zb));
+            if (a.kind == LISA_LFA_NLO) X[ch] += lfa_nlo_channel15<Real>(Ta, Tb, za, zb, a.dt);
         }
     }
     Real* out = (Real*)a.xyz;
@@ -160,6 +179,10 @@ __global__ void __launch_bounds__(kTile) tdi_lfa_kernel(TdiLfaArgs a)
 int launch_tdi_lfa(const SegTable& tab, double L_nominal, const lisa_grid& zg, const void* z, int precision, int gen,
                    int kind, int channels, void* xyz, cudaStream_t st)
 {
+    if (kind == LISA_LFA_NLO && precision == LISA_MIXED) {
+        set_error("the next-to-leading-order LFA is an FP64 form");
+        return LISA_EINVAL;
+    }
     if (zg.n <= 0) return LISA_OK;
     TdiLfaArgs a{tab, L_nominal / kC, zg.dt, gen, kind, channels, z, xyz, zg.n};
     const int64_t tiles = (zg.n + kTile - 1) / kTile;

@@ -119,6 +119,28 @@ __device__ __forceinline__ Real hdot_global(const Real* __restrict__ h, int64_t 
     return ((at(idx + 1) - at(idx - 1)) * Real(8) - (at(idx + 2) - at(idx - 2))) * inv12dt;
 }
 
+// Third derivative of h at grid sample idx straight from global memory: the
+// 5-point second derivative of hdot, both zero off the grid (fallback path).
+template <typename Real>
+__device__ __forceinline__ Real hthird_global(const Real* __restrict__ h, int64_t n, int64_t idx, Real inv12dt,
+                                             Real inv_dt)
+{
+    if (idx < 0 || idx >= n) return Real(0);
+    return (-hdot_global(h, n, idx - 2, inv12dt) + Real(16) * hdot_global(h, n, idx - 1, inv12dt)
+            - Real(30) * hdot_global(h, n, idx, inv12dt) + Real(16) * hdot_global(h, n, idx + 1, inv12dt)
+            - hdot_global(h, n, idx + 2, inv12dt)) * inv12dt * inv_dt;
+}
+
+// NLO coefficient of the m = 1 link term: for a TDI-shifted series the mean
+// over the link and its reverse, (T/2)^2 (1 + (k.n)^2) / 6; for a link at its
+// own time (own != 0) [T (1 - k.n)/2]^2 / 6.
+template <typename Real>
+__device__ __forceinline__ Real nlo_kappa(Real T, Real kn, bool own)
+{
+    return own ? Real(0.25) * T * T * (Real(1) - kn) * (Real(1) - kn) / Real(6)
+               : Real(0.25) * T * T * (Real(1) + kn * kn) / Real(6);
+}
+
 template <typename Real>
 __device__ __forceinline__ void interp_hdot_global(const Real* __restrict__ hp, const Real* __restrict__ hc, int64_t n,
                                                    int64_t j, Real eps, Real inv12dt, Real& op, Real& oc)
@@ -182,6 +204,7 @@ struct LfaSmem64 {
     TileGeo g;
     double hb[2][kWinP];      // h+ and hx on the window
     double2 dw[kWinH];        // hdot window (interleaved pairs)
+    double2 d3w[kWinH];       // NLO: third derivative of h on the window (pairs)
     double zs[6][kZW];
     LfaWin win;
     int64_t jends[12];
@@ -378,10 +401,11 @@ __device__ inline void lfa_window(const LfaArgs& a, int64_t i0, int64_t ic, LfaS
         w.wlo = lo - 15 - 3;
         const int64_t len = (hi + 16 + 3) - w.wlo + 1;
         w.wlen = (len + 4 <= kWinH) ? (int)len : 0;
-        // h needed on [wlo - 2, wlo + wlen + 2)
+        // h needed on [wlo - 2, wlo + wlen + 2) for hdot, [wlo - 4, wlo + wlen + 4)
+        // for the third derivative (NLO)
         w.bulk = 0;
-        w.a0 = w.wlo - 2;
-        w.nh = w.wlen > 0 ? w.wlen + 4 : 0;
+        w.a0 = w.wlo - 4;
+        w.nh = w.wlen > 0 ? w.wlen + 8 : 0;
     }
     __syncthreads();
 }
@@ -401,15 +425,34 @@ __device__ inline void lfa_stage_hdot(const LfaArgs& a, LfaSmem64& sm)
     }
     __syncthreads();
     const double inv12dt = 1.0 / (12.0 * a.hm.dt_in);
-    const double* P = sm.hb[0];
+    const double* P = sm.hb[0];   // P[q] = h+ at sample wlo - 4 + q
     const double* C = sm.hb[1];
     for (int k = threadIdx.x; k < w.wlen; k += blockDim.x) {
         const int64_t idx = w.wlo + k;
         const bool in = (idx >= 0 && idx < a.hm.n_in);
         double2 d;
-        d.x = in ? ((P[k + 3] - P[k + 1]) * 8.0 - (P[k + 4] - P[k])) * inv12dt : 0.0;
-        d.y = in ? ((C[k + 3] - C[k + 1]) * 8.0 - (C[k + 4] - C[k])) * inv12dt : 0.0;
+        d.x = in ? ((P[k + 5] - P[k + 3]) * 8.0 - (P[k + 6] - P[k + 2])) * inv12dt : 0.0;
+        d.y = in ? ((C[k + 5] - C[k + 3]) * 8.0 - (C[k + 6] - C[k + 2])) * inv12dt : 0.0;
         sm.dw[k] = d;
+    }
+    if (a.kind == LISA_LFA_NLO) {
+        // third derivative: the 5-point second derivative of hdot (hdot zero
+        // off the h grid), zero off the grid
+        const double k2 = inv12dt / a.hm.dt_in;
+        auto hd = [&](const double* X, int q) -> double {   // hdot at sample wlo - 4 + q
+            const int64_t idx = w.wlo - 4 + q;
+            if (idx < 0 || idx >= a.hm.n_in) return 0.0;
+            return ((X[q + 1] - X[q - 1]) * 8.0 - (X[q + 2] - X[q - 2])) * inv12dt;
+        };
+        for (int k = threadIdx.x; k < w.wlen; k += blockDim.x) {
+            const int64_t idx = w.wlo + k;
+            double2 d = make_double2(0.0, 0.0);
+            if (idx >= 0 && idx < a.hm.n_in) {
+                d.x = (-hd(P, k + 2) + 16.0 * hd(P, k + 3) - 30.0 * hd(P, k + 4) + 16.0 * hd(P, k + 5) - hd(P, k + 6)) * k2;
+                d.y = (-hd(C, k + 2) + 16.0 * hd(C, k + 3) - 30.0 * hd(C, k + 4) + 16.0 * hd(C, k + 5) - hd(C, k + 6)) * k2;
+            }
+            sm.d3w[k] = d;
+        }
     }
     __syncthreads();
 }
@@ -543,11 +586,60 @@ __device__ inline void lfa_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lfa
             bool ok;
             dp = interp_pair_w<double>(sm.dw, wlo, wlen, nullptr, j, eps, dc, ok);
             if (!ok) interp_hdot_global<double>(hp, hc, a.hm.n_in, j, eps, inv12dt, dp, dc);
+            if (a.kind == LISA_LFA_NLO) {
+                const double kn = a.sky.k[0] * n3[0] + a.sky.k[1] * n3[1] + a.sky.k[2] * n3[2];
+                const double kap = nlo_kappa<double>(Tl, kn, a.gen == kLfaOwnTime);
+                double tp, tc;
+                bool ok3;
+                tp = interp_pair_w<double>(sm.d3w, wlo, wlen, nullptr, j, eps, tc, ok3);
+                if (!ok3) {
+                    tp = tc = 0.0;
+                    double w32[32];
+                    lagrange32_weights(eps, w32);
+                    const double idt = 1.0 / a.hm.dt_in;
+                    if (eps == 0.0) {
+                        tp = hthird_global<double>(hp, a.hm.n_in, j, inv12dt, idt);
+                        tc = hthird_global<double>(hc, a.hm.n_in, j, inv12dt, idt);
+                    } else {
+                        for (int k = 0; k < 32; ++k) {
+                            tp = fma(w32[k], hthird_global<double>(hp, a.hm.n_in, j - 15 + k, inv12dt, idt), tp);
+                            tc = fma(w32[k], hthird_global<double>(hc, a.hm.n_in, j - 15 + k, inv12dt, idt), tc);
+                        }
+                    }
+                }
+                dp = fma(kap, tp, dp);
+                dc = fma(kap, tc, dc);
+            }
             zval = -0.5 * Tl * (dp * (xp * c2 + xc * s2) + dc * (xc * c2 - xp * s2));
         }
         sm.zs[c][o] = zval;
     }
     __syncthreads();
+}
+
+// Next term of the Michelson expansions (kind NLO): about its centre the l =
+// +-2 part of X1.5 is (1 + D_Tb)(1 - D_2Ta) y = 4 T_a [d/dt + (T_a^2/6 +
+// T_b^2/8) d3/dt3] y, and of X2.0 (1 + D_Tb)(1 - D_2Ta)(1 - D_2(Ta+Tb)) y =
+// 8 T_a (T_a + T_b) [d2/dt2 + (T_b^2/8 + T_a^2/6 + (T_a + T_b)^2/6) d4/dt4] y
+// (D_x: delay by x; the l = +-3 part alike with a <-> b).  z[0..4] = z at
+// i-2 .. i+2; third and fourth derivatives by 5-point stencils.
+template <typename Real>
+__device__ __forceinline__ Real lfa_nlo_channel15(Real Ta, Real Tb, const Real* za, const Real* zb, double dt)
+{
+    const Real k3 = Real(1) / (Real(2) * Real(dt) * Real(dt) * Real(dt));
+    auto d3 = [&](const Real* z) { return ((z[4] - z[0]) - Real(2) * (z[3] - z[1])) * k3; };
+    const Real ka = Ta * Ta / Real(6) + Tb * Tb / Real(8), kb = Tb * Tb / Real(6) + Ta * Ta / Real(8);
+    return Real(4) * (Ta * ka * d3(za) - Tb * kb * d3(zb));
+}
+
+template <typename Real>
+__device__ __forceinline__ Real lfa_nlo_channel20(Real Ta, Real Tb, const Real* za, const Real* zb, double dt)
+{
+    const Real k4 = Real(1) / (Real(dt) * Real(dt) * Real(dt) * Real(dt));
+    auto d4 = [&](const Real* z) { return ((z[0] + z[4]) - Real(4) * (z[1] + z[3]) + Real(6) * z[2]) * k4; };
+    const Real s = (Ta + Tb) * (Ta + Tb) / Real(6);
+    const Real ka = Tb * Tb / Real(8) + Ta * Ta / Real(6) + s, kb = Ta * Ta / Real(8) + Tb * Tb / Real(6) + s;
+    return Real(8) * (Ta + Tb) * (Ta * ka * d4(za) - Tb * kb * d4(zb));
 }
 
 // FP64 form: channels of sample i0 + t from the z values in shared memory (and
@@ -580,9 +672,11 @@ __device__ inline void lfa_channels(const LfaArgs& a, int64_t i0, int64_t ic, co
                 return (14.0 * c0 - m1 - p1) * k2;
             };
             X[ch] = 8.0 * (Ta + Tb) * (Ta * d2(za) - Tb * d2(zb));
+            if (a.kind == LISA_LFA_NLO) X[ch] += lfa_nlo_channel20<double>(Ta, Tb, za, zb, a.dt_out);
         } else {
             auto d1 = [&](const double* z) { return ((z[3] - z[1]) * 8.0 - (z[4] - z[0])) * k1; };
             X[ch] = 4.0 * (Ta * d1(za) - Tb * d1(zb));
+            if (a.kind == LISA_LFA_NLO) X[ch] += lfa_nlo_channel15<double>(Ta, Tb, za, zb, a.dt_out);
         }
     }
 }
@@ -687,7 +781,8 @@ static __device__ void lfa2_windows(const LfaArgs& a, int64_t t0, int nsb, int64
         w.nh = bulk ? (int)(a1 - a0) : (w.wlen > 0 ? w.wlen + 8 : 0);
         // differenced form: the composite stencils and B-term differences of
         // every staged element stay inside the h grid (no zero padding)
-        w.diff = a.hm.unit_rho && a.gen != kLfaOwnTime && !a.z && w.wlen > 0 && s0 >= 0 && s1 <= a.hm.n_in;
+        w.diff = a.hm.unit_rho && a.gen != kLfaOwnTime && a.kind != LISA_LFA_NLO && !a.z && w.wlen > 0 && s0 >= 0 &&
+                 s1 <= a.hm.n_in;
         for (int c = 0; c < 6; ++c) w.jrel[c] = w.wlen ? (int)(sm.J[c] - w.wlo) - 15 : 0;
     }
     __syncthreads();

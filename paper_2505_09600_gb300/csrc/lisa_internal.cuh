@@ -34,8 +34,17 @@ private:
 // Tile size (output samples per CTA) of the response kernels.
 constexpr int kTile = 256;
 
-// Known LFA kinds (central unequal / equal arms, non-central backward / forward).
+// Known LFA kinds (central unequal / equal arms, non-central backward /
+// forward, next-to-leading order, strain-derivative form).
 inline bool lfa_kind_ok(int k)
+{
+    return k == LISA_LFA_UNEQUAL || k == LISA_LFA_EQUAL || k == LISA_LFA_BACKWARD || k == LISA_LFA_FORWARD ||
+           k == LISA_LFA_NLO || k == LISA_LFA_STRAIN;
+}
+// Kinds with link / z series (all but the strain-derivative form).
+inline bool lfa_kind_series_ok(int k) { return lfa_kind_ok(k) && k != LISA_LFA_STRAIN; }
+// Kinds of the batched plans (leading order).
+inline bool lfa_kind_lo(int k)
 {
     return k == LISA_LFA_UNEQUAL || k == LISA_LFA_EQUAL || k == LISA_LFA_BACKWARD || k == LISA_LFA_FORWARD;
 }

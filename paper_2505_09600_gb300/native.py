@@ -23,7 +23,7 @@ F64, MIXED = 0, 1
 TDI15, TDI20 = 15, 20
 XYZ, AET = 0, 1
 FROZEN, NESTED = 0, 1
-LFA_UNEQUAL, LFA_EQUAL, LFA_BACKWARD, LFA_FORWARD = 0, 1, 2, 3
+LFA_UNEQUAL, LFA_EQUAL, LFA_BACKWARD, LFA_FORWARD, LFA_NLO, LFA_STRAIN = 0, 1, 2, 3, 4, 5
 
 
 class LisaError(RuntimeError):
