@@ -25,6 +25,13 @@
  *    LISA_MIXED = interpolation, projection, TDI sums and LFA stencils in
  *    FP32 with absolute times, orbit phase and delays kept in FP64 (per tile)
  *    plus an FP32 in-tile offset; series are float*.
+ *    LISA_DF = FP64-accurate with series as double*, like LISA_F64: the LFA
+ *    channels (lisa_response_lfa, lisa_response_hybrid, lisa_response_hybrid_host,
+ *    leading-order kinds on a unit-ratio grid) run in double-float arithmetic
+ *    (pairs of FP32 numbers, ~48 significant bits, on the FP32 pipe, with an
+ *    FP64 set-up per group of tiles); every other step, and the LFA outside
+ *    those cases, runs in FP64 as LISA_F64 does.  Results stay within the FP64
+ *    tolerance of the oracle.
  *  - Samples outside an input grid are zero (the paper is silent on
  *    boundaries); every output sample is defined.
  *  - Scratch memory needed inside a call (orbit coefficient table, link or z
@@ -81,7 +88,7 @@ typedef struct {
 /* Ecliptic latitude beta, longitude lambda, polarisation angle psi (rad). */
 typedef struct { double beta, lambda, psi; } lisa_sky;
 
-enum { LISA_F64 = 0, LISA_MIXED = 1 };
+enum { LISA_F64 = 0, LISA_MIXED = 1, LISA_DF = 2 };
 enum { LISA_TDI15 = 15, LISA_TDI20 = 20 };
 enum { LISA_XYZ = 0, LISA_AET = 1 };
 enum { LISA_FROZEN = 0, LISA_NESTED = 1 };

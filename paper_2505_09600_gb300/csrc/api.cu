@@ -84,7 +84,10 @@ int check_orbit(const lisa_orbit* o)
 
 int check_common(int precision, int gen, int channels)
 {
-    if (precision != LISA_F64 && precision != LISA_MIXED) { set_error("precision %d unknown", precision); return LISA_EINVAL; }
+    if (precision != LISA_F64 && precision != LISA_MIXED && precision != LISA_DF) {
+        set_error("precision %d unknown", precision);
+        return LISA_EINVAL;
+    }
     if (gen != LISA_TDI15 && gen != LISA_TDI20) { set_error("tdi_gen must be 15 or 20 (got %d)", gen); return LISA_EINVAL; }
     if (channels != LISA_XYZ && channels != LISA_AET) { set_error("channels %d unknown", channels); return LISA_EINVAL; }
     return LISA_OK;

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kTile, LISA_LFA_MINB) lfa_kernel_mixed(LfaArgs
 int lfa_group_host(double dt) { return lfa_group(dt); }
 
 int launch_lfa_strain(const LfaArgs& a, double L_nominal, int precision, cudaStream_t st);
+int launch_lfa_df(const LfaArgs& a, cudaStream_t st);
 
 int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,
                const void* hc, int precision, int gen, int kind, int channels, const lisa_grid& og, void* z,
@@ -98,6 +99,14 @@ int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const l
         }
         prof_before(precision == LISA_MIXED ? "lfa_strain_mixed" : "lfa_strain_f64", st);
         const int rc = launch_lfa_strain(a, L_nominal, precision, st);
+        prof_after(st);
+        return rc;
+    }
+    if (precision == LISA_DF && a.hm.unit_rho && !z && gen != kLfaOwnTime && xyz &&
+        (kind == LISA_LFA_UNEQUAL || kind == LISA_LFA_EQUAL || kind == LISA_LFA_BACKWARD ||
+         kind == LISA_LFA_FORWARD)) {
+        prof_before("lfa_df", st);
+        const int rc = launch_lfa_df(a, st);
         prof_after(st);
         return rc;
     }

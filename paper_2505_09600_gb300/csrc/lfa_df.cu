@@ -1,0 +1,461 @@
+// LFA channels in double-float arithmetic (precision LISA_DF): FP64 inputs
+// and outputs, the per-sample arithmetic on the FP32 pipe in pairs of FP32
+// numbers (dfloat.cuh), with FP64 only in the per-group set-up and at the two
+// ends (staging of hdot, the store).  The method is the z-series form of the
+// LFA kernel (Sec. III, Eqs. yslr_strain_derivatives, X15_nonequal,
+// X20_nonequal; App. B for the expansion points):
+//   z_c(t) = F+_c(t) hdot+(x_c(t)) + Fx_c(t) hdotx(x_c(t)),
+//   X = 4 [T_a dz_a/dt - T_b dz_b/dt]  or  8 (T_a + T_b) [T_a d2z_a/dt2 - T_b d2z_b/dt2],
+// with F+-, Fx the link's projection factors (-T_l/2 times the rotated
+// antenna patterns), x_c the retarded position of series c on the h grid,
+// 32-point Lagrange interpolation and 5-point stencils.
+//
+// Layout: one CTA of kTile threads per group of up to G tiles sharing one
+// FP64 set-up at the group centre ic.  The set-up composes, for each of the
+// six series, the light time, the two end projections k.R/c and the link
+// vector with the series' retarded coordinate (TDI shift and light time) to
+// degree 5 in the block coordinate u = (m - ic) / (S/2), exactly in FP64
+// (Taylor shift of the orbit polynomials, then the composition with the
+// powers of the retarded offset), and from them the delay variation d(u) -
+// d(0) (degree 5) and the projection factors F+(u), Fx(u) (degree 4).  Over a
+// group |u| <= 0.0625 and the orbital phase moves by < 1e-3 rad, so the
+// dropped terms are below 1e-18 s in the delay and 1e-17 of the factors.  The
+// centre delay is split once into (J, f) in FP64.  Per sample, u is exact in
+// FP32 (S is a power of two), and every polynomial, the position, the 32
+// weights (the paired mirrored-node scheme of the FP32 weights, with
+// compensated products), the tap sums (two-sum accumulation of exact
+// products) and the channel stencils run in double-float.
+#include "dfloat.cuh"
+#include "lfa_tile.cuh"
+
+namespace lisa {
+
+#ifndef LISA_DF_MINB
+#define LISA_DF_MINB 3   // resident CTAs per SM the register budget is set for (fastest of 2, 3, 4)
+#endif
+
+constexpr int kDfD = 6;   // delay polynomial coefficients (degree 5)
+constexpr int kDfF = 5;   // projection factor coefficients (degree 4)
+
+struct DfSer {
+    df d[kDfD];          // delay variation d(u) - d(0) (s), d[0] = 0
+    df fp[kDfF], fc[kDfF];
+    df f0;               // fraction of the centre delay's split
+};
+
+struct DfSmem {
+    TileGeo g;
+    double hb[2][kWinP];          // h+, hx on the tile's window (FP64)
+    float4 dw[kWinH];             // hdot as double-floats (h+ hi, lo, hx hi, lo)
+    df zs[6][kZW];                // z of the tile and its 2-sample halos
+    DfSer ser[6];
+    int64_t J[6];
+    df arm[3][kDfF];              // light times of the links +1, +2, +3 (s), degree 4
+    double dp64[6][kDfD];         // FP64 delay polynomial of each series (window location)
+    double comp[6][6][kDfD];      // set-up scratch: composed quantities
+    LfaWin win;
+    int64_t jends[12];
+    float inv_half;
+    df inv_dt;                    // 1 / dt (double-float)
+};
+
+// Truncated product of two degree-N-1 polynomials.
+template <int N>
+__device__ __forceinline__ void poly_mul(const double* a, const double* b, double* c)
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j <= k; ++j) s = fma(a[j], b[k - j], s);
+        c[k] = s;
+    }
+}
+
+__device__ __forceinline__ df df_of(double d) { return df_from_double(d); }
+
+// Set-up of the group centred at ic (every thread; synchronises).
+static __device__ void df_prologue(const LfaArgs& a, int64_t ic, DfSmem& sm)
+{
+    TileGeo& g = sm.g;
+    const int t = threadIdx.x;
+    tile_geo_load(g, a.tab, ic, a.sky);
+    const bool equal = (a.kind == LISA_LFA_EQUAL);
+    const double u_per_s = 1.0 / (a.dt_out * 0.5 * a.tab.S);
+    if (t < 36) {
+        // series c, quantity r: 0 T_l, 1 k.R_s/c, 2 k.R_r/c, 3..5 n_l, composed
+        // with the retarded coordinate up(u) = u - sh(u) u_per_s
+        const int c = t / 6, r = t % 6;
+        const int ch = c >> 1, which = c & 1;
+        const int l = a.gen == kLfaOwnTime ? c : lfa_link(ch, which);
+        double sh[kDfD] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (a.gen != kLfaOwnTime) {
+            const double al = which ? (a.gen == LISA_TDI20 ? 1.5 : 0.5) : (a.gen == LISA_TDI20 ? 2.0 : 1.0);
+            const double be = which ? (a.gen == LISA_TDI20 ? 2.0 : 1.0) : (a.gen == LISA_TDI20 ? 1.5 : 0.5);
+            const int ra = kQT + lfa_arm(ch, 0), rb = kQT + lfa_arm(ch, 1);
+            for (int k = 0; k < kDfD; ++k)
+                sh[k] = equal ? (k == 0 ? (al + be) * a.Lc : 0.0) : al * g.b[ra][k] + be * g.b[rb][k];
+        }
+        // delta(u) = up(u) - up(0) and its powers
+        double dl[kDfD];
+        dl[0] = 0.0;
+        for (int k = 1; k < kDfD; ++k) dl[k] = (k == 1 ? 1.0 : 0.0) - sh[k] * u_per_s;
+        double out[kDfD];
+        if (r == 0 && equal) {
+            for (int k = 0; k < kDfD; ++k) out[k] = k == 0 ? a.Lc : 0.0;
+        } else {
+            const int row = r == 0 ? kQT + l : r == 1 ? kRowKR + link_sender(l)
+                          : r == 2 ? kRowKR + link_receiver(l) : kQN + 3 * l + (r - 3);
+            double b[7];
+            taylor_shift7(g.b[row], -sh[0] * u_per_s, b);
+            double pw[kDfD] = {1.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int k = 0; k < kDfD; ++k) out[k] = 0.0;
+            for (int p = 0; p < kDfD; ++p) {
+                for (int k = 0; k < kDfD; ++k) out[k] = fma(b[p], pw[k], out[k]);
+                double nx[kDfD];
+                poly_mul<kDfD>(pw, dl, nx);
+                for (int k = 0; k < kDfD; ++k) pw[k] = nx[k];
+            }
+        }
+        for (int k = 0; k < kDfD; ++k) sm.comp[c][r][k] = out[k];
+        // the TDI shift itself goes with the delay (r == 0 thread keeps it)
+        if (r == 0)
+            for (int k = 0; k < kDfD; ++k) sm.dp64[c][k] = sh[k];
+    }
+    if (t >= 64 && t < 64 + 15) {
+        const int q = (t - 64) / kDfF, k = (t - 64) % kDfF;
+        sm.arm[q][k] = df_of(equal ? (k == 0 ? a.Lc : 0.0) : g.b[kQT + 2 * q][k]);
+    }
+    if (t == 96) {
+        sm.inv_half = (float)(2.0 / a.tab.S);
+        sm.inv_dt = df_of(1.0 / a.hm.dt_in);
+    }
+    __syncthreads();
+    if (t < 6) {
+        const int c = t;
+        double d[kDfD];
+        for (int k = 0; k < kDfD; ++k) {
+            const double Tl = sm.comp[c][0][k], ks = sm.comp[c][1][k], kr = sm.comp[c][2][k];
+            d[k] = sm.dp64[c][k] + (a.kind == LISA_LFA_BACKWARD ? Tl + ks
+                                    : a.kind == LISA_LFA_FORWARD ? kr : 0.5 * (Tl + ks + kr));
+        }
+        for (int k = 0; k < kDfD; ++k) sm.dp64[c][k] = d[k];
+        int64_t j;
+        double eps;
+        split_f64(a.hm, ic, d[0], j, eps);
+        sm.J[c] = j;
+        DfSer& R = sm.ser[c];
+        R.f0 = df_of(eps);
+        R.d[0] = df{0.f, 0.f};
+        for (int k = 1; k < kDfD; ++k) R.d[k] = df_of(d[k]);
+        // projection factors: (u.n), (v.n), xi+, xix, rotated, times -T_l/2
+        double un[kDfF], vn[kDfF], T[kDfF];
+        for (int k = 0; k < kDfF; ++k) {
+            un[k] = a.sky.u[0] * sm.comp[c][3][k] + a.sky.u[1] * sm.comp[c][4][k] + a.sky.u[2] * sm.comp[c][5][k];
+            vn[k] = a.sky.v[0] * sm.comp[c][3][k] + a.sky.v[1] * sm.comp[c][4][k] + a.sky.v[2] * sm.comp[c][5][k];
+            T[k] = -0.5 * sm.comp[c][0][k];
+        }
+        double uu[kDfF], vv[kDfF], uv[kDfF], gp[kDfF], gc[kDfF], Fp[kDfF], Fc[kDfF];
+        poly_mul<kDfF>(un, un, uu);
+        poly_mul<kDfF>(vn, vn, vv);
+        poly_mul<kDfF>(un, vn, uv);
+        for (int k = 0; k < kDfF; ++k) {
+            const double xp = uu[k] - vv[k], xc = 2.0 * uv[k];
+            gp[k] = xp * a.sky.c2p + xc * a.sky.s2p;
+            gc[k] = xc * a.sky.c2p - xp * a.sky.s2p;
+        }
+        poly_mul<kDfF>(T, gp, Fp);
+        poly_mul<kDfF>(T, gc, Fc);
+        for (int k = 0; k < kDfF; ++k) {
+            R.fp[k] = df_of(Fp[k]);
+            R.fc[k] = df_of(Fc[k]);
+        }
+    }
+    __syncthreads();
+}
+
+// Window of the tile starting at i0: the retarded samples of the six series
+// at the tile's ends (2-sample halos included), FP64.  After the group's
+// first tile, the z values at i0 - 2 .. i0 + 1 (computed with the previous
+// tile) move to the front of the z buffer.  Synchronises twice.
+static __device__ void df_window(const LfaArgs& a, int64_t i0, int64_t ic, DfSmem& sm, bool first)
+{
+    const int t = threadIdx.x;
+    if (!first && t >= 32 && t < 32 + 24) {
+        const int c = (t - 32) >> 2, k = (t - 32) & 3;
+        sm.zs[c][k] = sm.zs[c][kTile + k];
+    }
+    if (t < 12) {
+        const int c = t % 6;
+        const int64_t m = (t < 6) ? i0 - 2 : i0 + kTile + 1;
+        const double u = (double)(m - ic) * (2.0 / a.tab.S);
+        const double d = horner_d<kDfD>(sm.dp64[c], u);
+        int64_t j;
+        double eps;
+        split_f64(a.hm, m, d, j, eps);
+        sm.jends[t] = j;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int64_t lo = sm.jends[0], hi = sm.jends[0];
+        for (int k = 1; k < 12; ++k) {
+            lo = sm.jends[k] < lo ? sm.jends[k] : lo;
+            hi = sm.jends[k] > hi ? sm.jends[k] : hi;
+        }
+        LfaWin& w = sm.win;
+        w.wlo = lo - 15 - 3;
+        const int64_t len = (hi + 16 + 3) - w.wlo + 1;
+        w.wlen = (len + 4 <= kWinH) ? (int)len : 0;
+        w.a0 = w.wlo - 2;
+        w.nh = w.wlen > 0 ? w.wlen + 4 : 0;
+    }
+    __syncthreads();
+}
+
+// hdot at h-grid sample idx in FP64 from global memory (zero off the grid).
+__device__ __forceinline__ double df_hdot_global(const double* __restrict__ h, int64_t n, int64_t idx, double i12)
+{
+    if (idx < 0 || idx >= n) return 0.0;
+    auto at = [&](int64_t k) { return (k >= 0 && k < n) ? h[k] : 0.0; };
+    return ((at(idx + 1) - at(idx - 1)) * 8.0 - (at(idx + 2) - at(idx - 2))) * i12;
+}
+
+__device__ __forceinline__ float4 df_pack(double p, double c)
+{
+    const df a = df_of(p), b = df_of(c);
+    return make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+// Stage h on the window and form hdot there (FP64), kept as double-floats.
+static __device__ void df_stage(const LfaArgs& a, DfSmem& sm)
+{
+    const LfaWin& w = sm.win;
+    const double* __restrict__ hp = (const double*)a.hp;
+    const double* __restrict__ hc = (const double*)a.hc;
+    for (int k = threadIdx.x; k < w.nh; k += blockDim.x) {
+        const int64_t idx = w.a0 + k;
+        const bool in = idx >= 0 && idx < a.hm.n_in;
+        sm.hb[0][k] = in ? hp[idx] : 0.0;
+        sm.hb[1][k] = in ? hc[idx] : 0.0;
+    }
+    __syncthreads();
+    const double i12 = 1.0 / (12.0 * a.hm.dt_in);
+    const double* P = sm.hb[0];
+    const double* C = sm.hb[1];
+    for (int k = threadIdx.x; k < w.wlen; k += blockDim.x) {
+        const int64_t idx = w.wlo + k;
+        const bool in = (idx >= 0 && idx < a.hm.n_in);
+        const double dp = in ? ((P[k + 3] - P[k + 1]) * 8.0 - (P[k + 4] - P[k])) * i12 : 0.0;
+        const double dc = in ? ((C[k + 3] - C[k + 1]) * 8.0 - (C[k + 4] - C[k])) * i12 : 0.0;
+        sm.dw[k] = df_pack(dp, dc);
+    }
+    __syncthreads();
+}
+
+// 32-point Lagrange interpolation of both polarisations at a double-float
+// fraction eps (the paired mirrored-node scheme of lagrange32_paired_f32:
+// s = eps - 1/2, e_k = s^2 - (k + 1/2)^2, e_0 = eps (eps - 1), Q_k =
+// K_{15-k} prod_{j != k} e_j, w_{15-k} = (s - k - 1/2) Q_k, w_{16+k} =
+// -(s + k + 1/2) Q_k), with compensated products, and the taps accumulated by
+// two-sum of the exact products (Ogita, Rump and Oishi's Dot2).  node(p)
+// gives node p's (h+ hi, lo, hx hi, lo).
+template <class Node>
+__device__ __forceinline__ void lagrange32_df(df eps, Node&& node, df& op, df& oc)
+{
+    df s = two_sum(eps.hi, -0.5f);
+    s.lo = __fadd_rn(s.lo, eps.lo);
+    const df sig = df_mul(s, s);
+    auto ek = [&](int k) -> df {   // s^2 - (k + 1/2)^2, k >= 1: |(k + 1/2)^2| > |sig|
+        const float c2 = float((k + 0.5) * (k + 0.5));
+        const df x = fast_two_sum(-c2, sig.hi);
+        return df{x.hi, __fadd_rn(x.lo, sig.lo)};
+    };
+    df em1 = fast_two_sum(-1.f, eps.hi);   // eps - 1, |1| > |eps|
+    em1.lo = __fadd_rn(em1.lo, eps.lo);
+    const df e0 = df_mul(eps, em1);
+    df S[16];   // S[k] = prod_{j>k} e_j
+    S[15] = df{1.f, 0.f};
+#pragma unroll
+    for (int k = 14; k >= 0; --k) S[k] = df_mul(S[k + 1], ek(k + 1));
+    df P = df{1.f, 0.f};   // prod_{j<k} e_j
+    float Sp = 0.f, Cp = 0.f, Sc = 0.f, Cc = 0.f;
+    auto tap = [&](df w, float4 h) {
+        // + polarisation: exact product (p, pe), two-sum into (Sp, Cp), cross terms
+        const float p = __fmul_rn(w.hi, h.x);
+        const float pe = __fmaf_rn(w.hi, h.x, -p);
+        const df t1 = two_sum(Sp, p);
+        Sp = t1.hi;
+        Cp = __fadd_rn(Cp, __fadd_rn(t1.lo, pe));
+        Cp = __fmaf_rn(w.hi, h.y, Cp);
+        Cp = __fmaf_rn(w.lo, h.x, Cp);
+        const float q = __fmul_rn(w.hi, h.z);
+        const float qe = __fmaf_rn(w.hi, h.z, -q);
+        const df t2 = two_sum(Sc, q);
+        Sc = t2.hi;
+        Cc = __fadd_rn(Cc, __fadd_rn(t2.lo, qe));
+        Cc = __fmaf_rn(w.hi, h.w, Cc);
+        Cc = __fmaf_rn(w.lo, h.z, Cc);
+    };
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const double Kd = lagrange32_k(15 - k);
+        const float Kh = float(Kd), Kl = float(Kd - double(float(Kd)));
+        const df Q = df_mul(df_mul(P, S[k]), df{Kh, Kl});
+        const float c = float(k + 0.5);
+        df am = fast_two_sum(-c, s.hi);   // s - c, |c| >= 1/2 >= |s|
+        am.lo = __fadd_rn(am.lo, s.lo);
+        df ap = fast_two_sum(c, s.hi);    // s + c
+        ap.lo = __fadd_rn(ap.lo, s.lo);
+        const df wl = df_mul(am, Q);       // w_{15-k}
+        df wr = df_mul(ap, Q);             // -w_{16+k}
+        wr.hi = -wr.hi;
+        wr.lo = -wr.lo;
+        tap(wl, node(15 - k));
+        tap(wr, node(16 + k));
+        if (k < 15) P = df_mul(P, k == 0 ? e0 : ek(k));
+    }
+    op = fast_two_sum(Sp, Cp);
+    oc = fast_two_sum(Sc, Cc);
+}
+
+// z of the tile starting at i0 and its 2-sample halos: all of them on the
+// group's first tile, else those at i0 + 2 .. i0 + kTile + 1 (one per
+// thread; the rest come from the previous tile).  Synchronises.
+static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSmem& sm, bool first)
+{
+    const int64_t wlo = sm.win.wlo;
+    const int wlen = sm.win.wlen;
+    const double* __restrict__ hp = (const double*)a.hp;
+    const double* __restrict__ hc = (const double*)a.hc;
+    const double i12 = 1.0 / (12.0 * a.hm.dt_in);
+    const bool interior = i0 - 2 >= 0 && i0 + kTile + 2 <= a.nout;
+    for (int w = threadIdx.x + (first ? 0 : 4); w < kZW; w += blockDim.x) {
+        const int64_t m = i0 - 2 + w;
+        const bool valid = interior || (m >= 0 && m < a.nout);
+        const int dm = (int)(m - ic);
+        const float u = (float)dm * sm.inv_half;   // exact: S is a power of two
+#pragma unroll 1
+        for (int c = 0; c < 6; ++c) {
+            df z = df{0.f, 0.f};
+            if (valid) {
+                const DfSer& R = sm.ser[c];
+                // position on the h grid: J + dm + f0 - (d(u) - d(0)) / dt
+                const df dv = df_horner<kDfD>(R.d, u);
+                const df v = df_sub(R.f0, df_renorm(df_mul(dv, sm.inv_dt)));
+                // fraction: v.hi - floor(v.hi) is not exact for negative v.hi
+                // (its ulp is finer than that of the fraction), so it is taken
+                // by two-sum, with v.lo added to the error term
+                float fl = floorf(v.hi);
+                const df fr = two_sum(v.hi, -fl);
+                df e = two_sum(fr.hi, __fadd_rn(fr.lo, v.lo));
+                if (e.hi < 0.f) {
+                    fl -= 1.f;
+                    e = df_add(e, df{1.f, 0.f});
+                } else if (e.hi >= 1.f) {
+                    fl += 1.f;
+                    e = df_add(e, df{-1.f, 0.f});
+                }
+                const int64_t j = sm.J[c] + dm + (int64_t)fl;
+                const int64_t base = j - 15 - wlo;
+                df ip, ic2;
+                if (wlen > 0 && base >= 0 && base + 32 <= wlen) {
+                    const float4* nb = sm.dw + base;
+                    lagrange32_df(e, [&](int p) { return nb[p]; }, ip, ic2);
+                } else {
+                    lagrange32_df(e, [&](int p) {
+                        const int64_t q = j - 15 + p;
+                        return df_pack(df_hdot_global(hp, a.hm.n_in, q, i12), df_hdot_global(hc, a.hm.n_in, q, i12));
+                    }, ip, ic2);
+                }
+                const df Fp = df_horner<kDfF>(R.fp, u), Fc = df_horner<kDfF>(R.fc, u);
+                z = df_add(df_renorm(df_mul(Fp, ip)), df_renorm(df_mul(Fc, ic2)));
+            }
+            sm.zs[c][w] = z;
+        }
+    }
+    __syncthreads();
+}
+
+// Channels of sample i0 + t, stored with AET and the blend (FP64).
+static __device__ void df_channels(const LfaArgs& a, int64_t i0, int64_t ic, const DfSmem& sm)
+{
+    const int t = threadIdx.x;
+    const int64_t i = i0 + t;
+    if (!a.xyz || i < a.i_begin || i >= a.i_end) return;
+    const float u = (float)(int)(i - ic) * sm.inv_half;
+    const bool tdi20 = a.gen == LISA_TDI20;
+    const df k1 = df_of(1.0 / (12.0 * a.dt_out)), k2 = df_of(1.0 / (12.0 * a.dt_out * a.dt_out));
+    df X[3];
+#pragma unroll 1
+    for (int ch = 0; ch < 3; ++ch) {
+        const df Ta = df_horner<kDfF>(sm.arm[lfa_arm(ch, 0) >> 1], u);
+        const df Tb = df_horner<kDfF>(sm.arm[lfa_arm(ch, 1) >> 1], u);
+        df R[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const df* z = sm.zs[2 * ch + q] + t;   // z[0..4] = z at i-2 .. i+2
+            if (tdi20) {
+                // 5-point second derivative as (14 d2_0 - d2_-1 - d2_1)/12, d2 from first differences
+                const df e0 = df_sub(z[1], z[0]), e1 = df_sub(z[2], z[1]), e2 = df_sub(z[3], z[2]), e3 = df_sub(z[4], z[3]);
+                const df m1 = df_sub(e1, e0), c0 = df_sub(e2, e1), p1 = df_sub(e3, e2);
+                R[q] = df_renorm(df_mul(df_sub(df_renorm(df_mul_f(c0, 14.f)), df_add(m1, p1)), k2));
+            } else {
+                const df d31 = df_sub(z[3], z[1]), d40 = df_sub(z[4], z[0]);
+                R[q] = df_renorm(df_mul(df_sub(df_renorm(df_mul_f(d31, 8.f)), d40), k1));
+            }
+        }
+        const df diff = df_sub(df_renorm(df_mul(Ta, R[0])), df_renorm(df_mul(Tb, R[1])));
+        X[ch] = tdi20 ? df_renorm(df_mul(df_renorm(df_mul_f(df_add(Ta, Tb), 8.f)), diff))
+                      : df_renorm(df_mul_f(diff, 4.f));
+    }
+    double o[3];
+    if (a.channels == LISA_AET) {
+        const df r2 = df_of(0.70710678118654752440), r6 = df_of(0.40824829046386301637),
+                 r3 = df_of(0.57735026918962576451);
+        o[0] = df_to_double(df_renorm(df_mul(df_sub(X[2], X[0]), r2)));
+        o[1] = df_to_double(df_renorm(df_mul(df_add(df_sub(X[0], df_renorm(df_mul_f(X[1], 2.f))), X[2]), r6)));
+        o[2] = df_to_double(df_renorm(df_mul(df_add(df_add(X[0], X[1]), X[2]), r3)));
+    } else {
+        for (int ch = 0; ch < 3; ++ch) o[ch] = df_to_double(X[ch]);
+    }
+    if (a.bl.enabled) {
+        const double ti = a.t0_out + (double)i * a.dt_out;
+        const double arg = a.bl.eps * (ti - a.bl.t_hyb) / a.bl.sigma;
+        if (arg > -40.0) {   // below, 1 / (1 + e^arg) is 1 to FP64 precision
+            const double wgt = 1.0 / (1.0 + exp(arg));
+            for (int ch = 0; ch < 3; ++ch) o[ch] *= wgt;
+        }
+    }
+    double* out = (double*)a.xyz;
+    out[i] = o[0];
+    out[a.nout + i] = o[1];
+    out[2 * a.nout + i] = o[2];
+}
+
+__global__ void __launch_bounds__(kTile, LISA_DF_MINB) lfa_kernel_df(LfaArgs a, int64_t tile_end, int G)
+{
+    __shared__ DfSmem sm;
+    const int64_t t0 = a.tile0 + (int64_t)blockIdx.x * G;
+    const int64_t ic = t0 * kTile + (int64_t)G * kTile / 2;
+    const int nt = (int)(tile_end - t0 < G ? tile_end - t0 : G);
+    df_prologue(a, ic, sm);
+    for (int q = 0; q < nt; ++q) {
+        const int64_t i0 = (t0 + q) * (int64_t)kTile;
+        __syncthreads();   // the previous tile's readers are done
+        df_window(a, i0, ic, sm, q == 0);
+        df_stage(a, sm);
+        df_zvalues(a, i0, ic, sm, q == 0);
+        df_channels(a, i0, ic, sm);
+    }
+}
+
+int launch_lfa_df(const LfaArgs& a, cudaStream_t st)
+{
+    const int64_t tiles = (a.i_end - 1) / kTile - a.tile0 + 1;
+    const int64_t tile_end = a.tile0 + tiles;
+    const int G = lfa_group(a.dt_out);
+    lfa_kernel_df<<<(unsigned)((tiles + G - 1) / G), kTile, 0, st>>>(a, tile_end, G);
+    return cuda_status(cudaGetLastError(), "lfa_kernel_df launch");
+}
+
+}  // namespace lisa

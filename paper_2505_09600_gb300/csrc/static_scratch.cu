@@ -78,7 +78,10 @@ extern "C" int lisa_response_hybrid_static(const lisa_orbit* orbit, const lisa_s
             return LISA_EINVAL;
         }
     }
-    if (precision != LISA_F64 && precision != LISA_MIXED) { set_error("precision unknown"); return LISA_EINVAL; }
+    if (precision != LISA_F64 && precision != LISA_MIXED && precision != LISA_DF) {
+        set_error("precision unknown");
+        return LISA_EINVAL;
+    }
     if (tdi_gen != LISA_TDI15 && tdi_gen != LISA_TDI20) { set_error("tdi_gen must be 15 or 20"); return LISA_EINVAL; }
     if (!lfa_kind_ok(lfa_kind)) { set_error("lfa_kind unknown"); return LISA_EINVAL; }
     if (channels != LISA_XYZ && channels != LISA_AET) { set_error("channels unknown"); return LISA_EINVAL; }

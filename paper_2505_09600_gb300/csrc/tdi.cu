@@ -41,6 +41,75 @@ __global__ void __launch_bounds__(kTile) tdi_kernel(TdiArgs a)
         store_channels<Real>(acc[0], acc[1], acc[2], a.channels, a.bl, a.t0_out, a.dt_out, i, (Real*)a.xyz, a.nout);
 }
 
+// FP64 form on short ranges: the TDI sums of one tile are split over kSplit
+// CTAs of kTile / kSplit samples each (the FP64 pipe of an SM, not its
+// threads, bounds the per-tile form, and a hybrid's full part covers only a
+// few tiles).  Thread t handles channel t / spc of sample t % spc; the three
+// channels meet in shared memory for A/E/T, the blend and the store.
+constexpr int kSplit = 4;
+
+__device__ __forceinline__ double tdi_channel_f64(const TdiArgs& a, const TileGeo& g, int64_t ic, int64_t i,
+                                                  const TdiTile<false>& s, int ch)
+{
+    const double* __restrict__ yg = (const double*)a.y;
+    const double half = 0.5 * a.tab.S;
+    const double u = (double)(i - ic) / half;
+    double T[6];
+#pragma unroll
+    for (int li = 0; li < 6; ++li) T[li] = tg_eval(g, kQT + li, u);
+    double acc = 0.0;
+#pragma unroll 1
+    for (int q = 0; q < a.nterm; ++q) {
+        const TdiTerm& tm = c_terms[q];
+        double D = 0.0;
+        for (int k = 0; k < tm.nd; ++k) {
+            const int li = c_cyc[ch][tm.d[k]];
+            if (a.mode == LISA_NESTED) {
+                D += tg_eval(g, kQT + li, u - D / (a.dt_out * half));
+            } else {
+                double Tl = T[0];
+                for (int r = 1; r < 6; ++r) Tl = (li == r) ? T[r] : Tl;
+                D += Tl;
+            }
+        }
+        int64_t j;
+        double eps;
+        split_f64(a.ym, i, D, j, eps);
+        const int ls = c_cyc[ch][tm.link];
+        const double v = interp_one<double>(s.win[ls], s.wlo, s.wlen, yg ? yg + (int64_t)ls * a.ny : nullptr,
+                                            yg ? a.ym.n_in : 0, j, eps);
+        acc += (tm.sign > 0) ? v : -v;
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kTile) tdi_kernel_f64_split(TdiArgs a)
+{
+    __shared__ TileGeo g;
+    __shared__ TdiTile<false> s;
+    __shared__ double xs[3][kTile / kSplit];
+    constexpr int spc = kTile / kSplit;
+    const int64_t i0 = (a.tile0 + blockIdx.x) * (int64_t)kTile;
+    const int64_t ic = i0 + kTile / 2;
+    tile_geo_load(g, a.tab, ic, SkyDev{});
+    tdi_tile_prologue<false>(a, g, ic, i0, s);
+    tdi_fill_global<false>(a, s);
+    const int t = threadIdx.x;
+    const int64_t ib = i0 + (int64_t)blockIdx.y * spc;
+    if (t < 3 * spc) {
+        const int ch = t / spc;
+        const int64_t i = ib + t % spc;
+        xs[ch][t % spc] = (i >= a.i_begin && i < a.i_end) ? tdi_channel_f64(a, g, ic, i, s, ch) : 0.0;
+    }
+    __syncthreads();
+    if (t < spc) {
+        const int64_t i = ib + t;
+        if (i >= a.i_begin && i < a.i_end)
+            store_channels<double>(xs[0][t], xs[1][t], xs[2][t], a.channels, a.bl, a.t0_out, a.dt_out, i,
+                                   (double*)a.xyz, a.nout);
+    }
+}
+
 int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int precision, int gen, int mode, int channels,
                const lisa_grid& og, void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st,
                int64_t y0)
@@ -73,6 +142,7 @@ int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int prec
         rc = launch_tdi_comb(a, tiles, st);
     } else {
         if (precision == LISA_MIXED) tdi_kernel<true><<<(unsigned)tiles, kTile, 0, st>>>(a);
+        else if (tiles < 2 * 152) tdi_kernel_f64_split<<<dim3((unsigned)tiles, kSplit), kTile, 0, st>>>(a);
         else tdi_kernel<false><<<(unsigned)tiles, kTile, 0, st>>>(a);
         rc = cuda_status(cudaGetLastError(), "tdi_kernel launch");
     }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "liblisa.so")
 LISA_OK, LISA_EINVAL, LISA_ERANGE, LISA_ECUDA, LISA_ETIMEOUT, LISA_ENOMEM, LISA_ECORRECTOR = 0, -1, -2, -3, -4, -5, -6
 ORB_KEPLER1, ORB_KEPLER2, ORB_STATIC = 0, 1, 2
 DELAY_LIGHTTIME, DELAY_ANALYTIC, DELAY_EQUAL, DELAY_LINEAR = 0, 1, 2, 3
-F64, MIXED = 0, 1
+F64, MIXED, DF = 0, 1, 2
 TDI15, TDI20 = 15, 20
 XYZ, AET = 0, 1
 FROZEN, NESTED = 0, 1
