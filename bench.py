@@ -7,7 +7,8 @@ q=3) to f_isco joined to a ringdown, exact Keplerian orbits with 1% arm
 flexing, 32-point Lagrange interpolation, LFA with 5-point central differences,
 switch at f_Hyb = 1e-3 Hz (T = 800 dt, sigma = T/40) -- computed in the
 FP64-accurate line-of-record form (REC_PRECISION: FP64 inputs and outputs,
-results within the FP64 tolerance of the oracle).  One step runs every stage:
+the LFA channels in double-float arithmetic on the FP32 pipe, the full part
+in FP64; results within the FP64 tolerance of the oracle).  One step runs every stage:
 orbit table, LFA z-series and channels, full links, TDI, A/E/T, sigmoid blend.
 
 Metric: TDI samples/s (one sample = one output time, all three channels).
@@ -61,10 +62,24 @@ FLOP_PER_SAMPLE = {
 }
 
 
-# Precision of the line of record: 0 = FP64 (the paper's arithmetic).
-REC_PRECISION = 0
-REC_DTYPE = {0: "f64"}
-REC_KERNEL = {0: "lfa_f64"}
+# Precision of the line of record: 2 = double-float (FP64 inputs and outputs,
+# the LFA channels in pairs of FP32 numbers, the full part in FP64; results
+# within the FP64 tolerance of the oracle); 0 = FP64 throughout.
+REC_PRECISION = 2
+REC_DTYPE = {0: "f64", 2: "df64"}
+REC_KERNEL = {0: "lfa_f64", 2: "lfa_df"}
+
+# FP32 operations (add, multiply or fused multiply-add: one each) of the
+# double-float LFA per output sample (TDI 2.0, A/E/T), counted from the
+# algorithm's operations:
+#   per z-series sample: 32 Lagrange weights and taps 1357 (weight products
+#   and mirrored-node factors 205, 16 x 2 taps x 2 polarisations x 12 for the
+#   two-sum accumulation of exact products 768, pair products of the weights
+#   384), position (delay polynomial, scale, fraction) 117, projection factors
+#   and z 161 -> 1635, x 6 series;
+#   channels: light-time polynomials, two 5-point second differences and the
+#   prefactors, 409 per channel x 3, A/E/T 82.
+DF_OPS_PER_SAMPLE = {"lfa20": 6 * 1635 + 3 * 409 + 82}
 
 
 def measured_fma_peaks(L):
@@ -90,9 +105,17 @@ def peaks():
     return d
 
 
-def kernel_src_hash():
+# Sources each profiled kernel is built from: a committed DRAM-traffic figure
+# counts only while these files are unchanged since the capture.
+KERNEL_SOURCES = {
+    "lfa_mixed": ("lfa.cu", "lfa_tile.cuh", "async_copy.cuh", "lisa_common.cuh", "tile_geo.cuh"),
+    "lfa_df": ("lfa_df.cu", "dfloat.cuh", "lfa_tile.cuh", "lisa_common.cuh", "tile_geo.cuh"),
+}
+
+
+def kernel_src_hash(kernel):
     h = hashlib.sha256()
-    for f in ("lfa.cu", "lfa_tile.cuh", "async_copy.cuh", "lisa_common.cuh", "tile_geo.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2505_09600_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -101,13 +124,13 @@ def committed_traffic(kernel):
     """DRAM bytes per launch of the dominant kernel from a committed ncu
     capture, if it was taken on this kernel and its current source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
     try:
-        d = json.load(open(p))
+        d = json.load(open(p)).get(kernel)
     except Exception:
         return None
-    if d.get("src_hash") != kernel_src_hash() or d.get("kernel", "lfa_mixed") != kernel:
+    if not d or d.get("src_hash") != kernel_src_hash(kernel):
         return None
     return d.get("bytes_per_launch")
 
@@ -737,6 +760,8 @@ def run_ours(args):
                                                          src.grid, out32),
             "hybrid20_f64": lambda: L.lisa_response_hybrid(orbit, sky, src.grid, hp64, hc64, L.F64, 20, 0, L.AET, tH,
                                                            Tw, sig, src.grid, out64),
+            "lfa20_df": lambda: L.lisa_response_lfa(orbit, sky, src.grid, hp64, hc64, L.DF, 20, 0, L.AET,
+                                                    src.grid, out64),
             "lfa20_f64": lambda: L.lisa_response_lfa(orbit, sky, src.grid, hp64, hc64, L.F64, 20, 0, L.AET,
                                                      src.grid, out64),
             "full20_f64": lambda: L.lisa_response_full(orbit, sky, src.grid, hp64, hc64, L.F64, 20, L.AET,
@@ -750,7 +775,7 @@ def run_ours(args):
         # measured FMA peak of the pipe the kernel runs on
         kern_flop = {"lfa_mixed": LFA_TAPS_FLOP, "lfa_f64": LFA_TAPS_FLOP,
                      "links_full_mixed": 12 * 2 * TAP, "links_full_f64": 12 * 2 * TAP,
-                     "tdi_mixed": 48 * TAP, "tdi_f64": 48 * TAP}
+                     "tdi_mixed": 48 * TAP, "tdi_f64": 48 * TAP, "lfa_df": LFA_TAPS_FLOP}
         for name, fn in cases.items():
             torch.cuda.nvtx.range_push("form_" + name)   # range for targeted profiler captures
             fn()
@@ -850,19 +875,34 @@ def run_ours(args):
     lfa_avg_ms = lfa_ms / max(lfa_launches, 1)
     # samples the LFA kernel covers per launch: t <= t_hyb + T/2
     i_l = int(math.floor((tH + 0.5 * Tw - src.t0) / src.dt)) + 1
-    achieved = flop * i_l / (lfa_avg_ms / 1e3) / 1e12
-    f64_pipe = prec == 0
-    peak = fma_peaks["fp64_tflops"] if f64_pipe else fma_peaks["fp32_tflops"]
-    roof = {"bound": "alu", "kernel": "%s (%s pipe)" % (REC_KERNEL[prec], "FP64" if f64_pipe else "FP32"),
-            "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
-            "peak_note": ("%s FMA throughput measured in this run by lisa_peak_fma (project microbenchmark); "
-                          "of measured" % ("FP64" if f64_pipe else "FP32")),
-            "flop_per_sample": flop, "flop_note": "Lagrange taps (2 flop/tap) + stencils; weights not counted",
-            "samples_per_launch": i_l, "avg_launch_ms": round(lfa_avg_ms, 5),
+    if prec == 2:
+        # double-float: FP32 operations per sample against the FP32 pipe's
+        # measured operation rate (one FMA per lane per cycle = flop / 2)
+        ops = DF_OPS_PER_SAMPLE["lfa20"]
+        achieved = ops * i_l / (lfa_avg_ms / 1e3) / 1e12
+        peak = fma_peaks["fp32_tflops"] / 2.0
+        roof = {"bound": "alu", "kernel": "lfa_df (FP32 pipe, double-float arithmetic)",
+                "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "T FP32 op/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_note": "FP32 FMA instruction rate measured in this run by lisa_peak_fma (TFLOP/s / 2); "
+                             "of measured",
+                "ops_per_sample": ops, "ops_note": "FP32 add/mul/fma of the double-float algorithm, one each "
+                "(weights, taps, positions, projection factors, stencils); FP64 set-up and hdot staging not counted",
+                "taps_flop_view": {"flop_per_sample": flop, "achieved_tflops":
+                                   round(flop * i_l / (lfa_avg_ms / 1e3) / 1e12, 4)}}
+    else:
+        achieved = flop * i_l / (lfa_avg_ms / 1e3) / 1e12
+        peak = fma_peaks["fp64_tflops"]
+        roof = {"bound": "alu", "kernel": "%s (FP64 pipe)" % REC_KERNEL[prec],
+                "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_note": "FP64 FMA throughput measured in this run by lisa_peak_fma (project microbenchmark); "
+                             "of measured",
+                "flop_per_sample": flop, "flop_note": "Lagrange taps (2 flop/tap) + stencils; weights not counted"}
+    roof.update({"samples_per_launch": i_l, "avg_launch_ms": round(lfa_avg_ms, 5),
             "share_of_step": round(lfa_ms / max(all_ms, 1e-9), 4),
             "hbm_gbs": round(40 * i_l / (lfa_avg_ms / 1e3) / 1e9, 1),
-            "hbm_frac_of_measured": round(40 * i_l / (lfa_avg_ms / 1e3) / 1e9 / float(pk.get("hbm_gbs", 6800.0)), 4)}
+            "hbm_frac_of_measured": round(40 * i_l / (lfa_avg_ms / 1e3) / 1e9 / float(pk.get("hbm_gbs", 6800.0)), 4)})
     tr = committed_traffic(REC_KERNEL[prec])
     if tr is not None:
         roof["traffic"] = tr
@@ -871,7 +911,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": REC_DTYPE[prec], "data": "synthetic",
         "config": {"workload": "hybrid TDI2.0 AET, chirp+ringdown Mc=1e6 q=3, 1 yr @ 5 s (6311520 samples), "
-                               "Kepler ellipses 1% flex, f_hyb=1e-3 Hz, FP64 inputs and outputs, FP64 arithmetic",
+                               "Kepler ellipses 1% flex, f_hyb=1e-3 Hz, FP64 inputs and outputs, " + (
+                               "double-float LFA (FP32 pairs), FP64 full part" if prec == 2 else "FP64 arithmetic"),
                    "precision_of_record": REC_DTYPE[prec],
                    "n_samples": n, "dt": src.dt, "sources_per_gpu": 1, "l2": "flushed between steps "
                    "(256 MiB write outside the timed events)", "parallelism": "replicas" if world > 1 else "single"},

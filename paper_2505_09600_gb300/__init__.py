@@ -11,5 +11,5 @@ from .native import Orbit, LisaError, LisaPlan, LisaCorrector, load, exported_sy
 __all__ = [n for n in dir() if n.startswith("lisa_")] + [
     "Orbit", "LisaError", "LisaPlan", "LisaCorrector", "load", "exported_symbols",
     "ORB_KEPLER1", "ORB_KEPLER2", "ORB_STATIC", "DELAY_LIGHTTIME", "DELAY_ANALYTIC", "DELAY_EQUAL",
-    "DELAY_LINEAR", "F64", "MIXED", "TDI15", "TDI20", "XYZ", "AET", "FROZEN", "NESTED", "LFA_UNEQUAL",
-    "LFA_EQUAL", "LFA_BACKWARD", "LFA_FORWARD"]
+    "DELAY_LINEAR", "F64", "MIXED", "DF", "TDI15", "TDI20", "XYZ", "AET", "FROZEN", "NESTED", "LFA_UNEQUAL",
+    "LFA_EQUAL", "LFA_BACKWARD", "LFA_FORWARD", "LFA_NLO", "LFA_STRAIN"]

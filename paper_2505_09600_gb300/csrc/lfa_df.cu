@@ -43,20 +43,28 @@ struct DfSer {
     df f0;               // fraction of the centre delay's split
 };
 
+constexpr int kDfGmax = 8;   // tiles per group (lfa_group)
+
+struct DfWin {
+    int64_t wlo;                  // first h sample of the tile's hdot window
+    int wlen;                     // its length (0: read h from global memory)
+};
+
 struct DfSmem {
     TileGeo g;
-    double hb[2][kWinP];          // h+, hx on the tile's window (FP64)
-    float4 dw[kWinH];             // hdot as double-floats (h+ hi, lo, hx hi, lo)
+    float4 dw[2][kWinH];          // hdot windows as double-floats (h+ hi, lo, hx hi, lo), two buffers
     df zs[6][kZW];                // z of the tile and its 2-sample halos
+    df halo[2][6][4];             // z at the next tile's left halo and first two samples, two buffers
     DfSer ser[6];
     int64_t J[6];
     df arm[3][kDfF];              // light times of the links +1, +2, +3 (s), degree 4
     double dp64[6][kDfD];         // FP64 delay polynomial of each series (window location)
     double comp[6][6][kDfD];      // set-up scratch: composed quantities
-    LfaWin win;
-    int64_t jends[12];
+    DfWin win[kDfGmax];
+    int64_t jends[kDfGmax][12];
     float inv_half;
     df inv_dt;                    // 1 / dt (double-float)
+    int blend;                    // the sigmoid weight differs from 1 somewhere in the group
 };
 
 // Truncated product of two degree-N-1 polynomials.
@@ -74,8 +82,9 @@ __device__ __forceinline__ void poly_mul(const double* a, const double* b, doubl
 
 __device__ __forceinline__ df df_of(double d) { return df_from_double(d); }
 
-// Set-up of the group centred at ic (every thread; synchronises).
-static __device__ void df_prologue(const LfaArgs& a, int64_t ic, DfSmem& sm)
+// Set-up of the group of nt tiles from tile t0, centred at ic, and the hdot
+// windows of its tiles (every thread; synchronises).
+static __device__ void df_prologue(const LfaArgs& a, int64_t t0, int nt, int64_t ic, DfSmem& sm)
 {
     TileGeo& g = sm.g;
     const int t = threadIdx.x;
@@ -172,42 +181,42 @@ static __device__ void df_prologue(const LfaArgs& a, int64_t ic, DfSmem& sm)
         }
     }
     __syncthreads();
-}
-
-// Window of the tile starting at i0: the retarded samples of the six series
-// at the tile's ends (2-sample halos included), FP64.  After the group's
-// first tile, the z values at i0 - 2 .. i0 + 1 (computed with the previous
-// tile) move to the front of the z buffer.  Synchronises twice.
-static __device__ void df_window(const LfaArgs& a, int64_t i0, int64_t ic, DfSmem& sm, bool first)
-{
-    const int t = threadIdx.x;
-    if (!first && t >= 32 && t < 32 + 24) {
-        const int c = (t - 32) >> 2, k = (t - 32) & 3;
-        sm.zs[c][k] = sm.zs[c][kTile + k];
-    }
-    if (t < 12) {
-        const int c = t % 6;
-        const int64_t m = (t < 6) ? i0 - 2 : i0 + kTile + 1;
+    // retarded samples of the six series at each tile's two ends (2-sample
+    // halos included), FP64
+    if (t < 12 * nt) {
+        const int q = t / 12, e = t % 12, c = e % 6;
+        const int64_t i0 = (t0 + q) * (int64_t)kTile;
+        const int64_t m = (e < 6) ? i0 - 2 : i0 + kTile + 1;
         const double u = (double)(m - ic) * (2.0 / a.tab.S);
         const double d = horner_d<kDfD>(sm.dp64[c], u);
         int64_t j;
         double eps;
         split_f64(a.hm, m, d, j, eps);
-        sm.jends[t] = j;
+        sm.jends[q][e] = j;
+    }
+    if (t == 128) {
+        // the weight 1 / (1 + e^arg) is 1 to FP64 precision for arg <= -40;
+        // arg is monotonic in the sample index: its two ends decide
+        int on = 0;
+        if (a.bl.enabled) {
+            const int64_t i_a = t0 * (int64_t)kTile, i_b = (t0 + nt) * (int64_t)kTile - 1;
+            const double ta = a.t0_out + (double)i_a * a.dt_out, tb = a.t0_out + (double)i_b * a.dt_out;
+            const double ga = a.bl.eps * (ta - a.bl.t_hyb) / a.bl.sigma, gb = a.bl.eps * (tb - a.bl.t_hyb) / a.bl.sigma;
+            on = (ga > -41.0 || gb > -41.0) ? 1 : 0;
+        }
+        sm.blend = on;
     }
     __syncthreads();
-    if (t == 0) {
-        int64_t lo = sm.jends[0], hi = sm.jends[0];
+    if (t < nt) {
+        int64_t lo = sm.jends[t][0], hi = sm.jends[t][0];
         for (int k = 1; k < 12; ++k) {
-            lo = sm.jends[k] < lo ? sm.jends[k] : lo;
-            hi = sm.jends[k] > hi ? sm.jends[k] : hi;
+            lo = sm.jends[t][k] < lo ? sm.jends[t][k] : lo;
+            hi = sm.jends[t][k] > hi ? sm.jends[t][k] : hi;
         }
-        LfaWin& w = sm.win;
+        DfWin& w = sm.win[t];
         w.wlo = lo - 15 - 3;
         const int64_t len = (hi + 16 + 3) - w.wlo + 1;
-        w.wlen = (len + 4 <= kWinH) ? (int)len : 0;
-        w.a0 = w.wlo - 2;
-        w.nh = w.wlen > 0 ? w.wlen + 4 : 0;
+        w.wlen = (len <= kWinH) ? (int)len : 0;
     }
     __syncthreads();
 }
@@ -226,30 +235,18 @@ __device__ __forceinline__ float4 df_pack(double p, double c)
     return make_float4(a.hi, a.lo, b.hi, b.lo);
 }
 
-// Stage h on the window and form hdot there (FP64), kept as double-floats.
-static __device__ void df_stage(const LfaArgs& a, DfSmem& sm)
+// hdot on the window of one tile (FP64 from h in global memory, kept as
+// double-floats) into buffer dw.  No synchronisation.
+static __device__ void df_stage(const LfaArgs& a, const DfWin& w, float4* __restrict__ dw)
 {
-    const LfaWin& w = sm.win;
     const double* __restrict__ hp = (const double*)a.hp;
     const double* __restrict__ hc = (const double*)a.hc;
-    for (int k = threadIdx.x; k < w.nh; k += blockDim.x) {
-        const int64_t idx = w.a0 + k;
-        const bool in = idx >= 0 && idx < a.hm.n_in;
-        sm.hb[0][k] = in ? hp[idx] : 0.0;
-        sm.hb[1][k] = in ? hc[idx] : 0.0;
-    }
-    __syncthreads();
     const double i12 = 1.0 / (12.0 * a.hm.dt_in);
-    const double* P = sm.hb[0];
-    const double* C = sm.hb[1];
+    const int64_t n = a.hm.n_in;
     for (int k = threadIdx.x; k < w.wlen; k += blockDim.x) {
         const int64_t idx = w.wlo + k;
-        const bool in = (idx >= 0 && idx < a.hm.n_in);
-        const double dp = in ? ((P[k + 3] - P[k + 1]) * 8.0 - (P[k + 4] - P[k])) * i12 : 0.0;
-        const double dc = in ? ((C[k + 3] - C[k + 1]) * 8.0 - (C[k + 4] - C[k])) * i12 : 0.0;
-        sm.dw[k] = df_pack(dp, dc);
+        dw[k] = df_pack(df_hdot_global(hp, n, idx, i12), df_hdot_global(hc, n, idx, i12));
     }
-    __syncthreads();
 }
 
 // 32-point Lagrange interpolation of both polarisations at a double-float
@@ -318,13 +315,21 @@ __device__ __forceinline__ void lagrange32_df(df eps, Node&& node, df& op, df& o
     oc = fast_two_sum(Sc, Cc);
 }
 
-// z of the tile starting at i0 and its 2-sample halos: all of them on the
-// group's first tile, else those at i0 + 2 .. i0 + kTile + 1 (one per
-// thread; the rest come from the previous tile).  Synchronises.
-static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSmem& sm, bool first)
+// z of tile q of the group (first sample i0) and its 2-sample halos: all of
+// them on the group's first tile, else those at i0 + 2 .. i0 + kTile + 1 (one
+// per thread), the first four coming from the previous tile through halo[q & 1];
+// the last four go to halo[(q + 1) & 1] for the next tile.  hdot is read from
+// buffer dw (window win).  No synchronisation.
+static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSmem& sm, const DfWin& win,
+                                  const float4* __restrict__ dw, int q, bool first)
 {
-    const int64_t wlo = sm.win.wlo;
-    const int wlen = sm.win.wlen;
+    const int t = threadIdx.x;
+    if (!first && t >= 32 && t < 32 + 24) {
+        const int c = (t - 32) >> 2, k = (t - 32) & 3;
+        sm.zs[c][k] = sm.halo[q & 1][c][k];
+    }
+    const int64_t wlo = win.wlo;
+    const int wlen = win.wlen;
     const double* __restrict__ hp = (const double*)a.hp;
     const double* __restrict__ hc = (const double*)a.hc;
     const double i12 = 1.0 / (12.0 * a.hm.dt_in);
@@ -359,7 +364,7 @@ static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSm
                 const int64_t base = j - 15 - wlo;
                 df ip, ic2;
                 if (wlen > 0 && base >= 0 && base + 32 <= wlen) {
-                    const float4* nb = sm.dw + base;
+                    const float4* nb = dw + base;
                     lagrange32_df(e, [&](int p) { return nb[p]; }, ip, ic2);
                 } else {
                     lagrange32_df(e, [&](int p) {
@@ -371,9 +376,9 @@ static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSm
                 z = df_add(df_renorm(df_mul(Fp, ip)), df_renorm(df_mul(Fc, ic2)));
             }
             sm.zs[c][w] = z;
+            if (w >= kTile) sm.halo[(q + 1) & 1][c][w - kTile] = z;
         }
     }
-    __syncthreads();
 }
 
 // Channels of sample i0 + t, stored with AET and the blend (FP64).
@@ -418,7 +423,7 @@ static __device__ void df_channels(const LfaArgs& a, int64_t i0, int64_t ic, con
     } else {
         for (int ch = 0; ch < 3; ++ch) o[ch] = df_to_double(X[ch]);
     }
-    if (a.bl.enabled) {
+    if (sm.blend) {
         const double ti = a.t0_out + (double)i * a.dt_out;
         const double arg = a.bl.eps * (ti - a.bl.t_hyb) / a.bl.sigma;
         if (arg > -40.0) {   // below, 1 / (1 + e^arg) is 1 to FP64 precision
@@ -438,14 +443,16 @@ __global__ void __launch_bounds__(kTile, LISA_DF_MINB) lfa_kernel_df(LfaArgs a, 
     const int64_t t0 = a.tile0 + (int64_t)blockIdx.x * G;
     const int64_t ic = t0 * kTile + (int64_t)G * kTile / 2;
     const int nt = (int)(tile_end - t0 < G ? tile_end - t0 : G);
-    df_prologue(a, ic, sm);
+    df_prologue(a, t0, nt, ic, sm);
+    df_stage(a, sm.win[0], sm.dw[0]);
+    __syncthreads();
     for (int q = 0; q < nt; ++q) {
         const int64_t i0 = (t0 + q) * (int64_t)kTile;
-        __syncthreads();   // the previous tile's readers are done
-        df_window(a, i0, ic, sm, q == 0);
-        df_stage(a, sm);
-        df_zvalues(a, i0, ic, sm, q == 0);
+        df_zvalues(a, i0, ic, sm, sm.win[q], sm.dw[q & 1], q, q == 0);
+        __syncthreads();   // z of the tile complete
         df_channels(a, i0, ic, sm);
+        if (q + 1 < nt) df_stage(a, sm.win[q + 1], sm.dw[(q + 1) & 1]);
+        __syncthreads();   // z read, next window staged
     }
 }
 

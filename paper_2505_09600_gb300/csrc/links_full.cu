@@ -38,6 +38,29 @@ __global__ void __launch_bounds__(kTile) links_full_kernel(LinksArgs a)
     links_sample<MIXED>(a, g, ic, i, s, (Real*)a.y + (i - a.y0), a.ny);
 }
 
+// FP64 form on short ranges (a hybrid's full part covers a few tiles): the
+// six links of a tile and its samples are split over 6 x parts CTAs, CTA
+// (tile, li * parts + part) holding link li of kTile / parts samples.
+__global__ void __launch_bounds__(kTile) links_full_kernel_f64_split(LinksArgs a, int parts)
+{
+    __shared__ TileGeo g;
+    __shared__ LinksTile<false> s;
+    const int64_t i0 = (a.tile0 + blockIdx.x) * (int64_t)kTile;
+    const int64_t ic = i0 + kTile / 2;
+    tile_geo_load(g, a.tab, ic, a.sky);
+    links_tile_prologue<false>(a, g, ic, i0, i0 + kTile - 1, s);
+    const int li = blockIdx.y / parts, part = blockIdx.y % parts;
+    const int per = kTile / parts;
+    if ((int)threadIdx.x >= per) return;
+    const int64_t i = i0 + (int64_t)part * per + threadIdx.x;
+    if (i < a.i_begin || i >= a.i_end) return;
+    const double u = (double)(i - ic) / (0.5 * a.tab.S);
+    double kR[3];
+#pragma unroll
+    for (int sc = 0; sc < 3; ++sc) kR[sc] = tg_eval(g, kRowKR + sc, u);
+    ((double*)a.y)[(int64_t)li * a.ny + (i - a.y0)] = link_value_f64(a, g, u, i, s, li, kR);
+}
+
 __global__ void __launch_bounds__(kTile, 3) links_group_kernel(LinksArgs a, int64_t tile_end, int G)
 {
     __shared__ LinksGroupSmem s;
@@ -77,6 +100,11 @@ int launch_links_full(const SegTable& tab, const SkyDev& sky, const lisa_grid& h
 #else
         links_full_kernel<true><<<(unsigned)tiles, kTile, 0, st>>>(a);
 #endif
+    } else if (tiles < 2 * 152) {
+        // split the links (and, for very short ranges, the samples) so that
+        // the launch fills about two CTAs per SM
+        const int parts = tiles * 6 >= 2 * 152 ? 1 : tiles * 12 >= 2 * 152 ? 2 : 4;
+        links_full_kernel_f64_split<<<dim3((unsigned)tiles, 6u * parts), kTile, 0, st>>>(a, parts);
     } else {
         links_full_kernel<false><<<(unsigned)tiles, kTile, 0, st>>>(a);
     }

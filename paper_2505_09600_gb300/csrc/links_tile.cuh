@@ -187,6 +187,40 @@ __device__ void links_tile_prologue(const LinksArgs& a, const TileGeo& g, int64_
     __syncthreads();
 }
 
+// FP64 link li at sample m (block coordinate u, k.R/c of the three
+// spacecraft kR): the projection of the polarisation tensors on n_l - k
+// over |n_l - k|^2, times the difference of h at the sender and receiver ends.
+__device__ __forceinline__ double link_value_f64(const LinksArgs& a, const TileGeo& g, double u, int64_t m,
+                                                 const LinksTile<false>& s, int li, const double* kR)
+{
+    const double* __restrict__ hp = (const double*)a.hp;
+    const double* __restrict__ hc = (const double*)a.hc;
+    double d[3], dd = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        d[c] = tg_eval(g, kQN + 3 * li + c, u) - a.sky.k[c];
+        dd = fma(d[c], d[c], dd);
+    }
+    if (!(dd >= 2e-12)) return 0.0;
+    const double* ku = a.sky.u;
+    const double* kv = a.sky.v;
+    const double c2 = a.sky.c2p, s2 = a.sky.s2p;
+    const double un = ku[0] * d[0] + ku[1] * d[1] + ku[2] * d[2];
+    const double vn = kv[0] * d[0] + kv[1] * d[1] + kv[2] * d[2];
+    const double xp = un * un - vn * vn, xc = 2.0 * un * vn;
+    const double Fp = (xp * c2 + xc * s2) / dd, Fc = (xc * c2 - xp * s2) / dd;
+    const double ds = tg_eval(g, kQT + li, u) + kR[link_sender(li)];
+    const double dr = kR[link_receiver(li)];
+    int64_t js, jr;
+    double es, er;
+    split_f64(a.hm, m, ds, js, es);
+    split_f64(a.hm, m, dr, jr, er);
+    double ps, cs, pr, cr;
+    interp_pair<double>(s.win, s.wlo, s.wlen, hp, hc, a.hm.n_in, js, es, ps, cs);
+    interp_pair<double>(s.win, s.wlo, s.wlen, hp, hc, a.hm.n_in, jr, er, pr, cr);
+    return Fp * (ps - pr) + Fc * (cs - cr);
+}
+
 // The six links at sample m of the link grid, stored to out[li * stride].
 template <bool MIXED>
 __device__ __forceinline__ void links_sample(const LinksArgs& a, const TileGeo& g, int64_t ic, int64_t m,
@@ -215,32 +249,7 @@ __device__ __forceinline__ void links_sample(const LinksArgs& a, const TileGeo& 
 #pragma unroll
         for (int sc = 0; sc < 3; ++sc) kR[sc] = tg_eval(g, kRowKR + sc, u);
 #pragma unroll 1
-        for (int li = 0; li < 6; ++li) {
-            double d[3], dd = 0.0;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                d[c] = tg_eval(g, kQN + 3 * li + c, u) - a.sky.k[c];
-                dd = fma(d[c], d[c], dd);
-            }
-            double y = 0.0;
-            if (dd >= 2e-12) {
-                const double un = ku[0] * d[0] + ku[1] * d[1] + ku[2] * d[2];
-                const double vn = kv[0] * d[0] + kv[1] * d[1] + kv[2] * d[2];
-                const double xp = un * un - vn * vn, xc = 2.0 * un * vn;
-                const double Fp = (xp * c2 + xc * s2) / dd, Fc = (xc * c2 - xp * s2) / dd;
-                const double ds = tg_eval(g, kQT + li, u) + kR[link_sender(li)];
-                const double dr = kR[link_receiver(li)];
-                int64_t js, jr;
-                double es, er;
-                split_f64(a.hm, m, ds, js, es);
-                split_f64(a.hm, m, dr, jr, er);
-                double ps, cs, pr, cr;
-                interp_pair<double>(s.win, wlo, wlen, hp, hc, a.hm.n_in, js, es, ps, cs);
-                interp_pair<double>(s.win, wlo, wlen, hp, hc, a.hm.n_in, jr, er, pr, cr);
-                y = Fp * (ps - pr) + Fc * (cs - cr);
-            }
-            out[li * stride] = y;
-        }
+        for (int li = 0; li < 6; ++li) out[li * stride] = link_value_f64(a, g, u, m, s, li, kR);
     } else {
         // in-tile offsets are 32-bit: no 64-bit conversions (FP64 pipe) per sample
         const float u = (float)(int)(m - ic) * s.inv_half;

@@ -41,12 +41,12 @@ __global__ void __launch_bounds__(kTile) tdi_kernel(TdiArgs a)
         store_channels<Real>(acc[0], acc[1], acc[2], a.channels, a.bl, a.t0_out, a.dt_out, i, (Real*)a.xyz, a.nout);
 }
 
-// FP64 form on short ranges: the TDI sums of one tile are split over kSplit
-// CTAs of kTile / kSplit samples each (the FP64 pipe of an SM, not its
+// FP64 form on short ranges: the TDI sums of one tile are split over
+// `split` CTAs of kTile / split samples each (the FP64 pipe of an SM, not its
 // threads, bounds the per-tile form, and a hybrid's full part covers only a
 // few tiles).  Thread t handles channel t / spc of sample t % spc; the three
 // channels meet in shared memory for A/E/T, the blend and the store.
-constexpr int kSplit = 4;
+constexpr int kSplitMin = 4;   // spc <= kTile / kSplitMin samples per CTA
 
 __device__ __forceinline__ double tdi_channel_f64(const TdiArgs& a, const TileGeo& g, int64_t ic, int64_t i,
                                                   const TdiTile<false>& s, int ch)
@@ -83,12 +83,11 @@ __device__ __forceinline__ double tdi_channel_f64(const TdiArgs& a, const TileGe
     return acc;
 }
 
-__global__ void __launch_bounds__(kTile) tdi_kernel_f64_split(TdiArgs a)
+__global__ void __launch_bounds__(kTile) tdi_kernel_f64_split(TdiArgs a, int spc)
 {
     __shared__ TileGeo g;
     __shared__ TdiTile<false> s;
-    __shared__ double xs[3][kTile / kSplit];
-    constexpr int spc = kTile / kSplit;
+    __shared__ double xs[3][kTile / kSplitMin];
     const int64_t i0 = (a.tile0 + blockIdx.x) * (int64_t)kTile;
     const int64_t ic = i0 + kTile / 2;
     tile_geo_load(g, a.tab, ic, SkyDev{});
@@ -142,7 +141,11 @@ int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int prec
         rc = launch_tdi_comb(a, tiles, st);
     } else {
         if (precision == LISA_MIXED) tdi_kernel<true><<<(unsigned)tiles, kTile, 0, st>>>(a);
-        else if (tiles < 2 * 152) tdi_kernel_f64_split<<<dim3((unsigned)tiles, kSplit), kTile, 0, st>>>(a);
+        else if (tiles < 2 * 152) {
+            // about two CTAs per SM: 4, 8 or 16 CTAs per tile
+            const int split = tiles * 4 >= 2 * 152 ? 4 : tiles * 8 >= 2 * 152 ? 8 : 16;
+            tdi_kernel_f64_split<<<dim3((unsigned)tiles, (unsigned)split), kTile, 0, st>>>(a, kTile / split);
+        }
         else tdi_kernel<false><<<(unsigned)tiles, kTile, 0, st>>>(a);
         rc = cuda_status(cudaGetLastError(), "tdi_kernel launch");
     }
