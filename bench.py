@@ -490,6 +490,61 @@ def bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, st
     return res
 
 
+def mismatches(L, torch, dev, src, orbit, sky, hp64, hc64, hp32, hc32, gens=(20, 15), f_hybs=(3e-4, 1e-3),
+               with_nlo=True):
+    """The paper's accuracy criteria (Sec. V A) on this workload: mismatch
+    1 - |O| of A, E, T (Eq. normalized_overlap; noise-weighted inner products
+    of Eq. scalar_product with the analytic PSDs, band 1e-4 Hz to 0.02 Hz for
+    TDI 2.0 and 0.05 Hz for TDI 1.5) of the hybrid (double-float, f_H = 3e-4
+    and 1e-3 Hz), the LFA (double-float; next-to-leading order in FP64) and
+    the mixed hybrid, each against the FP64 full response; and the mixed
+    hybrid against the double-float hybrid."""
+    n = src.n
+    nfft = L.lisa_fft_length(n)
+    nf = nfft // 2 + 1
+    Tw, sig = 800 * src.dt, 20 * src.dt
+    res = {}
+    w = torch.empty((2, nf), device=dev, dtype=torch.float64)
+    full = torch.empty((3, n), device=dev, dtype=torch.float64)
+    x = torch.empty((3, n), device=dev, dtype=torch.float64)
+    x32 = torch.empty((3, n), device=dev, dtype=torch.float32)
+    ip = torch.empty(9, device=dev, dtype=torch.float64)
+
+    def mm(a, b):
+        L.lisa_inner_aet(src.grid, nfft, a, b, L.F64, w, ip)
+        v = ip.cpu().numpy().reshape(3, 3)
+        return [float(1.0 - abs(v[c, 0] / math.sqrt(v[c, 1] * v[c, 2]))) for c in range(3)]
+
+    for gen in gens:
+        f_max = 0.02 if gen == 20 else 0.05
+        L.lisa_noise_weights_aet(src.grid, nfft, gen, ORBIT_KW.get("L_m", 2.5e9), 1.0, 1, 1e-4, f_max, w)
+        L.lisa_response_full(orbit, sky, src.grid, hp64, hc64, L.F64, gen, L.AET, src.grid, full)
+        r = {"band_hz": [1e-4, f_max]}
+        for fh in f_hybs:
+            tH = L.lisa_t_hyb_from_f(fh, src.mc_s, src.tc)
+            L.lisa_response_hybrid(orbit, sky, src.grid, hp64, hc64, L.DF, gen, L.LFA_UNEQUAL, L.AET, tH, Tw, sig,
+                                   src.grid, x)
+            r["hybrid_df_fH_%g" % fh] = mm(full, x)
+            if fh == f_hybs[-1]:
+                L.lisa_response_hybrid(orbit, sky, src.grid, hp32, hc32, L.MIXED, gen, L.LFA_UNEQUAL, L.AET, tH, Tw,
+                                       sig, src.grid, x32)
+                xm = x32.double()
+                r["hybrid_mixed_fH_%g" % fh] = mm(full, xm)
+                r["hybrid_mixed_vs_hybrid_df_fH_%g" % fh] = mm(x, xm)
+                del xm
+        L.lisa_response_lfa(orbit, sky, src.grid, hp64, hc64, L.DF, gen, L.LFA_UNEQUAL, L.AET, src.grid, x)
+        r["lfa_df"] = mm(full, x)
+        if with_nlo and gen == 20:
+            L.lisa_response_lfa(orbit, sky, src.grid, hp64, hc64, L.F64, gen, L.LFA_NLO, L.AET, src.grid, x)
+            r["lfa_nlo_f64"] = mm(full, x)
+        res["tdi%d" % gen] = r
+    res["channels"] = "A, E, T"
+    res["targets"] = ("Sec. V A: hybrid A,E < 1e-5 (1.5 and 2.0); LFA A,E < 1e-3 (1.5), < 1e-1 (2.0); "
+                      "T: LFA 10-100 %, hybrid < 10 %")
+    del w, full, x, x32, ip
+    return res
+
+
 def bench_loglike(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig):
     """Log-likelihood evaluation as the paper times it (Sec. IV, steps ii-v
     on given polarisations): hybrid response -> A, E, T -> real FFTs ->
@@ -856,6 +911,9 @@ def run_ours(args):
     corrector = None
     if not args.no_corrector and rank == 0:
         corrector = bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig)
+    mism = None
+    if not args.no_mismatch and rank == 0:
+        mism = mismatches(L, torch, dev, src, orbit, sky, hp64, hc64, hp32, hc32)
     loglike = None
     if not args.no_loglike and rank == 0:
         loglike = bench_loglike(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, stream, tH, Tw, sig)
@@ -934,6 +992,8 @@ def run_ours(args):
         line["pe_draws"] = pe_draws
     if loglike is not None:
         line["loglike"] = loglike
+    if mism is not None:
+        line["mismatch"] = mism
     if not args.no_cpu and world == 1:
         cb = oracle_hybrid_rate(src, budget_s=args.cpu_budget, one_core=True)
         er = sampled_errors(src, gpu_out, fp32_inputs=False, chunk=cb.get("chunk"))
@@ -988,6 +1048,7 @@ def main():
     ap.add_argument("--no-corrector", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-loglike", action="store_true")
+    ap.add_argument("--no-mismatch", action="store_true")
     ap.add_argument("--batch-sources", type=int, default=1024)
     ap.add_argument("--no-pe", action="store_true")
     ap.add_argument("--pe-draws", type=int, default=4096)
