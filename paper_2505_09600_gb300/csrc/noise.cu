@@ -133,10 +133,29 @@ __device__ __forceinline__ void inner_bins_f64(const Cplx* __restrict__ X, const
 //    scale 2^-128 and is used in FP32 when it is zero or in [2^-60, 2^61)
 //    after scaling (converted with integer operations, off the FP64 pipe).
 //  - A product with an operand or weight outside those ranges is formed in FP64.
-//    Each square is decided by its own operand, so <X|X> does not depend on Y.
-//  - A thread whose FP32 sums of squares reach 2^120 or overflow (the cross sums
-//    are bounded by them) recomputes its bins in FP64.
+//    Each square is decided by its own operand.
+//  - A thread whose FP32 sums of squares of X (or of Y) reach 2^120 or overflow
+//    recomputes those sums over its bins in FP64, and the cross sums with them
+//    (the cross sums are bounded by the squares).  The sums of squares of the
+//    other operand are kept, so <X|X> does not depend on Y.
 constexpr int kFlush = 16;
+
+// FP64 recomputation of a thread's bins for the sums selected: the squares of
+// X (redo_x), of Y (redo_y) and the cross sums (either).
+template <typename Cplx>
+__device__ __noinline__ void inner_bins_redo_f64(const Cplx* __restrict__ X, const Cplx* __restrict__ Y,
+                                                 const double* __restrict__ w, int64_t nf, bool redo_x, bool redo_y,
+                                                 double* acc)
+{
+    double r[9];
+    inner_bins_f64(X, Y, w, nf, r);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[3 * c + 0] = r[3 * c + 0];
+        if (redo_x) acc[3 * c + 1] = r[3 * c + 1];
+        if (redo_y) acc[3 * c + 2] = r[3 * c + 2];
+    }
+}
 
 // w * 2^-128 as an FP32 number, formed from the bits of w with integer
 // operations (round to nearest, ties away), for w == 0 or w * 2^-128 in
@@ -157,13 +176,17 @@ __device__ __forceinline__ void inner_bins_f32(const float2* __restrict__ X, con
     float s[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) { acc[q] = 0.0; s[q] = 0.f; }
-    bool bad = false;
+    bool bad_x = false, bad_y = false;
     int cnt = 0;
     auto flush = [&]() {
-        bool fine = true;
+        bool fine_x = true, fine_y = true;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) fine = fine && s[3 * c + 1] < 1.329228e36f && s[3 * c + 2] < 1.329228e36f;
-        bad = bad || !fine;
+        for (int c = 0; c < 3; ++c) {
+            fine_x = fine_x && s[3 * c + 1] < 1.329228e36f;
+            fine_y = fine_y && s[3 * c + 2] < 1.329228e36f;
+        }
+        bad_x = bad_x || !fine_x;
+        bad_y = bad_y || !fine_y;
 #pragma unroll
         for (int q = 0; q < 9; ++q) { acc[q] += (double)s[q]; s[q] = 0.f; }
     };
@@ -220,7 +243,7 @@ __device__ __forceinline__ void inner_bins_f32(const float2* __restrict__ X, con
         if (++cnt == kFlush) { flush(); cnt = 0; }
     }
     flush();
-    if (bad) inner_bins_f64(X, Y, w, nf, acc);
+    if (bad_x || bad_y) inner_bins_redo_f64(X, Y, w, nf, bad_x, bad_y, acc);
 }
 
 // Per block: the nine sums over the block's threads, FP64 in a fixed-order tree.

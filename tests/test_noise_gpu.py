@@ -88,7 +88,9 @@ def test_inner_products_match_oracle(L, precision, pad):
     got = out.cpu().numpy().reshape(3, 3)
     want = ON.inner_aet(x.double().cpu().numpy(), y.double().cpu().numpy(), s.dt, f_min, f_max, 20, L_M, 1.0, True,
                         nfft=m)
-    tol = 1e-11 if precision == 0 else 2e-5
+    # mixed: FP32 transforms, products and partial sums (measured against the
+    # FP64 products of the same FP32 series: 1.4e-7 for A and E, 6.5e-7 for T)
+    tol = 1e-11 if precision == 0 else 2e-6
     np.testing.assert_allclose(got, want, rtol=tol)
     np.testing.assert_allclose(ON.overlap(got), ON.overlap(want), rtol=tol, atol=tol)
     # <x|x> with y = x (one transform) equals the xx product of the pair call
@@ -151,3 +153,81 @@ def test_mismatch_of_response_forms(L):
     ip = out.cpu().numpy().reshape(3, 3)
     mm = ON.mismatch(ip)
     assert np.all(mm[:2] < 1e-8), mm
+
+
+def test_inner_products_overflow_recompute(L):
+    """A thread whose FP32 sums of weighted scaled squares overflow recomputes
+    them in FP64: spectra whose loudest component is 2^-1.5 (inside the
+    scaled FP32 window) with weights raised by 2^40 (their scaled values still
+    inside [2^-60, 2^61)) push a single bin's scaled product past 2^128.
+    Checked against the oracle (weights x 2^40: an exact power-of-two
+    scaling), and the sums of squares of a quiet operand are kept from its
+    FP32 path: <q|q> of the pair call (q, loud) equals that of (q, q)."""
+    s = synth.cfg2_small(n=30001)
+    x = _hybrid(L, s, 1)
+    peak = torch.fft.rfft(x.double(), dim=1).abs().max().item()
+    loud = (x * float(2.0 ** -1.5 / peak)).contiguous()
+    quiet = (x * float(2.0 ** -40 / peak)).contiguous()
+    f_min, f_max = 1e-4, 2.5e-2
+    nf = s.n // 2 + 1
+    w = torch.empty((2, nf), device="cuda", dtype=torch.float64)
+    L.lisa_noise_weights_aet(s.grid, 0, 20, L_M, 1.0, 1, f_min, f_max, w)
+    w = (w * 2.0 ** 40).contiguous()
+    # the FP32 path is taken for bins whose scaled weight and components lie in
+    # their windows; some of those bins alone overflow FP32 for the loud operand
+    ws = w.cpu().numpy() * 2.0 ** -128
+    X = np.fft.rfft(loud.double().cpu().numpy(), axis=1)
+    comp = np.maximum(np.abs(X.real), np.abs(X.imag))
+    w_in = (ws >= 2.0 ** -60) & (ws < 2.0 ** 61)
+    rows = np.stack([ws[0], ws[0], ws[1]])
+    win = np.stack([w_in[0], w_in[0], w_in[1]]) & (comp >= 2.0 ** -92) & (comp < 0.5)
+    prod = rows * (np.abs(X) * 2.0 ** 64) ** 2
+    assert (win & (prod >= 2.0 ** 128)).any()
+    Q = np.fft.rfft(quiet.double().cpu().numpy(), axis=1)
+    assert (rows * (np.abs(Q) * 2.0 ** 64) ** 2).max() < 2.0 ** 110
+
+    def ip(a, b):
+        out = torch.empty(9, device="cuda", dtype=torch.float64)
+        L.lisa_inner_aet(s.grid, 0, a, b, 1, w, out)
+        return out.cpu().numpy().reshape(3, 3)
+
+    def want(a, b):
+        return ON.inner_aet(a.double().cpu().numpy(), b.double().cpu().numpy(), s.dt, f_min, f_max, 20, L_M, 1.0,
+                            True) * 2.0 ** 40
+
+    got = {}
+    for key, (a, b) in {"ll": (loud, loud), "ql": (quiet, loud), "lq": (loud, quiet), "qq": (quiet, quiet)}.items():
+        got[key] = ip(a, b)
+        assert np.isfinite(got[key]).all(), key
+        np.testing.assert_allclose(got[key], want(a, b), rtol=2e-5, err_msg=key)
+    np.testing.assert_allclose(got["ql"][:, 1], got["qq"][:, 1], rtol=1e-12)
+    np.testing.assert_allclose(got["lq"][:, 2], got["qq"][:, 2], rtol=1e-12)
+    np.testing.assert_allclose(got["ql"][:, 2], got["ll"][:, 2], rtol=1e-12)
+
+
+def test_mixed_inner_products_against_f64(L):
+    """The mixed inner products (FP32 transforms, FP32 products and partial
+    sums) against the FP64 ones of the same FP32 series, and the mismatch
+    they give at the scale of the paper's criterion (Sec. V A: 1e-5)."""
+    s = synth.cfg2_small(n=30001)
+    x = _hybrid(L, s, 1)
+    f_min, f_max = 1e-4, 2.5e-2
+    nf = s.n // 2 + 1
+    w = torch.empty((2, nf), device="cuda", dtype=torch.float64)
+    L.lisa_noise_weights_aet(s.grid, 0, 20, L_M, 1.0, 1, f_min, f_max, w)
+    # y: x with a small admixture of a shifted copy, mismatch of order 1e-5
+    y = (x + 2e-2 * torch.roll(x, 1, dims=1)).contiguous()
+
+    def ip(a, b, precision):
+        out = torch.empty(9, device="cuda", dtype=torch.float64)
+        L.lisa_inner_aet(s.grid, 0, a, b, precision, w, out)
+        return out.cpu().numpy().reshape(3, 3)
+
+    m32 = ip(x, y, 1)
+    m64 = ip(x.double().contiguous(), y.double().contiguous(), 0)
+    rel = np.abs(m32 - m64) / np.abs(m64)
+    mm32, mm64 = ON.mismatch(m32), ON.mismatch(m64)
+    print("mixed vs FP64 inner products, relative:", rel.max(axis=1), "mismatch mixed", mm32, "FP64", mm64)
+    assert np.all(rel < 2e-6), rel
+    assert np.all(mm64[:2] > 1e-6) and np.all(mm64[:2] < 1e-4), mm64
+    assert np.all(np.abs(mm32 - mm64)[:2] < 2e-7), (mm32, mm64)
