@@ -335,8 +335,11 @@ int lisa_noise_weights_aet(lisa_grid grid, int64_t nfft, int tdi_gen, double L_m
  * in FP64.  LISA_MIXED: a bin's products and weighting in FP32 (spectra
  * scaled by 2^64, weights by 2^-128, both exact), FP32 running sums added to
  * FP64 ones every 16 bins; a bin whose spectrum components leave
- * [2^-92, 2^-1) or whose scaled weight leaves [2^-60, 2^61) is formed in FP64,
- * so any finite input is accepted.  Device scratch from the stream-ordered
+ * [2^-92, 2^-1) or whose scaled weight leaves [2^-60, 2^61) is formed in FP64;
+ * a thread whose FP32 sums of squares of x (or of y) reach 2^120 recomputes
+ * those sums and the cross sums over its bins in FP64, keeping the other
+ * operand's (so <x|x> does not depend on y).  Any finite input is accepted.
+ * Device scratch from the stream-ordered
  * allocator on `stream`. */
 int lisa_inner_aet(lisa_grid grid, int64_t nfft, const void* x, const void* y, int precision, const double* w,
                    double* out, void* stream);
@@ -461,11 +464,21 @@ int lisa_corrector_train(lisa_corrector* c, const float* feats, const float* tar
  * (decided on the device).  hp/hc are FP32 (LISA_MIXED). */
 int lisa_corrector_links(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
                          const void* hp, const void* hc, lisa_grid out, void* y, void* stream);
-/* Hybrid with the corrector (LISA_MIXED, frozen TDI): as lisa_response_hybrid,
- * but the LFA side is the full TDI combine of the corrected links. */
+/* Hybrid with the corrector (LISA_MIXED, frozen TDI), in three zones joined by
+ * the sigmoid of Sec. IV (Eqs. sigmoid, hybridized_xs) with window T_win and
+ * width sigma at each seam:
+ *   t <= t_lo + T/2            plain LFA channels (as lisa_response_hybrid),
+ *   t_lo - T/2 .. t_hyb + T/2  the full TDI combine of the corrected links,
+ *   t >= t_hyb - T/2           the full response.
+ * Weights: LFA S_lo(t) S_hi(t), corrected (1 - S_lo(t)) S_hi(t), full
+ * 1 - S_hi(t), with S(t; t_s) = 1 / (1 + exp((t - t_s) / sigma)); they sum to
+ * one at every sample.  The costly corrected zone is then only as long as
+ * the time the source spends between the two switch frequencies.
+ * t_lo = -INFINITY: no plain zone (corrected links up to t_hyb).
+ * LISA_EINVAL if t_lo is NaN, +INFINITY or later than t_hyb. */
 int lisa_response_hybrid_corrected(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
-                                   const void* hp, const void* hc, int tdi_gen, int channels, double t_hyb,
-                                   double T_win, double sigma, lisa_grid out, void* xyz, void* stream);
+                                   const void* hp, const void* hc, int tdi_gen, int channels, double t_lo,
+                                   double t_hyb, double T_win, double sigma, lisa_grid out, void* xyz, void* stream);
 /* Counters since the last reset (synchronises the device): spot-checked
  * tiles, failed spot checks, tiles above the band, tiles recomputed after a
  * failure, largest spot-check error.  Returns LISA_ECORRECTOR if any spot

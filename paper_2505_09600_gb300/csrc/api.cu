@@ -107,6 +107,21 @@ int make_table(const lisa_orbit* orbit, const lisa_grid& g, Scratch& sc, SegTabl
     return LISA_OK;
 }
 
+// The tables of two grids (one launch).
+int make_table_pair(const lisa_orbit* orbit, const lisa_grid& g1, const lisa_grid& g2, Scratch& sc, SegTable& tab1,
+                    SegTable& tab2, cudaStream_t st)
+{
+    const int S1 = seg_samples(g1.dt), S2 = seg_samples(g2.dt);
+    const int64_t n1 = seg_count(g1.n > 0 ? g1.n : 1, S1), n2 = seg_count(g2.n > 0 ? g2.n : 1, S2);
+    double* c1 = (double*)sc.alloc(sizeof(double) * (size_t)(n1 + n2) * kNQ * kNC);
+    if (!c1) return sc.status();
+    double* c2 = c1 + (size_t)n1 * kNQ * kNC;
+    LISA_TRY(build_seg_table_pair(make_orbit_dev(*orbit), g1, S1, c1, n1, g2, S2, c2, n2, st));
+    tab1 = SegTable{c1, n1, S1, g1.t0, g1.dt};
+    tab2 = SegTable{c2, n2, S2, g2.t0, g2.dt};
+    return LISA_OK;
+}
+
 // Upper bound of any single light time (for halo sizing).
 double max_light_time(const lisa_orbit* o, const lisa_grid& g)
 {
@@ -136,11 +151,17 @@ void hybrid_split(const lisa_grid& out, double t_hyb, double Tw, int64_t& iL_out
     const int64_t n = out.n;
     volatile double hi_thr = t_hyb + 0.5 * Tw, lo_thr = t_hyb - 0.5 * Tw;
     auto t_at = [&](int64_t i) { volatile double p = (double)i * out.dt; return out.t0 + p; };
-    int64_t iL = (int64_t)floor((hi_thr - out.t0) / out.dt);
+    // clamped in FP64 before the conversions (a far switch time stays defined)
+    const double lim = (double)n + 2.0;
+    double fl = floor((hi_thr - out.t0) / out.dt);
+    fl = fl < -2.0 ? -2.0 : (fl > lim ? lim : fl);
+    int64_t iL = (int64_t)fl;
     iL = iL < -1 ? -1 : (iL > n - 1 ? n - 1 : iL);
     while (iL + 1 <= n - 1 && t_at(iL + 1) <= hi_thr) ++iL;
     while (iL >= 0 && !(t_at(iL) <= hi_thr)) --iL;
-    int64_t iF = (int64_t)ceil((lo_thr - out.t0) / out.dt);
+    double cl = ceil((lo_thr - out.t0) / out.dt);
+    cl = cl < -1.0 ? -1.0 : (cl > lim ? lim : cl);
+    int64_t iF = (int64_t)cl;
     iF = iF < 0 ? 0 : (iF > n ? n : iF);
     while (iF - 1 >= 0 && t_at(iF - 1) >= lo_thr) --iF;
     while (iF < n && !(t_at(iF) >= lo_thr)) ++iF;

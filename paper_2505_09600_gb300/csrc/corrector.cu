@@ -43,17 +43,18 @@
 //                         layers fused; either on given features or fused with
 //                         the features and the y = z (1 + eps) + s * MLP
 //                         epilogue
-//   mlp_train_kernel      training: forward + MSE + backward fused on the
-//                         warp-level MMAs (nvcuda::wmma); weight gradients are
-//                         accumulated per block in shared memory and added to
-//                         the global FP32 gradient once per block
-//   adam_kernel           Adam on FP32 master weights
-//   publish_kernel        padded BF16 copies of the weights for the MMAs, and
-//   publish_tc_kernel     their image in the tensor-core operand layout
+//   mlp_train_tc_kernel   training: forward + MSE + backward fused on the
+//                         same tensor cores; weight gradients as MMAs over the
+//                         rows, accumulated in tensor memory; one partial
+//                         gradient per CTA
+//   grad_reduce_kernel    the partials summed in a fixed order
+//   adam_kernel           Adam on FP32 master weights (summing the partials
+//                         itself in training), then publishing
+//   publish_kernel        FP32 biases and the BF16 weight images of both
+//                         tensor-core kernels
 //   corr_fallback_kernel  full links on flagged / spot / failed tiles
 #include <cuda_bf16.h>
 #include <math.h>
-#include <mma.h>
 #include <string.h>
 
 #include <new>
@@ -65,19 +66,12 @@
 #include "tcgen05.cuh"
 #include "tile_geo.cuh"
 
-using namespace nvcuda;
-
 namespace lisa {
 
 constexpr int kIn = 47, kInP = 48, kWid = 64, kOut = 6, kOutP = 16;
 constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + kWid * kIn, kOffW2 = kOffB1 + kWid, kOffB2 = kOffW2 + kWid * kWid,
                   kOffW3 = kOffB2 + kWid, kOffB3 = kOffW3 + kWid * kWid, kOffW4 = kOffB3 + kWid,
                   kOffB4 = kOffW4 + kOut * kWid, kNParams = kOffB4 + kOut;
-
-struct MlpDev {
-    const __nv_bfloat16 *W1, *W2, *W3, *W4;   // padded: [64][48], [64][64], [64][64], [16][64]
-    const float *b1, *b2, *b3, *b4;           // padded: 64, 64, 64, 16
-};
 
 struct CorrStats {
     unsigned spot_tiles, spot_failed, band_tiles, fallback_tiles, call_failed, max_err_bits;
@@ -121,89 +115,6 @@ __device__ __forceinline__ float gelu_grad_f(float x)
     return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * c * fmaf(3.f * 0.044715f, x * x, 1.f);
 }
 
-using FragA = wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::row_major>;
-using FragAc = wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::col_major>;
-using FragBc = wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::col_major>;
-using FragBr = wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::row_major>;
-using FragC = wmma::fragment<wmma::accumulator, 16, 16, 16, float>;
-
-// acc[16][ldc] = act[16][K] . W[N][K]^T  (W row-major = B column-major)
-__device__ __forceinline__ void layer_mma(const __nv_bfloat16* act, int lda, const __nv_bfloat16* W, int K, int N,
-                                          float* acc, int ldc)
-{
-    for (int j = 0; j < N / 16; ++j) {
-        FragC c;
-        wmma::fill_fragment(c, 0.f);
-        for (int q = 0; q < K / 16; ++q) {
-            FragA a;
-            FragBc b;
-            wmma::load_matrix_sync(a, act + q * 16, lda);
-            wmma::load_matrix_sync(b, W + (size_t)j * 16 * K + q * 16, K);
-            wmma::mma_sync(c, a, b, c);
-        }
-        wmma::store_matrix_sync(acc + j * 16, c, ldc, wmma::mem_row_major);
-    }
-}
-
-// --------------------------------------------------------------------------
-// training: forward + MSE + backward
-// --------------------------------------------------------------------------
-struct __align__(128) TrainWarp {
-    __nv_bfloat16 a0[16][kInP];         // input (bf16)
-    __nv_bfloat16 a[3][16][kWid];       // hidden activations
-    float z[3][16][kWid];               // hidden pre-activations
-    __nv_bfloat16 dz[16][kWid];         // current dZ (bf16 operand of the MMAs)
-    float tmp[16][kWid];                // accumulator staging
-};
-struct __align__(128) TrainBlock {
-    float gW1[kWid][kInP], gW2[kWid][kWid], gW3[kWid][kWid], gW4[kOutP][kWid];
-    float gb1[kWid], gb2[kWid], gb3[kWid], gb4[kOutP];
-    float loss;
-};
-constexpr int kTrainWarps = 2;
-constexpr size_t kTrainSmem = sizeof(TrainBlock) + kTrainWarps * sizeof(TrainWarp);
-static_assert(sizeof(TrainBlock) % 128 == 0 && sizeof(TrainWarp) % 128 == 0, "WMMA pointers need 32-byte alignment");
-
-// g[N][K] += dz[16][N]^T . act[16][K]  (block accumulator, shared atomics)
-__device__ __forceinline__ void accum_weight_grad(const __nv_bfloat16* dz, int ldz, const __nv_bfloat16* act, int lda,
-                                                  int N, int K, float* g, int ldg, float* tmp)
-{
-    const int lane = threadIdx.x & 31;
-    for (int i = 0; i < N / 16; ++i) {
-        for (int j = 0; j < K / 16; ++j) {
-            FragC c;
-            wmma::fill_fragment(c, 0.f);
-            FragAc a;   // dz^T: element (n, m) at dz[m*ldz + n]
-            FragBr b;   // act: element (m, k) at act[m*lda + k]
-            wmma::load_matrix_sync(a, dz + i * 16, ldz);
-            wmma::load_matrix_sync(b, act + j * 16, lda);
-            wmma::mma_sync(c, a, b, c);
-            wmma::store_matrix_sync(tmp, c, 16, wmma::mem_row_major);
-            __syncwarp();
-            for (int e = lane; e < 256; e += 32) atomicAdd(&g[(i * 16 + e / 16) * ldg + j * 16 + e % 16], tmp[e]);
-            __syncwarp();
-        }
-    }
-}
-
-// dA[16][K] = dz[16][N] . W[N][K]
-__device__ __forceinline__ void input_grad(const __nv_bfloat16* dz, int ldz, const __nv_bfloat16* W, int N, int K,
-                                           float* dA, int ldd)
-{
-    for (int j = 0; j < K / 16; ++j) {
-        FragC c;
-        wmma::fill_fragment(c, 0.f);
-        for (int q = 0; q < N / 16; ++q) {
-            FragA a;
-            FragBr b;
-            wmma::load_matrix_sync(a, dz + q * 16, ldz);
-            wmma::load_matrix_sync(b, W + (size_t)q * 16 * K + j * 16, K);
-            wmma::mma_sync(c, a, b, c);
-        }
-        wmma::store_matrix_sync(dA + j * 16, c, ldd, wmma::mem_row_major);
-    }
-}
-
 // SplitMix64 (Steele, Lea, Flood 2014): minibatch row selection.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 {
@@ -213,159 +124,9 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
     return x ^ (x >> 31);
 }
 
-struct TrainArgs {
-    MlpDev m;
-    const float* x;        // [n_data][kInP]
-    const float* tgt;      // [n_data][kOut]
-    int64_t n_data;
-    int64_t M;             // rows of this pass (batch size, or n_data)
-    int sampled;           // 1: row r is data row splitmix64(seed + r) % n_data
-    uint64_t seed;
-    int rows_per_block;
-    float* grad;           // [kNParams], accumulated
-    float* loss;           // accumulated (optional)
-};
-
-__device__ __forceinline__ int64_t data_row(const TrainArgs& A, int64_t r)
-{
-    return A.sampled ? (int64_t)(splitmix64(A.seed + (uint64_t)r) % (uint64_t)A.n_data) : r;
-}
-
-__global__ void __launch_bounds__(32 * kTrainWarps) mlp_train_kernel(TrainArgs A)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    TrainBlock& B = *reinterpret_cast<TrainBlock*>(smem_raw);
-    TrainWarp* warps = reinterpret_cast<TrainWarp*>(smem_raw + sizeof(TrainBlock));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    TrainWarp& W = warps[warp];
-    const MlpDev& m = A.m;
-    float* gb = &B.gW1[0][0];
-    for (int e = threadIdx.x; e < (int)(sizeof(TrainBlock) / sizeof(float)); e += blockDim.x) gb[e] = 0.f;
-    __syncthreads();
-    const float inv_m = 1.f / (float)A.M;
-    const __nv_bfloat16* Ws[3] = {m.W1, m.W2, m.W3};
-    const float* bs[3] = {m.b1, m.b2, m.b3};
-    const int64_t row_begin = (int64_t)blockIdx.x * A.rows_per_block;
-    const int64_t row_end = row_begin + A.rows_per_block < A.M ? row_begin + A.rows_per_block : A.M;
-    for (int64_t r0 = row_begin + warp * 16; r0 < row_end; r0 += 16 * kTrainWarps) {
-        // ---- forward
-        for (int e = lane; e < 16 * (kInP / 4); e += 32) {
-            const int r = e / (kInP / 4), c4 = e % (kInP / 4);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r0 + r < row_end) v = *reinterpret_cast<const float4*>(A.x + data_row(A, r0 + r) * kInP + 4 * c4);
-            W.a0[r][4 * c4] = __float2bfloat16(v.x);
-            W.a0[r][4 * c4 + 1] = __float2bfloat16(v.y);
-            W.a0[r][4 * c4 + 2] = __float2bfloat16(v.z);
-            W.a0[r][4 * c4 + 3] = __float2bfloat16(v.w);
-        }
-        __syncwarp();
-        for (int l = 0; l < 3; ++l) {
-            if (l == 0) layer_mma(&W.a0[0][0], kInP, Ws[0], kInP, kWid, &W.z[0][0][0], kWid);
-            else layer_mma(&W.a[l - 1][0][0], kWid, Ws[l], kWid, kWid, &W.z[l][0][0], kWid);
-            __syncwarp();
-            for (int e = lane; e < 16 * kWid; e += 32) {
-                const int r = e / kWid, c = e % kWid;
-                const float zz = W.z[l][r][c] + bs[l][c];
-                W.z[l][r][c] = zz;
-                W.a[l][r][c] = __float2bfloat16(gelu_f(zz));
-            }
-            __syncwarp();
-        }
-        layer_mma(&W.a[2][0][0], kWid, m.W4, kWid, kOutP, &W.tmp[0][0], kWid);
-        __syncwarp();
-        // ---- loss = mean over rows of the squared error summed over outputs
-        float lsum = 0.f;
-        for (int e = lane; e < 16 * kOutP; e += 32) {
-            const int r = e / kOutP, c = e % kOutP;
-            float d = 0.f;
-            if (c < kOut && r0 + r < row_end) {
-                const float yhat = W.tmp[r][c] + m.b4[c];
-                const float diff = yhat - A.tgt[data_row(A, r0 + r) * kOut + c];
-                lsum = fmaf(diff, diff, lsum);
-                d = 2.f * diff * inv_m;
-                atomicAdd(&B.gb4[c], d);
-            }
-            W.dz[r][c] = __float2bfloat16(d);
-        }
-        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-        if (lane == 0) atomicAdd(&B.loss, lsum * inv_m);
-        __syncwarp();
-        // ---- output layer
-        accum_weight_grad(&W.dz[0][0], kWid, &W.a[2][0][0], kWid, kOutP, kWid, &B.gW4[0][0], kWid, &W.tmp[0][0]);
-        input_grad(&W.dz[0][0], kWid, m.W4, kOutP, kWid, &W.tmp[0][0], kWid);
-        __syncwarp();
-        // ---- hidden layers, top down
-        for (int l = 2; l >= 0; --l) {
-            float s0 = 0.f, s1 = 0.f;   // bias gradients of columns lane, lane + 32
-            for (int e = lane; e < 16 * kWid; e += 32) {
-                const int r = e / kWid, c = e % kWid;
-                const float d = W.tmp[r][c] * gelu_grad_f(W.z[l][r][c]);
-                if (c < 32) s0 += d; else s1 += d;
-                W.dz[r][c] = __float2bfloat16(d);
-            }
-            float* gbl = l == 2 ? B.gb3 : l == 1 ? B.gb2 : B.gb1;
-            atomicAdd(&gbl[lane], s0);
-            atomicAdd(&gbl[lane + 32], s1);
-            __syncwarp();
-            if (l > 0) {
-                float* gWl = l == 2 ? &B.gW3[0][0] : &B.gW2[0][0];
-                accum_weight_grad(&W.dz[0][0], kWid, &W.a[l - 1][0][0], kWid, kWid, kWid, gWl, kWid, &W.tmp[0][0]);
-                input_grad(&W.dz[0][0], kWid, Ws[l], kWid, kWid, &W.tmp[0][0], kWid);
-            } else {
-                accum_weight_grad(&W.dz[0][0], kWid, &W.a0[0][0], kInP, kWid, kInP, &B.gW1[0][0], kInP, &W.tmp[0][0]);
-            }
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    // ---- one global add per parameter per block (flat, unpadded layout)
-    for (int e = threadIdx.x; e < kNParams; e += blockDim.x) {
-        float v;
-        int64_t k = e;
-        if (k < kOffB1) v = B.gW1[k / kIn][k % kIn];
-        else if (k < kOffW2) v = B.gb1[k - kOffB1];
-        else if (k < kOffB2) { k -= kOffW2; v = B.gW2[k / kWid][k % kWid]; }
-        else if (k < kOffW3) v = B.gb2[k - kOffB2];
-        else if (k < kOffB3) { k -= kOffW3; v = B.gW3[k / kWid][k % kWid]; }
-        else if (k < kOffW4) v = B.gb3[k - kOffB3];
-        else if (k < kOffB4) { k -= kOffW4; v = B.gW4[k / kWid][k % kWid]; }
-        else v = B.gb4[k - kOffB4];
-        atomicAdd(&A.grad[e], v);
-    }
-    if (threadIdx.x == 0 && A.loss) atomicAdd(A.loss, B.loss);
-}
-
 // --------------------------------------------------------------------------
-// parameters: padded BF16 copies; Adam
+// parameters
 // --------------------------------------------------------------------------
-struct MlpBuf {
-    __nv_bfloat16 *W1, *W2, *W3, *W4;
-    float *b1, *b2, *b3, *b4;
-};
-
-__global__ void publish_kernel(const float* __restrict__ p, MlpBuf m)
-{
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid < kWid * kInP) {
-        const int r = tid / kInP, c = tid % kInP;
-        m.W1[tid] = __float2bfloat16(c < kIn ? p[kOffW1 + r * kIn + c] : 0.f);
-    }
-    if (tid < kWid * kWid) {
-        m.W2[tid] = __float2bfloat16(p[kOffW2 + tid]);
-        m.W3[tid] = __float2bfloat16(p[kOffW3 + tid]);
-    }
-    if (tid < kOutP * kWid) {
-        const int r = tid / kWid;
-        m.W4[tid] = __float2bfloat16(r < kOut ? p[kOffW4 + tid] : 0.f);
-    }
-    if (tid < kWid) {
-        m.b1[tid] = p[kOffB1 + tid];
-        m.b2[tid] = p[kOffB2 + tid];
-        m.b3[tid] = p[kOffB3 + tid];
-    }
-    if (tid < kOutP) m.b4[tid] = tid < kOut ? p[kOffB4 + tid] : 0.f;
-}
-
 // Default initialisation: W ~ U(-1/sqrt(n_in), 1/sqrt(n_in)) from SplitMix64
 // of (seed, index), biases zero.
 __global__ void init_params_kernel(float* __restrict__ p, uint64_t seed)
@@ -381,21 +142,6 @@ __global__ void init_params_kernel(float* __restrict__ p, uint64_t seed)
     const uint64_t r = splitmix64(seed * 0x100000000ull + (uint64_t)i);
     const float u = (float)(r >> 40) * (1.f / 16777216.f);        // [0, 1)
     p[i] = (2.f * u - 1.f) * rsqrtf((float)fan_in);
-}
-
-// Adam (Kingma & Ba 2015) with bias correction; c1 = 1 - beta1^t, c2 = 1 - beta2^t.
-__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ mom,
-                            float* __restrict__ vel, int64_t n, float lr, float b1, float b2, float eps, float c1,
-                            float c2)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * mom[i] + (1.f - b1) * gi;
-    const float vi = b2 * vel[i] + (1.f - b2) * gi * gi;
-    mom[i] = mi;
-    vel[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
 // --------------------------------------------------------------------------
@@ -584,29 +330,6 @@ struct __align__(128) TcSmem {
     uint64_t bar_w, bar_mma;
     uint32_t tmem_base;
 };
-
-// The BF16 weight image in the operand layout (W1 at kTcW1 with SBO 768,
-// W2, W3 at kTcW2, kTcW3 and W4 (16 rows, 6 used) at kTcW4 with SBO 1024).
-__global__ void publish_tc_kernel(const float* __restrict__ p, unsigned char* __restrict__ img)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    __nv_bfloat16* o = (__nv_bfloat16*)img;
-    if (t < kWid * kInP) {           // W1: 64 x 48
-        const int n = t / kInP, k = t % kInP;
-        o[(kTcW1 + tc_off(n, k, 768)) / 2] = __float2bfloat16(k < kIn ? p[kOffW1 + n * kIn + k] : 0.f);
-    }
-    // the layers after a GELU take half their weights: the kernel feeds them
-    // 2 GELU (see gelu2_f); BF16(w / 2) = BF16(w) / 2 exactly
-    if (t < kWid * kWid) {           // W2, W3: 64 x 64
-        const int n = t / kWid, k = t % kWid;
-        o[(kTcW2 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(0.5f * p[kOffW2 + t]);
-        o[(kTcW3 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(0.5f * p[kOffW3 + t]);
-    }
-    if (t < kOutP * kWid) {          // W4: 16 x 64
-        const int n = t / kWid, k = t % kWid;
-        o[(kTcW4 + tc_off(n, k, 1024)) / 2] = __float2bfloat16(n < kOut ? 0.5f * p[kOffW4 + n * kWid + k] : 0.f);
-    }
-}
 
 struct TcArgs {
     const unsigned char* wimg;       // 16-byte aligned
@@ -798,6 +521,431 @@ __global__ void __launch_bounds__(kTcRows, kCorrCtas) corr_mlp_tc_kernel(TcArgs 
 }
 
 // --------------------------------------------------------------------------
+// training on the fifth-generation tensor cores
+// --------------------------------------------------------------------------
+// One CTA of four warps per 128-row tile at a time (persistent over the tiles
+// of the pass): thread r owns row r, which is tensor-memory lane r.
+//  Forward: as in inference (plain GELU, unscaled weights), the
+//    pre-activations z1..z3 kept in tensor memory for the backward pass.
+//  Backward, per row: dZ4 = 2 (yhat - target) / M on the six outputs;
+//    dA_l = dZ_{l+1} W_{l+1} (an MMA with the BF16 rows of dZ_{l+1} as A and
+//    the image of W_{l+1}^T as B), dZ_l = dA_l * GELU'(z_l).
+//  Weight gradients G_l = dZ_l^T A_{l-1} reduce over the rows: MMAs whose K
+//    dimension is the tile's 128 rows, with operands stored transposed (row
+//    = feature, K-major along the rows), accumulated in tensor memory over the
+//    CTA's tiles.  Their M dimension (a layer's inputs, 64) is filled to 128
+//    by pairing two layers in one MMA: rows (l', k) hold A_{l'-1}^T, columns
+//    (l, n) hold dZ_l^T, and only the diagonal blocks l' = l are read back
+//    (layers 2 and 3: one 128 x 128 accumulator; layers 1 and 4: 128 x 80).
+//  Bias gradients: row sums of the transposed dZ tiles.
+// Each CTA writes its partial gradient and loss; a second kernel adds the
+// partials in a fixed order (run-to-run identical).
+constexpr int kTrRows = 128;
+// Training weight image (bytes, K-major operand layout): W_l [n][k] for the
+// forward MMAs, W_l^T [k][n] for the input-gradient MMAs.
+constexpr uint32_t kTrW1 = 0, kTrW2 = 6144, kTrW3 = 14336, kTrW4 = 22528;      // SBO 768, 1024, 1024, 1024
+constexpr uint32_t kTrW2t = 24576, kTrW3t = 32768, kTrW4t = 40960;             // SBO 1024, 1024, 256
+constexpr uint32_t kTrWBytes = 43008;
+constexpr uint32_t kTrSboT = 2048;   // transposed tiles: 16 core columns (K = 128 rows)
+// tensor-memory columns: paired weight-gradient accumulators, output, dA, z1..z3
+constexpr uint32_t kTmD2 = 0, kTmD1 = 128, kTmOut = 224, kTmDA = 256, kTmZ1 = 320, kTmCols = 512;
+
+struct __align__(128) TrainSmem {
+    unsigned char w[kTrWBytes];
+    unsigned char act[16384];     // [128 rows][64] K-major (SBO 1024): forward operand
+    unsigned char dz[16384];      // [128 rows][64] K-major: backward operand
+    unsigned char p1a[32768];     // [128][128 rows]: A0^T (features, rows 0..46) | A3^T
+    unsigned char p1b[20480];     // [80][128 rows]:  dZ1^T | dZ4^T (rows 64..69)
+    unsigned char p2a[32768];     // A1^T | A2^T
+    unsigned char p2b[32768];     // dZ2^T | dZ3^T
+    float bias[3 * kWid + kOutP];
+    float gb[3 * kWid + kOutP];   // bias gradients of this CTA
+    float loss;
+    uint64_t bar_w, bar_mma;
+    uint32_t tmem_base;
+};
+constexpr size_t kTrSmem = sizeof(TrainSmem);
+static_assert(kTrSmem <= 227 * 1024, "training tile exceeds shared memory");
+
+struct TrainArgs {
+    const unsigned char* wimg;    // training image (16-byte aligned)
+    const float* bias;            // b1 | b2 | b3 | b4 (padded 64, 64, 64, 16)
+    const float* x;               // [n_data][kInP]
+    const float* tgt;             // [n_data][kOut]
+    int64_t n_data;
+    int64_t M;                    // rows of this pass (batch size, or n_data)
+    int sampled;                  // 1: row r is data row splitmix64(seed + r) % n_data
+    uint64_t seed;
+    float* part;                  // [gridDim.x][kNParams + 1]: partial gradient, then partial loss
+    unsigned int* status;
+};
+
+__device__ __forceinline__ int64_t data_row(const TrainArgs& A, int64_t r)
+{
+    return A.sampled ? (int64_t)(splitmix64(A.seed + (uint64_t)r) % (uint64_t)A.n_data) : r;
+}
+
+// Element (row, m) of a transposed [rows][128] tile.
+__device__ __forceinline__ void store_t(unsigned char* P, int row, int m, float v)
+{
+    *reinterpret_cast<__nv_bfloat16*>(P + tc_off(row, m, kTrSboT)) = __float2bfloat16(v);
+}
+
+// D (+)= A . B^T over K (a multiple of 16): A rows in a K-major tile at a
+// (SBO sa), B rows at b (SBO sb).  Issued by one thread.
+__device__ __forceinline__ void tr_mma(uint32_t d, const unsigned char* a, uint32_t sa, const unsigned char* b,
+                                       uint32_t sb, int M, int N, int K, bool acc)
+{
+    const uint32_t idesc = idesc_bf16_f32(M, N);
+    for (int s = 0; s < K / 16; ++s)
+        tc_mma_bf16(d, smem_desc(a + 256 * s, 128u, sa), smem_desc(b + 256 * s, 128u, sb), idesc,
+                    (acc || s > 0) ? 1u : 0u);
+}
+
+// Operand tiles complete -> thread 0 issues `issue` -> bounded wait for the
+// MMAs.  Same result in every thread; on false the phase is left at the one
+// that did not complete.
+template <class F>
+__device__ __forceinline__ bool tr_step(TrainSmem& sm, uint32_t& phase, F issue)
+{
+    fence_async_shared();
+    tc_fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc_fence_after_sync();
+        issue();
+        tc_commit(&sm.bar_mma);
+    }
+    const bool ok = mbar_wait_bounded(&sm.bar_mma, phase);
+    const bool all_ok = __syncthreads_or(ok ? 0 : 1) == 0;
+    if (all_ok) phase ^= 1u;
+    tc_fence_after_sync();
+    return all_ok;
+}
+
+// Sum over the 128 rows (K) of row `row` of a transposed tile.
+__device__ __forceinline__ float row_sum_t(const unsigned char* P, int row)
+{
+    float s = 0.f;
+#pragma unroll 4
+    for (int cb = 0; cb < kTrRows / 8; ++cb) {
+        const uint4 u = *reinterpret_cast<const uint4*>(P + tc_off(row, 8 * cb, kTrSboT));
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h[q]);
+            s += f.x + f.y;
+        }
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(kTrRows, 1) mlp_train_tc_kernel(TrainArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
+    const int t = threadIdx.x, warp = t >> 5;
+    if (t == 0) {
+        mbar_init(&sm.bar_w, 1);
+        mbar_init(&sm.bar_mma, 1);
+        mbar_init_fence();
+        sm.loss = 0.f;
+    }
+    if (warp == 0) tmem_alloc(&sm.tmem_base, kTmCols);
+    for (int e = t; e < 3 * kWid + kOutP; e += blockDim.x) {
+        sm.bias[e] = A.bias[e];
+        sm.gb[e] = 0.f;
+    }
+    // transposed tiles start at zero (their padding rows are never written)
+    {
+        uint4* z = reinterpret_cast<uint4*>(sm.p1a);
+        const int n16 = (32768 + 20480 + 32768 + 32768) / 16;
+        for (int e = t; e < n16; e += blockDim.x) z[e] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    if (t == 0) {
+        mbar_arrive_expect_tx(&sm.bar_w, kTrWBytes);
+        bulk_copy_g2s(sm.w, A.wimg, kTrWBytes, &sm.bar_w);
+    }
+    const bool okw = __syncthreads_or(mbar_wait_bounded(&sm.bar_w, 0) ? 0 : 1) == 0;
+    bool ok = okw;
+    uint32_t phase = 0;
+    const uint32_t tb = sm.tmem_base;
+    const uint32_t lane = tb + ((uint32_t)(warp * 32) << 16);
+    const float inv_m = 1.f / (float)A.M;
+    const int64_t ntiles = (A.M + kTrRows - 1) / kTrRows;
+    bool first = true;
+    float lsum = 0.f;
+    const uint32_t wf[4] = {kTrW1, kTrW2, kTrW3, kTrW4};
+    const uint32_t wt[4] = {0u, kTrW2t, kTrW3t, kTrW4t};
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int64_t r = tile * kTrRows + t;
+        const bool live = r < A.M;
+        const int64_t dr = live ? data_row(A, r) : 0;
+        // ---- layer-1 operand, its transposed copy, and the target row
+        float ft[kInP];
+        if (live) {
+            const float4* xr = reinterpret_cast<const float4*>(A.x + dr * kInP);
+#pragma unroll
+            for (int c = 0; c < kInP / 4; ++c) {
+                const float4 v = xr[c];
+                ft[4 * c] = v.x; ft[4 * c + 1] = v.y; ft[4 * c + 2] = v.z; ft[4 * c + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < kInP; ++c) ft[c] = 0.f;
+        }
+        ft[kIn] = 0.f;
+#pragma unroll
+        for (int kb = 0; kb < kInP / 8; ++kb) store_row_bf16(sm.act, t, kb, ft + 8 * kb);
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) store_t(sm.p1a, k, t, ft[k]);
+        float tg[kOut];
+#pragma unroll
+        for (int l = 0; l < kOut; ++l) tg[l] = live ? A.tgt[dr * kOut + l] : 0.f;
+        // ---- forward: hidden layers (a1 -> p2a rows 0.., a2 -> p2a rows 64.., a3 -> p1a rows 64..)
+#pragma unroll 1
+        for (int l = 0; l < 3; ++l) {
+            const uint32_t zc = kTmZ1 + 64u * (uint32_t)l;
+            ok = tr_step(sm, phase, [&] {
+                tr_mma(tb + zc, sm.act, 1024u, sm.w + wf[l], l == 0 ? 768u : 1024u, kTrRows, kWid,
+                       l == 0 ? kInP : kWid, false);
+            });
+            if (!ok) break;
+            unsigned char* P = l == 2 ? sm.p1a : sm.p2a;
+            const int roff = l == 0 ? 0 : 64;
+#pragma unroll
+            for (int cb = 0; cb < kWid / 16; ++cb) {
+                float v[16];
+                tmem_ld16(lane + zc + cb * 16, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) v[k] = live ? gelu_f(v[k] + sm.bias[l * kWid + cb * 16 + k]) : 0.f;
+                store_row_bf16(sm.act, t, 2 * cb, v);
+                store_row_bf16(sm.act, t, 2 * cb + 1, v + 8);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) store_t(P, roff + cb * 16 + k, t, v[k]);
+            }
+        }
+        if (!ok) break;
+        // ---- output layer, loss and dZ4 (-> dz, p1b rows 64..79)
+        ok = tr_step(sm, phase, [&] { tr_mma(tb + kTmOut, sm.act, 1024u, sm.w + kTrW4, 1024u, kTrRows, kOutP, kWid, false); });
+        if (!ok) break;
+        {
+            float v[16], d[16];
+            tmem_ld16(lane + kTmOut, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                d[c] = 0.f;
+                if (c < kOut && live) {
+                    const float diff = v[c] + sm.bias[3 * kWid + c] - tg[c];
+                    lsum = fmaf(diff, diff, lsum);
+                    d[c] = 2.f * diff * inv_m;
+                }
+            }
+            store_row_bf16(sm.dz, t, 0, d);
+            store_row_bf16(sm.dz, t, 1, d + 8);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) store_t(sm.p1b, 64 + c, t, d[c]);
+        }
+        // ---- hidden layers, top down (dZ3 -> p2b rows 64.., dZ2 -> p2b rows 0.., dZ1 -> p1b rows 0..)
+#pragma unroll 1
+        for (int l = 2; l >= 0; --l) {
+            ok = tr_step(sm, phase, [&] {
+                tr_mma(tb + kTmDA, sm.dz, 1024u, sm.w + wt[l + 1], l == 2 ? 256u : 1024u, kTrRows, kWid,
+                       l == 2 ? kOutP : kWid, false);
+            });
+            if (!ok) break;
+            const uint32_t zc = kTmZ1 + 64u * (uint32_t)l;
+            unsigned char* P = l == 0 ? sm.p1b : sm.p2b;
+            const int roff = l == 2 ? 64 : 0;
+#pragma unroll
+            for (int cb = 0; cb < kWid / 16; ++cb) {
+                float da[16], z[16], d[16];
+                tmem_ld16(lane + kTmDA + cb * 16, da);
+                tmem_ld16(lane + zc + cb * 16, z);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    d[k] = live ? da[k] * gelu_grad_f(z[k] + sm.bias[l * kWid + cb * 16 + k]) : 0.f;
+                if (l > 0) {
+                    store_row_bf16(sm.dz, t, 2 * cb, d);
+                    store_row_bf16(sm.dz, t, 2 * cb + 1, d + 8);
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) store_t(P, roff + cb * 16 + k, t, d[k]);
+            }
+        }
+        if (!ok) break;
+        // ---- weight gradients of the tile, accumulated over the CTA's tiles
+        const bool acc = !first;
+        ok = tr_step(sm, phase, [&] {
+            tr_mma(tb + kTmD2, sm.p2a, kTrSboT, sm.p2b, kTrSboT, kTrRows, 128, kTrRows, acc);
+            tr_mma(tb + kTmD1, sm.p1a, kTrSboT, sm.p1b, kTrSboT, kTrRows, 80, kTrRows, acc);
+        });
+        first = false;
+        if (!ok) break;
+        // bias gradients: row sums of the transposed dZ tiles (thread t owns row t)
+        sm.gb[(t < 64 ? kWid : 2 * kWid) + (t & 63)] += row_sum_t(sm.p2b, t);
+        if (t < 64) sm.gb[t] += row_sum_t(sm.p1b, t);
+        else if (t < 64 + kOut) sm.gb[3 * kWid + t - 64] += row_sum_t(sm.p1b, t);
+    }
+    if (ok) {
+        float* P = A.part + (int64_t)blockIdx.x * (kNParams + 1);
+        const bool hi = t >= 64;
+        const int k = t & 63;
+        if (first) {
+            for (int e = t; e < kNParams + 1; e += blockDim.x) P[e] = 0.f;
+        } else {
+            // layers 2 (lanes 0..63) and 3 (lanes 64..127): G_l[n][k] = D2[(l, k)][(l, n)]
+#pragma unroll
+            for (int cb = 0; cb < kWid / 16; ++cb) {
+                float v[16];
+                tmem_ld16(lane + kTmD2 + (hi ? 64u : 0u) + cb * 16, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) P[(hi ? kOffW3 : kOffW2) + (cb * 16 + j) * kWid + k] = v[j];
+            }
+            // layers 1 (lanes 0..46, columns 0..63) and 4 (lanes 64..127, columns 64..69)
+            if (!hi) {
+#pragma unroll
+                for (int cb = 0; cb < kWid / 16; ++cb) {
+                    float v[16];
+                    tmem_ld16(lane + kTmD1 + cb * 16, v);
+                    tmem_wait_ld();
+                    if (k < kIn) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) P[kOffW1 + (cb * 16 + j) * kIn + k] = v[j];
+                    }
+                }
+            } else {
+                float v[16];
+                tmem_ld16(lane + kTmD1 + 64u, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < kOut; ++j) P[kOffW4 + j * kWid + k] = v[j];
+            }
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            if ((t & 31) == 0) atomicAdd(&sm.loss, lsum);
+            __syncthreads();
+            if (t < kWid) {
+                P[kOffB1 + t] = sm.gb[t];
+                P[kOffB2 + t] = sm.gb[kWid + t];
+                P[kOffB3 + t] = sm.gb[2 * kWid + t];
+            }
+            if (t < kOut) P[kOffB4 + t] = sm.gb[3 * kWid + t];
+            if (t == 0) P[kNParams] = sm.loss * inv_m;
+        }
+    } else {
+        if (t == 0) flag_timeout(A.status);
+        if (!okw) mbar_wait_bounded(&sm.bar_w, 0);
+        else mbar_wait_bounded(&sm.bar_mma, phase);
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after_sync();
+        tmem_dealloc(sm.tmem_base, kTmCols);
+    }
+}
+
+// grad[i] = sum over the CTA partials in order (i < kNParams); loss likewise.
+__global__ void grad_reduce_kernel(const float* __restrict__ part, int nblk, float* __restrict__ grad,
+                                   float* __restrict__ loss)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > kNParams) return;
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * (kNParams + 1) + i];
+    if (i < kNParams) grad[i] = s;
+    else if (loss) *loss = s;
+}
+
+// --------------------------------------------------------------------------
+// publishing the parameters: FP32 biases (padded) and the BF16 images of the
+// inference kernel (W/2 after a GELU, see gelu2_f) and of the training kernel
+// --------------------------------------------------------------------------
+struct ParamImages {
+    float* bias;            // b1 | b2 | b3 | b4 padded (64, 64, 64, 16)
+    unsigned char* inf;     // inference image (kTcWBytes)
+    unsigned char* train;   // training image (kTrWBytes)
+};
+
+// Write parameter i (value v) into every image that holds it.  Padding
+// entries are not touched (zero since creation).
+__device__ __forceinline__ void publish_param(const ParamImages& im, int64_t i, float v)
+{
+    __nv_bfloat16* fi = (__nv_bfloat16*)im.inf;
+    __nv_bfloat16* ft = (__nv_bfloat16*)im.train;
+    const __nv_bfloat16 b = __float2bfloat16(v), bh = __float2bfloat16(0.5f * v);
+    if (i < kOffB1) {                       // W1 [64][47]
+        const int n = (int)(i / kIn), k = (int)(i % kIn);
+        fi[(kTcW1 + tc_off(n, k, 768)) / 2] = b;
+        ft[(kTrW1 + tc_off(n, k, 768)) / 2] = b;
+    } else if (i < kOffW2) {
+        im.bias[i - kOffB1] = v;
+    } else if (i < kOffB2 || (i >= kOffW3 && i < kOffB3)) {   // W2, W3 [64][64]
+        const bool l3 = i >= kOffW3;
+        const int64_t j = i - (l3 ? kOffW3 : kOffW2);
+        const int n = (int)(j / kWid), k = (int)(j % kWid);
+        fi[((l3 ? kTcW3 : kTcW2) + tc_off(n, k, 1024)) / 2] = bh;
+        ft[((l3 ? kTrW3 : kTrW2) + tc_off(n, k, 1024)) / 2] = b;
+        ft[((l3 ? kTrW3t : kTrW2t) + tc_off(k, n, 1024)) / 2] = b;
+    } else if (i < kOffW3) {
+        im.bias[kWid + i - kOffB2] = v;
+    } else if (i < kOffW4) {
+        im.bias[2 * kWid + i - kOffB3] = v;
+    } else if (i < kOffB4) {                // W4 [6][64]
+        const int64_t j = i - kOffW4;
+        const int n = (int)(j / kWid), k = (int)(j % kWid);
+        fi[(kTcW4 + tc_off(n, k, 1024)) / 2] = bh;
+        ft[(kTrW4 + tc_off(n, k, 1024)) / 2] = b;
+        ft[(kTrW4t + tc_off(k, n, 256)) / 2] = b;
+    } else if (i < kNParams) {
+        im.bias[3 * kWid + i - kOffB4] = v;
+    }
+}
+
+__global__ void publish_kernel(const float* __restrict__ p, ParamImages im)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kNParams) publish_param(im, i, p[i]);
+}
+
+// Adam (Kingma & Ba 2015) with bias correction (c1 = 1 - beta1^t,
+// c2 = 1 - beta2^t) on the FP32 master parameters, then publishing.  The
+// gradient is g, or, if g is null, the sum of the nblk training partials.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, const float* __restrict__ part,
+                            int nblk, float* __restrict__ loss, float* __restrict__ mom, float* __restrict__ vel,
+                            float lr, float b1, float b2, float eps, float c1, float c2, ParamImages im)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > kNParams) return;
+    float gi;
+    if (g) {
+        if (i == kNParams) return;
+        gi = g[i];
+    } else {
+        gi = 0.f;
+        for (int b = 0; b < nblk; ++b) gi += part[(int64_t)b * (kNParams + 1) + i];
+        if (i == kNParams) {
+            if (loss) *loss = gi;
+            return;
+        }
+    }
+    const float mi = b1 * mom[i] + (1.f - b1) * gi;
+    const float vi = b2 * vel[i] + (1.f - b2) * gi * gi;
+    mom[i] = mi;
+    vel[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    publish_param(im, i, pi);
+}
+
+// --------------------------------------------------------------------------
 // full-link fallback and spot checks
 // --------------------------------------------------------------------------
 struct FallbackArgs {
@@ -912,11 +1060,13 @@ struct lisa_corrector {
     float* p = nullptr;       // FP32 master parameters
     float* mom = nullptr;     // Adam moments
     float* vel = nullptr;
-    void* wbuf = nullptr;     // padded BF16 weights + FP32 biases
-    MlpBuf buf{};
-    unsigned char* wimg = nullptr;   // BF16 weights in the tensor-core operand layout
+    float* bias = nullptr;    // FP32 biases, padded (64, 64, 64, 16)
+    unsigned char* wimg = nullptr;    // BF16 weights, inference image (tensor-core operand layout)
+    unsigned char* wtrain = nullptr;  // BF16 weights, training image
+    float* part = nullptr;    // training partials: [SMs][n_params + 1]
+    int part_rows = 0;
     CorrStats* stats = nullptr;
-    float* grad = nullptr;    // gradient buffer of lisa_corrector_train
+    float* grad = nullptr;    // gradient buffer of lisa_corrector_gradient callers
     int64_t step = 0;
     double f_lo = 1e-4, f_hi = 2e-2;
     int spot_every = 64;
@@ -925,21 +1075,18 @@ struct lisa_corrector {
 
 namespace lisa {
 
-static MlpDev mlp_dev(const lisa_corrector* c)
+static ParamImages images(const lisa_corrector* c)
 {
-    return MlpDev{c->buf.W1, c->buf.W2, c->buf.W3, c->buf.W4, c->buf.b1, c->buf.b2, c->buf.b3, c->buf.b4};
+    return ParamImages{c->bias, c->wimg, c->wtrain};
 }
 
+// All parameters into the images (their padding is zero since creation).
 static int publish(lisa_corrector* c, cudaStream_t st)
 {
     prof_before("corr_publish", st);
-    publish_kernel<<<(kWid * kWid + 255) / 256, 256, 0, st>>>(c->p, c->buf);
+    publish_kernel<<<(unsigned)((kNParams + 255) / 256), 256, 0, st>>>(c->p, images(c));
     prof_after(st);
-    LISA_TRY(cuda_status(cudaGetLastError(), "publish_kernel launch"));
-    prof_before("corr_publish", st);
-    publish_tc_kernel<<<(kWid * kWid + 255) / 256, 256, 0, st>>>(c->p, c->wimg);
-    prof_after(st);
-    return cuda_status(cudaGetLastError(), "publish_tc_kernel launch");
+    return cuda_status(cudaGetLastError(), "publish_kernel launch");
 }
 
 static int sm_count()
@@ -964,7 +1111,7 @@ static int run_mlp_tc(const lisa_corrector* c, int64_t rows, const float* x, flo
     TcArgs A;
     memset(&A, 0, sizeof(A));
     A.wimg = c->wimg;
-    A.bias = c->buf.b1;
+    A.bias = c->bias;
     A.rows = rows;
     A.x = x;
     A.out = out;
@@ -985,11 +1132,60 @@ static void free_corrector(lisa_corrector* c)
     cudaFree(c->p);
     cudaFree(c->mom);
     cudaFree(c->vel);
-    cudaFree(c->wbuf);
+    cudaFree(c->bias);
     cudaFree(c->wimg);
+    cudaFree(c->wtrain);
+    cudaFree(c->part);
     cudaFree(c->stats);
     cudaFree(c->grad);
     delete c;
+}
+
+// One pass of the tensor-core training kernel over M rows (batch > 0: rows
+// drawn from the data by SplitMix64(seed + r)), partials into c->part; the
+// number of partial rows written is returned in *nblk.
+static int run_train_tc(lisa_corrector* c, const float* feats, const float* target, int64_t n_data, int64_t batch,
+                        uint64_t seed, int* nblk, cudaStream_t st)
+{
+    static int attr_dev = -1;
+    int dev = 0;
+    LISA_TRY(cuda_status(cudaGetDevice(&dev), "cudaGetDevice"));
+    if (attr_dev != dev) {
+        LISA_TRY(cuda_status(cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)kTrSmem), "cudaFuncSetAttribute"));
+        attr_dev = dev;
+    }
+    TrainArgs A;
+    A.wimg = c->wtrain;
+    A.bias = c->bias;
+    A.x = feats;
+    A.tgt = target;
+    A.n_data = n_data;
+    A.M = batch > 0 ? batch : n_data;
+    A.sampled = batch > 0;
+    A.seed = seed;
+    A.part = c->part;
+    A.status = device_status_ptr();
+    const int64_t tiles = (A.M + kTrRows - 1) / kTrRows;
+    const int grid = (int)(tiles < c->part_rows ? tiles : c->part_rows);
+    prof_before("mlp_train_tc", st);
+    mlp_train_tc_kernel<<<(unsigned)grid, kTrRows, kTrSmem, st>>>(A);
+    prof_after(st);
+    *nblk = grid;
+    return cuda_status(cudaGetLastError(), "mlp_train_tc_kernel launch");
+}
+
+static int adam_launch(lisa_corrector* c, const float* grad, int nblk, float* loss, float lr, cudaStream_t st)
+{
+    c->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - pow(b1, (double)c->step)), c2 = (float)(1.0 - pow(b2, (double)c->step));
+    prof_before("mlp_adam", st);
+    adam_kernel<<<(unsigned)((kNParams + 1 + 255) / 256), 256, 0, st>>>(c->p, grad, c->part, nblk, loss, c->mom,
+                                                                        c->vel, lr, (float)b1, (float)b2, 1e-8f, c1,
+                                                                        c2, images(c));
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "adam_kernel launch");
 }
 
 static FeatArgs make_feat_args(const SegTable& tab, const SkyDev& sky, double Tbar, double dt, const float* z,
@@ -1075,6 +1271,11 @@ static int corrected_links(lisa_corrector* c, const lisa_orbit* orbit, const lis
     const double Tbar = orbit->L_m / kC;
     int64_t safe_lo, safe_hi;
     safe_range(out, h_grid, max_light_time(orbit, out), safe_lo, safe_hi);
+    // the feature stencils of the first two rows reach z before the grid's
+    // start (zero): those rows take full links, and the first tile is neither
+    // band-flagged nor spot-checked
+    if (safe_lo < 2) safe_lo = rows < 2 ? rows : 2;
+    if (safe_hi < safe_lo) safe_hi = safe_lo;
     // features, network and z (1 + eps) + s * MLP in one tensor-core kernel
     const FeatArgs fa = make_feat_args(tab, skyd, Tbar, out.dt, z, n, nz, rows, c->f_lo, c->f_hi, nullptr, nullptr,
                                        nullptr, flags, safe_lo, safe_hi, nullptr, nullptr, nullptr);
@@ -1124,27 +1325,24 @@ int lisa_corrector_create(lisa_corrector** out, const float* host_params, int64_
     lisa_corrector* c = new (std::nothrow) lisa_corrector();
     if (!c) { set_error("lisa_corrector_create: out of host memory"); return LISA_ENOMEM; }
     const size_t pb = sizeof(float) * kNParams;
-    const size_t wb = sizeof(__nv_bfloat16) * (kWid * kInP + 2 * kWid * kWid + kOutP * kWid);
     const size_t bb = sizeof(float) * (3 * kWid + kOutP);
+    c->part_rows = sm_count();
     int rc = cuda_status(cudaMalloc(&c->p, pb), "cudaMalloc");
     if (!rc) rc = cuda_status(cudaMalloc(&c->mom, pb), "cudaMalloc");
     if (!rc) rc = cuda_status(cudaMalloc(&c->vel, pb), "cudaMalloc");
-    if (!rc) rc = cuda_status(cudaMalloc(&c->wbuf, wb + bb), "cudaMalloc");
+    if (!rc) rc = cuda_status(cudaMalloc(&c->bias, bb), "cudaMalloc");
     if (!rc) rc = cuda_status(cudaMalloc(&c->stats, sizeof(CorrStats)), "cudaMalloc");
     if (!rc) rc = cuda_status(cudaMalloc(&c->grad, pb), "cudaMalloc");
     if (!rc) rc = cuda_status(cudaMalloc(&c->wimg, kTcWBytes), "cudaMalloc");
+    if (!rc) rc = cuda_status(cudaMalloc(&c->wtrain, kTrWBytes), "cudaMalloc");
+    if (!rc) rc = cuda_status(cudaMalloc(&c->part, sizeof(float) * (size_t)c->part_rows * (kNParams + 1)), "cudaMalloc");
     if (rc) { free_corrector(c); return rc; }
-    __nv_bfloat16* w = (__nv_bfloat16*)c->wbuf;
-    c->buf.W1 = w;
-    c->buf.W2 = c->buf.W1 + kWid * kInP;
-    c->buf.W3 = c->buf.W2 + kWid * kWid;
-    c->buf.W4 = c->buf.W3 + kWid * kWid;
-    float* b = (float*)((char*)c->wbuf + wb);
-    c->buf.b1 = b;
-    c->buf.b2 = b + kWid;
-    c->buf.b3 = b + 2 * kWid;
-    c->buf.b4 = b + 3 * kWid;
-    if (host_params) {
+    // image padding stays zero: publishing writes parameter entries only
+    rc = cuda_status(cudaMemset(c->bias, 0, bb), "cudaMemset");
+    if (!rc) rc = cuda_status(cudaMemset(c->wimg, 0, kTcWBytes), "cudaMemset");
+    if (!rc) rc = cuda_status(cudaMemset(c->wtrain, 0, kTrWBytes), "cudaMemset");
+    if (rc) {
+    } else if (host_params) {
         rc = cuda_status(cudaMemcpy(c->p, host_params, pb, cudaMemcpyHostToDevice), "cudaMemcpy");
     } else {
         prof_before("corr_init", 0);
@@ -1225,50 +1423,18 @@ int lisa_corrector_gradient(lisa_corrector* c, const float* feats, const float* 
     }
     if (((uintptr_t)feats & 15) != 0) { set_error("lisa_corrector_gradient: feats must be 16-byte aligned"); return LISA_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
-    LISA_TRY(cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * kNParams, st), "cudaMemsetAsync"));
-    if (loss) LISA_TRY(cuda_status(cudaMemsetAsync(loss, 0, sizeof(float), st), "cudaMemsetAsync"));
-    static int attr_dev = -1;
-    int dev = 0;
-    LISA_TRY(cuda_status(cudaGetDevice(&dev), "cudaGetDevice"));
-    if (attr_dev != dev) {
-        LISA_TRY(cuda_status(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)kTrainSmem), "cudaFuncSetAttribute"));
-        attr_dev = dev;
-    }
-    TrainArgs A;
-    A.m = mlp_dev(c);
-    A.x = feats;
-    A.tgt = target;
-    A.n_data = n_data;
-    A.M = batch > 0 ? batch : n_data;
-    A.sampled = batch > 0;
-    A.seed = seed;
-    // about two blocks of 32 rows or more per SM (fewer global flushes for large passes)
-    int64_t rpb = (A.M + 303) / 304;
-    rpb = (rpb + 31) / 32 * 32;
-    A.rows_per_block = (int)(rpb < 32 ? 32 : rpb > 1024 ? 1024 : rpb);
-    A.grad = grad;
-    A.loss = loss;
-    const int64_t blocks = (A.M + A.rows_per_block - 1) / A.rows_per_block;
-    prof_before("mlp_train", st);
-    mlp_train_kernel<<<(unsigned)blocks, 32 * kTrainWarps, kTrainSmem, st>>>(A);
+    int nblk = 0;
+    LISA_TRY(run_train_tc(c, feats, target, n_data, batch, seed, &nblk, st));
+    prof_before("mlp_grad_reduce", st);
+    grad_reduce_kernel<<<(unsigned)((kNParams + 1 + 255) / 256), 256, 0, st>>>(c->part, nblk, grad, loss);
     prof_after(st);
-    return cuda_status(cudaGetLastError(), "mlp_train_kernel launch");
+    return cuda_status(cudaGetLastError(), "grad_reduce_kernel launch");
 }
 
 int lisa_corrector_adam_step(lisa_corrector* c, const float* grad, float lr, void* stream)
 {
     if (!c || !grad || !(lr > 0.f)) { set_error("lisa_corrector_adam_step: bad arguments"); return LISA_EINVAL; }
-    cudaStream_t st = (cudaStream_t)stream;
-    c->step += 1;
-    const double b1 = 0.9, b2 = 0.999;
-    const float c1 = (float)(1.0 - pow(b1, (double)c->step)), c2 = (float)(1.0 - pow(b2, (double)c->step));
-    prof_before("mlp_adam", st);
-    adam_kernel<<<(unsigned)((kNParams + 255) / 256), 256, 0, st>>>(c->p, grad, c->mom, c->vel, kNParams, lr,
-                                                                   (float)b1, (float)b2, 1e-8f, c1, c2);
-    prof_after(st);
-    LISA_TRY(cuda_status(cudaGetLastError(), "adam_kernel launch"));
-    return publish(c, st);
+    return adam_launch(c, grad, 0, nullptr, lr, (cudaStream_t)stream);
 }
 
 int lisa_corrector_train(lisa_corrector* c, const float* feats, const float* target, int64_t n_data, int64_t steps,
@@ -1279,12 +1445,14 @@ int lisa_corrector_train(lisa_corrector* c, const float* feats, const float* tar
         set_error("lisa_corrector_train: bad arguments");
         return LISA_EINVAL;
     }
+    if (((uintptr_t)feats & 15) != 0) { set_error("lisa_corrector_train: feats must be 16-byte aligned"); return LISA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
     for (int64_t k = 0; k < steps; ++k) {
-        // cosine decay from lr_max to lr_min
+        // cosine decay from lr_max to lr_min; the Adam kernel sums the partials
         const double lr = lr_min + 0.5 * (lr_max - lr_min) * (1.0 + cos(M_PI * (double)k / (double)steps));
-        LISA_TRY(lisa_corrector_gradient(c, feats, target, n_data, batch, seed + ((uint64_t)k << 32), c->grad,
-                                         losses ? losses + k : nullptr, stream));
-        LISA_TRY(lisa_corrector_adam_step(c, c->grad, (float)lr, stream));
+        int nblk = 0;
+        LISA_TRY(run_train_tc(c, feats, target, n_data, batch, seed + ((uint64_t)k << 32), &nblk, st));
+        LISA_TRY(adam_launch(c, nullptr, nblk, losses ? losses + k : nullptr, (float)lr, st));
     }
     return LISA_OK;
 }
@@ -1327,8 +1495,8 @@ int lisa_corrector_links(lisa_corrector* c, const lisa_orbit* orbit, const lisa_
 }
 
 int lisa_response_hybrid_corrected(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
-                                   const void* hp, const void* hc, int tdi_gen, int channels, double t_hyb,
-                                   double T_win, double sigma, lisa_grid out, void* xyz, void* stream)
+                                   const void* hp, const void* hc, int tdi_gen, int channels, double t_lo,
+                                   double t_hyb, double T_win, double sigma, lisa_grid out, void* xyz, void* stream)
 {
     if (!c) { set_error("corrector is NULL"); return LISA_EINVAL; }
     LISA_TRY(check_orbit(orbit));
@@ -1337,42 +1505,66 @@ int lisa_response_hybrid_corrected(lisa_corrector* c, const lisa_orbit* orbit, c
     LISA_TRY(check_common(LISA_MIXED, tdi_gen, channels));
     if (!sky) { set_error("sky is NULL"); return LISA_EINVAL; }
     if (!isfinite(t_hyb)) { set_error("t_hyb must be finite"); return LISA_EINVAL; }
+    if (isnan(t_lo) || t_lo == INFINITY || t_lo > t_hyb) {
+        set_error("t_lo must be -INFINITY or a finite time <= t_hyb");
+        return LISA_EINVAL;
+    }
     if (out.n == 0) return LISA_OK;
     if (!xyz || (h_grid.n > 0 && (!hp || !hc))) { set_error("NULL series pointer"); return LISA_EINVAL; }
     const double Tw = T_win > 0.0 ? T_win : 800.0 * out.dt;
     const double sg = sigma > 0.0 ? sigma : Tw / 40.0;
     const int64_t n = out.n;
-    int64_t iL, iF;
-    hybrid_split(out, t_hyb, Tw, iL, iF);
+    // plain LFA on [0, iLa], corrected links on [iFa, iLb], full on [iFb, n)
+    int64_t iLa = -1, iFa = 0, iLb, iFb;
+    if (isfinite(t_lo)) hybrid_split(out, t_lo, Tw, iLa, iFa);
+    hybrid_split(out, t_hyb, Tw, iLb, iFb);
     cudaStream_t st = (cudaStream_t)stream;
     Scratch sc(st);
-    SegTable tab;
-    LISA_TRY(make_table(orbit, out, sc, tab, st));
     const SkyDev skyd = make_sky_dev(*sky);
-    if (iF > iL + 1) {
+    const double Dmax = 8.0 * max_light_time(orbit, out);
+    const int64_t reach = (int64_t)ceil(Dmax / out.dt) + 40;   // TDI delays + stencil, backwards
+    // corrected links on the sub-grid [r0, n) of samples [r0, r1): those the TDI
+    // of the corrected zone reaches (delays backwards, stencil 16 samples forwards)
+    const bool corr_zone = iLb >= iFa;
+    const int64_t r0 = corr_zone && iFa - reach > 0 ? iFa - reach : 0;
+    const int64_t r1 = iLb + 1 + 32 < n ? iLb + 1 + 32 : n;
+    const lisa_grid sub{out.t0 + (double)r0 * out.dt, out.dt, n - r0};
+    SegTable tab, tab_sub;
+    if (corr_zone) LISA_TRY(make_table_pair(orbit, out, sub, sc, tab, tab_sub, st));
+    else LISA_TRY(make_table(orbit, out, sc, tab, st));
+    if (iFb > iLb + 1) {
         for (int ch = 0; ch < 3; ++ch) {
-            LISA_TRY(cuda_status(cudaMemsetAsync((float*)xyz + (size_t)ch * n + (size_t)(iL + 1), 0,
-                                                 sizeof(float) * (size_t)(iF - iL - 1), st), "cudaMemsetAsync"));
+            LISA_TRY(cuda_status(cudaMemsetAsync((float*)xyz + (size_t)ch * n + (size_t)(iLb + 1), 0,
+                                                 sizeof(float) * (size_t)(iFb - iLb - 1), st), "cudaMemsetAsync"));
         }
     }
-    if (iL >= 0) {
-        // corrected links up to the forward reach of the TDI stencil (16 samples)
-        const int64_t rows = iL + 1 + 32 < n ? iL + 1 + 32 : n;
-        float* yc = (float*)sc.alloc(sizeof(float) * 6 * (size_t)n);
-        if (!yc) return sc.status();
-        LISA_TRY(corrected_links(c, orbit, sky, h_grid, hp, hc, out, tab, rows, yc, sc, st));
-        BlendSpec bl{1, t_hyb, sg, +1.0, 0, 0};
-        LISA_TRY(launch_tdi(tab, out, yc, LISA_MIXED, tdi_gen, LISA_FROZEN, channels, out, xyz, 0, iL + 1, bl, st));
+    // 1. plain LFA channels below the lower seam, weight S(t; t_lo, +)
+    if (iLa >= 0) {
+        BlendSpec bl{1, t_lo, sg, +1.0, 0, 0};
+        LISA_TRY(launch_lfa(tab, skyd, orbit->L_m, h_grid, hp, hc, LISA_MIXED, tdi_gen, LISA_LFA_UNEQUAL, channels, out,
+                            nullptr, xyz, 0, iLa + 1, bl, st));
     }
-    if (iF < n) {
-        const double Dmax = 8.0 * max_light_time(orbit, out);
-        int64_t lo = iF - (int64_t)ceil(Dmax / out.dt) - 40;
-        lo = lo < 0 ? 0 : lo;
-        float* y = (float*)sc.alloc(sizeof(float) * 6 * (size_t)n);
+    // 2. TDI of the corrected links on [iFa, iLb]: weight S(t; t_lo, -) added to
+    //    the plain LFA over the lower window; the links are laid out as the TDI
+    //    reads samples [r0, n) of the output grid.
+    if (corr_zone) {
+        float* yc = (float*)sc.alloc(sizeof(float) * 6 * (size_t)(n - r0));
+        if (!yc) return sc.status();
+        LISA_TRY(corrected_links(c, orbit, sky, h_grid, hp, hc, sub, tab_sub, r1 - r0, yc, sc, st));
+        BlendSpec bl{};
+        if (iLa >= 0) bl = BlendSpec{1, t_lo, sg, -1.0, iFa, iLa + 1};
+        LISA_TRY(launch_tdi(tab, out, yc, LISA_MIXED, tdi_gen, LISA_FROZEN, channels, out, xyz, iFa, iLb + 1, bl, st,
+                            r0));
+    }
+    // 3. full response above the upper seam: S(t; t_hyb, -) x + (1 - S) out
+    //    over the upper window, so that the three weights sum to one
+    if (iFb < n) {
+        const int64_t lo = iFb - reach > 0 ? iFb - reach : 0;
+        float* y = (float*)sc.alloc(sizeof(float) * 6 * (size_t)(n - lo));
         if (!y) return sc.status();
-        LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, LISA_MIXED, out, y, lo, n, st));
-        BlendSpec bl{1, t_hyb, sg, -1.0, iF, iL + 1};
-        LISA_TRY(launch_tdi(tab, out, y, LISA_MIXED, tdi_gen, LISA_FROZEN, channels, out, xyz, iF, n, bl, st));
+        LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, LISA_MIXED, out, y, lo, n, st, lo));
+        BlendSpec bl{1, t_hyb, sg, -1.0, iFb, iLb + 1, 1};
+        LISA_TRY(launch_tdi(tab, out, y, LISA_MIXED, tdi_gen, LISA_FROZEN, channels, out, xyz, iFb, n, bl, st, lo));
     }
     return LISA_OK;
 }

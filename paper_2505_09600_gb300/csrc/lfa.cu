@@ -62,7 +62,7 @@ int launch_lfa_df(const LfaArgs& a, cudaStream_t st);
 
 int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,
                const void* hc, int precision, int gen, int kind, int channels, const lisa_grid& og, void* z,
-               void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st)
+               void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st, int group)
 {
     if (kind == LISA_LFA_NLO && precision == LISA_MIXED) {
         set_error("the next-to-leading-order LFA is an FP64 form: its third- and fourth-derivative stencils "
@@ -115,7 +115,22 @@ int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const l
     prof_before(gen == kLfaOwnTime ? (precision == LISA_MIXED ? "lfa_own_mixed" : "lfa_own_f64")
                                    : (precision == LISA_MIXED ? "lfa_mixed" : "lfa_f64"), st);
     if (precision == LISA_MIXED) {
-        const int G = lfa_group(og.dt);
+        const int G0 = lfa_group(og.dt);
+        int G = group > 0 && group < G0 ? group : G0;
+        if (gen == kLfaOwnTime && group == 0) {
+            // link series at their own time: groups narrowed on short ranges so
+            // that the CTAs fill the SMs (2 tiles at least: one sub-block)
+            static int sms = 0;
+            if (sms == 0) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                if (sms <= 0) sms = 1;
+            }
+            const int64_t per_sm = tiles / sms;
+            const int Gs = per_sm < 2 ? 2 : (per_sm > 8 ? 8 : (int)per_sm);
+            if (Gs < G) G = Gs;
+        }
         lfa_kernel_mixed<<<(unsigned)((tiles + G - 1) / G), kTile, 0, st>>>(a, tile_end, G);
     } else {
         lfa_kernel_f64<<<(unsigned)tiles, kTile, 0, st>>>(a, tile_end, 1);

@@ -330,6 +330,8 @@ __device__ void geometry_exact(const OrbitDev& o, double t, double* q);
 
 // Host-side helpers ----------------------------------------------------------
 int build_seg_table(const OrbitDev& orb, const lisa_grid& g, int S, double* coef_dev, int64_t nseg, cudaStream_t st);
+int build_seg_table_pair(const OrbitDev& orb, const lisa_grid& g1, int S1, double* c1, int64_t n1,
+                         const lisa_grid& g2, int S2, double* c2, int64_t n2, cudaStream_t st);
 int64_t seg_count(int64_t n, int S);
 
 // Error plumbing.

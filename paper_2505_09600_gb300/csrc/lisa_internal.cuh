@@ -74,6 +74,8 @@ struct BlendSpec {
     int enabled;        // 0: plain output
     double t_hyb, sigma, eps;   // weight S(t; t_hyb, sigma, eps)
     int64_t acc_begin, acc_end; // samples where the existing output is added
+    int lerp;           // TDI stores only: on [acc_begin, acc_end) the output
+                        // becomes S x + (1 - S) out instead of S x + out
 };
 // y holds the samples [y0, yg.n) of the link grid yg, laid out as in
 // launch_links_full; samples below y0 read as zero.
@@ -87,9 +89,10 @@ int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int prec
 // at its own reception time (no TDI shift): z[6][og.n] in link order (xyz
 // must be null).
 constexpr int kLfaOwnTime = 0;
+// group: tiles per CTA of the mixed kernel (0: lfa_group of the grid step).
 int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,
                const void* hc, int precision, int gen, int kind, int channels, const lisa_grid& og, void* z,
-               void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st);
+               void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st, int group = 0);
 int launch_tdi_lfa(const SegTable& tab, double L_nominal, const lisa_grid& zg, const void* z, int precision, int gen,
                    int kind, int channels, void* xyz, cudaStream_t st);
 
@@ -105,6 +108,8 @@ int check_common(int precision, int gen, int channels);
 size_t real_size(int precision);
 // Orbit polynomial table on grid g, in scratch.
 int make_table(const lisa_orbit* orbit, const lisa_grid& g, Scratch& sc, SegTable& tab, cudaStream_t st);
+int make_table_pair(const lisa_orbit* orbit, const lisa_grid& g1, const lisa_grid& g2, Scratch& sc, SegTable& tab1,
+                    SegTable& tab2, cudaStream_t st);
 // Upper bound of any single light time (halo sizing).
 double max_light_time(const lisa_orbit* o, const lisa_grid& g);
 // Tiles per CTA group of the mixed LFA kernel for a grid step dt (host side).

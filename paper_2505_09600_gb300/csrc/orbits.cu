@@ -310,6 +310,29 @@ seg_table_kernel(OrbitDev o, double t0, double dt, int S, int64_t nseg, double* 
     seg_fit_block(o, t0, dt, S, s, coef + s * kNQ * kNC);
 }
 
+// The tables of two grids in one launch: blocks [0, n1) fit the segments of
+// grid 1, the next n2 blocks those of grid 2 (a block's fit is a chain of
+// FP64 latencies, so two short tables cost about one).
+__global__ void __launch_bounds__(kSegThreads)
+seg_table_pair_kernel(OrbitDev o, double t01, double dt1, int S1, int64_t n1, double* __restrict__ c1, double t02,
+                      double dt2, int S2, int64_t n2, double* __restrict__ c2)
+{
+    const int64_t s = blockIdx.x;
+    if (s < n1) seg_fit_block(o, t01, dt1, S1, s, c1 + s * kNQ * kNC);
+    else if (s - n1 < n2) seg_fit_block(o, t02, dt2, S2, s - n1, c2 + (s - n1) * kNQ * kNC);
+}
+
+int build_seg_table_pair(const OrbitDev& orb, const lisa_grid& g1, int S1, double* c1, int64_t n1,
+                         const lisa_grid& g2, int S2, double* c2, int64_t n2, cudaStream_t st)
+{
+    if (n1 + n2 <= 0) return LISA_OK;
+    prof_before("seg_table", st);
+    seg_table_pair_kernel<<<(unsigned)(n1 + n2), kSegThreads, 0, st>>>(orb, g1.t0, g1.dt, S1, n1, c1, g2.t0, g2.dt,
+                                                                      S2, n2, c2);
+    prof_after(st);
+    return cuda_status(cudaGetLastError(), "seg_table_pair_kernel launch");
+}
+
 int build_seg_table(const OrbitDev& orb, const lisa_grid& g, int S, double* coef_dev, int64_t nseg, cudaStream_t st)
 {
     if (nseg <= 0) return LISA_OK;

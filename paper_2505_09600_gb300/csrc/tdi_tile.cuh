@@ -86,14 +86,17 @@ __device__ __forceinline__ void store_channels_f32(float X, float Y, float Z, in
         o2 = (X + Y + Z) * 0.57735026918962576451f;
     }
     if (bl.enabled) {
-        const float wgt = 1.f / (1.f + expf(fmaf((float)di, barg_d, barg_c)));
+        const float e = expf(fmaf((float)di, barg_d, barg_c));
+        const float wgt = 1.f / (1.f + e);
         o0 *= wgt;
         o1 *= wgt;
         o2 *= wgt;
         if (i >= bl.acc_begin && i < bl.acc_end) {
-            o0 += out[i];
-            o1 += out[n + i];
-            o2 += out[2 * n + i];
+            // 1 - S = e S, formed without the cancellation of 1 - S
+            const float keep = bl.lerp ? e * wgt : 1.f;
+            o0 = fmaf(keep, out[i], o0);
+            o1 = fmaf(keep, out[n + i], o1);
+            o2 = fmaf(keep, out[2 * n + i], o2);
         }
     }
     out[i] = o0;
@@ -114,16 +117,28 @@ __device__ __forceinline__ void store_channels(Real X, Real Y, Real Z, int chann
     if (bl.enabled) {
         const double ti = t0 + (double)i * dt;
         const double arg = bl.eps * (ti - bl.t_hyb) / bl.sigma;
-        Real wgt;
-        if constexpr (sizeof(Real) == 8) wgt = 1.0 / (1.0 + exp(arg));
-        else wgt = 1.f / (1.f + expf((float)arg));
+        Real wgt, e;
+        if constexpr (sizeof(Real) == 8) {
+            e = exp(arg);
+            wgt = 1.0 / (1.0 + e);
+        } else {
+            e = expf((float)arg);
+            wgt = 1.f / (1.f + e);
+        }
         o0 *= wgt;
         o1 *= wgt;
         o2 *= wgt;
         if (i >= bl.acc_begin && i < bl.acc_end) {
-            o0 += out[i];
-            o1 += out[n + i];
-            o2 += out[2 * n + i];
+            if (bl.lerp) {
+                const Real keep = e * wgt;   // 1 - S
+                o0 += keep * out[i];
+                o1 += keep * out[n + i];
+                o2 += keep * out[2 * n + i];
+            } else {
+                o0 += out[i];
+                o1 += out[n + i];
+                o2 += out[2 * n + i];
+            }
         }
     }
     out[i] = o0;

@@ -9,6 +9,7 @@ CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import threading
 from dataclasses import dataclass
@@ -167,7 +168,7 @@ _SIGS = {
                                      lisa_grid, _P, _P]),
     "lisa_response_hybrid_corrected": (C.c_int, [C.c_void_p, C.POINTER(lisa_orbit), C.POINTER(lisa_sky), lisa_grid,
                                                  _P, _P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
-                                                 lisa_grid, _P, _P]),
+                                                 C.c_double, lisa_grid, _P, _P]),
     "lisa_corrector_report": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_float), C.c_int]),
 }
@@ -641,14 +642,18 @@ class LisaCorrector:
                                            og, _ptr(y, torch.float32, 6 * og.n, "y"), _stream(stream)),
                "lisa_corrector_links")
 
-    def hybrid(self, orbit, sky, h_grid, hp, hc, tdi_gen, channels, t_hyb, T_win, sigma, out_grid, xyz, stream=None):
+    def hybrid(self, orbit, sky, h_grid, hp, hc, tdi_gen, channels, t_hyb, T_win, sigma, out_grid, xyz, stream=None,
+               t_lo=-math.inf):
+        """Corrected hybrid: plain LFA for t <= t_lo, corrected links and the
+        full TDI combine between t_lo and t_hyb, full response after t_hyb
+        (t_lo = -inf: no plain-LFA zone)."""
         import torch
         hg, og = _grid(h_grid), _grid(out_grid)
         o, s = _orb(orbit), _sky(sky)
         _check(load().lisa_response_hybrid_corrected(self.handle, C.byref(o), C.byref(s), hg,
                                                      _ptr(hp, torch.float32, hg.n, "hp"),
                                                      _ptr(hc, torch.float32, hg.n, "hc"), tdi_gen, channels,
-                                                     float(t_hyb), float(T_win), float(sigma), og,
+                                                     float(t_lo), float(t_hyb), float(T_win), float(sigma), og,
                                                      _ptr(xyz, torch.float32, 3 * og.n, "xyz"), _stream(stream)),
                "lisa_response_hybrid_corrected")
 

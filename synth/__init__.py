@@ -262,12 +262,14 @@ def pe_source(p, n=3155760, dt=10.0, t0=2.0e7):
 
 
 
-def corrector_params(nsrc=4096, seed=SEED_BASE + 4, n=4883, fmin=1e-4, fmax=2e-2):
+def corrector_params(nsrc=4096, seed=SEED_BASE + 4, n=4883, fmin=1e-4, fmax=2e-2, ecc_frac=0.5, e0_max=0.3):
     """Sources of the corrector's training and held-out sets: chirps whose GW
     frequency stays inside [fmin, fmax] over their grid.  Start frequency
     log-U[fmin, fmax/1.02], sweep ratio f_end/f_start log-U[1.001, min(3,
     fmax/f_start)], dt in {5, 10} s, n samples, isotropic sky, cos(iota)
-    U[-1, 1], t0 U[1e7, 4e7] s (orbit phase), distance 10 Gpc."""
+    U[-1, 1], t0 U[1e7, 4e7] s (orbit phase), distance 10 Gpc; a fraction
+    ecc_frac of them eccentric, e0 U[0, e0_max] at the start frequency (the
+    leading-order phase modulation of chirp_0pn)."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(nsrc):
@@ -279,7 +281,9 @@ def corrector_params(nsrc=4096, seed=SEED_BASE + 4, n=4883, fmin=1e-4, fmax=2e-2
         iota = math.acos(rng.uniform(-1.0, 1.0))
         phi_c = rng.uniform(0.0, 2.0 * math.pi)
         t0 = rng.uniform(1.0e7, 4.0e7)
-        out.append(dict(f0=f0, ratio=r, dt=dt, n=n, beta=beta, lam=lam, psi=psi, iota=iota, phi_c=phi_c, t0=t0))
+        e0 = rng.uniform(0.0, e0_max) if rng.uniform() < ecc_frac else 0.0
+        out.append(dict(f0=f0, ratio=r, dt=dt, n=n, beta=beta, lam=lam, psi=psi, iota=iota, phi_c=phi_c, t0=t0,
+                        e0=e0))
     return out
 
 
@@ -296,7 +300,7 @@ def corrector_source(p, dist_gpc=10.0):
     t0 = p["t0"]
     tc = t0 + dur + tau_end
     t = t0 + np.arange(n) * dt
-    hp, hc = chirp_0pn(t, tc, mc_s, dist_gpc * GPC, p["iota"], p["phi_c"])
+    hp, hc = chirp_0pn(t, tc, mc_s, dist_gpc * GPC, p["iota"], p["phi_c"], ecc0=p.get("e0", 0.0), f_ecc_ref=p["f0"])
     return Source(t0, dt, n, hp, hc, p["beta"], p["lam"], p["psi"], tc, mc_s, dict(p))
 
 

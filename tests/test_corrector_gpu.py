@@ -7,8 +7,9 @@
 * the full-link fallbacks (above the band, failed spot check) and the
   below-band base link;
 * training on the GPU and what the trained network gains over the plain LFA,
-  per link and in the hybrid (the switch frequency it allows at the error of
-  the plain hybrid switched at 1e-3 Hz).
+  per link and in the hybrid (the error of the three-zone corrected hybrid
+  against the plain hybrid's at the same switch frequency, and its cost on
+  the one-year workload).
 
 BF16-scaled tolerances: the network runs with BF16 weights and activations
 (unit roundoff u = 2^-8) and FP32 accumulation; a forward pass rounds four
@@ -47,7 +48,7 @@ def _dev_source(s):
 
 def _small_source(n=900, f0=3e-3, ratio=1.5, dt=5.0, seed=1):
     p = synth.corrector_params(nsrc=1, seed=synth.SEED_BASE + 400 + seed, n=n)[0]
-    p.update(f0=f0, ratio=ratio, dt=dt)
+    p.update(f0=f0, ratio=ratio, dt=dt, e0=0.0)
     return synth.corrector_source(p)
 
 
@@ -377,19 +378,70 @@ def test_link_gain_on_held_out_sources(L, trained):
     assert np.all(rows[:, 3] <= np.maximum(rows[:, 2], 2e-5))
 
 
-F_H = (1e-3, 1.5e-3, 2e-3, 3e-3, 4e-3, 6e-3, 8e-3, 1e-2, 1.4e-2, 2e-2)
-
-
-def _lfa_side_error(got, ref, i_end, m):
+def _side_error(got, ref, i_end, m):
     g, r = got[:, m:i_end], ref[:, m:i_end]
     return np.abs(g - r).max() / np.abs(r).max()
 
 
-def test_hybrid_switch_frequency_gain(L, trained):
+def _sigmoid_keep(t, ts, sigma):
+    """S(t; t_s) = 1 / (1 + exp((t - t_s) / sigma)) (Sec. IV, Eq. sigmoid)."""
+    return 1.0 / (1.0 + np.exp(np.clip((t - ts) / sigma, -700.0, 700.0)))
+
+
+def test_three_zone_hybrid_blend(L, trained):
+    """The corrected hybrid is plain LFA below t_lo, corrected links with the
+    full TDI combine between t_lo and t_hyb and the full response above,
+    joined by the paper's sigmoid at both seams: it equals
+    S_lo S_hi X_LFA + (1 - S_lo) S_hi X_corr + (1 - S_hi) X_full formed here
+    from the separate calls (each zone's weights summing to one)."""
+    c, lo, _, _, _ = trained
+    c.configure(f_lo=1e-4, f_hi=2e-2, spot_every=64, spot_tol=0.05)
+    p = synth.sweep_params(nsrc=1, seed=synth.SEED_BASE + 41)[0]
+    s = synth.sweep_source(p)
+    d = _dev_source(s)
+    n = s.n
+    Tw, sig = 800 * s.dt, 20 * s.dt
+    t_hi = L.lisa_t_hyb_from_f(2e-3, s.mc_s, s.tc)
+    t_lo = L.lisa_t_hyb_from_f(1e-3, s.mc_s, s.tc)
+    x_lfa = torch.empty((3, n), device="cuda")
+    L.lisa_response_lfa(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, L.TDI20, L.LFA_UNEQUAL, L.AET, s.grid,
+                        x_lfa)
+    y = torch.empty((6, n), device="cuda")
+    c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
+    x_cor = torch.empty((3, n), device="cuda")
+    L.lisa_tdi(lo, s.grid, y, L.MIXED, L.TDI20, L.FROZEN, L.AET, s.grid, x_cor)
+    x_full = torch.empty((3, n), device="cuda")
+    L.lisa_response_full(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, L.TDI20, L.AET, s.grid, x_full)
+    got = torch.full((3, n), float("nan"), device="cuda")
+    c.hybrid(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.TDI20, L.AET, t_hi, Tw, sig, s.grid, got, t_lo=t_lo)
+    assert c.report()["status"] == 0
+    t = s.t0 + np.arange(n) * s.dt
+    s_lo, s_hi = _sigmoid_keep(t, t_lo, sig), _sigmoid_keep(t, t_hi, sig)
+    want = (s_lo * s_hi * x_lfa.cpu().numpy().astype(np.float64)
+            + (1.0 - s_lo) * s_hi * x_cor.cpu().numpy().astype(np.float64)
+            + (1.0 - s_hi) * x_full.cpu().numpy().astype(np.float64))
+    g = got.cpu().numpy().astype(np.float64)
+    assert np.isfinite(g).all()
+    # zones: both seams and all three parts are present on this grid
+    i_lo, i_hi = np.searchsorted(t, t_lo), np.searchsorted(t, t_hi)
+    assert 1000 < i_lo < i_hi - 1000 and i_hi < n - 500
+    err = np.abs(g - want).max(axis=1) / np.abs(want).max()
+    print("three-zone blend vs separate calls: A/E/T", err)
+    assert np.all(err < MIXED_TOL["hybrid20"]["aet"][0]), err
+
+
+F_H_EVAL = (1e-3, 2e-3)
+
+
+def test_hybrid_error_gain_at_fixed_switch(L, trained):
+    """What the trained network gains in the hybrid: at the same switch
+    frequency f_H, the error of the corrected hybrid (plain LFA below f_H/2,
+    corrected links up to f_H) against the plain hybrid's, both against the
+    FP64 full response on the approximate side (no ceiling on the measure)."""
     from paper_2505_09600_gb300 import corrector as CT
     c, lo, _, _, _ = trained
     c.configure(f_lo=1e-4, f_hi=2e-2, spot_every=64, spot_tol=0.05)
-    ratios = []
+    ratios = {fH: [] for fH in F_H_EVAL}
     for p in synth.sweep_params(nsrc=6, seed=synth.SEED_BASE + 41):
         s = synth.sweep_source(p)
         d = _dev_source(s)
@@ -399,26 +451,54 @@ def test_hybrid_switch_frequency_gain(L, trained):
         ref = ref.cpu().numpy()
         Tw = 800 * s.dt
         out = torch.empty((3, n), device="cuda")
-
-        def i_end(tH):
-            return int(min(n, max(0, math.floor((tH + Tw / 2 - s.t0) / s.dt) + 1)))
-
-        tH = L.lisa_t_hyb_from_f(1e-3, s.mc_s, s.tc)
-        L.lisa_response_hybrid(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, L.TDI20, L.LFA_UNEQUAL, L.AET,
-                               tH, 0.0, 0.0, s.grid, out)
-        e0 = _lfa_side_error(out.cpu().numpy(), ref, i_end(tH), m)
-        best = 1e-3
-        errs = []
-        for fH in F_H:
+        for fH in F_H_EVAL:
             tH = L.lisa_t_hyb_from_f(fH, s.mc_s, s.tc)
-            c.hybrid(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.TDI20, L.AET, tH, 0.0, 0.0, s.grid, out)
-            e = _lfa_side_error(out.cpu().numpy(), ref, i_end(tH), m)
-            errs.append(e)
-            if e <= e0:
-                best = fH
-        print("Mc %.3g: plain hybrid at 1e-3 Hz err %.2e; corrected %s -> f_H %.3g" %
-              (p["mc"], e0, " ".join("%.1e" % e for e in errs), best))
-        ratios.append(best / 1e-3)
+            tL = L.lisa_t_hyb_from_f(0.5 * fH, s.mc_s, s.tc)
+            i_end = int(min(n, max(0, math.floor((tH + Tw / 2 - s.t0) / s.dt) + 1)))
+            L.lisa_response_hybrid(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.MIXED, L.TDI20, L.LFA_UNEQUAL,
+                                   L.AET, tH, 0.0, 0.0, s.grid, out)
+            ep = _side_error(out.cpu().numpy(), ref, i_end, m)
+            c.hybrid(lo, d["sky"], s.grid, d["hp32"], d["hc32"], L.TDI20, L.AET, tH, 0.0, 0.0, s.grid, out, t_lo=tL)
+            ec = _side_error(out.cpu().numpy(), ref, i_end, m)
+            print("Mc %.3g f_H %.0e: plain %.2e corrected %.2e ratio %.1f" % (p["mc"], fH, ep, ec, ep / ec))
+            ratios[fH].append(ep / ec)
     assert c.report()["status"] == 0
-    print("switch-frequency ratio R per source:", ratios)
-    assert np.median(ratios) >= 5.0
+    for fH, r in ratios.items():
+        r = np.asarray(r)
+        assert np.all(r > 2.0), (fH, r)
+        assert np.median(r) >= 5.0, (fH, r)
+
+
+def test_corrected_hybrid_cost(L, trained):
+    """On the one-year workload (6.3M samples at 5 s, switch at 1e-3 Hz) the
+    corrected hybrid, whose corrected zone spans f_H/2..f_H, costs at most
+    1.2 times the plain mixed hybrid."""
+    c, lo, _, _, _ = trained
+    c.configure(f_lo=1e-4, f_hi=2e-2, spot_every=64, spot_tol=0.05)
+    s = synth.cfg2_source()
+    hp, hc = to_dev(s.hp, 1), to_dev(s.hc, 1)
+    sky = (s.beta, s.lam, s.psi)
+    out = torch.empty((3, s.n), device="cuda")
+    tH = L.lisa_t_hyb_from_f(1e-3, s.mc_s, s.tc)
+    tL = L.lisa_t_hyb_from_f(5e-4, s.mc_s, s.tc)
+    Tw, sig = 800 * s.dt, 20 * s.dt
+
+    def timed(fn, reps=7):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    mp = timed(lambda: L.lisa_response_hybrid(lo, sky, s.grid, hp, hc, L.MIXED, L.TDI20, L.LFA_UNEQUAL, L.AET, tH,
+                                              Tw, sig, s.grid, out))
+    mc = timed(lambda: c.hybrid(lo, sky, s.grid, hp, hc, L.TDI20, L.AET, tH, Tw, sig, s.grid, out, t_lo=tL))
+    print("config-2 year: plain hybrid %.3f ms, corrected hybrid %.3f ms (ratio %.2f)" % (mp, mc, mc / mp))
+    assert c.report()["status"] == 0
+    assert mc <= 1.2 * mp, (mp, mc)
