@@ -423,7 +423,9 @@ int lisa_corrector_num_features(void);       /* 47 */
 /* Create on the current device (cudaMalloc of its parameters, Adam state and
  * counters; synchronising).  host_params: n_params FP32 values, or NULL for
  * W ~ U(-1/sqrt(n_in), 1/sqrt(n_in)) drawn from SplitMix64(seed), b = 0.
- * Defaults: band [1e-4, 2e-2] Hz, a spot check every 64th tile, tolerance 0.05. */
+ * Defaults: band [1e-4, 2e-2] Hz, a spot check every 64th tile (from the
+ * first tile whose retarded times stay on the h grid, so that every call
+ * checks at least one tile), tolerance 0.05. */
 int lisa_corrector_create(lisa_corrector** c, const float* host_params, int64_t n_params, uint64_t seed);
 int lisa_corrector_destroy(lisa_corrector* c);
 /* Trained band (Hz), spot-check period in tiles (0 = none) and tolerance

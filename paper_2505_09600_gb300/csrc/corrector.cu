@@ -27,7 +27,8 @@
 // for a sinusoid) selects, per sample: below the trained band the plain LFA
 // link (no correction: the LFA is already closer than at the band's lower
 // edge); above it the full link (the whole 256-sample tile is recomputed by
-// the full links kernel).  Every spot_every-th tile is also recomputed with
+// the full links kernel).  Every spot_every-th tile, counted from the call's
+// first tile inside the h grid (so every call checks one), is also recomputed with
 // full links and compared (band flags and spot checks only where the retarded
 // times stay on the h grid; samples whose retarded times leave it, at the grid
 // ends, take the full links, the form whose boundary convention the reference
@@ -955,6 +956,7 @@ struct FallbackArgs {
     float spot_tol;
     int global_pass;       // 0: flagged and spot tiles; 1: all others if this call failed a spot check
     int64_t safe_lo, safe_hi;  // spot checks only on tiles inside [safe_lo, safe_hi)
+    int64_t spot0;         // first tile inside: spot checks on spot0, spot0 + spot_every, ...
     CorrStats* stats;
 };
 
@@ -967,7 +969,7 @@ __global__ void __launch_bounds__(kTile) corr_fallback_kernel(FallbackArgs A)
     const int64_t tile = a.tile0 + blockIdx.x;
     const int flag = A.tile_flag[tile];
     const bool inside = tile * kTile >= A.safe_lo && (tile + 1) * kTile <= A.safe_hi;
-    const bool spot = A.spot_every > 0 && (tile % A.spot_every) == 0 && inside;
+    const bool spot = A.spot_every > 0 && inside && ((tile - A.spot0) % A.spot_every) == 0;
     if (A.global_pass) {
         if (flag || spot || A.stats->call_failed == 0) return;
     } else if (!flag && !spot && inside) {
@@ -1297,6 +1299,7 @@ static int corrected_links(lisa_corrector* c, const lisa_orbit* orbit, const lis
     A.stats = c->stats;
     A.safe_lo = safe_lo;
     A.safe_hi = safe_hi;
+    A.spot0 = (safe_lo + kTile - 1) / kTile;   // every call checks its first inside tile
     for (int pass = 0; pass < 2; ++pass) {
         A.global_pass = pass;
         prof_before(pass ? "corr_fallback_all" : "corr_fallback", st);

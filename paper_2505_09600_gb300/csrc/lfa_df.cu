@@ -334,13 +334,20 @@ static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSm
     const double* __restrict__ hc = (const double*)a.hc;
     const double i12 = 1.0 / (12.0 * a.hm.dt_in);
     const bool interior = i0 - 2 >= 0 && i0 + kTile + 2 <= a.nout;
-    for (int w = threadIdx.x + (first ? 0 : 4); w < kZW; w += blockDim.x) {
+    // (series, sample) items, series-major so that a warp's items share a
+    // series: the group's first tile has 260 samples, so its items spread
+    // 6 or 7 to a thread (one sample per thread with its 6 series would leave
+    // 4 threads with 12 evaluations while the block waits for them)
+    const int w0 = first ? 0 : 4, nw = kZW - w0;
+#pragma unroll 1
+    for (int item = threadIdx.x; item < 6 * nw; item += blockDim.x) {
+        const int c = item / nw;
+        const int w = w0 + item - c * nw;
         const int64_t m = i0 - 2 + w;
         const bool valid = interior || (m >= 0 && m < a.nout);
         const int dm = (int)(m - ic);
         const float u = (float)dm * sm.inv_half;   // exact: S is a power of two
-#pragma unroll 1
-        for (int c = 0; c < 6; ++c) {
+        {
             df z = df{0.f, 0.f};
             if (valid) {
                 const DfSer& R = sm.ser[c];

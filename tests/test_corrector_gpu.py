@@ -300,10 +300,11 @@ def test_failed_spot_check_recomputes_every_tile(L):
     c.links(lo, d["sky"], s.grid, d["hp32"], d["hc32"], s.grid, y)
     r = c.report()
     ntile = (s.n + 255) // 256
-    # spot checks only on tiles whose retarded times stay on the h grid
-    # (tiles 4 and 8 of 12 here: about 670 s = 134 samples lost at each end)
+    # spot checks only on tiles whose retarded times stay on the h grid (about
+    # 670 s = 134 samples lost at each end: tiles 1..10 of 12), every 4th from
+    # the first of them: tiles 1, 5 and 9
     assert r["status"] == L.LISA_ECORRECTOR
-    assert r["spot_tiles"] == 2 and r["spot_failed"] == r["spot_tiles"]
+    assert r["spot_tiles"] == 3 and r["spot_failed"] == r["spot_tiles"]
     assert r["fallback_tiles"] == ntile - r["spot_tiles"]
     assert _same_links(y, full)
     # counters were reset by the report; a lenient tolerance passes
