@@ -18,6 +18,12 @@ namespace lisa {
 
 // Mixed frozen form on a common grid: per-link combined filters (tdi_comb.cu).
 int launch_tdi_comb(const TdiArgs& a, int64_t tiles, cudaStream_t st);
+// FP64 frozen form on a common grid: per-link combined filters (tdi_comb64.cu).
+int launch_tdi_comb64(const TdiArgs& a, cudaStream_t st);
+
+#ifndef LISA_TDI_COMB64
+#define LISA_TDI_COMB64 1   // FP64 frozen TDI on combined filters (0: the per-term kernels)
+#endif
 
 template <bool MIXED>
 __global__ void __launch_bounds__(kTile) tdi_kernel(TdiArgs a)
@@ -139,6 +145,8 @@ int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int prec
     int rc;
     if (precision == LISA_MIXED && mode == LISA_FROZEN && a.ym.unit_rho) {
         rc = launch_tdi_comb(a, tiles, st);
+    } else if (LISA_TDI_COMB64 && precision != LISA_MIXED && mode == LISA_FROZEN && a.ym.unit_rho) {
+        rc = launch_tdi_comb64(a, st);
     } else {
         if (precision == LISA_MIXED) tdi_kernel<true><<<(unsigned)tiles, kTile, 0, st>>>(a);
         else if (tiles < 2 * 152) {
