@@ -52,7 +52,7 @@ struct DfWin {
 
 struct DfSmem {
     TileGeo g;
-    float4 dw[2][kWinH];          // hdot windows as double-floats (h+ hi, lo, hx hi, lo), two buffers
+    float4 dw[2][kWinH];          // hdot windows as double-floats (h+ hi, hx hi, h+ lo, hx lo), two buffers
     df zs[6][kZW];                // z of the tile and its 2-sample halos
     df halo[2][6][4];             // z at the next tile's left halo and first two samples, two buffers
     DfSer ser[6];
@@ -229,10 +229,12 @@ __device__ __forceinline__ double df_hdot_global(const double* __restrict__ h, i
     return ((at(idx + 1) - at(idx - 1)) * 8.0 - (at(idx + 2) - at(idx - 2))) * i12;
 }
 
+// (h+ hi, hx hi, h+ lo, hx lo): the two polarisations' high parts, then
+// their low parts, as the register pairs of the packed tap arithmetic.
 __device__ __forceinline__ float4 df_pack(double p, double c)
 {
     const df a = df_of(p), b = df_of(c);
-    return make_float4(a.hi, a.lo, b.hi, b.lo);
+    return make_float4(a.hi, b.hi, a.lo, b.lo);
 }
 
 // hdot on the window of one tile (FP64 from h in global memory, kept as
@@ -275,23 +277,25 @@ __device__ __forceinline__ void lagrange32_df(df eps, Node&& node, df& op, df& o
 #pragma unroll
     for (int k = 14; k >= 0; --k) S[k] = df_mul(S[k + 1], ek(k + 1));
     df P = df{1.f, 0.f};   // prod_{j<k} e_j
-    float Sp = 0.f, Cp = 0.f, Sc = 0.f, Cc = 0.f;
+    // both polarisations at once in packed FP32 pair instructions (one issue
+    // slot for two operations): sums (S+, Sx) and corrections (C+, Cx)
+    float2 S2 = make_float2(0.f, 0.f), C2 = make_float2(0.f, 0.f);
+    const float2 M1 = make_float2(-1.f, -1.f);
     auto tap = [&](df w, float4 h) {
-        // + polarisation: exact product (p, pe), two-sum into (Sp, Cp), cross terms
-        const float p = __fmul_rn(w.hi, h.x);
-        const float pe = __fmaf_rn(w.hi, h.x, -p);
-        const df t1 = two_sum(Sp, p);
-        Sp = t1.hi;
-        Cp = __fadd_rn(Cp, __fadd_rn(t1.lo, pe));
-        Cp = __fmaf_rn(w.hi, h.y, Cp);
-        Cp = __fmaf_rn(w.lo, h.x, Cp);
-        const float q = __fmul_rn(w.hi, h.z);
-        const float qe = __fmaf_rn(w.hi, h.z, -q);
-        const df t2 = two_sum(Sc, q);
-        Sc = t2.hi;
-        Cc = __fadd_rn(Cc, __fadd_rn(t2.lo, qe));
-        Cc = __fmaf_rn(w.hi, h.w, Cc);
-        Cc = __fmaf_rn(w.lo, h.z, Cc);
+        const float2 W = make_float2(w.hi, w.hi), NW = make_float2(-w.hi, -w.hi), WL = make_float2(w.lo, w.lo);
+        const float2 Hh = make_float2(h.x, h.y), Hl = make_float2(h.z, h.w);
+        // exact product: P rounded, Pn = P - w h (minus its rounding error)
+        const float2 P = __fmul2_rn(W, Hh);
+        const float2 Pn = __ffma2_rn(NW, Hh, P);
+        // two-sum of (S, P); x - y as fma(y, -1, x) (exact negation, one rounding)
+        const float2 s = __fadd2_rn(S2, P);
+        const float2 bb = __ffma2_rn(S2, M1, s);
+        const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, M1, s), M1, S2), __ffma2_rn(bb, M1, P));
+        S2 = s;
+        // corrections: the two-sum error, the product error, the cross terms
+        C2 = __fadd2_rn(C2, __ffma2_rn(Pn, M1, e));
+        C2 = __ffma2_rn(W, Hl, C2);
+        C2 = __ffma2_rn(WL, Hh, C2);
     };
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -311,8 +315,8 @@ __device__ __forceinline__ void lagrange32_df(df eps, Node&& node, df& op, df& o
         tap(wr, node(16 + k));
         if (k < 15) P = df_mul(P, k == 0 ? e0 : ek(k));
     }
-    op = fast_two_sum(Sp, Cp);
-    oc = fast_two_sum(Sc, Cc);
+    op = fast_two_sum(S2.x, C2.x);
+    oc = fast_two_sum(S2.y, C2.y);
 }
 
 // z of tile q of the group (first sample i0) and its 2-sample halos: all of
