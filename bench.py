@@ -72,17 +72,17 @@ REC_PRECISION = 2
 REC_DTYPE = {0: "f64", 2: "df64"}
 REC_KERNEL = {0: "lfa_f64", 2: "lfa_df"}
 
-# FP32 operations (add, multiply or fused multiply-add: one each) of the
-# double-float LFA per output sample (TDI 2.0, A/E/T), counted from the
-# algorithm's operations:
+# FP32 operations (add, multiply or fused multiply-add: one each; a packed
+# pair instruction counts as two) of the double-float LFA per output sample
+# (TDI 2.0, A/E/T), counted from the algorithm's operations:
 #   per z-series sample: 32 Lagrange weights and taps 1357 (weight products
 #   and mirrored-node factors 205, 16 x 2 taps x 2 polarisations x 12 for the
 #   two-sum accumulation of exact products 768, pair products of the weights
-#   384), position (delay polynomial, scale, fraction) 117, projection factors
-#   and z 161 -> 1635, x 6 series;
+#   384), position (delay polynomial with its FP32 tail, scale, fraction) 69,
+#   projection factors (FP32 tails from u^3) and z 119 -> 1545, x 6 series;
 #   channels: light-time polynomials, two 5-point second differences and the
-#   prefactors, 409 per channel x 3, A/E/T 82.
-DF_OPS_PER_SAMPLE = {"lfa20": 6 * 1635 + 3 * 409 + 82}
+#   prefactors, 367 per channel x 3, A/E/T 82.
+DF_OPS_PER_SAMPLE = {"lfa20": 6 * 1545 + 3 * 367 + 82}
 
 
 def measured_fma_peaks(L):

@@ -92,4 +92,20 @@ __device__ __forceinline__ df df_horner(const df* c, float u)
     return r;
 }
 
+// The same sum with only c_0 .. c_{K-1} in double-float: the tail
+// sum_{k>=K} c_k u^k is formed from the coefficients' high parts in FP32, for
+// series whose tail is small enough that its FP32 rounding is below the
+// accuracy the caller needs.
+template <int N, int K>
+__device__ __forceinline__ df df_horner_tail(const df* c, float u)
+{
+    float r = c[N - 1].hi;
+#pragma unroll
+    for (int k = N - 2; k >= K; --k) r = __fmaf_rn(r, u, c[k].hi);
+    df acc = df_add(c[K - 1], df{__fmul_rn(r, u), 0.f});
+#pragma unroll
+    for (int k = K - 2; k >= 0; --k) acc = df_add(df_renorm(df_mul_f(acc, u)), c[k]);
+    return acc;
+}
+
 }  // namespace lisa

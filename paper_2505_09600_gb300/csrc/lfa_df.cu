@@ -24,7 +24,12 @@
 // FP32 (S is a power of two), and every polynomial, the position, the 32
 // weights (the paired mirrored-node scheme of the FP32 weights, with
 // compensated products), the tap sums (two-sum accumulation of exact
-// products) and the channel stencils run in double-float.
+// products, both polarisations per packed FP32 pair instruction) and the
+// channel stencils run in double-float; the polynomials' tails (the terms
+// from u^3 on) run in FP32: over a group of half-span <= 1.1e4 s they are
+// below 1e-6 s in the delay (FP32 rounding < 1e-13 s, < 2e-14 of a sample at
+// dt >= 5 s, an interpolation error at the level of the taps' own rounding)
+// and below 2e-9 of the projection factors and light times.
 #include "dfloat.cuh"
 #include "lfa_tile.cuh"
 
@@ -53,7 +58,7 @@ struct DfWin {
 struct DfSmem {
     TileGeo g;
     float4 dw[2][kWinH];          // hdot windows as double-floats (h+ hi, hx hi, h+ lo, hx lo), two buffers
-    df zs[6][kZW];                // z of the tile and its 2-sample halos
+    df zs[2][6][kZW];             // z of a tile and its 2-sample halos, two buffers (tiles q, q - 1)
     df halo[2][6][4];             // z at the next tile's left halo and first two samples, two buffers
     DfSer ser[6];
     int64_t J[6];
@@ -64,6 +69,7 @@ struct DfSmem {
     int64_t jends[kDfGmax][12];
     float inv_half;
     df inv_dt;                    // 1 / dt (double-float)
+    df k1, k2;                    // 1 / (12 dt), 1 / (12 dt^2) of the output grid (stencils)
     int blend;                    // the sigmoid weight differs from 1 somewhere in the group
 };
 
@@ -138,6 +144,8 @@ static __device__ void df_prologue(const LfaArgs& a, int64_t t0, int nt, int64_t
     if (t == 96) {
         sm.inv_half = (float)(2.0 / a.tab.S);
         sm.inv_dt = df_of(1.0 / a.hm.dt_in);
+        sm.k1 = df_of(1.0 / (12.0 * a.dt_out));
+        sm.k2 = df_of(1.0 / (12.0 * a.dt_out * a.dt_out));
     }
     __syncthreads();
     if (t < 6) {
@@ -330,7 +338,7 @@ static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSm
     const int t = threadIdx.x;
     if (!first && t >= 32 && t < 32 + 24) {
         const int c = (t - 32) >> 2, k = (t - 32) & 3;
-        sm.zs[c][k] = sm.halo[q & 1][c][k];
+        sm.zs[q & 1][c][k] = sm.halo[q & 1][c][k];
     }
     const int64_t wlo = win.wlo;
     const int wlen = win.wlen;
@@ -356,7 +364,8 @@ static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSm
             if (valid) {
                 const DfSer& R = sm.ser[c];
                 // position on the h grid: J + dm + f0 - (d(u) - d(0)) / dt
-                const df dv = df_horner<kDfD>(R.d, u);
+                // d(u) - d(0): d_1, d_2 in double-float, the tail from d_3 in FP32
+                const df dv = df_renorm(df_mul_f(df_horner_tail<kDfD - 1, 2>(R.d + 1, u), u));
                 const df v = df_sub(R.f0, df_renorm(df_mul(dv, sm.inv_dt)));
                 // fraction: v.hi - floor(v.hi) is not exact for negative v.hi
                 // (its ulp is finer than that of the fraction), so it is taken
@@ -383,33 +392,36 @@ static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSm
                         return df_pack(df_hdot_global(hp, a.hm.n_in, q, i12), df_hdot_global(hc, a.hm.n_in, q, i12));
                     }, ip, ic2);
                 }
-                const df Fp = df_horner<kDfF>(R.fp, u), Fc = df_horner<kDfF>(R.fc, u);
+                // factors: F_0..F_2 in double-float, the tail from F_3 in FP32
+                const df Fp = df_horner_tail<kDfF, 3>(R.fp, u), Fc = df_horner_tail<kDfF, 3>(R.fc, u);
                 z = df_add(df_renorm(df_mul(Fp, ip)), df_renorm(df_mul(Fc, ic2)));
             }
-            sm.zs[c][w] = z;
+            sm.zs[q & 1][c][w] = z;
             if (w >= kTile) sm.halo[(q + 1) & 1][c][w - kTile] = z;
         }
     }
 }
 
-// Channels of sample i0 + t, stored with AET and the blend (FP64).
-static __device__ void df_channels(const LfaArgs& a, int64_t i0, int64_t ic, const DfSmem& sm)
+// Channels of sample i0 + t from the tile's z buffer zs, stored with AET and
+// the blend (FP64).
+static __device__ void df_channels(const LfaArgs& a, int64_t i0, int64_t ic, const DfSmem& sm,
+                                   const df (*__restrict__ zs)[kZW])
 {
     const int t = threadIdx.x;
     const int64_t i = i0 + t;
     if (!a.xyz || i < a.i_begin || i >= a.i_end) return;
     const float u = (float)(int)(i - ic) * sm.inv_half;
     const bool tdi20 = a.gen == LISA_TDI20;
-    const df k1 = df_of(1.0 / (12.0 * a.dt_out)), k2 = df_of(1.0 / (12.0 * a.dt_out * a.dt_out));
+    const df k1 = sm.k1, k2 = sm.k2;
     df X[3];
 #pragma unroll 1
     for (int ch = 0; ch < 3; ++ch) {
-        const df Ta = df_horner<kDfF>(sm.arm[lfa_arm(ch, 0) >> 1], u);
-        const df Tb = df_horner<kDfF>(sm.arm[lfa_arm(ch, 1) >> 1], u);
+        const df Ta = df_horner_tail<kDfF, 3>(sm.arm[lfa_arm(ch, 0) >> 1], u);
+        const df Tb = df_horner_tail<kDfF, 3>(sm.arm[lfa_arm(ch, 1) >> 1], u);
         df R[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const df* z = sm.zs[2 * ch + q] + t;   // z[0..4] = z at i-2 .. i+2
+            const df* z = zs[2 * ch + q] + t;   // z[0..4] = z at i-2 .. i+2
             if (tdi20) {
                 // 5-point second derivative as (14 d2_0 - d2_-1 - d2_1)/12, d2 from first differences
                 const df e0 = df_sub(z[1], z[0]), e1 = df_sub(z[2], z[1]), e2 = df_sub(z[3], z[2]), e3 = df_sub(z[4], z[3]);
@@ -448,9 +460,15 @@ static __device__ void df_channels(const LfaArgs& a, int64_t i0, int64_t ic, con
     out[2 * a.nout + i] = o[2];
 }
 
+// One barrier per tile: iteration q forms the z of tile q (buffer q & 1),
+// the channels of tile q - 1 (buffer (q - 1) & 1) and stages the hdot window
+// of tile q + 1 (buffer (q + 1) & 1, last read by the z of tile q - 1), so a
+// warp done with its z items goes on to channels and staging instead of
+// waiting at a barrier between them.
 __global__ void __launch_bounds__(kTile, LISA_DF_MINB) lfa_kernel_df(LfaArgs a, int64_t tile_end, int G)
 {
-    __shared__ DfSmem sm;
+    extern __shared__ __align__(16) unsigned char df_raw[];
+    DfSmem& sm = *reinterpret_cast<DfSmem*>(df_raw);
     const int64_t t0 = a.tile0 + (int64_t)blockIdx.x * G;
     const int64_t ic = t0 * kTile + (int64_t)G * kTile / 2;
     const int nt = (int)(tile_end - t0 < G ? tile_end - t0 : G);
@@ -460,19 +478,29 @@ __global__ void __launch_bounds__(kTile, LISA_DF_MINB) lfa_kernel_df(LfaArgs a, 
     for (int q = 0; q < nt; ++q) {
         const int64_t i0 = (t0 + q) * (int64_t)kTile;
         df_zvalues(a, i0, ic, sm, sm.win[q], sm.dw[q & 1], q, q == 0);
-        __syncthreads();   // z of the tile complete
-        df_channels(a, i0, ic, sm);
+        if (q > 0) df_channels(a, i0 - kTile, ic, sm, sm.zs[(q - 1) & 1]);
         if (q + 1 < nt) df_stage(a, sm.win[q + 1], sm.dw[(q + 1) & 1]);
-        __syncthreads();   // z read, next window staged
+        __syncthreads();   // z of tile q complete, channels of q - 1 read, window of q + 1 staged
     }
+    df_channels(a, (t0 + nt - 1) * (int64_t)kTile, ic, sm, sm.zs[(nt - 1) & 1]);
 }
 
 int launch_lfa_df(const LfaArgs& a, cudaStream_t st)
 {
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int d = dev < 64 ? dev : 63;
+    if (!attr[d]) {
+        const cudaError_t e = cudaFuncSetAttribute(lfa_kernel_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sizeof(DfSmem));
+        if (e != cudaSuccess) return cuda_status(e, "lfa_kernel_df shared memory");
+        attr[d] = true;
+    }
     const int64_t tiles = (a.i_end - 1) / kTile - a.tile0 + 1;
     const int64_t tile_end = a.tile0 + tiles;
     const int G = lfa_group(a.dt_out);
-    lfa_kernel_df<<<(unsigned)((tiles + G - 1) / G), kTile, 0, st>>>(a, tile_end, G);
+    lfa_kernel_df<<<(unsigned)((tiles + G - 1) / G), kTile, sizeof(DfSmem), st>>>(a, tile_end, G);
     return cuda_status(cudaGetLastError(), "lfa_kernel_df launch");
 }
 
