@@ -3,8 +3,9 @@ kernels in up to 8 chunks) against lisa_response_hybrid on device copies of
 the same series, and against the oracle.
 
 Chunk boundaries fall on the LFA tile groups, so the LFA-only samples are
-bit-identical; the TDI blocks follow the chunks, so the full-response samples
-agree to FP32 rounding (mixed) and exactly in FP64 (per-tile TDI there)."""
+bit-identical; the TDI blocks (and, on short ranges, the split of the FP64
+links and TDI over more CTAs) follow the chunks, so the full-response samples
+agree to FP32 rounding (mixed) and to FP64 rounding (FP64)."""
 import numpy as np
 import pytest
 
@@ -64,10 +65,14 @@ def test_host_pipeline_mixed_matches_device(L, gen):
     assert np.abs(host - dev).max() <= 2e-6 * np.abs(dev).max()
 
 
-def test_host_pipeline_f64_exact(L):
+def test_host_pipeline_f64(L):
     s = synth.cfg2_small(n=20000)
-    dev, host, _ = _pair(L, s, L.F64, 20, 0)
-    assert np.array_equal(host, dev)
+    dev, host, (_, _, _, tH, Tw, _) = _pair(L, s, L.F64, 20, 0)
+    iF = _split(s, tH, Tw)
+    assert 0 < iF < s.n
+    assert np.array_equal(host[:, :iF], dev[:, :iF])          # LFA only: same tiles, same groups
+    # full part: the same FP64 arithmetic over other block boundaries
+    assert np.abs(host - dev).max() <= 1e-13 * np.abs(dev).max()
 
 
 def test_host_pipeline_pageable_and_oracle(L, oracle_mod):
