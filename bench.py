@@ -75,14 +75,18 @@ REC_KERNEL = {0: "lfa_f64", 2: "lfa_df"}
 # FP32 operations (add, multiply or fused multiply-add: one each; a packed
 # pair instruction counts as two) of the double-float LFA per output sample
 # (TDI 2.0, A/E/T), counted from the algorithm's operations:
-#   per z-series sample: 32 Lagrange weights and taps 1357 (weight products
-#   and mirrored-node factors 205, 16 x 2 taps x 2 polarisations x 12 for the
-#   two-sum accumulation of exact products 768, pair products of the weights
-#   384), position (delay polynomial with its FP32 tail, scale, fraction) 69,
-#   projection factors (FP32 tails from u^3) and z 119 -> 1545, x 6 series;
+#   per z-series sample: 32 Lagrange weights and taps 1052 (weights 552: the
+#   running products, the mirrored-node factors and the pair products in
+#   double-float, the four outermost weights in FP32; taps of both
+#   polarisations 480: the eight central taps by two-sum accumulation of
+#   exact products, 24 each, twenty outer taps split against a power of two,
+#   14 each, the four outermost as plain multiply-adds, 2 each; joining the
+#   exact sums and the correction 20), position (delay polynomial with its
+#   FP32 tail, scale, fraction) 69, projection factors (FP32 tails from u^3)
+#   and z 119 -> 1240, x 6 series;
 #   channels: light-time polynomials, two 5-point second differences and the
 #   prefactors, 367 per channel x 3, A/E/T 82.
-DF_OPS_PER_SAMPLE = {"lfa20": 6 * 1545 + 3 * 367 + 82}
+DF_OPS_PER_SAMPLE = {"lfa20": 6 * 1240 + 3 * 367 + 82}
 
 
 def measured_fma_peaks(L):

@@ -58,6 +58,7 @@ struct DfWin {
 struct DfSmem {
     TileGeo g;
     float4 dw[2][kWinH];          // hdot windows as double-floats (h+ hi, hx hi, h+ lo, hx lo), two buffers
+    float2 wmax[2][kTile / 32];   // per warp: largest |h+ hi|, |hx hi| it staged into buffer 0 / 1
     df zs[2][6][kZW];             // z of a tile and its 2-sample halos, two buffers (tiles q, q - 1)
     df halo[2][6][4];             // z at the next tile's left halo and first two samples, two buffers
     DfSer ser[6];
@@ -246,28 +247,64 @@ __device__ __forceinline__ float4 df_pack(double p, double c)
 }
 
 // hdot on the window of one tile (FP64 from h in global memory, kept as
-// double-floats) into buffer dw.  No synchronisation.
-static __device__ void df_stage(const LfaArgs& a, const DfWin& w, float4* __restrict__ dw)
+// double-floats) into buffer dw, and each warp's largest |high part| of either
+// polarisation into wm[warp].  No synchronisation.
+static __device__ void df_stage(const LfaArgs& a, const DfWin& w, float4* __restrict__ dw, float2* __restrict__ wm)
 {
     const double* __restrict__ hp = (const double*)a.hp;
     const double* __restrict__ hc = (const double*)a.hc;
     const double i12 = 1.0 / (12.0 * a.hm.dt_in);
     const int64_t n = a.hm.n_in;
+    float mp = 0.f, mc = 0.f;
     for (int k = threadIdx.x; k < w.wlen; k += blockDim.x) {
         const int64_t idx = w.wlo + k;
-        dw[k] = df_pack(df_hdot_global(hp, n, idx, i12), df_hdot_global(hc, n, idx, i12));
+        const float4 v = df_pack(df_hdot_global(hp, n, idx, i12), df_hdot_global(hc, n, idx, i12));
+        dw[k] = v;
+        mp = fmaxf(mp, fabsf(v.x));
+        mc = fmaxf(mc, fabsf(v.y));
     }
+    // non-negative floats order as their bit patterns
+    const unsigned int bp = __reduce_max_sync(0xffffffffu, __float_as_uint(mp));
+    const unsigned int bc = __reduce_max_sync(0xffffffffu, __float_as_uint(mc));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = make_float2(__uint_as_float(bp), __uint_as_float(bc));
+}
+
+// The splitting constant of one polarisation's outer taps (below) over a
+// window whose largest |node| is M, 2^e <= M < 2^(e+1): sigma = 2^(e-2)
+// (1 for an all-zero window).
+__device__ __forceinline__ float df_split_sigma(float M)
+{
+    const int e = (int)((__float_as_uint(M) >> 23) & 0xffu);
+    if (M == 0.f) return 1.f;
+    const int es = e < 3 ? 1 : e - 2;
+    return __uint_as_float((unsigned int)(es < 254 ? es : 254) << 23);
 }
 
 // 32-point Lagrange interpolation of both polarisations at a double-float
 // fraction eps (the paired mirrored-node scheme of lagrange32_paired_f32:
 // s = eps - 1/2, e_k = s^2 - (k + 1/2)^2, e_0 = eps (eps - 1), Q_k =
 // K_{15-k} prod_{j != k} e_j, w_{15-k} = (s - k - 1/2) Q_k, w_{16+k} =
-// -(s + k + 1/2) Q_k), with compensated products, and the taps accumulated by
-// two-sum of the exact products (Ogita, Rump and Oishi's Dot2).  node(p)
-// gives node p's (h+ hi, lo, hx hi, lo).
-template <class Node>
-__device__ __forceinline__ void lagrange32_df(df eps, Node&& node, df& op, df& oc)
+// -(s + k + 1/2) Q_k), with compensated products.  node(p) gives node p's
+// (h+ hi, hx hi, h+ lo, hx lo).  Both polarisations run in packed FP32 pair
+// instructions, and the taps are summed exactly in one of two ways:
+//  - two-sum of the exact products (Ogita, Rump and Oishi's Dot2), twelve
+//    pair instructions a tap: every tap when kSplit is false (any node
+//    values), else the eight central ones (pairs k = 0..3, nodes -3..4);
+//  - with kSplit, the 24 outer taps (pairs k = 4..15, |w| <= 0.0197 and
+//    sum |w| <= 0.0656 for eps in [0, 1], from the Lagrange basis of the 32
+//    equispaced nodes): each product w h of the high parts is split against
+//    the power of two sigma = 2^(e-2), 2^e <= max|h| over the window < 2^(e+1)
+//    (Rump, Ogita and Oishi's ExtractScalar, with the product fused into the
+//    split): u = fl(w h + sigma), q = u - sigma exactly (|w h| < sigma / 2,
+//    Sterbenz's lemma), the q, multiples of 2^-24 sigma whose partial sums
+//    stay below sigma, are summed exactly, and the remainders fl(w h - q) go
+//    to the correction sum; seven pair instructions a tap.  The remainders
+//    are bounded by 2^-26 max|h|, below the two-sum errors of the central
+//    taps, so the correction's rounding stays at the level of Dot2's.  The
+//    four outermost of them (pairs 14, 15, |w| <= 2.3e-9) take FP32 weights
+//    and plain multiply-adds into the correction sum.
+template <bool kSplit, class Node>
+__device__ __forceinline__ void lagrange32_df(df eps, Node&& node, float2 sigma, df& op, df& oc)
 {
     df s = two_sum(eps.hi, -0.5f);
     s.lo = __fadd_rn(s.lo, eps.lo);
@@ -289,19 +326,30 @@ __device__ __forceinline__ void lagrange32_df(df eps, Node&& node, df& op, df& o
     // slot for two operations): sums (S+, Sx) and corrections (C+, Cx)
     float2 S2 = make_float2(0.f, 0.f), C2 = make_float2(0.f, 0.f);
     const float2 M1 = make_float2(-1.f, -1.f);
-    auto tap = [&](df w, float4 h) {
-        const float2 W = make_float2(w.hi, w.hi), NW = make_float2(-w.hi, -w.hi), WL = make_float2(w.lo, w.lo);
+    // the outer taps' exact sum, negated (kSplit)
+    float2 NS2 = make_float2(0.f, 0.f);
+    auto tap = [&](df w, float4 h, bool split) {
+        const float2 W = make_float2(w.hi, w.hi), WL = make_float2(w.lo, w.lo);
         const float2 Hh = make_float2(h.x, h.y), Hl = make_float2(h.z, h.w);
-        // exact product: P rounded, Pn = P - w h (minus its rounding error)
-        const float2 P = __fmul2_rn(W, Hh);
-        const float2 Pn = __ffma2_rn(NW, Hh, P);
-        // two-sum of (S, P); x - y as fma(y, -1, x) (exact negation, one rounding)
-        const float2 s = __fadd2_rn(S2, P);
-        const float2 bb = __ffma2_rn(S2, M1, s);
-        const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, M1, s), M1, S2), __ffma2_rn(bb, M1, P));
-        S2 = s;
-        // corrections: the two-sum error, the product error, the cross terms
-        C2 = __fadd2_rn(C2, __ffma2_rn(Pn, M1, e));
+        if (split) {
+            const float2 U = __ffma2_rn(W, Hh, sigma);        // fl(w h + sigma)
+            const float2 NQ = __ffma2_rn(U, M1, sigma);       // sigma - u = -q, exact
+            NS2 = __fadd2_rn(NS2, NQ);                         // exact
+            C2 = __fadd2_rn(C2, __ffma2_rn(W, Hh, NQ));        // w h - q
+        } else {
+            const float2 NW = make_float2(-w.hi, -w.hi);
+            // exact product: P rounded, Pn = P - w h (minus its rounding error)
+            const float2 P = __fmul2_rn(W, Hh);
+            const float2 Pn = __ffma2_rn(NW, Hh, P);
+            // two-sum of (S, P); x - y as fma(y, -1, x) (exact negation, one rounding)
+            const float2 s = __fadd2_rn(S2, P);
+            const float2 bb = __ffma2_rn(S2, M1, s);
+            const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, M1, s), M1, S2), __ffma2_rn(bb, M1, P));
+            S2 = s;
+            // corrections: the two-sum error, the product error
+            C2 = __fadd2_rn(C2, __ffma2_rn(Pn, M1, e));
+        }
+        // the cross terms
         C2 = __ffma2_rn(W, Hl, C2);
         C2 = __ffma2_rn(WL, Hh, C2);
     };
@@ -309,6 +357,20 @@ __device__ __forceinline__ void lagrange32_df(df eps, Node&& node, df& op, df& o
     for (int k = 0; k < 16; ++k) {
         const double Kd = lagrange32_k(15 - k);
         const float Kh = float(Kd), Kl = float(Kd - double(float(Kd)));
+        if (kSplit && k >= 14) {
+            // the four outermost nodes: |w| <= 2.3e-9, so FP32 weights (a
+            // few units of 2^-24 off) move the sum by < 2^-49 max|h|, and the
+            // taps go straight into the correction sum
+            const float Q = __fmul_rn(__fmul_rn(P.hi, S[k].hi), Kh);
+            const float c = float(k + 0.5);
+            const float2 W = make_float2(__fmul_rn(__fadd_rn(s.hi, -c), Q), __fmul_rn(__fadd_rn(s.hi, -c), Q));
+            const float2 NWr = make_float2(__fmul_rn(__fadd_rn(s.hi, c), Q), __fmul_rn(__fadd_rn(s.hi, c), Q));
+            const float4 hl = node(15 - k), hr = node(16 + k);
+            C2 = __ffma2_rn(W, make_float2(hl.x, hl.y), C2);
+            C2 = __ffma2_rn(NWr, make_float2(-hr.x, -hr.y), C2);
+            if (k < 15) P.hi = __fmul_rn(P.hi, ek(k).hi);
+            continue;
+        }
         const df Q = df_mul(df_mul(P, S[k]), df{Kh, Kl});
         const float c = float(k + 0.5);
         df am = fast_two_sum(-c, s.hi);   // s - c, |c| >= 1/2 >= |s|
@@ -319,12 +381,18 @@ __device__ __forceinline__ void lagrange32_df(df eps, Node&& node, df& op, df& o
         df wr = df_mul(ap, Q);             // -w_{16+k}
         wr.hi = -wr.hi;
         wr.lo = -wr.lo;
-        tap(wl, node(15 - k));
-        tap(wr, node(16 + k));
+        tap(wl, node(15 - k), kSplit && k >= 4);
+        tap(wr, node(16 + k), kSplit && k >= 4);
         if (k < 15) P = df_mul(P, k == 0 ? e0 : ek(k));
     }
-    op = fast_two_sum(S2.x, C2.x);
-    oc = fast_two_sum(S2.y, C2.y);
+    if (kSplit) {
+        const df ap = two_sum(S2.x, -NS2.x), ac = two_sum(S2.y, -NS2.y);
+        op = two_sum(ap.hi, __fadd_rn(ap.lo, C2.x));
+        oc = two_sum(ac.hi, __fadd_rn(ac.lo, C2.y));
+    } else {
+        op = fast_two_sum(S2.x, C2.x);
+        oc = fast_two_sum(S2.y, C2.y);
+    }
 }
 
 // z of tile q of the group (first sample i0) and its 2-sample halos: all of
@@ -342,6 +410,19 @@ static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSm
     }
     const int64_t wlo = win.wlo;
     const int wlen = win.wlen;
+    // splitting constants of the staged window's outer taps (from its largest
+    // |high part|, the maximum over the warps' maxima)
+    float2 sigma;
+    {
+        float mp = 0.f, mc = 0.f;
+#pragma unroll
+        for (int k = 0; k < kTile / 32; ++k) {
+            const float2 m = sm.wmax[q & 1][k];
+            mp = fmaxf(mp, m.x);
+            mc = fmaxf(mc, m.y);
+        }
+        sigma = make_float2(df_split_sigma(mp), df_split_sigma(mc));
+    }
     const double* __restrict__ hp = (const double*)a.hp;
     const double* __restrict__ hc = (const double*)a.hc;
     const double i12 = 1.0 / (12.0 * a.hm.dt_in);
@@ -385,12 +466,12 @@ static __device__ void df_zvalues(const LfaArgs& a, int64_t i0, int64_t ic, DfSm
                 df ip, ic2;
                 if (wlen > 0 && base >= 0 && base + 32 <= wlen) {
                     const float4* nb = dw + base;
-                    lagrange32_df(e, [&](int p) { return nb[p]; }, ip, ic2);
+                    lagrange32_df<true>(e, [&](int p) { return nb[p]; }, sigma, ip, ic2);
                 } else {
-                    lagrange32_df(e, [&](int p) {
+                    lagrange32_df<false>(e, [&](int p) {
                         const int64_t q = j - 15 + p;
                         return df_pack(df_hdot_global(hp, a.hm.n_in, q, i12), df_hdot_global(hc, a.hm.n_in, q, i12));
-                    }, ip, ic2);
+                    }, sigma, ip, ic2);
                 }
                 // factors: F_0..F_2 in double-float, the tail from F_3 in FP32
                 const df Fp = df_horner_tail<kDfF, 3>(R.fp, u), Fc = df_horner_tail<kDfF, 3>(R.fc, u);
@@ -473,13 +554,13 @@ __global__ void __launch_bounds__(kTile, LISA_DF_MINB) lfa_kernel_df(LfaArgs a, 
     const int64_t ic = t0 * kTile + (int64_t)G * kTile / 2;
     const int nt = (int)(tile_end - t0 < G ? tile_end - t0 : G);
     df_prologue(a, t0, nt, ic, sm);
-    df_stage(a, sm.win[0], sm.dw[0]);
+    df_stage(a, sm.win[0], sm.dw[0], sm.wmax[0]);
     __syncthreads();
     for (int q = 0; q < nt; ++q) {
         const int64_t i0 = (t0 + q) * (int64_t)kTile;
         df_zvalues(a, i0, ic, sm, sm.win[q], sm.dw[q & 1], q, q == 0);
         if (q > 0) df_channels(a, i0 - kTile, ic, sm, sm.zs[(q - 1) & 1]);
-        if (q + 1 < nt) df_stage(a, sm.win[q + 1], sm.dw[(q + 1) & 1]);
+        if (q + 1 < nt) df_stage(a, sm.win[q + 1], sm.dw[(q + 1) & 1], sm.wmax[(q + 1) & 1]);
         __syncthreads();   // z of tile q complete, channels of q - 1 read, window of q + 1 staged
     }
     df_channels(a, (t0 + nt - 1) * (int64_t)kTile, ic, sm, sm.zs[(nt - 1) & 1]);

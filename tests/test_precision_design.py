@@ -19,3 +19,31 @@ def test_fp32_absolute_time_is_not_enough(oracle_mod):
                         for k in range(idx.size)], axis=1)
     err = np.abs(shifted - exact).max() / np.abs(exact).max()
     assert err > 1e-3, err
+
+
+def test_split_accumulation_bounds_of_the_outer_taps():
+    """The double-float LFA sums its 24 outer taps (nodes -15..-4 and 5..16 of
+    the 32-point stencil) exactly by splitting each product against
+    sigma = 2^(e-2), where 2^e <= M < 2^(e+1) bounds the window's nodes.  That
+    is exact when every outer |w_k| M stays below sigma / 2 and their sum below
+    sigma, i.e. max |w_k| < 1/16 and sum |w_k| < 1/8 for every fraction in
+    [0, 1].  The Lagrange basis, evaluated here in exact rational arithmetic
+    at 257 fractions (the extremes sit at 0.5 and near the ends), gives
+    max |w_k| = 0.0197 and sum |w_k| = 0.0656: margins of 3.2 and 1.9."""
+    from fractions import Fraction
+    nodes = list(range(-15, 17))
+    outer = [k for k in nodes if k <= -4 or k >= 5]
+    worst_max, worst_sum = Fraction(0), Fraction(0)
+    for i in range(257):
+        e = Fraction(i, 256)
+        ws = []
+        for k in outer:
+            w = Fraction(1)
+            for m in nodes:
+                if m != k:
+                    w *= (e - m) / Fraction(k - m)
+            ws.append(abs(w))
+        worst_max = max(worst_max, max(ws))
+        worst_sum = max(worst_sum, sum(ws))
+    assert worst_max < Fraction(1, 16) / 3, float(worst_max)
+    assert worst_sum < Fraction(1, 8) / Fraction(3, 2), float(worst_sum)
