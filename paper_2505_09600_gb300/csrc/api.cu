@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "lisa_common.cuh"
 #include "lisa_internal.cuh"
@@ -172,6 +173,68 @@ void hybrid_split(const lisa_grid& out, double t_hyb, double Tw, int64_t& iL_out
 }  // namespace lisa
 
 using namespace lisa;
+
+// ---------------------------------------------------------------------------
+// side stream of the hybrid call
+// ---------------------------------------------------------------------------
+// The full-response links of a hybrid call depend only on the orbit table and
+// h, not on the LFA part: they run on a second stream beside the LFA kernel,
+// whose last wave leaves SMs idle, and the TDI waits for them.  A set (stream,
+// fork and join events) serves one call at a time and is reused by later
+// calls on the same device; it is released once the caller's stream has been
+// told to wait for the join (a wait takes the event's state when it is
+// queued, so a later call may re-record it).
+struct SideRes {
+    int device = -1;
+    bool busy = false;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static std::mutex g_side_mu;
+static std::vector<SideRes*> g_side;
+
+static SideRes* side_acquire()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_side_mu);
+        for (SideRes* r : g_side)
+            if (!r->busy && r->device == dev) {
+                r->busy = true;
+                return r;
+            }
+    }
+    SideRes* r = new SideRes;
+    r->device = dev;
+    bool ok = cudaStreamCreateWithFlags(&r->s, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&r->join, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        if (r->fork) cudaEventDestroy(r->fork);
+        if (r->join) cudaEventDestroy(r->join);
+        if (r->s) cudaStreamDestroy(r->s);
+        delete r;
+        cudaGetLastError();   // the caller falls back to one stream
+        return nullptr;
+    }
+    r->busy = true;
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    g_side.push_back(r);
+    return r;
+}
+
+struct SideGuard {
+    SideRes* r;
+    ~SideGuard()
+    {
+        if (r) {
+            std::lock_guard<std::mutex> lk(g_side_mu);
+            r->busy = false;
+        }
+    }
+};
 
 extern "C" {
 
@@ -370,17 +433,38 @@ int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid
                                                  (size_t)(iF - iL - 1) * rs, st), "cudaMemsetAsync"));
         }
     }
-    if (iL >= 0) {
-        BlendSpec bl{1, t_hyb, sg, +1.0, 0, 0};
-        LISA_TRY(launch_lfa(tab, skyd, orbit->L_m, h_grid, hp, hc, precision, tdi_gen, lfa_kind, channels, out, nullptr,
-                            xyz, 0, iL + 1, bl, st));
-    }
+    void* y = nullptr;
+    int64_t lo = 0;
     if (iF < n) {
-        const int64_t lo = hybrid_links_begin(orbit, out, iF);
+        lo = hybrid_links_begin(orbit, out, iF);
         // the links are held for samples [lo, n) only
-        void* y = sc.alloc(6 * (size_t)(n - lo) * rs);
+        y = sc.alloc(6 * (size_t)(n - lo) * rs);
         if (!y) return sc.status();
-        LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, precision, out, y, lo, n, st, lo));
+    }
+    // both parts: the links go on the side stream, forked after the table and
+    // the link buffer are ready on the caller's stream; the caller's stream
+    // joins it after the LFA launch (also after an error, so that nothing
+    // queued there outlives the call's scratch)
+    SideGuard side{(iL >= 0 && iF < n) ? side_acquire() : nullptr};
+    int rc_links = 0, rc_join = 0;
+    if (side.r) {
+        LISA_TRY(cuda_status(cudaEventRecord(side.r->fork, st), "cudaEventRecord"));
+        LISA_TRY(cuda_status(cudaStreamWaitEvent(side.r->s, side.r->fork, 0), "cudaStreamWaitEvent"));
+        rc_links = launch_links_full(tab, skyd, h_grid, hp, hc, precision, out, y, lo, n, side.r->s, lo);
+        rc_join = cuda_status(cudaEventRecord(side.r->join, side.r->s), "cudaEventRecord");
+    }
+    int rc_lfa = 0;
+    if (iL >= 0 && !rc_links && !rc_join) {
+        BlendSpec bl{1, t_hyb, sg, +1.0, 0, 0};
+        rc_lfa = launch_lfa(tab, skyd, orbit->L_m, h_grid, hp, hc, precision, tdi_gen, lfa_kind, channels, out, nullptr,
+                            xyz, 0, iL + 1, bl, st);
+    }
+    if (side.r && !rc_join) rc_join = cuda_status(cudaStreamWaitEvent(st, side.r->join, 0), "cudaStreamWaitEvent");
+    if (rc_links) return rc_links;
+    if (rc_join) return rc_join;
+    if (rc_lfa) return rc_lfa;
+    if (iF < n) {
+        if (!side.r) LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, precision, out, y, lo, n, st, lo));
         BlendSpec bl{1, t_hyb, sg, -1.0, iF, iL + 1};
         LISA_TRY(launch_tdi(tab, out, y, precision, tdi_gen, LISA_FROZEN, channels, out, xyz, iF, n, bl, st, lo));
     }
