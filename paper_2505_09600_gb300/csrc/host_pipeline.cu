@@ -147,7 +147,7 @@ extern "C" int lisa_response_hybrid_host(const lisa_orbit* orbit, const lisa_sky
     // the first and last chunks are half as long as the others: the first
     // copy-in and the last read-back are the parts of the pipeline that
     // nothing overlaps.
-    const int64_t gt = (int64_t)lfa_group_host(grid.dt) * kTile;
+    const int64_t gt = (int64_t)lfa_group_host(grid.dt, precision) * kTile;
     const int64_t groups = (n + gt - 1) / gt;
     const int K = (int)(groups < kChunks ? groups : kChunks);
     int64_t cb[kMaxChunks + 1];   // chunk c = samples [cb[c], cb[c + 1])

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kTile, LISA_LFA_MINB) lfa_kernel_mixed(LfaArgs
 }
 
 int lfa_group_host(double dt) { return lfa_group(dt); }
+int lfa_group_host(double dt, int precision) { return precision == LISA_DF ? lfa_group_df(dt) : lfa_group(dt); }
 
 int launch_lfa_strain(const LfaArgs& a, double L_nominal, int precision, cudaStream_t st);
 int launch_lfa_df(const LfaArgs& a, cudaStream_t st);

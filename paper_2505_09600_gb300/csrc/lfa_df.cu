@@ -580,7 +580,7 @@ int launch_lfa_df(const LfaArgs& a, cudaStream_t st)
     }
     const int64_t tiles = (a.i_end - 1) / kTile - a.tile0 + 1;
     const int64_t tile_end = a.tile0 + tiles;
-    const int G = lfa_group(a.dt_out);
+    const int G = lfa_group_df(a.dt_out);
     lfa_kernel_df<<<(unsigned)((tiles + G - 1) / G), kTile, sizeof(DfSmem), st>>>(a, tile_end, G);
     return cuda_status(cudaGetLastError(), "lfa_kernel_df launch");
 }

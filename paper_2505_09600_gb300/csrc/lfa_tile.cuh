@@ -706,6 +706,16 @@ inline int lfa_group(double dt)
     return G < 1 ? 1 : (G > 8 ? 8 : G);
 }
 
+// Tiles per CTA of the double-float kernel: at most 6 (its groups take ~0.3 ms
+// each, so smaller groups shorten the last wave of CTAs more than their
+// prologues cost; on one year at 5 s, 24,644 tiles at 3 CTAs per SM, groups of
+// 8, 7, 6 and 5 tiles gave 2.254, 2.174, 2.155 and 2.168 ms).
+inline int lfa_group_df(double dt)
+{
+    const int G = lfa_group(dt);
+    return G < 6 ? G : 6;
+}
+
 // ---------------------------------------------------------------------------
 // Mixed form in sub-blocks of two tiles (the LFA kernel).
 //

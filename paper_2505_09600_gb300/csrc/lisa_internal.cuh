@@ -114,6 +114,8 @@ int make_table_pair(const lisa_orbit* orbit, const lisa_grid& g1, const lisa_gri
 double max_light_time(const lisa_orbit* o, const lisa_grid& g);
 // Tiles per CTA group of the mixed LFA kernel for a grid step dt (host side).
 int lfa_group_host(double dt);
+// tiles per LFA group of the kernel that serves the precision (chunk boundaries)
+int lfa_group_host(double dt, int precision);
 // Hybrid regions on grid `out`: LFA samples [0, iL] (t <= t_hyb + Tw/2), full
 // samples [iF, n) (t >= t_hyb - Tw/2).
 void hybrid_split(const lisa_grid& out, double t_hyb, double Tw, int64_t& iL, int64_t& iF);

@@ -75,6 +75,17 @@ def test_host_pipeline_f64(L):
     assert np.abs(host - dev).max() <= 1e-13 * np.abs(dev).max()
 
 
+def test_host_pipeline_double_float(L):
+    # chunks on the double-float kernel's own tile groups: LFA samples
+    # bit-identical; n spans several groups of 6 tiles and ends in a ragged one
+    s = synth.cfg2_small(n=40000)
+    dev, host, (_, _, _, tH, Tw, _) = _pair(L, s, L.DF, 20, 1)
+    iF = _split(s, tH, Tw)
+    assert 0 < iF < s.n
+    assert np.array_equal(host[:, :iF], dev[:, :iF])
+    assert np.abs(host - dev).max() <= 1e-13 * np.abs(dev).max()
+
+
 def test_host_pipeline_pageable_and_oracle(L, oracle_mod):
     s = synth.cfg2_small(n=20000)
     dev, host, (oo, hp, hc, tH, Tw, sig) = _pair(L, s, L.MIXED, 20, 1, pinned=False)
