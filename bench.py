@@ -552,6 +552,21 @@ def bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, st
     # the previous single-zone form (corrected links over the whole LFA side) for reference
     fo = lambda: c.hybrid(orbit, sky, src.grid, hp32, hc32, 20, L.AET, tH, Tw, sig, src.grid, out32)   # noqa: E731
     res["corrected_links_whole_lfa_side_ms"] = round(_timed(torch, stream, flush, fo), 4)
+    # the fused tensor-core corrector over the whole LFA side: its MMA work
+    # (padded shapes 48 -> 64 -> 64 -> 64 -> 16 per row) against the measured
+    # bf16 GEMM rate
+    kb = kernel_breakdown(L, torch, fo)
+    res["corrected_links_whole_lfa_side_kernels_ms"] = kb
+    if kb.get("corr_fused_tc"):
+        rows = int(math.floor((tH + 0.5 * Tw - src.t0) / src.dt)) + 1
+        rows = max(1, min(n, rows))
+        flop = 2.0 * (48 * 64 + 2 * 64 * 64 + 64 * 16) * rows
+        ach = flop / (kb["corr_fused_tc"] / 1e3) / 1e12
+        pk = float(peaks().get("bf16_tflops", 1886.2))
+        res["corr_fused_tc_roofline"] = {"bound": "tensor", "rows": rows, "flop_per_row": flop / rows,
+                                         "achieved": round(ach, 2), "peak": pk, "unit": "TFLOP/s",
+                                         "frac": round(ach / pk, 4),
+                                         "peak_note": "bf16 GEMM burst rate, MEASURED_PEAKS.json; of measured"}
     rep = c.report()
     res["spot_checks"] = {k: rep[k] for k in ("spot_tiles", "spot_failed", "band_tiles", "fallback_tiles",
                                              "max_spot_err", "status")}

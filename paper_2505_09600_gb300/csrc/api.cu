@@ -179,22 +179,18 @@ using namespace lisa;
 // ---------------------------------------------------------------------------
 // The full-response links of a hybrid call depend only on the orbit table and
 // h, not on the LFA part: they run on a second stream beside the LFA kernel,
-// whose last wave leaves SMs idle, and the TDI waits for them.  A set (stream,
+// whose last wave leaves SMs idle, and the TDI waits for them (here and in the
+// corrected hybrid).  A set (stream,
 // fork and join events) serves one call at a time and is reused by later
 // calls on the same device; it is released once the caller's stream has been
 // told to wait for the join (a wait takes the event's state when it is
 // queued, so a later call may re-record it).
-struct SideRes {
-    int device = -1;
-    bool busy = false;
-    cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-};
+namespace lisa {
 
 static std::mutex g_side_mu;
 static std::vector<SideRes*> g_side;
 
-static SideRes* side_acquire()
+SideRes* side_acquire()
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
@@ -225,16 +221,13 @@ static SideRes* side_acquire()
     return r;
 }
 
-struct SideGuard {
-    SideRes* r;
-    ~SideGuard()
-    {
-        if (r) {
-            std::lock_guard<std::mutex> lk(g_side_mu);
-            r->busy = false;
-        }
-    }
-};
+void side_release(SideRes* r)
+{
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    r->busy = false;
+}
+
+}  // namespace lisa
 
 extern "C" {
 

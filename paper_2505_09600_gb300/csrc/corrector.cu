@@ -170,32 +170,112 @@ struct FeatArgs {
     float* target;         // [rows][kOut] or null
 };
 
-// Features of sample i from the LFA links z and the FP32 coefficients cfs of
-// the orbit segment s holding i: the feature row ft (ft[46] = dt/Tbar,
+// Geometry of a block of consecutive samples inside one orbit segment, as a
+// value and a slope in the segment coordinate x at the block centre xc:
+// T_l (6), k.n_l (6) and k.v/c of each spacecraft (3, from the derivative of
+// its position polynomial).  A block spans at most 256 samples, over which the
+// orbit turns by < 1e-4 rad: the dropped curvature is below 1e-9 of T_l and
+// of k.n_l, under the FP32 rounding of the polynomials themselves.
+struct CorrGeo {
+    float xc;
+    float v[15], s[15];
+};
+
+// Quantity q of CorrGeo at xc from the FP32 segment coefficients cfs (one
+// thread per quantity).
+__device__ __forceinline__ void corr_geo_one(const FeatArgs& a, const float (*cfs)[7], float xc, int q, CorrGeo& g)
+{
+    // p(x), p'(x), p''(x) of row `row` at xc (Horner)
+    auto ev3 = [&](int row, float& p, float& d, float& dd) {
+        const float* b = cfs[row];
+        p = b[6];
+        d = 0.f;
+        dd = 0.f;
+#pragma unroll
+        for (int k = 5; k >= 0; --k) {
+            dd = fmaf(dd, xc, d);
+            d = fmaf(d, xc, p);
+            p = fmaf(p, xc, b[k]);
+        }
+        dd *= 2.f;
+    };
+    const float k3[3] = {a.sky.kf[0], a.sky.kf[1], a.sky.kf[2]};
+    float val = 0.f, slope = 0.f, p, d, dd;
+    if (q < 6) {
+        ev3(kQT + q, p, d, dd);
+        val = p;
+        slope = d;
+    } else if (q < 12) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ev3(kQN + 3 * (q - 6) + c, p, d, dd);
+            val = fmaf(k3[c], p, val);
+            slope = fmaf(k3[c], d, slope);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ev3(kQR + 3 * (q - 12) + c, p, d, dd);
+            val = fmaf(k3[c], d, val);
+            slope = fmaf(k3[c], dd, slope);
+        }
+        val *= a.vfac;
+        slope *= a.vfac;
+    }
+    g.v[q] = val;
+    g.s[q] = slope;
+    if (q == 0) g.xc = xc;
+}
+
+// The 5-point windows z_l(i - 2 .. i + 2) of the six links for the 32
+// consecutive rows of a warp (row i in lane i % 32, every lane calls it):
+// each lane loads z_l(i), the two lanes at each end one more value, and the
+// rest comes from the neighbours by shuffles.  Zero off [0, nz).
+__device__ __forceinline__ void corr_zwin(const FeatArgs& a, int64_t i, float (&v)[6][5])
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool edge = lane < 2 || lane >= 30;
+    const int64_t ke = lane < 2 ? i - 2 : i + 2;
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+        const float* __restrict__ zl = a.z + (int64_t)l * a.stride;
+        const float c = (i >= 0 && i < a.nz) ? zl[i] : 0.f;
+        const float x = (edge && ke >= 0 && ke < a.nz) ? zl[ke] : 0.f;
+        const float m2 = __shfl_sync(full, c, (lane + 30) & 31);
+        const float m1 = __shfl_sync(full, c, (lane + 31) & 31);
+        const float p1 = __shfl_sync(full, c, (lane + 1) & 31);
+        const float p2 = __shfl_sync(full, c, (lane + 2) & 31);
+        const float x1 = __shfl_sync(full, x, 1);     // z(i_1 - 2) = z(i_0 - 1)
+        const float x30 = __shfl_sync(full, x, 30);   // z(i_30 + 2) = z(i_31 + 1)
+        v[l][0] = lane < 2 ? x : m2;
+        v[l][1] = lane == 0 ? x1 : m1;
+        v[l][2] = c;
+        v[l][3] = lane == 31 ? x30 : p1;
+        v[l][4] = lane >= 30 ? x : p2;
+    }
+}
+
+// Features of sample i (segment coordinate x) from its link windows v
+// (corr_zwin) and the block geometry g: the feature row ft (ft[46] = dt/Tbar,
 // ft[47] = 0), the scale s (0 below the band), eps_l, the link values z_l(i),
 // and whether the local frequency is above the band.
-__device__ __forceinline__ void corr_feature_row(const FeatArgs& a, int64_t i, const float (*cfs)[7], int64_t s,
-                                                 float (&ft)[kInP], float& sc, float (&eps)[6], float (&z0)[6],
-                                                 bool& above)
+__device__ __forceinline__ void corr_feature_row(const FeatArgs& a, const float (&v)[6][5], const CorrGeo& g,
+                                                 float x, float (&ft)[kInP], float& sc, float (&eps)[6],
+                                                 float (&z0)[6], bool& above)
 {
     const float r1 = a.r1, r2 = r1 * r1;
     float q[5][6];
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
-        float v[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            const int64_t k = i - 2 + m;
-            v[m] = (k >= 0 && k < a.nz) ? a.z[(int64_t)l * a.stride + k] : 0.f;
-        }
         // differences first: the stencils of slowly varying series cancel less
-        const float d0 = v[1] - v[0], d1 = v[2] - v[1], d2 = v[3] - v[2], d3 = v[4] - v[3];
-        q[0][l] = v[2];
+        const float d0 = v[l][1] - v[l][0], d1 = v[l][2] - v[l][1], d2 = v[l][3] - v[l][2], d3 = v[l][4] - v[l][3];
+        q[0][l] = v[l][2];
         q[1][l] = r1 * (8.f * (d1 + d2) - (d0 + d1 + d2 + d3)) * (1.f / 12.f);
         q[2][l] = r2 * (14.f * (d2 - d1) - (d1 - d0) - (d3 - d2)) * (1.f / 12.f);
         q[3][l] = r2 * r1 * ((d0 + d1 + d2 + d3) - 2.f * (d1 + d2)) * 0.5f;
         q[4][l] = r2 * r2 * ((d3 - d2) - 2.f * (d2 - d1) + (d1 - d0));
-        z0[l] = v[2];
+        z0[l] = v[l][2];
     }
     float mk[5];
 #pragma unroll
@@ -210,37 +290,20 @@ __device__ __forceinline__ void corr_feature_row(const FeatArgs& a, int64_t i, c
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float lr = (mk[k] > 0.f && mk[k + 1] > 0.f) ? log10f(mk[k + 1] / mk[k]) : -8.f;
+        const float lr = (mk[k] > 0.f && mk[k + 1] > 0.f) ? log10f(__fdividef(mk[k + 1], mk[k])) : -8.f;
         ft[30 + k] = fminf(fmaxf(lr, -8.f), 8.f) * 0.25f;
     }
-    // geometry at sample i from the orbit table (FP32 evaluation suffices here)
-    const float x = (float)(int)(i - s * a.tab.S) * a.inv_half - 1.f;
-    auto ev = [&](int row) {
-        const float* b = cfs[row];
-        float r = b[6];
-#pragma unroll
-        for (int p = 5; p >= 0; --p) r = fmaf(r, x, b[p]);
-        return r;
-    };
-    // k.v / c of each spacecraft from the derivative of its position polynomial
-    auto evd = [&](int row) {
-        const float* b = cfs[row];
-        float r = 6.f * b[6];
-#pragma unroll
-        for (int p = 5; p >= 1; --p) r = fmaf(r, x, (float)p * b[p]);
-        return r;
-    };
-    const float k0 = a.sky.kf[0], k1 = a.sky.kf[1], k2 = a.sky.kf[2];
+    // geometry: linear in x about the block centre
+    const float dx = x - g.xc;
     float kv[3];
 #pragma unroll
-    for (int sc3 = 0; sc3 < 3; ++sc3)
-        kv[sc3] = (k0 * evd(kQR + 3 * sc3) + k1 * evd(kQR + 3 * sc3 + 1) + k2 * evd(kQR + 3 * sc3 + 2)) * a.vfac;
+    for (int s3 = 0; s3 < 3; ++s3) kv[s3] = fmaf(g.s[12 + s3], dx, g.v[12 + s3]);
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
-        ft[34 + l] = (ev(kQT + l) / a.Tbar - 1.f) * 100.f;
-        const float kn = k0 * ev(kQN + 3 * l) + k1 * ev(kQN + 3 * l + 1) + k2 * ev(kQN + 3 * l + 2);
-        ft[40 + l] = 1.f - kn;
-        eps[l] = (1.f - kn) > 1e-6f ? kv[link_sender(l)] / (1.f - kn) : 0.f;
+        ft[34 + l] = (fmaf(g.s[l], dx, g.v[l]) / a.Tbar - 1.f) * 100.f;
+        const float om = 1.f - fmaf(g.s[6 + l], dx, g.v[6 + l]);
+        ft[40 + l] = om;
+        eps[l] = om > 1e-6f ? __fdividef(kv[link_sender(l)], om) : 0.f;
     }
     ft[46] = a.dtr;
     ft[47] = 0.f;
@@ -265,16 +328,29 @@ __global__ void __launch_bounds__(256) corr_features_kernel(FeatArgs a)
     // multiples of 512 samples): its coefficients are converted to FP32 once
     // (conversions from FP64 run on the FP64 pipe).
     __shared__ float cfs[kNQ][7];
+    __shared__ CorrGeo geo[2];
     const int64_t b0 = (int64_t)blockIdx.x * blockDim.x;
     int64_t s = b0 / a.tab.S;
     if (s >= a.tab.nseg) s = a.tab.nseg - 1;
     load_segment_f32(a.tab, s, cfs);
     __syncthreads();
-    const int64_t i = b0 + threadIdx.x;
+    // geometry of the block's two 128-row halves about their centres, as the
+    // tensor-core kernel takes it for its 128-row tiles (same arithmetic, so
+    // both give the same features and base links)
+    const int t = threadIdx.x, half = t >> 7;
+    if (t % 128 < 15) {
+        const float xh = (float)(int)(b0 + 128 * half - s * a.tab.S) * a.inv_half - 1.f;
+        corr_geo_one(a, cfs, xh + 63.5f * a.inv_half, t % 128, geo[half]);
+    }
+    const int64_t i = b0 + t;
+    float v[6][5];
+    corr_zwin(a, i, v);   // every lane of the warp
+    __syncthreads();
     if (i >= a.rows) return;
     float ft[kInP], sc, eps[6], z0[6];
     bool above;
-    corr_feature_row(a, i, cfs, s, ft, sc, eps, z0, above);
+    const float x0 = (float)(int)(b0 + 128 * half - s * a.tab.S) * a.inv_half - 1.f;
+    corr_feature_row(a, v, geo[half], x0 + (float)(t & 127) * a.inv_half, ft, sc, eps, z0, above);
     float4* fo = reinterpret_cast<float4*>(a.feats + i * kInP);
 #pragma unroll
     for (int c = 0; c < kInP / 4; ++c) fo[c] = make_float4(ft[4 * c], ft[4 * c + 1], ft[4 * c + 2], ft[4 * c + 3]);
@@ -327,6 +403,7 @@ struct __align__(128) TcSmem {
     unsigned char act[16384];        // operand tile: 128 rows x 64 BF16
     float bias[3 * kWid + kOutP];
     float cfs[kNQ][7];               // FP32 orbit segment (fused mode)
+    CorrGeo geo;                     // the tile's geometry (fused mode)
     int64_t cseg;
     uint64_t bar_w, bar_mma;
     uint32_t tmem_base;
@@ -447,10 +524,17 @@ __global__ void __launch_bounds__(kTcRows, kCorrCtas) corr_mlp_tc_kernel(TcArgs 
                 __syncthreads();
                 if (t == 0) sm.cseg = s;
             }
+            // the tile's geometry about its centre row (the previous tile's
+            // readers are past the layer barriers)
+            const float x0 = (float)(int)(tile * kTcRows - s * A.fa.tab.S) * A.fa.inv_half - 1.f;
+            if (t < 15) corr_geo_one(A.fa, sm.cfs, x0 + 63.5f * A.fa.inv_half, t, sm.geo);
+            float v[6][5];
+            corr_zwin(A.fa, i, v);   // every lane of the warp
+            __syncthreads();
             if (live) {
                 float eps[6], z0[6];
                 bool above;
-                corr_feature_row(A.fa, i, sm.cfs, s, ft, sc, eps, z0, above);
+                corr_feature_row(A.fa, v, sm.geo, x0 + (float)t * A.fa.inv_half, ft, sc, eps, z0, above);
                 if (above && A.fa.tile_flag && i >= A.fa.safe_lo && i < A.fa.safe_hi)
                     atomicOr(&A.fa.tile_flag[i / kTile], 1);
 #pragma unroll
@@ -1541,31 +1625,51 @@ int lisa_response_hybrid_corrected(lisa_corrector* c, const lisa_orbit* orbit, c
                                                  sizeof(float) * (size_t)(iFb - iLb - 1), st), "cudaMemsetAsync"));
         }
     }
+    // the full-response links of step 3 depend only on the table and h: they
+    // run on a side stream beside steps 1 and 2, joined before step 3's TDI
+    float* y = nullptr;
+    int64_t lo = 0;
+    if (iFb < n) {
+        lo = iFb - reach > 0 ? iFb - reach : 0;
+        y = (float*)sc.alloc(sizeof(float) * 6 * (size_t)(n - lo));
+        if (!y) return sc.status();
+    }
+    SideGuard side{(iFb < n && (iLa >= 0 || corr_zone)) ? side_acquire() : nullptr};
+    int rc_links = 0, rc_join = 0;
+    if (side.r) {
+        LISA_TRY(cuda_status(cudaEventRecord(side.r->fork, st), "cudaEventRecord"));
+        LISA_TRY(cuda_status(cudaStreamWaitEvent(side.r->s, side.r->fork, 0), "cudaStreamWaitEvent"));
+        rc_links = launch_links_full(tab, skyd, h_grid, hp, hc, LISA_MIXED, out, y, lo, n, side.r->s, lo);
+        rc_join = cuda_status(cudaEventRecord(side.r->join, side.r->s), "cudaEventRecord");
+    }
+    // steps 1 and 2 on the caller's stream; it joins the side stream afterwards
+    // (also after an error, so that nothing queued there outlives the scratch)
+    int rc = rc_links ? rc_links : rc_join;
     // 1. plain LFA channels below the lower seam, weight S(t; t_lo, +)
-    if (iLa >= 0) {
+    if (!rc && iLa >= 0) {
         BlendSpec bl{1, t_lo, sg, +1.0, 0, 0};
-        LISA_TRY(launch_lfa(tab, skyd, orbit->L_m, h_grid, hp, hc, LISA_MIXED, tdi_gen, LISA_LFA_UNEQUAL, channels, out,
-                            nullptr, xyz, 0, iLa + 1, bl, st));
+        rc = launch_lfa(tab, skyd, orbit->L_m, h_grid, hp, hc, LISA_MIXED, tdi_gen, LISA_LFA_UNEQUAL, channels, out,
+                        nullptr, xyz, 0, iLa + 1, bl, st);
     }
     // 2. TDI of the corrected links on [iFa, iLb]: weight S(t; t_lo, -) added to
     //    the plain LFA over the lower window; the links are laid out as the TDI
     //    reads samples [r0, n) of the output grid.
-    if (corr_zone) {
+    if (!rc && corr_zone) {
         float* yc = (float*)sc.alloc(sizeof(float) * 6 * (size_t)(n - r0));
-        if (!yc) return sc.status();
-        LISA_TRY(corrected_links(c, orbit, sky, h_grid, hp, hc, sub, tab_sub, r1 - r0, yc, sc, st));
-        BlendSpec bl{};
-        if (iLa >= 0) bl = BlendSpec{1, t_lo, sg, -1.0, iFa, iLa + 1};
-        LISA_TRY(launch_tdi(tab, out, yc, LISA_MIXED, tdi_gen, LISA_FROZEN, channels, out, xyz, iFa, iLb + 1, bl, st,
-                            r0));
+        rc = yc ? corrected_links(c, orbit, sky, h_grid, hp, hc, sub, tab_sub, r1 - r0, yc, sc, st) : sc.status();
+        if (!rc) {
+            BlendSpec bl{};
+            if (iLa >= 0) bl = BlendSpec{1, t_lo, sg, -1.0, iFa, iLa + 1};
+            rc = launch_tdi(tab, out, yc, LISA_MIXED, tdi_gen, LISA_FROZEN, channels, out, xyz, iFa, iLb + 1, bl, st, r0);
+        }
     }
+    if (side.r && !rc_join) rc_join = cuda_status(cudaStreamWaitEvent(st, side.r->join, 0), "cudaStreamWaitEvent");
+    if (rc) return rc;
+    if (rc_join) return rc_join;
     // 3. full response above the upper seam: S(t; t_hyb, -) x + (1 - S) out
     //    over the upper window, so that the three weights sum to one
     if (iFb < n) {
-        const int64_t lo = iFb - reach > 0 ? iFb - reach : 0;
-        float* y = (float*)sc.alloc(sizeof(float) * 6 * (size_t)(n - lo));
-        if (!y) return sc.status();
-        LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, LISA_MIXED, out, y, lo, n, st, lo));
+        if (!side.r) LISA_TRY(launch_links_full(tab, skyd, h_grid, hp, hc, LISA_MIXED, out, y, lo, n, st, lo));
         BlendSpec bl{1, t_hyb, sg, -1.0, iFb, iLb + 1, 1};
         LISA_TRY(launch_tdi(tab, out, y, LISA_MIXED, tdi_gen, LISA_FROZEN, channels, out, xyz, iFb, n, bl, st, lo));
     }

@@ -113,6 +113,26 @@ int make_table_pair(const lisa_orbit* orbit, const lisa_grid& g1, const lisa_gri
 // Upper bound of any single light time (halo sizing).
 double max_light_time(const lisa_orbit* o, const lisa_grid& g);
 // Tiles per CTA group of the mixed LFA kernel for a grid step dt (host side).
+// A second stream (with a fork and a join event) for work of a call that does
+// not depend on the work queued before it on the caller's stream after the
+// fork; one set per concurrent call and device, reused (api.cu).  nullptr if
+// none can be created: the caller then stays on its own stream.
+struct SideRes {
+    int device = -1;
+    bool busy = false;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideRes* side_acquire();
+void side_release(SideRes* r);
+struct SideGuard {
+    SideRes* r;
+    ~SideGuard()
+    {
+        if (r) side_release(r);
+    }
+};
+
 int lfa_group_host(double dt);
 // tiles per LFA group of the kernel that serves the precision (chunk boundaries)
 int lfa_group_host(double dt, int precision);
