@@ -551,7 +551,9 @@ def bench_corrector(L, torch, dev, src, orbit, sky, hp32, hc32, out32, flush, st
     res["headline_workload_cost"] = cost
     # the previous single-zone form (corrected links over the whole LFA side) for reference
     fo = lambda: c.hybrid(orbit, sky, src.grid, hp32, hc32, 20, L.AET, tH, Tw, sig, src.grid, out32)   # noqa: E731
+    torch.cuda.nvtx.range_push("corrected_links_whole_lfa_side")   # range for targeted profiler captures
     res["corrected_links_whole_lfa_side_ms"] = round(_timed(torch, stream, flush, fo), 4)
+    torch.cuda.nvtx.range_pop()
     # the fused tensor-core corrector over the whole LFA side: its MMA work
     # (padded shapes 48 -> 64 -> 64 -> 64 -> 16 per row) against the measured
     # bf16 GEMM rate
