@@ -240,7 +240,11 @@ int lisa_response_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_
  *   S(t; eps) = 1 / (1 + exp(eps (t - t_hyb)/sigma)),
  * computing the LFA only where its indicator is set and the full response
  * (links and TDI) only where its own is.  T_win <= 0 selects the paper's
- * default 800 out.dt, sigma <= 0 selects T_win/40.  xyz: device [3][out.n]. */
+ * default 800 out.dt, sigma <= 0 selects T_win/40.  xyz: device [3][out.n].
+ * When both parts are present, the full part's links run on a second stream
+ * of the library's, forked from `stream` after the orbit table and joined
+ * back into `stream` before the TDI: all of the call's work is still ordered
+ * on `stream` (event fork and join, so the call can be captured in a graph). */
 int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
                          const void* hp, const void* hc, int precision, int tdi_gen, int lfa_kind,
                          int channels, double t_hyb, double T_win, double sigma,
@@ -477,7 +481,9 @@ int lisa_corrector_links(lisa_corrector* c, const lisa_orbit* orbit, const lisa_
  * one at every sample.  The costly corrected zone is then only as long as
  * the time the source spends between the two switch frequencies.
  * t_lo = -INFINITY: no plain zone (corrected links up to t_hyb).
- * LISA_EINVAL if t_lo is NaN, +INFINITY or later than t_hyb. */
+ * LISA_EINVAL if t_lo is NaN, +INFINITY or later than t_hyb.  The full zone's
+ * links run on the library's second stream as in lisa_response_hybrid
+ * (forked from and joined back into `stream`). */
 int lisa_response_hybrid_corrected(lisa_corrector* c, const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
                                    const void* hp, const void* hc, int tdi_gen, int channels, double t_lo,
                                    double t_hyb, double T_win, double sigma, lisa_grid out, void* xyz, void* stream);
