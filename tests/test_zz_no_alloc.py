@@ -40,7 +40,7 @@ def _call(L, fn, src, precision, tH, orbit):
     hp, hc = host_inputs(src, precision)
     hpd, hcd = to_dev(hp, precision), to_dev(hc, precision)
     out = torch.full((3, src.n), float("nan"), device="cuda",
-                     dtype=torch.float32 if precision else torch.float64)
+                     dtype=torch.float32 if precision == 1 else torch.float64)
     o = orbit.c()
     sky = N.lisa_sky(*sky_of(src))
     g = N.lisa_grid(src.t0, src.dt, src.n)
@@ -52,7 +52,7 @@ def _call(L, fn, src, precision, tH, orbit):
     return out.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_static_scratch_matches_allocating_call(L, precision):
     lib = L.load()
     _, lo = orbit_pair("kepler2_flex")
