@@ -56,7 +56,10 @@ __global__ void __launch_bounds__(kTile, LISA_LFA_MINB) lfa_kernel_mixed(LfaArgs
 }
 
 int lfa_group_host(double dt) { return lfa_group(dt); }
-int lfa_group_host(double dt, int precision) { return precision == LISA_DF ? lfa_group_df(dt) : lfa_group(dt); }
+int lfa_group_host(double dt, int precision)
+{
+    return precision == LISA_DF ? lfa_group_df(dt) : precision == LISA_MIXED ? lfa_group_mixed(dt) : lfa_group(dt);
+}
 
 int launch_lfa_strain(const LfaArgs& a, double L_nominal, int precision, cudaStream_t st);
 int launch_lfa_df(const LfaArgs& a, cudaStream_t st);
@@ -116,7 +119,7 @@ int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const l
     prof_before(gen == kLfaOwnTime ? (precision == LISA_MIXED ? "lfa_own_mixed" : "lfa_own_f64")
                                    : (precision == LISA_MIXED ? "lfa_mixed" : "lfa_f64"), st);
     if (precision == LISA_MIXED) {
-        const int G0 = lfa_group(og.dt);
+        const int G0 = lfa_group_mixed(og.dt);
         int G = group > 0 && group < G0 ? group : G0;
         if (gen == kLfaOwnTime && group == 0) {
             // link series at their own time: groups narrowed on short ranges so

@@ -706,6 +706,16 @@ inline int lfa_group(double dt)
     return G < 1 ? 1 : (G > 8 ? 8 : G);
 }
 
+// Tiles per CTA of the mixed LFA kernel in a single call: at most 6 (the
+// last wave of CTAs ends sooner; on one year at 5 s the kernel took 0.513,
+// 0.547 and 0.488 ms with groups of 8, 7 and 6 tiles).  The batched plan keeps
+// lfa_group: its work items are autotuned runs of groups.
+inline int lfa_group_mixed(double dt)
+{
+    const int G = lfa_group(dt);
+    return G < 6 ? G : 6;
+}
+
 // Tiles per CTA of the double-float kernel: at most 6 (its groups take ~0.3 ms
 // each, so smaller groups shorten the last wave of CTAs more than their
 // prologues cost; on one year at 5 s, 24,644 tiles at 3 CTAs per SM, groups of
