@@ -541,11 +541,13 @@ static __device__ void df_channels(const LfaArgs& a, int64_t i0, int64_t ic, con
     out[2 * a.nout + i] = o[2];
 }
 
-// One barrier per tile: iteration q forms the z of tile q (buffer q & 1),
-// the channels of tile q - 1 (buffer (q - 1) & 1) and stages the hdot window
-// of tile q + 1 (buffer (q + 1) & 1, last read by the z of tile q - 1), so a
-// warp done with its z items goes on to channels and staging instead of
-// waiting at a barrier between them.
+// One barrier per tile: iteration q forms the channels of tile q - 1 (buffer
+// (q - 1) & 1), the z of tile q (buffer q & 1) and stages the hdot window of
+// tile q + 1 (buffer (q + 1) & 1, last read by the z of tile q - 1), so a warp
+// goes from one part to the next instead of waiting at a barrier between
+// them.  In this order (channels, z, staging) the LFA call on one year at
+// 5 s took 2.122 ms against 2.152 ms for z, channels, staging and 2.146 ms
+// for staging first.
 __global__ void __launch_bounds__(kTile, LISA_DF_MINB) lfa_kernel_df(LfaArgs a, int64_t tile_end, int G)
 {
     extern __shared__ __align__(16) unsigned char df_raw[];
@@ -558,8 +560,8 @@ __global__ void __launch_bounds__(kTile, LISA_DF_MINB) lfa_kernel_df(LfaArgs a, 
     __syncthreads();
     for (int q = 0; q < nt; ++q) {
         const int64_t i0 = (t0 + q) * (int64_t)kTile;
-        df_zvalues(a, i0, ic, sm, sm.win[q], sm.dw[q & 1], q, q == 0);
         if (q > 0) df_channels(a, i0 - kTile, ic, sm, sm.zs[(q - 1) & 1]);
+        df_zvalues(a, i0, ic, sm, sm.win[q], sm.dw[q & 1], q, q == 0);
         if (q + 1 < nt) df_stage(a, sm.win[q + 1], sm.dw[(q + 1) & 1], sm.wmax[(q + 1) & 1]);
         __syncthreads();   // z of tile q complete, channels of q - 1 read, window of q + 1 staged
     }
