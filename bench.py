@@ -967,6 +967,36 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     lfa_ms, lfa_launches = L.lisa_profile_query(REC_KERNEL[prec])
     L.lisa_profile_enable(False)
+
+    # The same call captured once in a CUDA graph (its stream-ordered
+    # allocations, side-stream fork and join and kernels as graph nodes) and
+    # replayed K times: reported beside the line, which times the calls.
+    graph_ms = None
+    try:
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            step()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            step()
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            graph.replay()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            gev[k][0].record(stream)
+            graph.replay()
+            gev[k][1].record(stream)
+        torch.cuda.synchronize()
+        graph_ms = round(float(np.median([a.elapsed_time(b) for a, b in gev])), 5)
+        del graph
+    except Exception as e:   # capture refused: reported as such
+        graph_ms = "capture failed: %s" % type(e).__name__
+        torch.cuda.synchronize()
     total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     value = whole_job_rate(world, n, args.steps, total_ms)
 
@@ -1186,7 +1216,9 @@ def run_ours(args):
                                "double-float LFA (FP32 pairs), FP64 full part" if prec == 2 else "FP64 arithmetic"),
                    "precision_of_record": REC_DTYPE[prec],
                    "n_samples": n, "dt": src.dt, "sources_per_gpu": 1, "l2": "flushed between steps "
-                   "(256 MiB write outside the timed events)", "parallelism": "replicas" if world > 1 else "single"},
+                   "(256 MiB write outside the timed events)", "parallelism": "replicas" if world > 1 else "single",
+                   "timing": "library call per step",
+                   "graph_replay_ms_per_step_median": graph_ms},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": 3 * n * 8,
                 "call": "lisa_response_hybrid_host (page-locked host buffers, copies overlapped in chunks)",
