@@ -391,7 +391,7 @@ int lisa_plan_replay(lisa_plan* plan, void* stream);
  * size) whole groups (at least one), so the results do not depend on the
  * launch shape.  Drops a captured graph. */
 int lisa_plan_set_launch(lisa_plan* plan, int ctas_per_sm, int tiles_per_item);
-/* Time every (CTAs per SM in 1..4) x (tiles per item in 1,2,4,8) on this
+/* Time every (CTAs per SM in 1..4) x (tiles per item in 8,16,32,64: 1 to 8 groups) on this
  * plan's own data (synchronising), keep the fastest, report it. */
 int lisa_plan_autotune(lisa_plan* plan, void* stream, lisa_tune_result* best);
 int lisa_plan_info(const lisa_plan* plan, int64_t* total_samples, int64_t* total_tiles, int* ctas_per_sm,

@@ -477,7 +477,9 @@ int lisa_plan_autotune(lisa_plan* plan, void* stream, lisa_tune_result* best)
     if (!plan) { set_error("plan is NULL"); return LISA_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
     const int cps_opts[] = {1, 2, 3, 4};
-    const int tpi_opts[] = {1, 2, 4, 8};
+    // tiles per item: 1, 2, 4 or 8 whole groups of 8 tiles (an item holds at
+    // least one group, so fewer tiles than a group would change nothing)
+    const int tpi_opts[] = {8, 16, 32, 64};
     float best_ms = 1e30f;
     int best_cps = plan->ctas_per_sm, best_tpi = plan->tiles_per_item;
     cudaEvent_t a, b;
