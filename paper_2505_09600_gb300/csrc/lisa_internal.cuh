@@ -89,7 +89,7 @@ int launch_tdi(const SegTable& tab, const lisa_grid& yg, const void* y, int prec
 // at its own reception time (no TDI shift): z[6][og.n] in link order (xyz
 // must be null).
 constexpr int kLfaOwnTime = 0;
-// group: tiles per CTA of the mixed kernel (0: lfa_group of the grid step).
+// group: tiles per CTA of the mixed kernel (0: lfa_group_mixed of the grid step).
 int launch_lfa(const SegTable& tab, const SkyDev& sky, double L_nominal, const lisa_grid& hg, const void* hp,
                const void* hc, int precision, int gen, int kind, int channels, const lisa_grid& og, void* z,
                void* xyz, int64_t i_begin, int64_t i_end, const BlendSpec& bl, cudaStream_t st, int group = 0);
