@@ -84,9 +84,10 @@ REC_KERNEL = {0: "lfa_f64", 2: "lfa_df"}
 #   exact sums and the correction 20), position (delay polynomial with its
 #   FP32 tail, scale, fraction) 69, projection factors (FP32 tails from u^3)
 #   and z 119 -> 1240, x 6 series;
-#   channels: light-time polynomials, two 5-point second differences and the
-#   prefactors, 367 per channel x 3, A/E/T 82.
-DF_OPS_PER_SAMPLE = {"lfa20": 6 * 1240 + 3 * 367 + 82}
+#   channels: the three light-time polynomials 3 x 47 (each arm enters two
+#   channels), two 5-point second differences and the prefactors 273 per
+#   channel x 3, A/E/T 82.
+DF_OPS_PER_SAMPLE = {"lfa20": 6 * 1240 + 3 * 47 + 3 * 273 + 82}
 
 
 def measured_fma_peaks(L):
