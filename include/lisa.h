@@ -244,7 +244,9 @@ int lisa_response_lfa(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_
  * When both parts are present, the full part's links run on a second stream
  * of the library's, forked from `stream` after the orbit table and joined
  * back into `stream` before the TDI: all of the call's work is still ordered
- * on `stream` (event fork and join, so the call can be captured in a graph). */
+ * on `stream` (event fork and join, so the call can be captured in a graph).
+ * That stream and its two events are created by the first such call on a
+ * device (and reused); make one call before capturing any in a graph. */
 int lisa_response_hybrid(const lisa_orbit* orbit, const lisa_sky* sky, lisa_grid h_grid,
                          const void* hp, const void* hc, int precision, int tdi_gen, int lfa_kind,
                          int channels, double t_hyb, double T_win, double sigma,
