@@ -48,6 +48,10 @@ FP32_PEAK_TFLOPS_FALLBACK = None
 # (unequal arms).  The count that includes the weights (4 flop per weight)
 # is reported beside it.
 LFA_TAPS_FLOP = 6 * 2 * 32 * 2 + 62
+# The full response TDI 2.0 on the same view: links 6 x 2 retarded times x 2
+# polarisations x 32 taps x 2 flop = 1,536, TDI 48 interpolations x 32 taps x
+# 2 flop = 3,072.
+FULL20_TAPS_FLOP = 6 * 2 * 2 * 32 * 2 + 48 * 32 * 2
 W32 = 4 * 32
 TAP = 2 * 32
 FLOP_PER_SAMPLE = {
@@ -691,6 +695,7 @@ def bench_batch(L, torch, dev, orbit, flush, stream, args, fma_peaks=None):
     t0 = time.perf_counter()
     descs = []
     total = 0
+    n_lfa = n_full = 0   # samples each part computes (the blend window's in both)
     for p in params:
         s = synth.batch_source(p)
         tHs = L.lisa_t_hyb_from_f(F_HYB, s.mc_s, s.tc)
@@ -698,6 +703,11 @@ def bench_batch(L, torch, dev, orbit, flush, stream, args, fma_peaks=None):
                           hc=torch.as_tensor(s.hc.astype(np.float32), device=dev),
                           sky=(s.beta, s.lam, s.psi), t_hyb=tHs, out=torch.empty((3, s.n), device=dev)))
         total += s.n
+        half_w = 400 * s.dt      # the plan's default window, 800 samples
+        i_l = int(math.floor((tHs + half_w - s.t0) / s.dt))
+        i_f = int(math.ceil((tHs - half_w - s.t0) / s.dt))
+        n_lfa += min(s.n, max(0, i_l + 1))
+        n_full += min(s.n, max(0, s.n - max(0, i_f)))
     t_gen = time.perf_counter() - t0
     plan = L.LisaPlan(orbit, descs)
     st = torch.cuda.Stream()
@@ -712,13 +722,18 @@ def bench_batch(L, torch, dev, orbit, flush, stream, args, fma_peaks=None):
     res = {"sources": len(descs), "samples": total, "ms": round(ms, 3), "samples_per_s": total / (ms / 1e3),
            "autotune": tune, "source_generation_s": round(t_gen, 1),
            "workload": "hybrid TDI2.0 AET, f_hyb=1e-3 Hz, mixed precision, one persistent launch (graph replay)"}
+    res["lfa_samples"], res["full_samples"] = n_lfa, n_full
     if fma_peaks:
-        # every sample counted at the LFA's taps-and-stencils flop (the full part's
-        # samples, a small share, do more work than that)
-        ach = LFA_TAPS_FLOP * total / (ms / 1e3) / 1e12
+        # the hybrid's taps-and-stencils work: LFA samples at the LFA's flop,
+        # full-response samples at the full TDI 2.0's (the blend window's samples
+        # in both, as computed)
+        flop = LFA_TAPS_FLOP * n_lfa + FULL20_TAPS_FLOP * n_full
+        ach = flop / (ms / 1e3) / 1e12
         res["roofline"] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(fma_peaks["fp32_tflops"], 2),
                            "unit": "TFLOP/s", "frac": round(ach / fma_peaks["fp32_tflops"], 4),
-                           "flop_per_sample": LFA_TAPS_FLOP,
+                           "flop_per_sample": round(flop / max(total, 1), 1),
+                           "flop_note": "%d flop per LFA sample, %d per full-response sample (taps and stencils)"
+                                        % (LFA_TAPS_FLOP, FULL20_TAPS_FLOP),
                            "peak_note": "FP32 FMA, measured in this run (lisa_peak_fma); of measured"}
     return res
 
