@@ -1,7 +1,8 @@
-"""lisa_response_hybrid captured in a CUDA graph (its stream-ordered scratch,
-the side stream that runs the full part's links, and the kernels become graph
-nodes) and replayed: bit-identical to the direct call, replay after replay,
-including after the inputs in the captured buffers change."""
+"""The hybrid call's second stream (the full part's links run on it beside the
+LFA kernel): captured in a CUDA graph (its stream-ordered scratch, the side
+stream and the kernels become graph nodes) and replayed, bit-identical to the
+direct call, replay after replay, including after the inputs in the captured
+buffers change; and two calls in flight on two streams at once."""
 import numpy as np
 import pytest
 
@@ -59,3 +60,33 @@ def test_hybrid_graph_replay_matches_call(L, precision):
     torch.cuda.synchronize()
     assert torch.equal(out, want2)
     assert not torch.equal(want2, want)
+
+
+def test_hybrid_calls_in_flight_on_two_streams(L):
+    """Two hybrid calls queued back to back on two streams (each call forks
+    its own side stream from the library's pool) give the results of the
+    same calls run one after the other."""
+    _, lo = orbit_pair("kepler2_flex")
+    srcs = [synth.cfg2_small(n=30000), synth.cfg2_small(n=30000, seed_offset=5)]
+    args = []
+    for s in srcs:
+        tH = L.lisa_t_hyb_from_f(1e-3, s.mc_s, s.tc)
+        args.append((s, to_dev(s.hp, 2), to_dev(s.hc, 2), tH))
+
+    def call(k, o, stream=None):
+        s, hp, hc, tH = args[k]
+        L.lisa_response_hybrid(lo, sky_of(s), s.grid, hp, hc, 2, 20, 0, L.AET, tH, 800 * s.dt, 20 * s.dt, s.grid,
+                               o, stream=stream)
+
+    want = [torch.empty((3, s.n), device="cuda", dtype=torch.float64) for s in srcs]
+    for k in range(2):
+        call(k, want[k])
+    torch.cuda.synchronize()
+    got = [torch.full_like(w, float("nan")) for w in want]
+    st = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for k in range(2):
+        st[k].wait_stream(torch.cuda.current_stream())
+        call(k, got[k], stream=st[k].cuda_stream)
+    torch.cuda.synchronize()
+    for k in range(2):
+        assert torch.equal(got[k], want[k]), k
