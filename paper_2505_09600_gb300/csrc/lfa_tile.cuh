@@ -750,7 +750,7 @@ struct Lfa2Smem {
     union {
         float zs[6][kZW2];                // z values of a sub-block (z-series form)
         float4 d2[kWin2 + 8];             // second differences of h as (hi, lo) pairs (differenced form)
-        float xacc[6][kTile];             // differenced form: channel sums of a thread's two samples
+        float xacc[12][kTile];            // differenced form: channel sums of a thread's two samples (rows 0-5), the three arms' light times at them (rows 6-11)
     };
     LfaWin win[kMaxSub2];
     uint64_t bar[2];                      // completion barriers of the bulk copies
@@ -1184,9 +1184,19 @@ static __device__ void lfa2_dvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lf
     const bool tdi20 = a.gen == LISA_TDI20;
     const bool equal = a.kind == LISA_LFA_EQUAL;
     // channel sums of the thread's two samples live in shared memory (the
-    // pair weights need the registers); sm.xacc[2 ch + r][t]
+    // pair weights need the registers); sm.xacc[2 ch + r][t].  So do the
+    // three arms' light times at the two samples, sm.xacc[6 + 3 r + q][t]
+    // (arm q: link 2q), each used by two series and two channels.
 #pragma unroll
     for (int q = 0; q < 6; ++q) sm.xacc[q][t] = 0.f;
+    if (!equal) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float ur = (float)(dm0 + r * kTile) * sm.inv_half;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sm.xacc[6 + 3 * r + q][t] = sm.c0[kQT + 2 * q] + sm.cu[kQT + 2 * q](ur);
+        }
+    }
 #pragma unroll kLfaDUnroll
     for (int c = 0; c < 6; ++c) {
         const float ih = sm.inv_half, idt = sm.inv_dt;
@@ -1234,19 +1244,18 @@ static __device__ void lfa2_dvalues(const LfaArgs& a, int64_t i0, int64_t ic, Lf
                 R = fmaf(1.f + a1, m, (12.f * idt) * fmaf(Fp1, qp, Fc1 * qc));
             }
             // this series' arm factor: +T_a for link a, -T_b for link b
-            const float T = equal ? a.Lcf : sm.c0[kQT + arm] + sm.cu[kQT + arm](uu);
+            const float T = equal ? a.Lcf : sm.xacc[6 + 3 * r + (arm >> 1)][t];
             sm.xacc[2 * ch + r][t] = fmaf((c & 1) ? -T : T, R, sm.xacc[2 * ch + r][t]);
         }
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         if (r >= nr) break;
-        const float uu = (float)(dm0 + r * kTile) * sm.inv_half;
         float X[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            const float Ta = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 0)] + sm.cu[kQT + lfa_arm(ch, 0)](uu);
-            const float Tb = equal ? a.Lcf : sm.c0[kQT + lfa_arm(ch, 1)] + sm.cu[kQT + lfa_arm(ch, 1)](uu);
+            const float Ta = equal ? a.Lcf : sm.xacc[6 + 3 * r + (lfa_arm(ch, 0) >> 1)][t];
+            const float Tb = equal ? a.Lcf : sm.xacc[6 + 3 * r + (lfa_arm(ch, 1) >> 1)][t];
             const float pref = tdi20 ? 8.f * (Ta + Tb) * a.c2f : 4.f * a.c1f;
             X[ch] = pref * sm.xacc[2 * ch + r][t];
         }
